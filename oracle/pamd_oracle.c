@@ -23,7 +23,8 @@
  *     Langevin thermostat and a per-replica seed.
  *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) keyed on the run
  *     seed, counter = (atom, replica slot, step, purpose | molecule << 8).
- *     Normals: Box-Muller on 24-bit uniforms u = (top24 + 0.5) * 2^-24.
+ *     Normals: Box-Muller on 23-bit uniforms u = (top23 + 0.5) * 2^-23, which
+ *     binary32 and binary64 both represent exactly.
  *   - Multinomial resampling is realised with integer weights
  *     W_j = floor(2^s * exp(a_j - max a)), s = 63 - ceil(log2 R), an inclusive
  *     prefix sum C and R targets t_k = floor(u_k * C_total / 2^64) from 64-bit
@@ -82,8 +83,8 @@ static void philox_keyed(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, u
     orc_philox4x32_10(ctr, key, out);
 }
 
-/* Uniform in (0,1) from the top 24 bits of a 32-bit draw. */
-static double u24(uint32_t u) { return ((double)(u >> 8) + 0.5) * 0x1p-24; }
+/* Uniform in (0,1) from the top 23 bits of a 32-bit draw (exact in binary32). */
+static double u23(uint32_t u) { return ((double)(u >> 9) + 0.5) * 0x1p-23; }
 
 /* Three standard normals for (atom, slot, step, purpose) by Box-Muller. */
 void orc_normal3(uint64_t seed, uint32_t atom, uint32_t slot, uint32_t step, uint32_t purpose,
@@ -91,11 +92,11 @@ void orc_normal3(uint64_t seed, uint32_t atom, uint32_t slot, uint32_t step, uin
     uint32_t o[4];
     philox_keyed(seed, atom, slot, step, purpose, o);
     const double two_pi = 6.283185307179586476925286766559;
-    double r0 = sqrt(-2.0 * log(u24(o[0])));
-    double r1 = sqrt(-2.0 * log(u24(o[2])));
-    z[0] = r0 * cos(two_pi * u24(o[1]));
-    z[1] = r0 * sin(two_pi * u24(o[1]));
-    z[2] = r1 * cos(two_pi * u24(o[3]));
+    double r0 = sqrt(-2.0 * log(u23(o[0])));
+    double r1 = sqrt(-2.0 * log(u23(o[2])));
+    z[0] = r0 * cos(two_pi * u23(o[1]));
+    z[1] = r0 * sin(two_pi * u23(o[1]));
+    z[2] = r1 * cos(two_pi * u23(o[3]));
 }
 
 /* ------------------------------------------------------------------------- */
