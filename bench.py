@@ -1,0 +1,348 @@
+#!/usr/bin/env python3
+"""Benchmark of the PAMD hot path on one GB300 (or N independent GPUs).
+
+A step is one full anneal of the paper-shaped workload: a 75-atom synthetic
+peptide-like chain, R = 8192 replicas, theta = 1000 BAOAB steps of 1 fs per
+temperature, 100 geometric temperature steps 1000 -> 250 K (101 propagate
+blocks, 100 resamplings, 101 measurements), run as one CUDA graph after
+re-initialising the population on the device.  The metric is atom-steps per
+second over all replicas (and ms per full anneal).
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "c2": dict(
+        workload="paper-shaped plain PAMD: 75-atom chain, R=8192, theta=1000, dt=1 fs, "
+                 "100 geometric temperature steps 1000->250 K",
+        n_atoms=75, gen_seed=1, R=8192, theta=1000, K=100, T0=1000.0, TK=250.0, dt=0.001,
+        gamma=1.0, seed=12345),
+    "c1": dict(
+        workload="plain PAMD: 22-atom chain, R=256, theta=100, dt=1 fs, "
+                 "20 geometric temperature steps 1000->300 K",
+        n_atoms=22, gen_seed=1, R=256, theta=100, K=20, T0=1000.0, TK=300.0, dt=0.001,
+        gamma=1.0, seed=12345),
+}
+
+METRIC = "atom-steps/sec over all replicas (full anneal)"
+UNIT = "atom-steps/s"
+
+# Algorithmic floating-point work per replica-step of the propagate kernel
+# (forces-only steps, Newton's third law): 36 flop per nonbonded pair (counted
+# from the kernel's pair arithmetic, fma = 2, rsqrt = 1), 30 per bond, 60 per
+# angle, 120 per dihedral, 20 per atom for the integrator and noise.
+FLOP_PAIR, FLOP_BOND, FLOP_ANGLE, FLOP_DIH, FLOP_ATOM = 36, 30, 60, 120, 20
+
+# FP32 peak of one GB300: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+
+# dram bytes (read + write) of one propagate launch from the ncu capture in
+# profiles/, keyed by the hash of the kernel source it was taken on; the value
+# is dropped automatically when the kernel source changes.
+NCU_TRAFFIC = {}
+
+
+def flop_per_replica_step(n):
+    pairs = n * (n - 1) // 2 - max(2 * n - 3, 0)
+    return (FLOP_PAIR * pairs + FLOP_BOND * max(n - 1, 0) + FLOP_ANGLE * max(n - 2, 0)
+            + FLOP_DIH * max(n - 3, 0) + FLOP_ATOM * n)
+
+
+def kernel_source_hash():
+    p = os.path.join(ROOT, "paper_1806_06016_gb300", "csrc", "propagate_impl.cuh")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def atom_steps(w, replicas):
+    return w["n_atoms"] * replicas * w["theta"] * (w["K"] + 1)
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- CPU legs
+
+def oracle_sample(w, reps=512, theta=100):
+    """The FP64 oracle on a bounded sample of the workload: `reps` replicas of
+    the same chain, two temperatures (theta steps each, one resampling)."""
+    import numpy as np
+
+    import oracle
+    import pamd_inputs as pi
+    top = pi.make_chain(w["n_atoms"], w["gen_seed"])
+    ratio = (w["TK"] / w["T0"]) ** (1.0 / w["K"])
+    temps = np.array([w["T0"], w["T0"] * ratio])
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.anneal(top, reps, temps, theta, w["dt"], w["gamma"], w["seed"], n_threads=cores)
+    dt = time.perf_counter() - t0
+    units = w["n_atoms"] * reps * theta * 2
+    sample = (f"{reps} replicas of the {w['n_atoms']}-atom chain, theta={theta}, "
+              f"2 temperatures (1 resampling), {units:.3g} atom-steps, FP64, {cores} threads")
+    return units / dt, dt, cores, sample
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle_sample(w)
+    times, rates = [], []
+    for _ in range(args.steps):
+        rate, dt, cores, sample = oracle_sample(w)
+        times.append(dt)
+        rates.append(rate)
+    value = sum(w["n_atoms"] * 512 * 100 * 2 for _ in times) / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_of(w, args),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_of(w, args):
+    return {"workload": w["workload"], "n_atoms": w["n_atoms"], "replicas_per_gpu": w["R"],
+            "theta": w["theta"], "temperature_steps": w["K"], "T_first_K": w["T0"],
+            "T_last_K": w["TK"], "dt_fs": w["dt"] * 1e3, "gamma_per_ps": w["gamma"],
+            "precision": "FP32 forces/integration, FP64 energies/weights/lnQ",
+            "parallelism": "replicas only" if args.gpus == 1 else f"independent anneals x{args.gpus}",
+            "l2": "flushed (512 MB write) between timed steps"}
+
+
+# ----------------------------------------------------------------- GPU leg
+
+def run_gpu(args, w):
+    import numpy as np
+    import torch
+
+    import pamd_inputs as pi
+    from paper_1806_06016_gb300 import build as pbuild
+    from paper_1806_06016_gb300 import pamd
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    if rank == 0 or world == 1:
+        pbuild.build()
+    if dist:
+        dist.barrier()
+    pamd.load()
+
+    top = pi.make_chain(w["n_atoms"], w["gen_seed"])
+    temps = pi.geometric_schedule(w["T0"], w["TK"], w["K"])
+    R, theta, dt = w["R"], w["theta"], w["dt"]
+    seed = w["seed"] + 7919 * rank
+    pop = pamd.Population(top, R, temps[0], seed, pamd.torch_options(gamma_per_ps=w["gamma"]))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def one_anneal():
+        pamd.pamd_reset(pop.ctx, temps[0], seed)
+        pamd.pamd_anneal(pop.ctx, temps, theta, dt)
+
+    for _ in range(args.warmup):
+        one_anneal()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(dev)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    launches0 = pamd.pamd_launch_count(pop.ctx)
+    elapsed_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        one_anneal()
+        ev1.record(stream)
+        ev1.synchronize()
+        elapsed_ms += ev0.elapsed_time(ev1)
+    torch.cuda.synchronize()
+    launches = pamd.pamd_launch_count(pop.ctx) - launches0
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop()
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_ms = float(t.item())
+    total_units = atom_steps(w, R) * args.steps * world
+    value = total_units / (max_ms / 1e3)
+
+    # dominant kernel: the persistent propagate launch, timed alone in the
+    # same shape (theta steps over all R replicas) with events on its stream
+    pamd.pamd_reset(pop.ctx, temps[0], seed)
+    prop_ms = []
+    for _ in range(3):
+        flush.zero_()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        pamd.pamd_propagate(pop.ctx, theta, dt, temps[0])
+        ev1.record(stream)
+        ev1.synchronize()
+        prop_ms.append(ev0.elapsed_time(ev1))
+    prop_avg = statistics.mean(prop_ms)
+    flops = flop_per_replica_step(w["n_atoms"]) * R * theta
+    achieved = flops / (prop_avg / 1e3) / 1e12
+    traffic = NCU_TRAFFIC.get(kernel_source_hash())
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                "kernel": "propagate_kernel", "launch_ms": prop_avg,
+                "flop_per_launch": flops,
+                "peak_basis": "152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz (derived, not measured)"}
+
+    # end to end through the C-ABI with host buffers: upload the initial
+    # population, run the anneal, read the per-temperature observables back
+    rng = np.random.default_rng(seed)
+    x_host = np.repeat((top.x0 - top.x0.mean(0))[None], R, axis=0)
+    v_host = rng.normal(0.0, math.sqrt(0.008314462618 * temps[0] / 12.0), (R, w["n_atoms"], 3))
+    fam_host = np.arange(R, dtype=np.int32)
+    e2e_steps = max(1, min(args.steps, 2))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        pamd.pamd_set_state(pop.ctx, x_host, v_host, None, fam_host)
+        pamd.pamd_set_counters(pop.ctx, 0, 0, 0.0)
+        obs = pamd.pamd_anneal(pop.ctx, temps, theta, dt)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    np_ = (w["n_atoms"] + 3) // 4 * 4
+    h2d = R * 6 * np_ * 4 + R * 4 + 8
+    d2h = (w["K"] + 1) * ctypes.sizeof(pamd.PamdObs) + 48
+    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e = {"value": atom_steps(w, R) * e2e_steps * world / float(e2e_t.item()), "unit": UNIT,
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "final_e_pot_kJmol": obs[-1]["e_pot"], "final_sum_lnQ": obs[-1]["sum_lnQ"]}
+    pop.close()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        rate, dt_s, cores, sample = oracle_sample(w)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_of(w, args), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": int(launches), "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_gpu(args, w)
+
+
+if __name__ == "__main__":
+    main()

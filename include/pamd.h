@@ -1,0 +1,256 @@
+/*
+ * pamd.h -- C interface of libpamd, a CUDA (sm_103a) implementation of the
+ * data-parallel hot path of population-annealing molecular dynamics (PAMD),
+ * Christiansen, Weigel & Janke, "Accelerating molecular dynamics simulations
+ * with population annealing", arXiv:1806.06016.
+ *
+ * The calls follow the paper's statement of the method (the five-step PAMD
+ * scheme): pamd_init sets up R copies of a molecule at T0 (step 1),
+ * pamd_resample replicates each copy in proportion to its relative Boltzmann
+ * weight and rescales velocities (step 2), pamd_propagate runs theta Langevin
+ * MD steps per copy (step 3), and pamd_observables returns population
+ * averages (step 4).  pamd_anneal runs steps 2-4 over a whole temperature
+ * schedule as one CUDA graph.
+ *
+ * Units: nm, ps, amu, elementary charge, K, kJ/mol.  k_B = 0.008314462618
+ * kJ/mol/K, Coulomb constant 138.935458 kJ mol^-1 nm e^-2.
+ *
+ * Conventions for every function below:
+ *   - The return value is PAMD_OK (0) or a negative PAMD_E* code; a
+ *     thread-local message is available from pamd_last_error().  No call
+ *     aborts or exits the process.
+ *   - On an argument error the context is left unchanged.  If a CUDA call
+ *     fails part-way the context is marked broken and every later call except
+ *     pamd_destroy returns PAMD_ESTATE.
+ *   - Host pointers are caller-owned and only read/written during the call.
+ *     Device memory is owned by the context and obtained from
+ *     pamd_options.dev_alloc (cudaMalloc when NULL).
+ *   - Work is issued on pamd_options.stream.  Calls that return host data
+ *     synchronise that stream; pamd_propagate and pamd_resample with NULL
+ *     host outputs return without synchronising.
+ *   - The library keeps all replica state on the device in FP32 (positions
+ *     relative to the molecule's centre of mass, velocities) with FP64
+ *     potential energies, weights, ln Q and the free-energy sum.
+ */
+#ifndef PAMD_H
+#define PAMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PAMD_OK 0
+#define PAMD_EINVAL (-1)      /* bad argument (null pointer, size, index, range) */
+#define PAMD_ENOMEM (-2)      /* device or host allocation failed */
+#define PAMD_ECUDA (-3)       /* a CUDA runtime call failed */
+#define PAMD_ETIMEOUT (-4)    /* a bounded device-side wait gave up */
+#define PAMD_ENONFINITE (-5)  /* a replica's energy became NaN or infinite */
+#define PAMD_ESTATE (-6)      /* the context is broken by an earlier failure */
+#define PAMD_EUNSUPPORTED (-7) /* valid request this build cannot serve */
+
+/* Largest molecule the shared-memory kernels hold (atoms). */
+#define PAMD_MAX_ATOMS 256
+
+#define PAMD_PREC_MIXED 0 /* FP32 forces/integration, FP64 energies and weights */
+#define PAMD_PREC_FP64 1  /* everything in FP64 on the GPU */
+
+typedef struct pamd_ctx pamd_ctx; /* opaque, owned by the library */
+
+/*
+ * Force field of one molecule (test-system paragraph: a peptide in vacuo,
+ * all pairs, no cutoff).  Arrays are read during pamd_init only.
+ *   bonds      E = 1/2 k (r - r0)^2                (pairs [n][2])
+ *   angles     E = 1/2 k (theta - theta0)^2        (triples [n][3], rad)
+ *   dihedrals  E = k (1 + cos(n phi - phase))      (quadruples [n][4], n in 1..6)
+ *   nonbonded  for every pair not in excl: LJ 4 eps [(sig/r)^12 - (sig/r)^6]
+ *              with sig = (sig_i + sig_j)/2, eps = sqrt(eps_i eps_j), plus
+ *              Coulomb k_e q_i q_j / r; pairs listed in pair14 are scaled by
+ *              scale14_lj and scale14_coul.  A pair in both lists is excluded.
+ */
+typedef struct pamd_topology {
+    int32_t n_atoms;          /* 1 .. PAMD_MAX_ATOMS */
+    const double* mass;       /* [N] amu, > 0 */
+    const double* charge;     /* [N] e */
+    const double* sigma;      /* [N] nm, >= 0 */
+    const double* epsilon;    /* [N] kJ/mol, >= 0 */
+    const double* x0;         /* [N][3] nm, start geometry */
+    int32_t n_bonds;
+    const int32_t* bond;      /* [n_bonds][2] */
+    const double* bond_r0;    /* [n_bonds] nm */
+    const double* bond_k;     /* [n_bonds] kJ/mol/nm^2 */
+    int32_t n_angles;
+    const int32_t* angle;     /* [n_angles][3], vertex in the middle */
+    const double* angle_t0;   /* [n_angles] rad */
+    const double* angle_k;    /* [n_angles] kJ/mol/rad^2 */
+    int32_t n_dihedrals;
+    const int32_t* dihedral;  /* [n_dihedrals][4] */
+    const int32_t* dih_n;     /* [n_dihedrals] multiplicity 1..6 */
+    const double* dih_k;      /* [n_dihedrals] kJ/mol */
+    const double* dih_phase;  /* [n_dihedrals] rad */
+    int32_t n_excl;
+    const int32_t* excl;      /* [n_excl][2] pairs left out of the nonbonded sum */
+    int32_t n_pair14;
+    const int32_t* pair14;    /* [n_pair14][2] pairs with scaled nonbonded terms */
+    double scale14_lj;
+    double scale14_coul;
+} pamd_topology;
+
+typedef struct pamd_options {
+    double gamma_per_ps;        /* Langevin friction (MD-parameters paragraph: 1/ps) */
+    int32_t precision;          /* PAMD_PREC_MIXED or PAMD_PREC_FP64 */
+    int32_t lanes_per_replica;  /* 0 = choose; else 4, 8, 16 or 32 */
+    int32_t warps_per_block;    /* 0 = choose (4); else 1..8 */
+    int32_t mol_id;             /* molecule index mixed into the random counters */
+    void* (*dev_alloc)(size_t bytes, void* user); /* NULL = cudaMalloc */
+    void (*dev_free)(void* ptr, void* user);      /* NULL = cudaFree */
+    void* alloc_user;
+    void* stream;               /* cudaStream_t; NULL = a non-blocking stream the context creates */
+} pamd_options;
+
+/* Per-temperature population averages (PAMD scheme, step 4) with jackknife
+ * errors over 64 family bins (paragraph on correlations after resampling). */
+typedef struct pamd_obs {
+    double T;          /* heat-bath temperature of this measurement */
+    double lnQ;        /* ln Q of the resampling that led here (0 at T0) */
+    double sum_lnQ;    /* sum of ln Q since T0 = ln Z(T) - ln Z(T0), configurational */
+    double e_pot, e_pot_se;
+    double e_kin, e_kin_se;
+    double t_meas;     /* 2 <E_kin> / (3 N k_B) */
+    double rg, rg_se;  /* radius of gyration sqrt(mean |x_i - xbar|^2) */
+    double rg2, rg2_se;
+    int64_t n_families; /* distinct family ids (ancestors at T0) alive */
+    int32_t max_copies; /* largest copy count of the resampling that led here */
+    int32_t pad_;
+} pamd_obs;
+
+/* Fill *opt with the defaults: gamma 1/ps, mixed precision, automatic
+ * launch shape, molecule 0, cudaMalloc/cudaFree, a stream of the context's own. */
+void pamd_options_default(pamd_options* opt);
+
+/*
+ * PAMD scheme, step 1.  Create a context holding R replicas of `top`: every
+ * replica starts from x0 (shifted to its centre of mass), velocities from the
+ * Maxwell-Boltzmann distribution at T0 drawn from Philox4x32-10 keyed on
+ * `seed`, family id = replica index.  The random counter layout is
+ * (atom, replica slot, step, purpose | mol_id << 8).
+ * The paper's "additionally apply theta MD steps" is the caller's first
+ * pamd_propagate at T0.
+ * out: receives the context.  R: 1 .. 2^31-1.  T0 > 0.  opt: NULL = defaults.
+ * Errors: PAMD_EINVAL (bad topology, R, T0), PAMD_ENOMEM, PAMD_ECUDA,
+ * PAMD_EUNSUPPORTED (n_atoms > PAMD_MAX_ATOMS).
+ */
+int pamd_init(pamd_ctx** out, const pamd_topology* top, int64_t R, double T0, uint64_t seed,
+              const pamd_options* opt);
+
+/*
+ * PAMD scheme, step 1 again on an existing context: the population is reset
+ * exactly as pamd_init left it for (T0, seed) -- start geometry, fresh
+ * Maxwell-Boltzmann velocities, family id = slot -- and the random counters
+ * and the running sum of ln Q return to zero.  No memory is allocated.
+ * Asynchronous on the context's stream.
+ */
+int pamd_reset(pamd_ctx* ctx, double T0, uint64_t seed);
+
+/*
+ * PAMD scheme, step 3.  theta BAOAB Langevin steps (B: v += dt/2 F/m,
+ * A: x += dt/2 v, O: v = c1 v + sqrt((1-c1^2) k_B T/m) xi, A, F(x), B;
+ * c1 = exp(-gamma dt)) for every replica, one persistent kernel launch with
+ * each replica held in shared memory for all theta steps.  Noise xi from
+ * Philox keyed on (seed; atom, slot, global step, 0 | mol << 8).  Afterwards
+ * the potential energy (FP64 sum of FP32 terms), kinetic energy and radius
+ * of gyration of every replica are stored on the device.  Velocities are not
+ * rescaled here.  theta >= 0 (0 only evaluates energies); dt_ps > 0; T > 0.
+ * Asynchronous on the context's stream.
+ */
+int pamd_propagate(pamd_ctx* ctx, int32_t theta, double dt_ps, double T);
+
+/*
+ * PAMD scheme, step 2.  Resample from T_prev to T_next with the relative
+ * Boltzmann weights tau_j = exp(-(beta_next - beta_prev) E_j) / Q,
+ * Q = (1/R) sum_j exp(-(beta_next - beta_prev) E_j), by R multinomial draws
+ * (paragraph on the resampling implementation: probabilities tau_j / R,
+ * population size constant, zero copies prune).  Realisation: integer
+ * weights W_j = floor(2^s exp(a_j - max a)), s = 63 - ceil(log2 R), inclusive
+ * prefix sum C, draw k targets floor(u_k C_total / 2^64) with u_k a 64-bit
+ * Philox uniform keyed on (slot k, resampling index, 0, 2 | mol << 8), and
+ * ancestor = first j with C_j > target.  The new population lists copies in
+ * ascending ancestor order; positions are recentred on the centre of mass,
+ * velocities scaled by sqrt(T_next / T_prev), family ids carried along.
+ * The running sum of ln Q is updated on the device.
+ * copies_out: host [R] int32 copy counts n_j by ancestor, or NULL.
+ * lnQ_out: host double, or NULL.  Either non-NULL synchronises the stream.
+ */
+int pamd_resample(pamd_ctx* ctx, double T_prev, double T_next, int32_t* copies_out,
+                  double* lnQ_out);
+
+/*
+ * PAMD scheme, step 4.  Population averages of the current population
+ * measured at temperature T (only recorded in out->T and t_meas is computed
+ * from velocities).  out->lnQ / sum_lnQ / max_copies refer to the last
+ * resampling.  Synchronises the stream.  Returns PAMD_ENONFINITE if any
+ * replica energy is not finite.
+ */
+int pamd_observables(pamd_ctx* ctx, double T, pamd_obs* out);
+
+/*
+ * Whole anneal (PAMD scheme, steps 2-5 after the initial block): theta steps
+ * at T[0], measure; then for i = 1..K: resample T[i-1] -> T[i] (or, with
+ * resample = 0, keep every copy once and only rescale velocities: the
+ * "anneal" control of the paper's Fig. 2), theta steps at T[i], measure.
+ * Captured once per (K, theta, dt, schedule) into a CUDA graph and launched
+ * as one graph.  per_step_out: host [K+1] or NULL.  Synchronises the stream.
+ */
+int pamd_anneal(pamd_ctx* ctx, int32_t K, const double* T, int32_t theta, double dt_ps,
+                int32_t resample, pamd_obs* per_step_out);
+
+/*
+ * Copy the population to the host.  x, v: [R][N][3] double (the FP32 device
+ * values widened), E: [R], fam: [R]; any may be NULL.  Synchronises.
+ */
+int pamd_get_state(pamd_ctx* ctx, double* x, double* v, double* E, int32_t* fam);
+
+/*
+ * Replace the population from the host.  x, v: [R][N][3] (rounded to FP32;
+ * positions are stored as given, the caller recentres if it wants), E: [R]
+ * or NULL (then left unchanged), fam: [R] or NULL (unchanged).
+ */
+int pamd_set_state(pamd_ctx* ctx, const double* x, const double* v, const double* E,
+                   const int32_t* fam);
+
+/*
+ * Forces and potential energies of the current population without moving it
+ * (the force evaluation of pamd_propagate, theta = 0).  f: host [R][N][3]
+ * kJ/mol/nm or NULL; E: host [R] or NULL.  Synchronises.
+ */
+int pamd_forces(pamd_ctx* ctx, double* f, double* E);
+
+/* Random-counter state: global MD step and resampling index.  A restarted
+ * run that restores both (with the same seed and population) continues
+ * bit-identically. */
+int pamd_get_counters(pamd_ctx* ctx, uint32_t* step, uint32_t* resample_index, double* sum_lnQ);
+int pamd_set_counters(pamd_ctx* ctx, uint32_t step, uint32_t resample_index, double sum_lnQ);
+
+/* Number of replicas and atoms; the launch shape picked for propagate. */
+int pamd_info(pamd_ctx* ctx, int64_t* R, int32_t* n_atoms, int32_t* lanes_per_replica,
+              int32_t* atoms_per_lane, int32_t* replicas_per_block);
+
+/* Number of kernel launches the library issued on this context so far. */
+int64_t pamd_launch_count(pamd_ctx* ctx);
+
+/* Wait for all work of the context; returns PAMD_ECUDA on an asynchronous
+ * CUDA error. */
+int pamd_sync(pamd_ctx* ctx);
+
+/* Free the context and its device memory (NULL is allowed). */
+void pamd_destroy(pamd_ctx* ctx);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* pamd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PAMD_H */

@@ -88,6 +88,7 @@ def _load():
             "orc_energy_forces": (D, [TP, P, P, P]),
             "orc_init": (None, [TP, I64, D, U64, I32, P, P, P]),
             "orc_propagate": (None, [TP, I64, P, P, P, I32, D, D, D, U64, U32, I32, I32]),
+            "orc_propagate_slots": (None, [TP, I64, P, P, P, P, I32, D, D, D, U64, U32, I32, I32]),
             "orc_energies": (None, [TP, I64, P, P]),
             "orc_weight_shift": (I32, [I64]),
             "orc_resample_weights": (D, [P, I64, D, D, P]),
@@ -190,15 +191,18 @@ def init(top, R, T0, seed, mol=0):
     return x, v, fam
 
 
-def propagate(top, x, v, theta, dt, T, gamma, seed, step0, mol=0, n_threads=None):
-    """In place on copies; returns (x, v, E)."""
+def propagate(top, x, v, theta, dt, T, gamma, seed, step0, mol=0, n_threads=None, slots=None):
+    """theta MD steps on copies of x, v; returns (x, v, E).  ``slots`` gives the
+    replica slot (noise counter) of each row; default: the row index."""
     t = _topo(top)
     x = _f64(x).copy()
     v = _f64(v).copy()
     R = x.shape[0]
     E = np.zeros(R)
     nt = n_threads or os.cpu_count() or 1
-    _load().orc_propagate(t.ref, R, _p(x), _p(v), _p(E), theta, dt, T, gamma, seed, step0, mol, nt)
+    sl = None if slots is None else np.ascontiguousarray(slots, dtype=np.int64)
+    _load().orc_propagate_slots(t.ref, R, _p(sl), _p(x), _p(v), _p(E), theta, dt, T, gamma, seed,
+                                step0, mol, nt)
     return x, v, E
 
 

@@ -387,6 +387,7 @@ static double propagate_one(const orc_topology* t, double* x, double* v, double*
 typedef struct {
     const orc_topology* t;
     double *x, *v, *E;
+    const int64_t* slots; /* noise slot of each replica, or NULL for its index */
     int64_t lo, hi;
     int32_t theta, mol;
     double dt, T, gamma;
@@ -399,7 +400,8 @@ static void* prop_worker(void* arg) {
     int n = j->t->n_atoms;
     double* f = (double*)malloc(sizeof(double) * 3 * (size_t)(n > 0 ? n : 1));
     for (int64_t k = j->lo; k < j->hi; ++k) {
-        double e = propagate_one(j->t, &j->x[(size_t)k * 3 * n], &j->v[(size_t)k * 3 * n], f, k,
+        int64_t slot = j->slots ? j->slots[k] : k;
+        double e = propagate_one(j->t, &j->x[(size_t)k * 3 * n], &j->v[(size_t)k * 3 * n], f, slot,
                                  j->theta, j->dt, j->T, j->gamma, j->seed, j->step0, j->mol);
         if (j->E) j->E[k] = e;
     }
@@ -407,16 +409,17 @@ static void* prop_worker(void* arg) {
     return NULL;
 }
 
-/* theta MD steps for every replica; x, v: [R][N][3]; E (may be NULL): [R]. */
-void orc_propagate(const orc_topology* t, int64_t R, double* x, double* v, double* E,
-                   int32_t theta, double dt, double T, double gamma, uint64_t seed,
-                   uint32_t step0, int32_t mol, int32_t n_threads) {
+/* theta MD steps for R replicas; replica k uses noise slot slots[k] (or k when
+ * slots is NULL).  x, v: [R][N][3]; E (may be NULL): [R]. */
+void orc_propagate_slots(const orc_topology* t, int64_t R, const int64_t* slots, double* x,
+                         double* v, double* E, int32_t theta, double dt, double T, double gamma,
+                         uint64_t seed, uint32_t step0, int32_t mol, int32_t n_threads) {
     if (n_threads < 1) n_threads = 1;
     if (n_threads > R) n_threads = (int32_t)(R > 0 ? R : 1);
     pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * n_threads);
     prop_job* jobs = (prop_job*)malloc(sizeof(prop_job) * n_threads);
     for (int w = 0; w < n_threads; ++w) {
-        prop_job jb = {t, x, v, E, R * w / n_threads, R * (w + 1) / n_threads, theta, mol,
+        prop_job jb = {t, x, v, E, slots, R * w / n_threads, R * (w + 1) / n_threads, theta, mol,
                        dt, T, gamma, seed, step0};
         jobs[w] = jb;
         if (n_threads == 1) prop_worker(&jobs[w]);
@@ -426,6 +429,13 @@ void orc_propagate(const orc_topology* t, int64_t R, double* x, double* v, doubl
         for (int w = 0; w < n_threads; ++w) pthread_join(th[w], NULL);
     free(th);
     free(jobs);
+}
+
+/* theta MD steps for every replica (slot = index). */
+void orc_propagate(const orc_topology* t, int64_t R, double* x, double* v, double* E,
+                   int32_t theta, double dt, double T, double gamma, uint64_t seed,
+                   uint32_t step0, int32_t mol, int32_t n_threads) {
+    orc_propagate_slots(t, R, NULL, x, v, E, theta, dt, T, gamma, seed, step0, mol, n_threads);
 }
 
 /* Potential energy of every replica (FP64). */

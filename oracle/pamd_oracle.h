@@ -56,6 +56,9 @@ void orc_init(const orc_topology* t, int64_t R, double T0, uint64_t seed, int32_
 void orc_propagate(const orc_topology* t, int64_t R, double* x, double* v, double* E,
                    int32_t theta, double dt, double T, double gamma, uint64_t seed,
                    uint32_t step0, int32_t mol, int32_t n_threads);
+void orc_propagate_slots(const orc_topology* t, int64_t R, const int64_t* slots, double* x,
+                         double* v, double* E, int32_t theta, double dt, double T, double gamma,
+                         uint64_t seed, uint32_t step0, int32_t mol, int32_t n_threads);
 void orc_energies(const orc_topology* t, int64_t R, const double* x, double* E);
 int32_t orc_weight_shift(int64_t R);
 double orc_resample_weights(const double* E, int64_t R, double T_prev, double T_next, uint64_t* W);

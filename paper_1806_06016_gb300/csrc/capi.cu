@@ -1,0 +1,782 @@
+// capi.cu -- the extern "C" entry points declared in include/pamd.h.
+//
+// Host-side runtime: validates the topology, packs it into the table the
+// propagate kernel keeps in shared memory (per-atom parameters, 64-bit
+// exclusion masks per pair tile, bonded terms split into atom-disjoint colour
+// classes), owns the device buffers, chooses the launch shape, and captures a
+// whole anneal into one CUDA graph.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pamd_internal.h"
+
+using namespace pamd;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(pamd_ctx* c, cudaError_t e, const char* what) {
+    if (c) c->broken = true;
+    return fail(PAMD_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define PAMD_CU(ctx, call)                                      \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call); \
+    } while (0)
+
+void* dalloc(pamd_ctx* c, size_t bytes) {
+    bytes = (bytes + 255) & ~size_t(255);
+    if (bytes == 0) bytes = 256;
+    void* p = nullptr;
+    if (c->dev_alloc) {
+        p = c->dev_alloc(bytes, c->alloc_user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) c->allocations.push_back(p);
+    return p;
+}
+
+void free_all(pamd_ctx* c) {
+    for (void* p : c->allocations) {
+        if (c->dev_free) c->dev_free(p, c->alloc_user);
+        else cudaFree(p);
+    }
+    c->allocations.clear();
+}
+
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+bool finite_all(const double* a, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(a[i])) return false;
+    return true;
+}
+
+int check_indices(const int32_t* idx, int n_terms, int arity, int N, const char* what) {
+    if (n_terms < 0) return fail(PAMD_EINVAL, std::string(what) + ": negative count");
+    if (n_terms > 0 && !idx) return fail(PAMD_EINVAL, std::string(what) + ": null index array");
+    for (int t = 0; t < n_terms; ++t) {
+        for (int a = 0; a < arity; ++a) {
+            const int i = idx[t * arity + a];
+            if (i < 0 || i >= N) return fail(PAMD_EINVAL, std::string(what) + ": atom index out of range");
+            for (int b = 0; b < a; ++b)
+                if (idx[t * arity + b] == i)
+                    return fail(PAMD_EINVAL, std::string(what) + ": repeated atom in one term");
+        }
+    }
+    return PAMD_OK;
+}
+
+// Greedy colouring: term t gets the smallest colour whose atoms it does not
+// touch.  Returns the permutation that sorts terms by colour and the colour
+// start offsets.
+int colour_terms(const std::vector<std::vector<int>>& atoms, int N, std::vector<int>& order,
+                 std::vector<int>& starts, int* n_colors) {
+    const int n = (int)atoms.size();
+    std::vector<int> col(n, -1);
+    std::vector<std::vector<char>> used;
+    int nc = 0;
+    for (int t = 0; t < n; ++t) {
+        int c = 0;
+        for (;; ++c) {
+            if (c == nc) {
+                used.emplace_back(N, 0);
+                ++nc;
+            }
+            bool ok = true;
+            for (int i : atoms[t])
+                if (used[c][i]) ok = false;
+            if (ok) break;
+        }
+        if (c >= kMaxColors) return fail(PAMD_EUNSUPPORTED, "bonded terms need more than 64 colour classes");
+        col[t] = c;
+        for (int i : atoms[t]) used[c][i] = 1;
+    }
+    order.resize(n);
+    for (int t = 0; t < n; ++t) order[t] = t;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return col[a] < col[b]; });
+    starts.assign(kMaxColors + 1, n);
+    for (int c = 0; c <= nc; ++c) {
+        int s = 0;
+        while (s < n && col[order[s]] < c) ++s;
+        starts[c] = s;
+    }
+    *n_colors = nc;
+    return PAMD_OK;
+}
+
+int choose_lanes(int N, int requested, int* L, int* B) {
+    if (requested) {
+        if (requested != 4 && requested != 8 && requested != 16 && requested != 32)
+            return fail(PAMD_EINVAL, "lanes_per_replica must be 0, 4, 8, 16 or 32");
+        *L = requested;
+        *B = (N + requested - 1) / requested;
+        if (*B > 8) return fail(PAMD_EINVAL, "lanes_per_replica too small for this molecule (8 atoms per lane at most)");
+        return PAMD_OK;
+    }
+    for (int l : {4, 8, 16, 32}) {
+        const int b = (N + l - 1) / l;
+        if (b <= 8) {
+            *L = l;
+            *B = b;
+            return PAMD_OK;
+        }
+    }
+    return fail(PAMD_EUNSUPPORTED, "molecule too large");
+}
+
+// Build the shared-memory table of the propagate kernel.
+int build_topology(pamd_ctx* c, const pamd_topology* t, int lanes_req, std::vector<unsigned char>& blob) {
+    const int N = t->n_atoms;
+    if (N < 1) return fail(PAMD_EINVAL, "n_atoms must be >= 1");
+    if (N > PAMD_MAX_ATOMS) return fail(PAMD_EUNSUPPORTED, "n_atoms exceeds PAMD_MAX_ATOMS");
+    if (!t->mass || !t->charge || !t->sigma || !t->epsilon || !t->x0)
+        return fail(PAMD_EINVAL, "null per-atom array");
+    if (!finite_all(t->mass, N) || !finite_all(t->charge, N) || !finite_all(t->sigma, N) ||
+        !finite_all(t->epsilon, N) || !finite_all(t->x0, 3 * N))
+        return fail(PAMD_EINVAL, "non-finite per-atom value");
+    for (int i = 0; i < N; ++i) {
+        if (!(t->mass[i] > 0)) return fail(PAMD_EINVAL, "masses must be > 0");
+        if (t->sigma[i] < 0 || t->epsilon[i] < 0) return fail(PAMD_EINVAL, "sigma and epsilon must be >= 0");
+    }
+    int rc;
+    if ((rc = check_indices(t->bond, t->n_bonds, 2, N, "bonds"))) return rc;
+    if ((rc = check_indices(t->angle, t->n_angles, 3, N, "angles"))) return rc;
+    if ((rc = check_indices(t->dihedral, t->n_dihedrals, 4, N, "dihedrals"))) return rc;
+    if ((rc = check_indices(t->excl, t->n_excl, 2, N, "exclusions"))) return rc;
+    if ((rc = check_indices(t->pair14, t->n_pair14, 2, N, "1-4 pairs"))) return rc;
+    if (t->n_bonds > 0 && (!t->bond_r0 || !t->bond_k || !finite_all(t->bond_r0, t->n_bonds) ||
+                           !finite_all(t->bond_k, t->n_bonds)))
+        return fail(PAMD_EINVAL, "bond parameters");
+    if (t->n_angles > 0 && (!t->angle_t0 || !t->angle_k || !finite_all(t->angle_t0, t->n_angles) ||
+                            !finite_all(t->angle_k, t->n_angles)))
+        return fail(PAMD_EINVAL, "angle parameters");
+    if (t->n_dihedrals > 0) {
+        if (!t->dih_n || !t->dih_k || !t->dih_phase || !finite_all(t->dih_k, t->n_dihedrals) ||
+            !finite_all(t->dih_phase, t->n_dihedrals))
+            return fail(PAMD_EINVAL, "dihedral parameters");
+        for (int d = 0; d < t->n_dihedrals; ++d)
+            if (t->dih_n[d] < 1 || t->dih_n[d] > 6) return fail(PAMD_EINVAL, "dihedral multiplicity must be 1..6");
+    }
+    if (!std::isfinite(t->scale14_lj) || !std::isfinite(t->scale14_coul))
+        return fail(PAMD_EINVAL, "1-4 scale factors");
+
+    int L, B;
+    if ((rc = choose_lanes(N, lanes_req, &L, &B))) return rc;
+    TopoLayout& lay = c->lay;
+    lay = TopoLayout{};
+    lay.n_atoms = N;
+    lay.n_pad = round_up(N, 4);
+    lay.lanes = L;
+    lay.per_lane = B;
+    lay.block_stride = (B % 2 == 1) ? B : B + 1;
+    lay.nk = L * lay.block_stride;
+    auto slot = [&](int i) { return (i / B) * lay.block_stride + i % B; };
+
+    // pair kinds: exclusions win over 1-4 entries
+    std::vector<char> excl((size_t)N * N, 0);
+    for (int p = 0; p < t->n_excl; ++p) {
+        const int i = t->excl[2 * p], j = t->excl[2 * p + 1];
+        excl[(size_t)i * N + j] = excl[(size_t)j * N + i] = 1;
+    }
+    std::vector<std::pair<int, int>> p14;
+    for (int p = 0; p < t->n_pair14; ++p) {
+        const int i = t->pair14[2 * p], j = t->pair14[2 * p + 1];
+        if (!excl[(size_t)i * N + j]) p14.emplace_back(i, j);
+    }
+    // tile masks
+    const int TH = L / 2;
+    std::vector<unsigned long long> masks((size_t)(TH + 1) * L, 0ull);
+    auto mask_pair = [&](int i, int j) {
+        const int gi = i / B, gj = j / B, ai = i % B, aj = j % B;
+        if (gi == gj) {
+            const int a = std::min(ai, aj), b = std::max(ai, aj);
+            masks[gi] |= 1ull << (a * B + b);
+            return;
+        }
+        const int tt = ((gj - gi) % L + L) % L;
+        if (tt < TH || (tt == TH && gi < TH)) {
+            masks[(size_t)tt * L + gi] |= 1ull << (ai * B + aj);
+        } else {
+            const int t2 = L - tt;
+            masks[(size_t)t2 * L + gj] |= 1ull << (aj * B + ai);
+        }
+    };
+    for (int p = 0; p < t->n_excl; ++p) mask_pair(t->excl[2 * p], t->excl[2 * p + 1]);
+    for (auto& q : p14) mask_pair(q.first, q.second);
+
+    // bonded records, coloured
+    std::vector<BondRec> bonds;
+    std::vector<AngleRec> angles;
+    std::vector<DihRec> dihs;
+    std::vector<Pair14Rec> prs;
+    std::vector<int> starts[4];
+    {
+        std::vector<std::vector<int>> at;
+        for (int b = 0; b < t->n_bonds; ++b) at.push_back({t->bond[2 * b], t->bond[2 * b + 1]});
+        std::vector<int> order;
+        if ((rc = colour_terms(at, N, order, starts[0], &lay.n_colors[0]))) return rc;
+        for (int o : order)
+            bonds.push_back({slot(t->bond[2 * o]), slot(t->bond[2 * o + 1]), (float)t->bond_r0[o],
+                             (float)t->bond_k[o]});
+    }
+    {
+        std::vector<std::vector<int>> at;
+        for (int a = 0; a < t->n_angles; ++a)
+            at.push_back({t->angle[3 * a], t->angle[3 * a + 1], t->angle[3 * a + 2]});
+        std::vector<int> order;
+        if ((rc = colour_terms(at, N, order, starts[1], &lay.n_colors[1]))) return rc;
+        for (int o : order)
+            angles.push_back({slot(t->angle[3 * o]), slot(t->angle[3 * o + 1]),
+                              slot(t->angle[3 * o + 2]), 0, (float)t->angle_t0[o],
+                              (float)t->angle_k[o], 0.f, 0.f});
+    }
+    {
+        std::vector<std::vector<int>> at;
+        for (int d = 0; d < t->n_dihedrals; ++d)
+            at.push_back({t->dihedral[4 * d], t->dihedral[4 * d + 1], t->dihedral[4 * d + 2],
+                          t->dihedral[4 * d + 3]});
+        std::vector<int> order;
+        if ((rc = colour_terms(at, N, order, starts[2], &lay.n_colors[2]))) return rc;
+        for (int o : order)
+            dihs.push_back({slot(t->dihedral[4 * o]), slot(t->dihedral[4 * o + 1]),
+                            slot(t->dihedral[4 * o + 2]), slot(t->dihedral[4 * o + 3]),
+                            (float)t->dih_k[o], (float)t->dih_n[o], (float)std::cos(t->dih_phase[o]),
+                            (float)std::sin(t->dih_phase[o])});
+    }
+    {
+        std::vector<std::vector<int>> at;
+        for (auto& q : p14) at.push_back({q.first, q.second});
+        std::vector<int> order;
+        if ((rc = colour_terms(at, N, order, starts[3], &lay.n_colors[3]))) return rc;
+        for (int o : order)
+            prs.push_back({slot(p14[o].first), slot(p14[o].second), (float)t->scale14_lj,
+                           (float)t->scale14_coul});
+    }
+    lay.n_bonds = (int)bonds.size();
+    lay.n_angles = (int)angles.size();
+    lay.n_dihs = (int)dihs.size();
+    lay.n_p14 = (int)prs.size();
+
+    int off = 0;
+    lay.off_params = off; off += round_up(lay.nk * 16, 16);
+    lay.off_masks = off; off += round_up((int)masks.size() * 8, 16);
+    lay.off_bonds = off; off += round_up(lay.n_bonds * 16, 16);
+    lay.off_angles = off; off += round_up(lay.n_angles * 32, 16);
+    lay.off_dihs = off; off += round_up(lay.n_dihs * 32, 16);
+    lay.off_p14 = off; off += round_up(lay.n_p14 * 16, 16);
+    lay.off_colors = off; off += round_up(4 * (kMaxColors + 1) * 4, 16);
+    lay.bytes = off;
+    blob.assign(off, 0);
+    float* prm = reinterpret_cast<float*>(blob.data() + lay.off_params);
+    const double sqrt_ke = std::sqrt(kCoulomb);
+    for (int i = 0; i < N; ++i) {
+        float* q = prm + 4 * slot(i);
+        q[0] = (float)(0.5 * t->sigma[i]);
+        q[1] = (float)std::sqrt(24.0 * t->epsilon[i]);
+        q[2] = (float)(t->charge[i] * sqrt_ke);
+        q[3] = (float)(1.0 / t->mass[i]);
+    }
+    std::memcpy(blob.data() + lay.off_masks, masks.data(), masks.size() * 8);
+    if (!bonds.empty()) std::memcpy(blob.data() + lay.off_bonds, bonds.data(), bonds.size() * 16);
+    if (!angles.empty()) std::memcpy(blob.data() + lay.off_angles, angles.data(), angles.size() * 32);
+    if (!dihs.empty()) std::memcpy(blob.data() + lay.off_dihs, dihs.data(), dihs.size() * 32);
+    if (!prs.empty()) std::memcpy(blob.data() + lay.off_p14, prs.data(), prs.size() * 16);
+    int* cols = reinterpret_cast<int*>(blob.data() + lay.off_colors);
+    for (int ty = 0; ty < 4; ++ty)
+        for (int q = 0; q <= kMaxColors; ++q) cols[ty * (kMaxColors + 1) + q] = starts[ty][q];
+    return PAMD_OK;
+}
+
+cudaError_t propagate_dispatch_any(int L, const PropParams* p, int B, int warps, int grid,
+                                   size_t smem, cudaStream_t s, int* occ) {
+    switch (L) {
+        case 4: return propagate_l4(p, B, warps, grid, smem, s, occ);
+        case 8: return propagate_l8(p, B, warps, grid, smem, s, occ);
+        case 16: return propagate_l16(p, B, warps, grid, smem, s, occ);
+        case 32: return propagate_l32(p, B, warps, grid, smem, s, occ);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+size_t prop_smem(const pamd_ctx* c) {
+    return (size_t)c->lay.bytes + (size_t)c->rpb * (2 * c->lay.nk + 1) * 16;
+}
+
+float* cur_state(pamd_ctx* c) { return c->cur_is_alt ? c->b.state_alt : c->b.state; }
+double* cur_E(pamd_ctx* c) { return c->cur_is_alt ? c->b.E_alt : c->b.E; }
+int32_t* cur_fam(pamd_ctx* c) { return c->cur_is_alt ? c->b.fam_alt : c->b.fam; }
+
+int launch_prop(pamd_ctx* c, int theta, double dt, double T, const uint32_t* dev_ctr,
+                uint32_t step0, float* fout) {
+    PropParams p{};
+    p.state_in = cur_state(c);
+    p.state_out = cur_state(c);
+    p.E = cur_E(c);
+    p.ke = c->b.ke;
+    p.rg = c->b.rg;
+    p.fout = fout;
+    p.masses = c->b.masses;
+    p.topo = c->b.topo;
+    p.status = &c->b.scal->status;
+    p.dev_counters = dev_ctr;
+    p.lay = c->lay;
+    p.R = c->R;
+    p.theta = theta;
+    p.hdt = (float)(0.5 * dt);
+    const double c1 = std::exp(-c->gamma * dt);
+    p.c1 = (float)c1;
+    p.c2kT = (float)std::sqrt((1.0 - c1 * c1) * kBoltzmann * T);
+    p.seed = c->seed;
+    p.step0 = step0;
+    p.purpose_mol = kPurposeNoise | ((uint32_t)c->mol << 8);
+    cudaError_t e = propagate_dispatch_any(c->lay.lanes, &p, c->lay.per_lane, c->warps_per_block,
+                                           c->grid_prop, prop_smem(c), c->stream, nullptr);
+    c->launches += 1;
+    if (e != cudaSuccess) return cuda_fail(c, e, "propagate launch");
+    return PAMD_OK;
+}
+
+int check_ctx(pamd_ctx* c) {
+    if (!c) return fail(PAMD_EINVAL, "null context");
+    if (c->broken) return fail(PAMD_ESTATE, "context broken by an earlier CUDA failure");
+    return PAMD_OK;
+}
+
+int read_status(pamd_ctx* c) {
+    DevScalars s;
+    PAMD_CU(c, cudaMemcpyAsync(&s, c->b.scal, sizeof(s), cudaMemcpyDeviceToHost, c->stream));
+    PAMD_CU(c, cudaStreamSynchronize(c->stream));
+    if (s.status == 0) return PAMD_OK;
+    // report once, then clear so that the caller can repair the state and go on
+    const int zero[2] = {0, -1};
+    PAMD_CU(c, cudaMemcpyAsync(&c->b.scal->status, zero, sizeof(zero), cudaMemcpyHostToDevice, c->stream));
+    PAMD_CU(c, cudaStreamSynchronize(c->stream));
+    if (s.status == PAMD_ENONFINITE)
+        return fail(PAMD_ENONFINITE, "non-finite energy in replica " + std::to_string(s.bad_replica));
+    return fail(s.status, "device status " + std::to_string(s.status));
+}
+
+int ensure_obs_cap(pamd_ctx* c, int n) {
+    if (c->obs_cap >= n) return PAMD_OK;
+    void* p = dalloc(c, sizeof(pamd_obs) * (size_t)n);
+    if (!p) return fail(PAMD_ENOMEM, "observable buffer");
+    c->b.obs = (pamd_obs*)p;  // the old buffer stays owned until destroy
+    c->obs_cap = n;
+    return PAMD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pamd_options_default(pamd_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->gamma_per_ps = 1.0;
+    o->precision = PAMD_PREC_MIXED;
+}
+
+const char* pamd_last_error(void) { return g_err.c_str(); }
+
+int pamd_init(pamd_ctx** out, const pamd_topology* top, int64_t R, double T0, uint64_t seed,
+              const pamd_options* opt) {
+    g_err.clear();
+    if (!out || !top) return fail(PAMD_EINVAL, "null argument");
+    *out = nullptr;
+    if (R < 1 || R > 0x7fffffffLL) return fail(PAMD_EINVAL, "R must be in 1 .. 2^31-1");
+    if (!(T0 > 0) || !std::isfinite(T0)) return fail(PAMD_EINVAL, "T0 must be > 0");
+    pamd_options o;
+    pamd_options_default(&o);
+    if (opt) o = *opt;
+    if (!(o.gamma_per_ps >= 0) || !std::isfinite(o.gamma_per_ps))
+        return fail(PAMD_EINVAL, "gamma must be >= 0");
+    if (o.precision != PAMD_PREC_MIXED)
+        return fail(PAMD_EUNSUPPORTED, "only PAMD_PREC_MIXED is built");
+    if (o.warps_per_block < 0 || o.warps_per_block > 8)
+        return fail(PAMD_EINVAL, "warps_per_block must be 0..8");
+    if (o.mol_id < 0 || o.mol_id > 0xffffff) return fail(PAMD_EINVAL, "mol_id must be 0..2^24-1");
+    if ((o.dev_alloc == nullptr) != (o.dev_free == nullptr))
+        return fail(PAMD_EINVAL, "dev_alloc and dev_free must both be set or both be NULL");
+
+    pamd_ctx* c = new (std::nothrow) pamd_ctx();
+    if (!c) return fail(PAMD_ENOMEM, "host allocation");
+    c->R = R;
+    c->gamma = o.gamma_per_ps;
+    c->seed = seed;
+    c->mol = o.mol_id;
+    c->dev_alloc = o.dev_alloc;
+    c->dev_free = o.dev_free;
+    c->alloc_user = o.alloc_user;
+    std::vector<unsigned char> blob;
+    int rc = build_topology(c, top, o.lanes_per_replica, blob);
+    if (rc) {
+        delete c;
+        return rc;
+    }
+    c->N = c->lay.n_atoms;
+    c->Np = c->lay.n_pad;
+    auto bail = [&](int code, const std::string& m) {
+        free_all(c);
+        if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+        delete c;
+        return fail(code, m);
+    };
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return bail(PAMD_ECUDA, "no CUDA device");
+    if (o.stream) {
+        c->stream = (cudaStream_t)o.stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(PAMD_ECUDA, "stream creation");
+        c->own_stream = true;
+    }
+    // launch shape
+    const int groups_per_warp = 32 / c->lay.lanes;
+    int warps = o.warps_per_block ? o.warps_per_block : 4;
+    int max_smem = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    for (;;) {
+        c->warps_per_block = warps;
+        c->rpb = warps * groups_per_warp;
+        if ((long long)prop_smem(c) <= max_smem || warps == 1) break;
+        --warps;
+    }
+    if ((long long)prop_smem(c) > max_smem) return bail(PAMD_EUNSUPPORTED, "molecule tables exceed shared memory");
+    int occ = 0;
+    cudaError_t e = propagate_dispatch_any(c->lay.lanes, nullptr, c->lay.per_lane, c->warps_per_block,
+                                           0, prop_smem(c), nullptr, &occ);
+    if (e != cudaSuccess || occ < 1) return bail(PAMD_ECUDA, std::string("propagate occupancy: ") + cudaGetErrorString(e));
+    const long long batches = (R + c->rpb - 1) / c->rpb;
+    c->grid_prop = (int)std::min<long long>(batches, (long long)c->num_sms * occ);
+
+    // host-side tables
+    c->host_mass.assign(top->mass, top->mass + c->N);
+    std::vector<float> masses(c->Np, 0.0f), x0(3 * (size_t)c->Np, 0.0f);
+    double com[3] = {0, 0, 0}, mt = 0;
+    for (int i = 0; i < c->N; ++i) {
+        for (int q = 0; q < 3; ++q) com[q] += top->mass[i] * top->x0[3 * i + q];
+        mt += top->mass[i];
+    }
+    for (int i = 0; i < c->N; ++i) {
+        masses[i] = (float)top->mass[i];
+        for (int q = 0; q < 3; ++q) x0[(size_t)q * c->Np + i] = (float)(top->x0[3 * i + q] - com[q] / mt);
+    }
+    // buffers
+    const size_t st_bytes = sizeof(float) * 6 * (size_t)c->Np * (size_t)R;
+    c->n_blk = (int)((R + 1023) / 1024);
+    Buffers& b = c->b;
+    b.state = (float*)dalloc(c, st_bytes);
+    b.state_alt = (float*)dalloc(c, st_bytes);
+    b.E = (double*)dalloc(c, sizeof(double) * R);
+    b.E_alt = (double*)dalloc(c, sizeof(double) * R);
+    b.fam = (int32_t*)dalloc(c, sizeof(int32_t) * R);
+    b.fam_alt = (int32_t*)dalloc(c, sizeof(int32_t) * R);
+    b.ke = (double*)dalloc(c, sizeof(double) * R);
+    b.rg = (double*)dalloc(c, sizeof(double) * R);
+    b.masses = (float*)dalloc(c, sizeof(float) * c->Np);
+    b.topo = (unsigned char*)dalloc(c, blob.size());
+    b.x0 = (float*)dalloc(c, sizeof(float) * 3 * c->Np);
+    b.W = (unsigned long long*)dalloc(c, 8 * (size_t)R);
+    b.C = (unsigned long long*)dalloc(c, 8 * (size_t)R);
+    b.cnt = (int32_t*)dalloc(c, 4 * (size_t)R);
+    b.cnt_incl = (int32_t*)dalloc(c, 4 * (size_t)R);
+    b.blk_u64 = (unsigned long long*)dalloc(c, 8 * (size_t)c->n_blk);
+    b.blk_f64 = (double*)dalloc(c, 8 * (size_t)c->n_blk);
+    b.blk_i32 = (int32_t*)dalloc(c, 8 * (size_t)c->n_blk);
+    b.flags = (unsigned char*)dalloc(c, (size_t)R);
+    b.obs_part = (double*)dalloc(c, sizeof(double) * (64 * 5 + 1) * (size_t)c->n_blk);
+    b.scal = (DevScalars*)dalloc(c, sizeof(DevScalars));
+    b.counters = (uint32_t*)dalloc(c, 16);
+    if (!b.state || !b.state_alt || !b.E || !b.E_alt || !b.fam || !b.fam_alt || !b.ke || !b.rg ||
+        !b.masses || !b.topo || !b.x0 || !b.W || !b.C || !b.cnt || !b.cnt_incl || !b.blk_u64 ||
+        !b.blk_f64 || !b.blk_i32 || !b.flags || !b.obs_part || !b.scal || !b.counters)
+        return bail(PAMD_ENOMEM, "device allocation failed");
+    if (ensure_obs_cap(c, 2)) return bail(PAMD_ENOMEM, "device allocation failed");
+    bool ok = cudaMemcpyAsync(b.masses, masses.data(), sizeof(float) * c->Np, cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
+              cudaMemcpyAsync(b.topo, blob.data(), blob.size(), cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
+              cudaMemcpyAsync(b.x0, x0.data(), sizeof(float) * 3 * c->Np, cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
+              cudaMemsetAsync(b.state_alt, 0, st_bytes, c->stream) == cudaSuccess &&
+              cudaMemsetAsync(b.ke, 0, sizeof(double) * R, c->stream) == cudaSuccess &&
+              cudaMemsetAsync(b.rg, 0, sizeof(double) * R, c->stream) == cudaSuccess &&
+              launch_init(c, T0) == cudaSuccess &&
+              launch_set_counters(c, 0, 0) == cudaSuccess &&
+              cudaStreamSynchronize(c->stream) == cudaSuccess;
+    if (!ok) return bail(PAMD_ECUDA, std::string("initialisation: ") + cudaGetErrorString(cudaGetLastError()));
+    *out = c;
+    return PAMD_OK;
+}
+
+int pamd_reset(pamd_ctx* c, double T0, uint64_t seed) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!(T0 > 0) || !std::isfinite(T0)) return fail(PAMD_EINVAL, "T0 must be > 0");
+    c->seed = seed;
+    c->cur_is_alt = false;
+    c->step = 0;
+    c->resample_index = 0;
+    cudaError_t e = launch_init(c, T0);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reset");
+    return PAMD_OK;
+}
+
+int pamd_propagate(pamd_ctx* c, int32_t theta, double dt_ps, double T) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (theta < 0) return fail(PAMD_EINVAL, "theta must be >= 0");
+    if (!(dt_ps > 0) || !std::isfinite(dt_ps)) return fail(PAMD_EINVAL, "dt must be > 0");
+    if (!(T > 0) || !std::isfinite(T)) return fail(PAMD_EINVAL, "T must be > 0");
+    rc = launch_prop(c, theta, dt_ps, T, nullptr, c->step, nullptr);
+    if (rc) return rc;
+    c->step += (uint32_t)theta;
+    return PAMD_OK;
+}
+
+int pamd_resample(pamd_ctx* c, double T_prev, double T_next, int32_t* copies_out, double* lnQ_out) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!(T_prev > 0) || !(T_next > 0) || !std::isfinite(T_prev) || !std::isfinite(T_next))
+        return fail(PAMD_EINVAL, "temperatures must be > 0");
+    c->resample_index += 1;
+    cudaError_t e = launch_resample(c, T_prev, T_next, 1, nullptr, c->resample_index);
+    if (e != cudaSuccess) return cuda_fail(c, e, "resample launch");
+    c->cur_is_alt = !c->cur_is_alt;
+    if (copies_out)
+        PAMD_CU(c, cudaMemcpyAsync(copies_out, c->b.cnt, sizeof(int32_t) * c->R, cudaMemcpyDeviceToHost, c->stream));
+    if (lnQ_out)
+        PAMD_CU(c, cudaMemcpyAsync(lnQ_out, &c->b.scal->lnQ, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (copies_out || lnQ_out) return read_status(c);
+    return PAMD_OK;
+}
+
+int pamd_observables(pamd_ctx* c, double T, pamd_obs* out) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!out) return fail(PAMD_EINVAL, "null output");
+    cudaError_t e = launch_observe(c, T, c->b.obs);
+    if (e != cudaSuccess) return cuda_fail(c, e, "observables launch");
+    PAMD_CU(c, cudaMemcpyAsync(out, c->b.obs, sizeof(pamd_obs), cudaMemcpyDeviceToHost, c->stream));
+    rc = read_status(c);
+    out->pad_ = 0;
+    return rc;
+}
+
+int pamd_anneal(pamd_ctx* c, int32_t K, const double* T, int32_t theta, double dt_ps,
+                int32_t resample, pamd_obs* per_step_out) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (K < 0 || !T) return fail(PAMD_EINVAL, "K must be >= 0 and T non-null");
+    if (theta < 0 || !(dt_ps > 0) || !std::isfinite(dt_ps)) return fail(PAMD_EINVAL, "theta / dt");
+    for (int i = 0; i <= K; ++i)
+        if (!(T[i] > 0) || !std::isfinite(T[i])) return fail(PAMD_EINVAL, "temperatures must be > 0");
+    if ((rc = ensure_obs_cap(c, K + 1))) return rc;
+    GraphKey key;
+    key.K = K;
+    key.theta = theta;
+    key.resample = resample ? 1 : 0;
+    key.dt = dt_ps;
+    key.T.assign(T, T + K + 1);
+    // the captured graph starts from the main buffers
+    if (c->cur_is_alt) {
+        const size_t st_bytes = sizeof(float) * 6 * (size_t)c->Np * (size_t)c->R;
+        PAMD_CU(c, cudaMemcpyAsync(c->b.state, c->b.state_alt, st_bytes, cudaMemcpyDeviceToDevice, c->stream));
+        PAMD_CU(c, cudaMemcpyAsync(c->b.E, c->b.E_alt, 8 * (size_t)c->R, cudaMemcpyDeviceToDevice, c->stream));
+        PAMD_CU(c, cudaMemcpyAsync(c->b.fam, c->b.fam_alt, 4 * (size_t)c->R, cudaMemcpyDeviceToDevice, c->stream));
+        c->cur_is_alt = false;
+    }
+    if (!c->graph_exec || !(c->graph_key == key)) {
+        if (c->graph_exec) {
+            cudaGraphExecDestroy(c->graph_exec);
+            c->graph_exec = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        PAMD_CU(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        const long long before = c->launches;
+        int err = launch_prop(c, theta, dt_ps, T[0], c->b.counters, 0u, nullptr);
+        if (!err && launch_observe(c, T[0], c->b.obs) != cudaSuccess) err = PAMD_ECUDA;
+        for (int i = 1; i <= K && !err; ++i) {
+            if (launch_resample(c, T[i - 1], T[i], resample ? 1 : 0, c->b.counters, (uint32_t)i) != cudaSuccess) {
+                err = PAMD_ECUDA;
+                break;
+            }
+            c->cur_is_alt = !c->cur_is_alt;
+            err = launch_prop(c, theta, dt_ps, T[i], c->b.counters, (uint32_t)i * (uint32_t)theta, nullptr);
+            if (!err && launch_observe(c, T[i], c->b.obs + i) != cudaSuccess) err = PAMD_ECUDA;
+        }
+        if (!err && c->cur_is_alt) {
+            const size_t st_bytes = sizeof(float) * 6 * (size_t)c->Np * (size_t)c->R;
+            if (cudaMemcpyAsync(c->b.state, c->b.state_alt, st_bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
+                cudaMemcpyAsync(c->b.E, c->b.E_alt, 8 * (size_t)c->R, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
+                cudaMemcpyAsync(c->b.fam, c->b.fam_alt, 4 * (size_t)c->R, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+                err = PAMD_ECUDA;
+        }
+        c->cur_is_alt = false;
+        c->graph_kernels = c->launches - before;
+        c->launches = before;
+        cudaError_t ec = cudaStreamEndCapture(c->stream, &g);
+        if (err || ec != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            c->broken = true;
+            return fail(PAMD_ECUDA, std::string("anneal capture failed: ") + cudaGetErrorString(ec) + " " + g_err);
+        }
+        cudaError_t ei = cudaGraphInstantiate(&c->graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) return cuda_fail(c, ei, "graph instantiate");
+        c->graph_key = key;
+    }
+    cudaError_t e = launch_set_counters(c, c->step, c->resample_index);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set counters");
+    PAMD_CU(c, cudaGraphLaunch(c->graph_exec, c->stream));
+    c->launches += c->graph_kernels;
+    c->step += (uint32_t)(K + 1) * (uint32_t)theta;
+    c->resample_index += (uint32_t)K;
+    if (per_step_out) {
+        PAMD_CU(c, cudaMemcpyAsync(per_step_out, c->b.obs, sizeof(pamd_obs) * (size_t)(K + 1),
+                                   cudaMemcpyDeviceToHost, c->stream));
+        rc = read_status(c);
+        for (int i = 0; i <= K; ++i) per_step_out[i].pad_ = 0;
+        return rc;
+    }
+    return read_status(c);
+}
+
+int pamd_get_state(pamd_ctx* c, double* x, double* v, double* E, int32_t* fam) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    const int N = c->N, Np = c->Np;
+    const long long R = c->R;
+    std::vector<float> st;
+    if (x || v) {
+        st.resize((size_t)R * 6 * Np);
+        PAMD_CU(c, cudaMemcpyAsync(st.data(), cur_state(c), st.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+    }
+    if (E) PAMD_CU(c, cudaMemcpyAsync(E, cur_E(c), 8 * (size_t)R, cudaMemcpyDeviceToHost, c->stream));
+    if (fam) PAMD_CU(c, cudaMemcpyAsync(fam, cur_fam(c), 4 * (size_t)R, cudaMemcpyDeviceToHost, c->stream));
+    PAMD_CU(c, cudaStreamSynchronize(c->stream));
+    for (long long k = 0; k < R && (x || v); ++k) {
+        const float* s = st.data() + (size_t)k * 6 * Np;
+        for (int i = 0; i < N; ++i)
+            for (int q = 0; q < 3; ++q) {
+                if (x) x[((size_t)k * N + i) * 3 + q] = s[(size_t)q * Np + i];
+                if (v) v[((size_t)k * N + i) * 3 + q] = s[(size_t)(3 + q) * Np + i];
+            }
+    }
+    return PAMD_OK;
+}
+
+int pamd_set_state(pamd_ctx* c, const double* x, const double* v, const double* E, const int32_t* fam) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!x || !v) return fail(PAMD_EINVAL, "x and v are required");
+    const int N = c->N, Np = c->Np;
+    const long long R = c->R;
+    if (!finite_all(x, (int)std::min<long long>(R * N * 3, 0x7fffffff)) ||
+        !finite_all(v, (int)std::min<long long>(R * N * 3, 0x7fffffff)))
+        return fail(PAMD_EINVAL, "non-finite state");
+    std::vector<float> st((size_t)R * 6 * Np, 0.0f);
+    for (long long k = 0; k < R; ++k) {
+        float* s = st.data() + (size_t)k * 6 * Np;
+        for (int i = 0; i < N; ++i)
+            for (int q = 0; q < 3; ++q) {
+                s[(size_t)q * Np + i] = (float)x[((size_t)k * N + i) * 3 + q];
+                s[(size_t)(3 + q) * Np + i] = (float)v[((size_t)k * N + i) * 3 + q];
+            }
+    }
+    PAMD_CU(c, cudaMemcpyAsync(cur_state(c), st.data(), st.size() * 4, cudaMemcpyHostToDevice, c->stream));
+    if (E) PAMD_CU(c, cudaMemcpyAsync(cur_E(c), E, 8 * (size_t)R, cudaMemcpyHostToDevice, c->stream));
+    if (fam) PAMD_CU(c, cudaMemcpyAsync(cur_fam(c), fam, 4 * (size_t)R, cudaMemcpyHostToDevice, c->stream));
+    PAMD_CU(c, cudaStreamSynchronize(c->stream));
+    return PAMD_OK;
+}
+
+int pamd_forces(pamd_ctx* c, double* f, double* E) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    const int N = c->N, Np = c->Np;
+    const long long R = c->R;
+    if (!c->b.fout) {
+        c->b.fout = (float*)dalloc(c, sizeof(float) * 3 * (size_t)Np * (size_t)R);
+        if (!c->b.fout) return fail(PAMD_ENOMEM, "force buffer");
+    }
+    if ((rc = launch_prop(c, 0, 0.001, 300.0, nullptr, c->step, c->b.fout))) return rc;
+    std::vector<float> fo;
+    if (f) {
+        fo.resize((size_t)R * 3 * Np);
+        PAMD_CU(c, cudaMemcpyAsync(fo.data(), c->b.fout, fo.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+    }
+    if (E) PAMD_CU(c, cudaMemcpyAsync(E, cur_E(c), 8 * (size_t)R, cudaMemcpyDeviceToHost, c->stream));
+    PAMD_CU(c, cudaStreamSynchronize(c->stream));
+    for (long long k = 0; k < R && f; ++k)
+        for (int i = 0; i < N; ++i)
+            for (int q = 0; q < 3; ++q)
+                f[((size_t)k * N + i) * 3 + q] = fo[(size_t)k * 3 * Np + (size_t)q * Np + i];
+    return read_status(c);
+}
+
+int pamd_get_counters(pamd_ctx* c, uint32_t* step, uint32_t* ridx, double* sum_lnQ) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (step) *step = c->step;
+    if (ridx) *ridx = c->resample_index;
+    if (sum_lnQ) {
+        PAMD_CU(c, cudaMemcpyAsync(sum_lnQ, &c->b.scal->sum_lnQ, 8, cudaMemcpyDeviceToHost, c->stream));
+        PAMD_CU(c, cudaStreamSynchronize(c->stream));
+    }
+    return PAMD_OK;
+}
+
+int pamd_set_counters(pamd_ctx* c, uint32_t step, uint32_t ridx, double sum_lnQ) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (!std::isfinite(sum_lnQ)) return fail(PAMD_EINVAL, "sum_lnQ must be finite");
+    c->step = step;
+    c->resample_index = ridx;
+    PAMD_CU(c, cudaMemcpyAsync(&c->b.scal->sum_lnQ, &sum_lnQ, 8, cudaMemcpyHostToDevice, c->stream));
+    PAMD_CU(c, cudaStreamSynchronize(c->stream));
+    return PAMD_OK;
+}
+
+int pamd_info(pamd_ctx* c, int64_t* R, int32_t* n_atoms, int32_t* lanes, int32_t* per_lane, int32_t* rpb) {
+    if (!c) return fail(PAMD_EINVAL, "null context");
+    if (R) *R = c->R;
+    if (n_atoms) *n_atoms = c->N;
+    if (lanes) *lanes = c->lay.lanes;
+    if (per_lane) *per_lane = c->lay.per_lane;
+    if (rpb) *rpb = c->rpb;
+    return PAMD_OK;
+}
+
+int64_t pamd_launch_count(pamd_ctx* c) { return c ? c->launches : -1; }
+
+int pamd_sync(pamd_ctx* c) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    PAMD_CU(c, cudaStreamSynchronize(c->stream));
+    return PAMD_OK;
+}
+
+void pamd_destroy(pamd_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    free_all(c);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+}  // extern "C"

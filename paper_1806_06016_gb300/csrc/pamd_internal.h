@@ -1,0 +1,171 @@
+// pamd_internal.h -- definitions shared by libpamd's translation units
+// (host context, kernel parameter blocks, launcher entry points).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pamd.h"
+
+namespace pamd {
+
+constexpr double kBoltzmann = 0.008314462618;  // kJ/mol/K
+constexpr double kCoulomb = 138.935458;        // kJ mol^-1 nm e^-2
+constexpr int kNumBins = 64;                   // family bins for jackknife errors
+constexpr uint32_t kPurposeNoise = 0u, kPurposeInit = 1u, kPurposeResample = 2u;
+constexpr int kMaxColors = 64;                 // colour classes per bonded term type
+
+// Bonded terms as laid out in the topology blob (16-byte aligned records).
+struct BondRec { int32_t i, j; float r0, k; };
+struct AngleRec { int32_t i, j, k, pad; float t0, kk, pad1, pad2; };
+struct DihRec { int32_t i, j, k, l; float kd, n, cos_ph, sin_ph; };
+struct Pair14Rec { int32_t i, j; float s_lj, s_c; };
+
+// Byte layout of the per-molecule table the propagate kernel copies to
+// shared memory once per CTA.  All offsets are multiples of 16.
+struct TopoLayout {
+    int n_atoms, n_pad;        // N and Np = round_up(N, 4) (global state stride)
+    int lanes, per_lane;       // L lanes per replica, B atoms per lane
+    int block_stride;          // B rounded up to odd (smem atoms per lane block)
+    int nk;                    // L * block_stride smem atom slots
+    int off_params;            // float4 [nk]: {sigma/2, sqrt(24 eps), q sqrt(k_e), 1/m}
+    int off_masks;             // uint64 [(L/2+1) * L]: excluded pairs per tile
+    int off_bonds, n_bonds;
+    int off_angles, n_angles;
+    int off_dihs, n_dihs;
+    int off_p14, n_p14;
+    int off_colors;            // int32 [4][kMaxColors+1] colour start offsets
+    int n_colors[4];           // bonds, angles, dihedrals, 1-4 pairs
+    int bytes;                 // total, multiple of 16
+};
+
+struct PropParams {
+    const float* state_in;     // [R][6][Np]
+    float* state_out;          // may equal state_in
+    double* E;                 // [R]
+    double* ke;                // [R]
+    double* rg;                // [R]
+    float* fout;               // [R][3][Np] or null (force dump)
+    const float* masses;       // [Np] (0 for padding)
+    const unsigned char* topo; // TopoLayout.bytes
+    int* status;               // [2]: code, replica
+    const uint32_t* dev_counters;  // null, or {step, resample index} base
+    TopoLayout lay;
+    long long R;
+    int theta;
+    float hdt;                 // dt / 2
+    float c1;                  // exp(-gamma dt)
+    float c2kT;                // sqrt((1 - c1^2) k_B T)
+    unsigned long long seed;
+    uint32_t step0;            // added to dev_counters[0] (or absolute when null)
+    uint32_t purpose_mol;      // mol << 8
+};
+
+struct DevScalars {
+    double m;                  // max a_j
+    double S;                  // sum exp(a_j - m)
+    double lnQ;
+    double sum_lnQ;
+    unsigned long long C_total;
+    int max_copies;
+    int status;                // PAMD status code set by kernels (0 = ok)
+    int bad_replica;
+    int pad_;
+};
+
+struct Buffers {
+    float* state = nullptr;
+    float* state_alt = nullptr;
+    double* E = nullptr;
+    double* E_alt = nullptr;
+    int32_t* fam = nullptr;
+    int32_t* fam_alt = nullptr;
+    double* ke = nullptr;
+    double* rg = nullptr;
+    float* masses = nullptr;
+    unsigned char* topo = nullptr;
+    float* x0 = nullptr;          // [3][Np] recentred start geometry
+    // resampling scratch
+    unsigned long long* W = nullptr;
+    unsigned long long* C = nullptr;
+    int32_t* cnt = nullptr;
+    int32_t* cnt_incl = nullptr;
+    unsigned long long* blk_u64 = nullptr;
+    double* blk_f64 = nullptr;
+    int32_t* blk_i32 = nullptr;
+    unsigned char* flags = nullptr;
+    double* obs_part = nullptr;
+    DevScalars* scal = nullptr;
+    uint32_t* counters = nullptr;
+    pamd_obs* obs = nullptr;      // [obs_cap]
+    float* fout = nullptr;        // [R][3][Np] allocated on demand
+};
+
+struct GraphKey {
+    int K = -1, theta = -1, resample = -1;
+    double dt = 0;
+    std::vector<double> T;
+    bool operator==(const GraphKey& o) const {
+        return K == o.K && theta == o.theta && resample == o.resample && dt == o.dt && T == o.T;
+    }
+};
+
+}  // namespace pamd
+
+struct pamd_ctx {
+    long long R = 0;
+    int N = 0, Np = 0;
+    pamd::TopoLayout lay{};
+    int warps_per_block = 4;
+    int rpb = 0;               // replicas per block
+    int grid_prop = 0;         // persistent grid size for propagate
+    int num_sms = 0;
+    int precision = PAMD_PREC_MIXED;
+    double gamma = 1.0;
+    unsigned long long seed = 0;
+    int mol = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    void* (*dev_alloc)(size_t, void*) = nullptr;
+    void (*dev_free)(void*, void*) = nullptr;
+    void* alloc_user = nullptr;
+    pamd::Buffers b;
+    std::vector<void*> allocations;
+    int n_blk = 0;             // blocks of the 1024-element scans
+    int obs_cap = 0;
+    uint32_t step = 0;
+    uint32_t resample_index = 0;
+    long long launches = 0;
+    long long graph_kernels = 0;  // kernel launches inside the cached anneal graph
+    bool broken = false;
+    cudaGraphExec_t graph_exec = nullptr;
+    pamd::GraphKey graph_key;
+    bool cur_is_alt = false;   // population currently in state_alt
+    std::vector<double> host_mass;
+};
+
+namespace pamd {
+
+// propagate kernels (one translation unit per lane count).  With p == null
+// they only report how many blocks of that shape fit on one SM.
+cudaError_t propagate_l4(const PropParams* p, int per_lane, int warps, int grid, size_t smem,
+                         cudaStream_t s, int* blocks_per_sm);
+cudaError_t propagate_l8(const PropParams* p, int per_lane, int warps, int grid, size_t smem,
+                         cudaStream_t s, int* blocks_per_sm);
+cudaError_t propagate_l16(const PropParams* p, int per_lane, int warps, int grid, size_t smem,
+                          cudaStream_t s, int* blocks_per_sm);
+cudaError_t propagate_l32(const PropParams* p, int per_lane, int warps, int grid, size_t smem,
+                          cudaStream_t s, int* blocks_per_sm);
+
+// resampling / observables / init kernels (resample.cu)
+cudaError_t launch_init(pamd_ctx* c, double T0);
+cudaError_t launch_resample(pamd_ctx* c, double T_prev, double T_next, int do_resample,
+                            const uint32_t* dev_counters, uint32_t resample_offset);
+cudaError_t launch_observe(pamd_ctx* c, double T, pamd_obs* dst);
+cudaError_t launch_set_counters(pamd_ctx* c, uint32_t step, uint32_t ridx);
+
+
+}  // namespace pamd

@@ -1,0 +1,671 @@
+// resample.cu -- population set-up, resampling, gather and observables.
+//
+// PAMD scheme, step 1 (init), step 2 (resampling with relative Boltzmann
+// weights, velocity rescaling) and step 4 (population averages with
+// family-binned errors).  Everything here is O(R) work between the
+// propagate launches; the gather is the one HBM-bound kernel.
+#include <math.h>
+
+#include "pamd_device.cuh"
+#include "pamd_internal.h"
+
+namespace pamd {
+
+constexpr int kScanBlock = 1024;  // elements per scan block (256 threads x 4)
+constexpr int kScanThreads = 256;
+
+// ------------------------------------------------------------------ helpers
+
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const T n = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += n;
+    }
+    return v;
+}
+
+// Inclusive scan of the 4 values held by each of the 256 threads (1024
+// consecutive elements); returns the block total.
+template <typename T>
+__device__ __forceinline__ T block_scan4(T (&v)[4], T* sh /* [8] */) {
+    v[1] += v[0];
+    v[2] += v[1];
+    v[3] += v[2];
+    const T tsum = v[3];
+    const T incl = warp_incl_scan(tsum);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 31) sh[w] = incl;
+    __syncthreads();
+    T wpre = 0, total = 0;
+#pragma unroll
+    for (int i = 0; i < kScanThreads / 32; ++i) {
+        if (i < w) wpre += sh[i];
+        total += sh[i];
+    }
+    const T pre = wpre + incl - tsum;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] += pre;
+    __syncthreads();
+    return total;
+}
+
+__device__ __forceinline__ double block_max_d(double v, double* sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double m = -INFINITY;
+    for (int i = 0; i < nw; ++i) m = fmax(m, sh[i]);
+    __syncthreads();
+    return m;
+}
+
+// Sum in a fixed tree order (deterministic for a given launch shape).
+__device__ __forceinline__ double block_sum_d(double v, double* sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int i = 0; i < nw; ++i) s += sh[i];
+    __syncthreads();
+    return s;
+}
+
+// ------------------------------------------------------------------ init
+
+// Step 1: x = recentred start geometry, v ~ Maxwell-Boltzmann(T0) from
+// Philox(seed; atom, slot, 0, INIT | mol << 8), family = slot.
+__global__ void init_kernel(float* state, double* E, int32_t* fam, const float* x0,
+                            const float* masses, long long R, int N, int Np, float kT0,
+                            unsigned long long seed, uint32_t purpose) {
+    const long long total = R * (long long)Np;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long k = t / Np;
+        const int i = (int)(t - k * Np);
+        float* st = state + (size_t)k * 6 * Np;
+        if (i < N) {
+            const float3 z = normal3(seed, (uint32_t)i, (uint32_t)k, 0u, purpose);
+            const float sdv = sqrtf(kT0 / masses[i]);
+            st[i] = x0[i];
+            st[Np + i] = x0[Np + i];
+            st[2 * Np + i] = x0[2 * Np + i];
+            st[3 * Np + i] = sdv * z.x;
+            st[4 * Np + i] = sdv * z.y;
+            st[5 * Np + i] = sdv * z.z;
+        } else {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) st[c * Np + i] = 0.0f;
+        }
+        if (i == 0) {
+            fam[k] = (int32_t)k;
+            E[k] = 0.0;
+        }
+    }
+}
+
+__global__ void reset_scalars_kernel(DevScalars* s) {
+    s->m = 0.0;
+    s->S = 0.0;
+    s->lnQ = 0.0;
+    s->sum_lnQ = 0.0;
+    s->C_total = 0ull;
+    s->max_copies = 1;
+    s->status = 0;
+    s->bad_replica = -1;
+}
+
+__global__ void set_counters_kernel(uint32_t* ctr, uint32_t step, uint32_t ridx) {
+    ctr[0] = step;
+    ctr[1] = ridx;
+}
+
+// ------------------------------------------------------------------ weights
+
+// a_j = -(beta_next - beta_prev) E_j ; block maxima.
+__global__ void amax_kernel(const double* E, long long R, double dbeta, double* blk_max) {
+    __shared__ double sh[32];
+    const long long base = (long long)blockIdx.x * kScanBlock;
+    double m = -INFINITY;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const long long j = base + threadIdx.x * 4 + q;
+        if (j < R && isfinite(E[j])) m = fmax(m, __dmul_rn(-dbeta, E[j]));
+    }
+    m = block_max_d(m, sh);
+    if (threadIdx.x == 0) blk_max[blockIdx.x] = m;
+}
+
+__global__ void max_top_kernel(const double* blk_max, int nblk, DevScalars* s) {
+    __shared__ double sh[32];
+    double m = -INFINITY;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) m = fmax(m, blk_max[b]);
+    m = block_max_d(m, sh);
+    if (threadIdx.x == 0) s->m = m;
+}
+
+// W_j = floor(2^s exp_det(a_j - m)); block sums of W (exact) and of the
+// exponentials (for Q).
+__global__ void weights_kernel(const double* E, long long R, double dbeta, double two_s,
+                               DevScalars* s, ExpCoef cf, unsigned long long* W,
+                               unsigned long long* blk_w, double* blk_e) {
+    __shared__ double sh[32];
+    __shared__ unsigned long long shw[8];
+    const long long base = (long long)blockIdx.x * kScanBlock;
+    const double m = s->m;
+    unsigned long long w[4];
+    double es = 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const long long j = base + threadIdx.x * 4 + q;
+        w[q] = 0ull;
+        if (j < R) {
+            const double Ej = E[j];
+            double e = 0.0;
+            if (isfinite(Ej)) {
+                const double a = __dmul_rn(-dbeta, Ej);
+                e = exp_det(__dsub_rn(a, m), cf);
+                w[q] = __double2ull_rz(__dmul_rn(two_s, e));
+            } else if (atomicCAS(&s->status, 0, PAMD_ENONFINITE) == 0) {
+                s->bad_replica = (int)j;  // a non-finite energy gets weight 0
+            }
+            W[j] = w[q];
+            es += e;
+        }
+    }
+    const double bs = block_sum_d(es, sh);
+    const unsigned long long tot = block_scan4(w, shw);
+    if (threadIdx.x == 0) {
+        blk_w[blockIdx.x] = tot;
+        blk_e[blockIdx.x] = bs;
+    }
+}
+
+// Exclusive scan of the block sums of W (in place), C_total, ln Q.
+__global__ void weights_top_kernel(unsigned long long* blk_w, const double* blk_e, int nblk,
+                                   long long R, DevScalars* s) {
+    __shared__ unsigned long long shw[8];
+    __shared__ unsigned long long carry;
+    if (threadIdx.x == 0) carry = 0ull;
+    __syncthreads();
+    for (int b0 = 0; b0 < nblk; b0 += kScanBlock) {
+        unsigned long long v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int b = b0 + threadIdx.x * 4 + q;
+            v[q] = (b < nblk) ? blk_w[b] : 0ull;
+        }
+        unsigned long long orig[4] = {v[0], v[1], v[2], v[3]};
+        const unsigned long long tot = block_scan4(v, shw);
+        const unsigned long long c = carry;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int b = b0 + threadIdx.x * 4 + q;
+            if (b < nblk) blk_w[b] = c + v[q] - orig[q];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) carry = c + tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double S = 0.0;
+        for (int b = 0; b < nblk; ++b) S += blk_e[b];
+        s->S = S;
+        s->C_total = carry;
+        const double lnq = s->m + (log(S) - log((double)R));
+        s->lnQ = lnq;
+        s->sum_lnQ += lnq;
+    }
+}
+
+// C_j = block offset + inclusive scan of W inside the block.
+__global__ void scan_local_u64_kernel(unsigned long long* W, long long R,
+                                      const unsigned long long* blk_off, unsigned long long* C) {
+    __shared__ unsigned long long shw[8];
+    const long long base = (long long)blockIdx.x * kScanBlock;
+    unsigned long long v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const long long j = base + threadIdx.x * 4 + q;
+        v[q] = (j < R) ? W[j] : 0ull;
+    }
+    block_scan4(v, shw);
+    const unsigned long long off = blk_off[blockIdx.x];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const long long j = base + threadIdx.x * 4 + q;
+        if (j < R) C[j] = off + v[q];
+    }
+}
+
+// ------------------------------------------------------------------ counts
+
+// Draw k: u_k from Philox(seed; k, resampling index, 0, RESAMPLE | mol << 8),
+// target t = floor(u_k C_total / 2^64), ancestor = first j with C_j > t.
+__global__ void counts_kernel(const unsigned long long* C, long long R, const DevScalars* s,
+                              unsigned long long seed, const uint32_t* dev_counters,
+                              uint32_t ridx_off, uint32_t purpose, int do_resample,
+                              int32_t* cnt) {
+    const uint32_t ridx = (dev_counters ? dev_counters[1] : 0u) + ridx_off;
+    const unsigned long long total = s->C_total;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < R;
+         k += (long long)gridDim.x * blockDim.x) {
+        if (!do_resample) {
+            cnt[k] = 1;
+            continue;
+        }
+        const uint4 o = philox4x32_10(make_uint4((uint32_t)k, ridx, 0u, purpose), seed_key(seed));
+        const unsigned long long u = (unsigned long long)o.x | ((unsigned long long)o.y << 32);
+        const unsigned long long t = __umul64hi(u, total);
+        long long lo = 0, hi = R;
+        while (lo < hi) {
+            const long long mid = lo + ((hi - lo) >> 1);
+            if (C[mid] > t) hi = mid;
+            else lo = mid + 1;
+        }
+        // t < C_total whenever C_total > 0, so lo < R; the clamp only guards
+        // a population whose weights are all zero (all energies non-finite)
+        atomicAdd(&cnt[lo < R ? lo : R - 1], 1);
+    }
+}
+
+__global__ void cnt_block_kernel(const int32_t* cnt, long long R, int32_t* blk_sum,
+                                 int32_t* blk_max) {
+    __shared__ int32_t shs[8];
+    __shared__ int32_t shm[8];
+    const long long base = (long long)blockIdx.x * kScanBlock;
+    int32_t v[4], mx = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const long long j = base + threadIdx.x * 4 + q;
+        v[q] = (j < R) ? cnt[j] : 0;
+        mx = max(mx, v[q]);
+    }
+    const int32_t tot = block_scan4(v, shs);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t m = 0;
+        for (int i = 0; i < kScanThreads / 32; ++i) m = max(m, shm[i]);
+        blk_sum[blockIdx.x] = tot;
+        blk_max[blockIdx.x] = m;
+    }
+}
+
+__global__ void cnt_top_kernel(int32_t* blk_sum, const int32_t* blk_max, int nblk, DevScalars* s) {
+    __shared__ int32_t shs[8];
+    __shared__ int32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nblk; b0 += kScanBlock) {
+        int32_t v[4], orig[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int b = b0 + threadIdx.x * 4 + q;
+            v[q] = orig[q] = (b < nblk) ? blk_sum[b] : 0;
+        }
+        const int32_t tot = block_scan4(v, shs);
+        const int32_t c = carry;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int b = b0 + threadIdx.x * 4 + q;
+            if (b < nblk) blk_sum[b] = c + v[q] - orig[q];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) carry = c + tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        int32_t m = 0;
+        for (int b = 0; b < nblk; ++b) m = max(m, blk_max[b]);
+        s->max_copies = m;
+    }
+}
+
+__global__ void cnt_local_kernel(const int32_t* cnt, long long R, const int32_t* blk_off,
+                                 int32_t* incl) {
+    __shared__ int32_t shs[8];
+    const long long base = (long long)blockIdx.x * kScanBlock;
+    int32_t v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const long long j = base + threadIdx.x * 4 + q;
+        v[q] = (j < R) ? cnt[j] : 0;
+    }
+    block_scan4(v, shs);
+    const int32_t off = blk_off[blockIdx.x];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const long long j = base + threadIdx.x * 4 + q;
+        if (j < R) incl[j] = off + v[q];
+    }
+}
+
+// ------------------------------------------------------------------ gather
+
+// One warp per new slot k: ancestor j = first index with incl_j > k; the
+// replica's state (6 Np floats, Np % 4 == 0) is moved as float4s.  Positions
+// are shifted to the centre of mass, velocities scaled by vscale, and the new
+// replica's kinetic energy and radius of gyration are recomputed from the
+// moved state.
+__global__ void gather_kernel(const float* __restrict__ st_in, float* __restrict__ st_out,
+                              const double* E_in, double* E_out, const int32_t* fam_in,
+                              int32_t* fam_out, double* ke_out, double* rg_out,
+                              const int32_t* incl, const float* masses, long long R, int N,
+                              int Np, float vscale, float inv_mtot) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int q4 = Np / 4;          // float4s per component
+    const int nq = 6 * q4;          // float4s per replica
+    for (long long k = warp; k < R; k += nwarps) {
+        long long lo = 0, hi = R;
+        while (lo < hi) {
+            const long long mid = lo + ((hi - lo) >> 1);
+            if (incl[mid] > k) hi = mid;
+            else lo = mid + 1;
+        }
+        const long long j = lo < R ? lo : R - 1;
+        const float4* src = reinterpret_cast<const float4*>(st_in + (size_t)j * 6 * Np);
+        float4* dst = reinterpret_cast<float4*>(st_out + (size_t)k * 6 * Np);
+        constexpr int kMaxPer = 12;  // float4s per lane: 6 Np / 4 <= 384 for Np <= 256
+        float4 v[kMaxPer];
+        float sx = 0.f, sy = 0.f, sz = 0.f;
+#pragma unroll
+        for (int r = 0; r < kMaxPer; ++r) {
+            const int q = lane + 32 * r;
+            if (q < nq) {
+                v[r] = src[q];
+                const int comp = q / q4;
+                if (comp < 3) {
+                    const float4 m = reinterpret_cast<const float4*>(masses)[q - comp * q4];
+                    const float s = m.x * v[r].x + m.y * v[r].y + m.z * v[r].z + m.w * v[r].w;
+                    if (comp == 0) sx += s;
+                    else if (comp == 1) sy += s;
+                    else sz += s;
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            sy += __shfl_xor_sync(0xffffffffu, sy, o);
+            sz += __shfl_xor_sync(0xffffffffu, sz, o);
+        }
+        const float cx = sx * inv_mtot, cy = sy * inv_mtot, cz = sz * inv_mtot;
+        double mv2 = 0.0, ux = 0.0, uy = 0.0, uz = 0.0, u2 = 0.0;
+#pragma unroll
+        for (int r = 0; r < kMaxPer; ++r) {
+            const int q = lane + 32 * r;
+            if (q < nq) {
+                const int comp = q / q4;
+                const int i0 = (q - comp * q4) * 4;
+                float4 w = v[r];
+                if (comp < 3) {
+                    const float c = (comp == 0) ? cx : (comp == 1) ? cy : cz;
+                    w.x -= c; w.y -= c; w.z -= c; w.w -= c;
+                    const float e[4] = {w.x, w.y, w.z, w.w};
+                    double s1 = 0.0;
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        if (i0 + t < N) {
+                            s1 += e[t];
+                            u2 += (double)e[t] * e[t];
+                        }
+                    }
+                    if (comp == 0) ux += s1;
+                    else if (comp == 1) uy += s1;
+                    else uz += s1;
+                } else {
+                    w.x *= vscale; w.y *= vscale; w.z *= vscale; w.w *= vscale;
+                    const float4 m = reinterpret_cast<const float4*>(masses)[q - comp * q4];
+                    mv2 += (double)m.x * w.x * w.x + (double)m.y * w.y * w.y +
+                           (double)m.z * w.z * w.z + (double)m.w * w.w * w.w;
+                }
+                dst[q] = w;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mv2 += __shfl_xor_sync(0xffffffffu, mv2, o);
+            ux += __shfl_xor_sync(0xffffffffu, ux, o);
+            uy += __shfl_xor_sync(0xffffffffu, uy, o);
+            uz += __shfl_xor_sync(0xffffffffu, uz, o);
+            u2 += __shfl_xor_sync(0xffffffffu, u2, o);
+        }
+        if (lane == 0) {
+            E_out[k] = E_in[j];
+            fam_out[k] = fam_in[j];
+            ke_out[k] = 0.5 * mv2;
+            const double mx = ux / N, my = uy / N, mz = uz / N;
+            const double r2 = u2 / N - (mx * mx + my * my + mz * mz);
+            rg_out[k] = sqrt(fmax(r2, 0.0));
+        }
+    }
+}
+
+// ------------------------------------------------------------------ observables
+
+__global__ void mark_kernel(const int32_t* fam, long long R, unsigned char* flags) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < R;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int32_t f = fam[k];
+        if (f >= 0 && f < R) flags[f] = 1;
+    }
+}
+
+constexpr int kObsVals = 5;  // count, E, E_kin, R_g, R_g^2
+constexpr int kObsStride = kNumBins * kObsVals + 1;
+
+// Partial sums per family bin over 1024 replicas, in replica order per bin.
+__global__ void obs_partial_kernel(const int32_t* fam, const double* E, const double* ke,
+                                   const double* rg, const unsigned char* flags, long long R,
+                                   double* part) {
+    __shared__ int32_t sf[kScanBlock];
+    __shared__ double se[kScanBlock], sk[kScanBlock], sr[kScanBlock];
+    __shared__ int32_t famcount[kScanThreads / 32];
+    const long long base = (long long)blockIdx.x * kScanBlock;
+    int fc = 0;
+    for (int t = threadIdx.x; t < kScanBlock; t += blockDim.x) {
+        const long long k = base + t;
+        if (k < R) {
+            sf[t] = fam[k] & (kNumBins - 1);
+            se[t] = E[k];
+            sk[t] = ke[k];
+            sr[t] = rg[k];
+            fc += flags[k];
+        } else {
+            sf[t] = -1;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) fc += __shfl_xor_sync(0xffffffffu, fc, o);
+    if ((threadIdx.x & 31) == 0) famcount[threadIdx.x >> 5] = fc;
+    __syncthreads();
+    double* out = part + (size_t)blockIdx.x * kObsStride;
+    if (threadIdx.x < kNumBins) {
+        const int b = threadIdx.x;
+        double c = 0, e = 0, k2 = 0, r = 0, r2 = 0;
+        for (int t = 0; t < kScanBlock; ++t) {
+            if (sf[t] == b) {
+                c += 1.0;
+                e += se[t];
+                k2 += sk[t];
+                r += sr[t];
+                r2 += sr[t] * sr[t];
+            }
+        }
+        out[b * kObsVals + 0] = c;
+        out[b * kObsVals + 1] = e;
+        out[b * kObsVals + 2] = k2;
+        out[b * kObsVals + 3] = r;
+        out[b * kObsVals + 4] = r2;
+    }
+    if (threadIdx.x == 0) {
+        int s = 0;
+        for (int i = 0; i < kScanThreads / 32; ++i) s += famcount[i];
+        out[kNumBins * kObsVals] = (double)s;
+    }
+}
+
+__device__ double jackknife_se(const double* cnt, const double* sum, double tot, double R) {
+    double jk[kNumBins];
+    int nb = 0;
+    for (int b = 0; b < kNumBins; ++b) {
+        if (cnt[b] == 0.0 || cnt[b] == R) continue;
+        jk[nb++] = (tot - sum[b]) / (R - cnt[b]);
+    }
+    if (nb < 2) return 0.0;
+    double jm = 0.0;
+    for (int b = 0; b < nb; ++b) jm += jk[b];
+    jm /= nb;
+    double ss = 0.0;
+    for (int b = 0; b < nb; ++b) ss += (jk[b] - jm) * (jk[b] - jm);
+    return sqrt((double)(nb - 1) / nb * ss);
+}
+
+__global__ void obs_final_kernel(const double* part, int nblk, long long R, int N, double T,
+                                 const DevScalars* s, pamd_obs* dst) {
+    __shared__ double bins[kObsVals][kNumBins];
+    __shared__ double nfam;
+    if (threadIdx.x < kNumBins) {
+        const int b = threadIdx.x;
+        double acc[kObsVals] = {0, 0, 0, 0, 0};
+        for (int blk = 0; blk < nblk; ++blk)
+            for (int v = 0; v < kObsVals; ++v) acc[v] += part[(size_t)blk * kObsStride + b * kObsVals + v];
+        for (int v = 0; v < kObsVals; ++v) bins[v][b] = acc[v];
+    }
+    if (threadIdx.x == kNumBins) {
+        double f = 0;
+        for (int blk = 0; blk < nblk; ++blk) f += part[(size_t)blk * kObsStride + kNumBins * kObsVals];
+        nfam = f;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double Rd = (double)R;
+        double tot[kObsVals];
+        for (int v = 1; v < kObsVals; ++v) {
+            double t = 0;
+            for (int b = 0; b < kNumBins; ++b) t += bins[v][b];
+            tot[v] = t;
+        }
+        pamd_obs o;
+        o.T = T;
+        o.lnQ = s->lnQ;
+        o.sum_lnQ = s->sum_lnQ;
+        o.e_pot = tot[1] / Rd;
+        o.e_pot_se = jackknife_se(bins[0], bins[1], tot[1], Rd);
+        o.e_kin = tot[2] / Rd;
+        o.e_kin_se = jackknife_se(bins[0], bins[2], tot[2], Rd);
+        o.t_meas = 2.0 * o.e_kin / (3.0 * N * kBoltzmann);
+        o.rg = tot[3] / Rd;
+        o.rg_se = jackknife_se(bins[0], bins[3], tot[3], Rd);
+        o.rg2 = tot[4] / Rd;
+        o.rg2_se = jackknife_se(bins[0], bins[4], tot[4], Rd);
+        o.n_families = (int64_t)nfam;
+        o.max_copies = s->max_copies;
+        o.pad_ = s->status;
+        *dst = o;
+    }
+}
+
+// ------------------------------------------------------------------ host side
+
+static int grid_for(long long n, int threads, int cap) {
+    long long b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+cudaError_t launch_init(pamd_ctx* c, double T0) {
+    const long long total = c->R * c->Np;
+    init_kernel<<<grid_for(total, 256, c->num_sms * 16), 256, 0, c->stream>>>(
+        c->b.state, c->b.E, c->b.fam, c->b.x0, c->b.masses, c->R, c->N, c->Np,
+        (float)(kBoltzmann * T0), c->seed, kPurposeInit | ((uint32_t)c->mol << 8));
+    reset_scalars_kernel<<<1, 1, 0, c->stream>>>(c->b.scal);
+    c->launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_counters(pamd_ctx* c, uint32_t step, uint32_t ridx) {
+    set_counters_kernel<<<1, 1, 0, c->stream>>>(c->b.counters, step, ridx);
+    c->launches += 1;
+    return cudaGetLastError();
+}
+
+static ExpCoef exp_coefficients() {
+    ExpCoef cf;
+    double f = 1.0;
+    for (int n = 0; n < 14; ++n) {
+        if (n > 0) f *= (double)n;
+        cf.c[n] = 1.0 / f;
+    }
+    return cf;
+}
+
+cudaError_t launch_resample(pamd_ctx* c, double T_prev, double T_next, int do_resample,
+                            const uint32_t* dev_counters, uint32_t resample_offset) {
+    const long long R = c->R;
+    const int nblk = c->n_blk;
+    cudaStream_t s = c->stream;
+    const double dbeta = 1.0 / (kBoltzmann * T_next) - 1.0 / (kBoltzmann * T_prev);
+    int bits = 0;
+    while ((1LL << bits) < R) ++bits;
+    const double two_s = ldexp(1.0, 63 - bits);
+    static const ExpCoef cf = exp_coefficients();
+
+    amax_kernel<<<nblk, kScanThreads, 0, s>>>(c->b.E, R, dbeta, c->b.blk_f64);
+    max_top_kernel<<<1, 1024, 0, s>>>(c->b.blk_f64, nblk, c->b.scal);
+    weights_kernel<<<nblk, kScanThreads, 0, s>>>(c->b.E, R, dbeta, two_s, c->b.scal, cf, c->b.W,
+                                                 c->b.blk_u64, c->b.blk_f64);
+    weights_top_kernel<<<1, kScanThreads, 0, s>>>(c->b.blk_u64, c->b.blk_f64, nblk, R, c->b.scal);
+    scan_local_u64_kernel<<<nblk, kScanThreads, 0, s>>>(c->b.W, R, c->b.blk_u64, c->b.C);
+    cudaError_t e = cudaMemsetAsync(c->b.cnt, 0, sizeof(int32_t) * (size_t)R, s);
+    if (e != cudaSuccess) return e;
+    counts_kernel<<<grid_for(R, 256, c->num_sms * 16), 256, 0, s>>>(
+        c->b.C, R, c->b.scal, c->seed, dev_counters, resample_offset,
+        kPurposeResample | ((uint32_t)c->mol << 8), do_resample, c->b.cnt);
+    cnt_block_kernel<<<nblk, kScanThreads, 0, s>>>(c->b.cnt, R, c->b.blk_i32, c->b.blk_i32 + nblk);
+    cnt_top_kernel<<<1, kScanThreads, 0, s>>>(c->b.blk_i32, c->b.blk_i32 + nblk, nblk, c->b.scal);
+    cnt_local_kernel<<<nblk, kScanThreads, 0, s>>>(c->b.cnt, R, c->b.blk_i32, c->b.cnt_incl);
+    double mt = 0.0;
+    for (double m : c->host_mass) mt += m;
+    const float* src = c->cur_is_alt ? c->b.state_alt : c->b.state;
+    float* dst = c->cur_is_alt ? c->b.state : c->b.state_alt;
+    const double* Ein = c->cur_is_alt ? c->b.E_alt : c->b.E;
+    double* Eout = c->cur_is_alt ? c->b.E : c->b.E_alt;
+    const int32_t* fin = c->cur_is_alt ? c->b.fam_alt : c->b.fam;
+    int32_t* fout = c->cur_is_alt ? c->b.fam : c->b.fam_alt;
+    const long long warps_needed = R;
+    gather_kernel<<<grid_for(warps_needed * 32, 256, c->num_sms * 32), 256, 0, s>>>(
+        src, dst, Ein, Eout, fin, fout, c->b.ke, c->b.rg, c->b.cnt_incl, c->b.masses, R, c->N,
+        c->Np, (float)sqrt(T_next / T_prev), (float)(1.0 / mt));
+    c->launches += 10;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_observe(pamd_ctx* c, double T, pamd_obs* dst) {
+    cudaStream_t s = c->stream;
+    const long long R = c->R;
+    const int32_t* fam = c->cur_is_alt ? c->b.fam_alt : c->b.fam;
+    const double* E = c->cur_is_alt ? c->b.E_alt : c->b.E;
+    cudaError_t e = cudaMemsetAsync(c->b.flags, 0, (size_t)R, s);
+    if (e != cudaSuccess) return e;
+    mark_kernel<<<grid_for(R, 256, c->num_sms * 16), 256, 0, s>>>(fam, R, c->b.flags);
+    obs_partial_kernel<<<c->n_blk, kScanThreads, 0, s>>>(fam, E, c->b.ke, c->b.rg, c->b.flags, R,
+                                                        c->b.obs_part);
+    obs_final_kernel<<<1, 128, 0, s>>>(c->b.obs_part, c->n_blk, R, c->N, T, c->b.scal, dst);
+    c->launches += 3;
+    return cudaGetLastError();
+}
+
+}  // namespace pamd

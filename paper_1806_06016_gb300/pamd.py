@@ -1,0 +1,360 @@
+"""ctypes binding of libpamd (include/pamd.h), one Python function per C entry point.
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  If the library is missing the functions raise ``RuntimeError``;
+there is no CPU fallback.  Device memory and the CUDA stream can come from
+PyTorch (``torch_options``); PyTorch is not otherwise used.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libpamd.so")
+
+PAMD_OK = 0
+PAMD_EINVAL, PAMD_ENOMEM, PAMD_ECUDA, PAMD_ETIMEOUT = -1, -2, -3, -4
+PAMD_ENONFINITE, PAMD_ESTATE, PAMD_EUNSUPPORTED = -5, -6, -7
+PAMD_PREC_MIXED, PAMD_PREC_FP64 = 0, 1
+PAMD_MAX_ATOMS = 256
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class PamdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"pamd error {code}: {msg}")
+        self.code = code
+
+
+class PamdTopology(C.Structure):
+    _fields_ = [
+        ("n_atoms", C.c_int32),
+        ("mass", C.c_void_p), ("charge", C.c_void_p), ("sigma", C.c_void_p),
+        ("epsilon", C.c_void_p), ("x0", C.c_void_p),
+        ("n_bonds", C.c_int32), ("bond", C.c_void_p), ("bond_r0", C.c_void_p), ("bond_k", C.c_void_p),
+        ("n_angles", C.c_int32), ("angle", C.c_void_p), ("angle_t0", C.c_void_p), ("angle_k", C.c_void_p),
+        ("n_dihedrals", C.c_int32), ("dihedral", C.c_void_p), ("dih_n", C.c_void_p),
+        ("dih_k", C.c_void_p), ("dih_phase", C.c_void_p),
+        ("n_excl", C.c_int32), ("excl", C.c_void_p),
+        ("n_pair14", C.c_int32), ("pair14", C.c_void_p),
+        ("scale14_lj", C.c_double), ("scale14_coul", C.c_double),
+    ]
+
+
+class PamdOptions(C.Structure):
+    _fields_ = [
+        ("gamma_per_ps", C.c_double),
+        ("precision", C.c_int32),
+        ("lanes_per_replica", C.c_int32),
+        ("warps_per_block", C.c_int32),
+        ("mol_id", C.c_int32),
+        ("dev_alloc", ALLOC_FN),
+        ("dev_free", FREE_FN),
+        ("alloc_user", C.c_void_p),
+        ("stream", C.c_void_p),
+    ]
+
+
+class PamdObs(C.Structure):
+    _fields_ = [
+        ("T", C.c_double), ("lnQ", C.c_double), ("sum_lnQ", C.c_double),
+        ("e_pot", C.c_double), ("e_pot_se", C.c_double), ("e_kin", C.c_double),
+        ("e_kin_se", C.c_double), ("t_meas", C.c_double),
+        ("rg", C.c_double), ("rg_se", C.c_double), ("rg2", C.c_double), ("rg2_se", C.c_double),
+        ("n_families", C.c_int64), ("max_copies", C.c_int32), ("pad_", C.c_int32),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
+EXPORTS = [
+    "pamd_options_default", "pamd_init", "pamd_reset", "pamd_propagate", "pamd_resample", "pamd_observables",
+    "pamd_anneal", "pamd_get_state", "pamd_set_state", "pamd_forces", "pamd_get_counters",
+    "pamd_set_counters", "pamd_info", "pamd_launch_count", "pamd_sync", "pamd_destroy",
+    "pamd_last_error",
+]
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str | None = None):
+    """Load libpamd.so (built by ``paper_1806_06016_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libpamd.so not built ({p}); run paper_1806_06016_gb300.build.build()")
+        lib = C.CDLL(p)
+        P, I32, I64, U32, U64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_uint64, C.c_double
+        sig = {
+            "pamd_options_default": (None, [C.POINTER(PamdOptions)]),
+            "pamd_init": (C.c_int, [C.POINTER(P), C.POINTER(PamdTopology), I64, D, U64,
+                                    C.POINTER(PamdOptions)]),
+            "pamd_reset": (C.c_int, [P, D, U64]),
+            "pamd_propagate": (C.c_int, [P, I32, D, D]),
+            "pamd_resample": (C.c_int, [P, D, D, P, P]),
+            "pamd_observables": (C.c_int, [P, D, C.POINTER(PamdObs)]),
+            "pamd_anneal": (C.c_int, [P, I32, P, I32, D, I32, C.POINTER(PamdObs)]),
+            "pamd_get_state": (C.c_int, [P, P, P, P, P]),
+            "pamd_set_state": (C.c_int, [P, P, P, P, P]),
+            "pamd_forces": (C.c_int, [P, P, P]),
+            "pamd_get_counters": (C.c_int, [P, C.POINTER(U32), C.POINTER(U32), C.POINTER(D)]),
+            "pamd_set_counters": (C.c_int, [P, U32, U32, D]),
+            "pamd_info": (C.c_int, [P, C.POINTER(I64), C.POINTER(I32), C.POINTER(I32),
+                                    C.POINTER(I32), C.POINTER(I32)]),
+            "pamd_launch_count": (I64, [P]),
+            "pamd_sync": (C.c_int, [P]),
+            "pamd_destroy": (None, [P]),
+            "pamd_last_error": (C.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def _check(rc):
+    if rc != PAMD_OK:
+        msg = load().pamd_last_error().decode(errors="replace")
+        raise PamdError(rc, msg)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+class _TopologyArgs:
+    """Keeps the numpy arrays behind a PamdTopology alive for the duration of a call."""
+
+    def __init__(self, top):
+        a = top.arrays()
+        self._a = a
+        self.s = PamdTopology(
+            top.n_atoms, _ptr(a["mass"]), _ptr(a["charge"]), _ptr(a["sigma"]), _ptr(a["epsilon"]),
+            _ptr(a["x0"]),
+            len(a["bond"]), _ptr(a["bond"]), _ptr(a["bond_r0"]), _ptr(a["bond_k"]),
+            len(a["angle"]), _ptr(a["angle"]), _ptr(a["angle_t0"]), _ptr(a["angle_k"]),
+            len(a["dihedral"]), _ptr(a["dihedral"]), _ptr(a["dih_n"]), _ptr(a["dih_k"]),
+            _ptr(a["dih_phase"]),
+            len(a["excl"]), _ptr(a["excl"]), len(a["pair14"]), _ptr(a["pair14"]),
+            float(top.scale14_lj), float(top.scale14_coul),
+        )
+
+
+def pamd_options_default() -> PamdOptions:
+    o = PamdOptions()
+    load().pamd_options_default(C.byref(o))
+    return o
+
+
+class _TorchAllocator:
+    """Device memory from PyTorch's caching allocator on the current device."""
+
+    def __init__(self):
+        import torch
+        self.torch = torch
+        self.device = torch.cuda.current_device()
+        self.stream = torch.cuda.current_stream()
+        self.alloc = ALLOC_FN(self._alloc)
+        self.free = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, _user):
+        try:
+            return self.torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream)
+        except Exception:  # allocation failure is reported to the library as NULL
+            return None
+
+    def _free(self, ptr, _user):
+        self.torch.cuda.caching_allocator_delete(ptr)
+
+
+_keepalive: dict[int, object] = {}
+
+
+def torch_options(gamma_per_ps: float = 1.0, **kw) -> PamdOptions:
+    """Options whose device memory and stream come from PyTorch."""
+    o = pamd_options_default()
+    o.gamma_per_ps = gamma_per_ps
+    for k, v in kw.items():
+        setattr(o, k, v)
+    al = _TorchAllocator()
+    o.dev_alloc = al.alloc
+    o.dev_free = al.free
+    o.stream = al.stream.cuda_stream
+    o._allocator = al  # keeps the callbacks alive with the options object
+    return o
+
+
+def pamd_init(top, R: int, T0: float, seed: int, options: PamdOptions | None = None):
+    lib = load()
+    ctx = C.c_void_p()
+    ta = _TopologyArgs(top)
+    opt = options if options is not None else pamd_options_default()
+    _check(lib.pamd_init(C.byref(ctx), C.byref(ta.s), int(R), float(T0), int(seed), C.byref(opt)))
+    _keepalive[ctx.value] = getattr(opt, "_allocator", None)
+    return ctx
+
+
+def pamd_reset(ctx, T0: float, seed: int) -> None:
+    _check(load().pamd_reset(ctx, float(T0), int(seed)))
+
+
+def pamd_propagate(ctx, theta: int, dt_ps: float, T: float) -> None:
+    _check(load().pamd_propagate(ctx, int(theta), float(dt_ps), float(T)))
+
+
+def pamd_resample(ctx, T_prev: float, T_next: float, want_copies: bool = True):
+    """Returns (copies[R] int32 or None, lnQ)."""
+    R = pamd_info(ctx)["R"]
+    cnt = np.zeros(R, np.int32) if want_copies else None
+    lnq = C.c_double(0.0)
+    _check(load().pamd_resample(ctx, float(T_prev), float(T_next), _ptr(cnt), C.byref(lnq)))
+    return cnt, lnq.value
+
+
+def pamd_observables(ctx, T: float) -> dict:
+    o = PamdObs()
+    _check(load().pamd_observables(ctx, float(T), C.byref(o)))
+    return o.as_dict()
+
+
+def pamd_anneal(ctx, temps, theta: int, dt_ps: float, resample: bool = True) -> list[dict]:
+    t = np.ascontiguousarray(temps, dtype=np.float64)
+    K = len(t) - 1
+    out = (PamdObs * (K + 1))()
+    _check(load().pamd_anneal(ctx, K, _ptr(t), int(theta), float(dt_ps), int(bool(resample)), out))
+    return [o.as_dict() for o in out]
+
+
+def pamd_info(ctx) -> dict:
+    R, n, L, B, rpb = C.c_int64(), C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+    _check(load().pamd_info(ctx, C.byref(R), C.byref(n), C.byref(L), C.byref(B), C.byref(rpb)))
+    return {"R": R.value, "n_atoms": n.value, "lanes_per_replica": L.value,
+            "atoms_per_lane": B.value, "replicas_per_block": rpb.value}
+
+
+def pamd_get_state(ctx, positions=True, velocities=True, energies=True, families=True):
+    """(x[R,N,3], v[R,N,3], E[R], fam[R]); parts not asked for are None."""
+    info = pamd_info(ctx)
+    R, N = info["R"], info["n_atoms"]
+    x = np.zeros((R, N, 3)) if positions else None
+    v = np.zeros((R, N, 3)) if velocities else None
+    E = np.zeros(R) if energies else None
+    fam = np.zeros(R, np.int32) if families else None
+    _check(load().pamd_get_state(ctx, _ptr(x), _ptr(v), _ptr(E), _ptr(fam)))
+    return x, v, E, fam
+
+
+def pamd_set_state(ctx, x, v, E=None, fam=None) -> None:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    E = None if E is None else np.ascontiguousarray(E, dtype=np.float64)
+    fam = None if fam is None else np.ascontiguousarray(fam, dtype=np.int32)
+    info = pamd_info(ctx)
+    shape = (info["R"], info["n_atoms"], 3)
+    if x.shape != shape or v.shape != shape:
+        raise ValueError(f"x and v must have shape {shape}")
+    _check(load().pamd_set_state(ctx, _ptr(x), _ptr(v), _ptr(E), _ptr(fam)))
+
+
+def pamd_forces(ctx):
+    """(F[R,N,3], E[R]) of the current population."""
+    info = pamd_info(ctx)
+    f = np.zeros((info["R"], info["n_atoms"], 3)); E = np.zeros(info["R"])
+    _check(load().pamd_forces(ctx, _ptr(f), _ptr(E)))
+    return f, E
+
+
+def pamd_get_counters(ctx):
+    s, r, q = C.c_uint32(), C.c_uint32(), C.c_double()
+    _check(load().pamd_get_counters(ctx, C.byref(s), C.byref(r), C.byref(q)))
+    return s.value, r.value, q.value
+
+
+def pamd_set_counters(ctx, step: int, resample_index: int, sum_lnQ: float) -> None:
+    _check(load().pamd_set_counters(ctx, int(step), int(resample_index), float(sum_lnQ)))
+
+
+def pamd_launch_count(ctx) -> int:
+    return int(load().pamd_launch_count(ctx))
+
+
+def pamd_sync(ctx) -> None:
+    _check(load().pamd_sync(ctx))
+
+
+def pamd_destroy(ctx) -> None:
+    if ctx is None or not ctx.value:
+        return
+    load().pamd_destroy(ctx)
+    _keepalive.pop(ctx.value, None)
+
+
+def pamd_last_error() -> str:
+    return load().pamd_last_error().decode(errors="replace")
+
+
+class Population:
+    """A PAMD population on the GPU (R replicas of one molecule)."""
+
+    def __init__(self, top, R: int, T0: float, seed: int, options: PamdOptions | None = None):
+        self.top = top
+        self.ctx = pamd_init(top, R, T0, seed, options)
+        self.R = R
+
+    def reset(self, T0, seed):
+        pamd_reset(self.ctx, T0, seed)
+
+    def propagate(self, theta, dt_ps, T):
+        pamd_propagate(self.ctx, theta, dt_ps, T)
+
+    def resample(self, T_prev, T_next, want_copies=True):
+        return pamd_resample(self.ctx, T_prev, T_next, want_copies)
+
+    def observables(self, T):
+        return pamd_observables(self.ctx, T)
+
+    def anneal(self, temps, theta, dt_ps, resample=True):
+        return pamd_anneal(self.ctx, temps, theta, dt_ps, resample)
+
+    def state(self):
+        return pamd_get_state(self.ctx)
+
+    def set_state(self, x, v, E=None, fam=None):
+        pamd_set_state(self.ctx, x, v, E, fam)
+
+    def forces(self):
+        return pamd_forces(self.ctx)
+
+    def info(self):
+        return pamd_info(self.ctx)
+
+    def close(self):
+        if self.ctx is not None:
+            pamd_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

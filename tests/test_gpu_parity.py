@@ -1,0 +1,360 @@
+"""GPU parity: the CUDA library (through the C-ABI) against the FP64 oracle.
+
+Tolerances (from the method's precision contract):
+  * forces: relative RMS error <= 1e-5 per replica (FP32 forces);
+  * energies: |dE| <= 1e-5 * sum of the magnitudes of the energy terms
+    (FP32 terms summed in FP64);
+  * trajectories: every position within 1e-4 nm of the oracle after each of
+    10 BAOAB steps from the same state and the same Philox stream;
+  * copy counts: bit-exact, given the same energies;
+  * ln Q: 1e-12 absolute (FP64 log-sum-exp, different summation order);
+  * population averages of an anneal: within 3 combined standard errors.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import pamd_inputs as pi
+
+pytestmark = pytest.mark.gpu
+
+KB = 0.008314462618
+
+
+@pytest.fixture(scope="module")
+def lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1806_06016_gb300 import build, pamd
+    build.build()
+    pamd.load()
+    return pamd
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def _opts(lib, **kw):
+    o = lib.pamd_options_default()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _oracle_forces(orc, top, x):
+    t = orc.Topo(top)
+    F = np.zeros_like(x)
+    E = np.zeros(x.shape[0])
+    scale = np.zeros(x.shape[0])
+    for k in range(x.shape[0]):
+        e, f, terms = orc.energy_forces(t, x[k])
+        F[k], E[k] = f, e
+        # magnitude of the individual contributions, for the energy tolerance
+        scale[k] = np.abs(terms).sum()
+    return F, E, scale
+
+
+FORCE_CASES = [(1, 0), (2, 0), (3, 0), (4, 0), (5, 0), (13, 0), (22, 0), (22, 8), (22, 16),
+               (31, 0), (33, 0), (64, 0), (75, 0), (75, 32), (129, 0), (200, 0), (256, 0)]
+
+
+@pytest.mark.parametrize("n,lanes", FORCE_CASES)
+def test_forces_and_energies(lib, orc, n, lanes):
+    top = pi.make_chain(n, 100 + n)
+    top.dih_phase = np.linspace(0.2, 1.7, len(top.dih_phase))  # exercise the torsion sign
+    R = 7
+    x = f32(pi.perturbed_positions(top, R, 0.01, n))
+    v = np.zeros_like(x)
+    ctx = lib.pamd_init(top, R, 300.0, 1, _opts(lib, lanes_per_replica=lanes))
+    try:
+        lib.pamd_set_state(ctx, x, v)
+        fg, eg = lib.pamd_forces(ctx)
+    finally:
+        lib.pamd_destroy(ctx)
+    fo, eo, scale = _oracle_forces(orc, top, x)
+    for k in range(R):
+        rms = math.sqrt(np.mean(fo[k] ** 2))
+        if rms > 0:
+            assert math.sqrt(np.mean((fg[k] - fo[k]) ** 2)) <= 1e-5 * rms, (k, n)
+        assert abs(eg[k] - eo[k]) <= 1e-5 * max(scale[k], 1e-3), (k, eg[k], eo[k])
+
+
+def test_forces_excluded_overlapping_pairs(lib, orc):
+    # bonds-only chain: every pair excluded, atoms may sit on top of each other
+    top = pi.make_harmonic_chain(9, 400.0, 0.0, seed=3)
+    R = 5
+    x = f32(pi.perturbed_positions(top, R, 0.05, 2))
+    x[0, 3] = x[0, 5]  # coincident non-bonded (excluded) atoms
+    ctx = lib.pamd_init(top, R, 300.0, 1)
+    try:
+        lib.pamd_set_state(ctx, x, np.zeros_like(x))
+        fg, eg = lib.pamd_forces(ctx)
+    finally:
+        lib.pamd_destroy(ctx)
+    fo, eo, _ = _oracle_forces(orc, top, x)
+    assert np.all(np.isfinite(fg)) and np.all(np.isfinite(eg))
+    np.testing.assert_allclose(fg, fo, rtol=1e-5, atol=1e-4)
+    np.testing.assert_allclose(eg, eo, rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("n,R", [(22, 5), (75, 3), (200, 2), (7, 40)])
+def test_ten_step_trajectory(lib, orc, n, R):
+    top = pi.make_chain(n, 7)
+    T, dt, gamma, seed = 400.0, 0.001, 1.0, 4242
+    x = f32(pi.perturbed_positions(top, R, 0.005, 1))
+    x -= x.mean(axis=1, keepdims=True)
+    x = f32(x)
+    v = f32(pi.gaussian_velocities(R, n, math.sqrt(KB * T / 12.0), 2))
+    ctx = lib.pamd_init(top, R, T, seed, _opts(lib, gamma_per_ps=gamma))
+    try:
+        lib.pamd_set_state(ctx, x, v)
+        xo, vo = x.copy(), v.copy()
+        for s in range(10):
+            lib.pamd_propagate(ctx, 1, dt, T)
+            xg, vg, eg, _ = lib.pamd_get_state(ctx)
+            xo, vo, eo = orc.propagate(top, xo, vo, 1, dt, T, gamma, seed, s)
+            assert np.abs(xg - xo).max() < 1e-4, (s, np.abs(xg - xo).max())
+        assert np.abs(vg - vo).max() < 1e-2 * np.abs(vo).max()
+        scale = max(np.abs(eo).max(), 1.0)
+        assert np.abs(eg - eo).max() < 1e-4 * scale
+    finally:
+        lib.pamd_destroy(ctx)
+
+
+def test_init_matches_oracle(lib, orc):
+    top = pi.make_chain(22, 3)
+    ctx = lib.pamd_init(top, 300, 800.0, 77)
+    try:
+        xg, vg, _, fam = lib.pamd_get_state(ctx)
+    finally:
+        lib.pamd_destroy(ctx)
+    xo, vo, fo = orc.init(top, 300, 800.0, 77)
+    np.testing.assert_array_equal(fam, fo)
+    assert np.abs(xg - xo).max() < 1e-6
+    assert np.abs(vg - vo).max() < 1e-5 * np.abs(vo).max()
+
+
+RESAMPLE_CASES = [(1, 100.0), (2, 30.0), (3, 30.0), (1000, 30.0), (1025, 5.0), (4097, 60.0),
+                  (3000, 1e5), (2048, 0.0)]
+
+
+@pytest.mark.parametrize("R,spread", RESAMPLE_CASES)
+def test_resample_bit_exact(lib, orc, R, spread):
+    top = pi.make_chain(9, 2)
+    seed = 99 + R
+    x = f32(pi.perturbed_positions(top, R, 0.02, 5))
+    v = f32(pi.gaussian_velocities(R, 9, 0.5, 6))
+    E = pi.random_energies(R, -50.0, spread, 8)
+    fam = np.arange(R, dtype=np.int32)[::-1].copy()
+    Tp, Tn = 700.0, 640.0
+    ctx = lib.pamd_init(top, R, Tp, seed)
+    try:
+        lib.pamd_set_state(ctx, x, v, E, fam)
+        cnt, lnq = lib.pamd_resample(ctx, Tp, Tn)
+        xg, vg, eg, fg = lib.pamd_get_state(ctx)
+        obs = lib.pamd_observables(ctx, Tn)
+    finally:
+        lib.pamd_destroy(ctx)
+    lnq_o, W = orc.resample_weights(E, Tp, Tn)
+    cnt_o = orc.multinomial_counts(W, seed, 1)
+    np.testing.assert_array_equal(cnt, cnt_o)
+    assert cnt.sum() == R
+    assert abs(lnq - lnq_o) <= 1e-12 * max(1.0, abs(lnq_o))
+    xo, vo, fo, eo = orc.gather(top, cnt_o, x, v, fam, E, math.sqrt(Tn / Tp))
+    np.testing.assert_array_equal(fg, fo)
+    np.testing.assert_array_equal(eg, eo)
+    assert np.abs(xg - xo).max() < 2e-6
+    assert np.abs(vg - vo).max() <= 1e-6 * max(np.abs(vo).max(), 1e-30)
+    assert obs["max_copies"] == cnt_o.max()
+    assert abs(obs["lnQ"] - lnq_o) <= 1e-12 * max(1.0, abs(lnq_o))
+
+
+def test_observables_match_oracle(lib, orc):
+    top = pi.make_chain(22, 4)
+    R = 3000
+    ctx = lib.pamd_init(top, R, 600.0, 5)
+    try:
+        lib.pamd_propagate(ctx, 30, 0.001, 600.0)
+        lib.pamd_resample(ctx, 600.0, 560.0)
+        lib.pamd_propagate(ctx, 5, 0.001, 560.0)
+        og = lib.pamd_observables(ctx, 560.0)
+        x, v, E, fam = lib.pamd_get_state(ctx)
+    finally:
+        lib.pamd_destroy(ctx)
+    oo = orc.observables(top, x, v, fam, E)
+    for key in ("e_pot", "e_kin", "t_meas", "rg", "rg2"):
+        assert abs(og[key] - oo[key]) <= 1e-9 * abs(oo[key]), key
+    for key in ("e_pot_se", "e_kin_se", "rg_se", "rg2_se"):
+        assert abs(og[key] - oo[key]) <= 1e-7 * abs(oo[key]) + 1e-12, key
+    assert og["n_families"] == oo["n_families"]
+    assert og["n_families"] < R  # resampling pruned some families
+
+
+def test_anneal_graph_equals_stepwise_calls(lib):
+    top = pi.make_chain(22, 1)
+    temps = pi.geometric_schedule(1000.0, 600.0, 4)
+    R, theta, dt = 256, 20, 0.001
+    a = lib.pamd_init(top, R, temps[0], 3)
+    b = lib.pamd_init(top, R, temps[0], 3)
+    try:
+        obs_a = lib.pamd_anneal(a, temps, theta, dt)
+        obs_b = []
+        lib.pamd_propagate(b, theta, dt, temps[0])
+        obs_b.append(lib.pamd_observables(b, temps[0]))
+        for i in range(1, len(temps)):
+            lib.pamd_resample(b, temps[i - 1], temps[i], want_copies=False)
+            lib.pamd_propagate(b, theta, dt, temps[i])
+            obs_b.append(lib.pamd_observables(b, temps[i]))
+        sa, sb = lib.pamd_get_state(a), lib.pamd_get_state(b)
+        for u, w in zip(sa, sb):
+            np.testing.assert_array_equal(u, w)
+        for oa, ob in zip(obs_a, obs_b):
+            for k in oa:
+                assert oa[k] == ob[k], k
+        assert lib.pamd_get_counters(a) == lib.pamd_get_counters(b)
+        # a second graph launch continues with fresh counters
+        obs_a2 = lib.pamd_anneal(a, temps, theta, dt)
+        assert obs_a2[-1]["e_pot"] != obs_a[-1]["e_pot"]
+    finally:
+        lib.pamd_destroy(a)
+        lib.pamd_destroy(b)
+
+
+def test_c1_anneal_statistical_parity(lib, orc):
+    """22-atom chain, R=256, theta=100, 20 geometric steps 1000 -> 300 K."""
+    top = pi.make_chain(22, 1)
+    temps = pi.geometric_schedule(1000.0, 300.0, 20)
+    R, theta, dt, gamma, seed = 256, 100, 0.001, 1.0, 12345
+    ctx = lib.pamd_init(top, R, temps[0], seed, _opts(lib, gamma_per_ps=gamma))
+    try:
+        og = lib.pamd_anneal(ctx, temps, theta, dt)
+    finally:
+        lib.pamd_destroy(ctx)
+    oo, *_ = orc.anneal(top, R, temps, theta, dt, gamma, seed)
+    for key, se in (("e_pot", "e_pot_se"), ("rg", "rg_se")):
+        g = np.array([o[key] for o in og])
+        o = np.array([o[key] for o in oo])
+        s = np.sqrt(np.array([x[se] for x in og]) ** 2 + np.array([x[se] for x in oo]) ** 2)
+        assert np.all(np.abs(g - o) <= 3 * s), (key, (g - o) / s)
+    tm = np.array([o["t_meas"] for o in og])
+    assert np.all(np.abs(tm / temps - 1) < 0.1)
+
+
+def test_harmonic_chain_closed_forms_on_gpu(lib):
+    n, kb = 6, 400.0
+    top = pi.make_harmonic_chain(n, kb, 0.0)
+    temps = pi.geometric_schedule(400.0, 200.0, 6)
+    ctx = lib.pamd_init(top, 4096, temps[0], 11, _opts(lib, gamma_per_ps=5.0))
+    try:
+        obs = lib.pamd_anneal(ctx, temps, 200, 0.002)
+    finally:
+        lib.pamd_destroy(ctx)
+    e = np.array([o["e_pot"] for o in obs]); se = np.array([o["e_pot_se"] for o in obs])
+    f = np.array([o["sum_lnQ"] for o in obs])
+    e_exact = 1.5 * (n - 1) * KB * temps
+    assert np.all(np.abs(e - e_exact) < 4 * se + 0.005 * e_exact), (e - e_exact) / se
+    assert np.all(np.abs(f - 1.5 * (n - 1) * np.log(temps / temps[0])) < 0.05)
+
+
+def test_nonfinite_energy_is_reported(lib):
+    top = pi.make_chain(6, 1)
+    R = 4
+    x = f32(pi.perturbed_positions(top, R, 0.01, 1))
+    x[2, 5] = x[2, 0]  # a non-excluded pair on top of each other
+    ctx = lib.pamd_init(top, R, 300.0, 1)
+    try:
+        lib.pamd_set_state(ctx, x, np.zeros_like(x))
+        with pytest.raises(lib.PamdError) as ei:
+            lib.pamd_forces(ctx)
+        assert ei.value.code == lib.PAMD_ENONFINITE and "replica 2" in str(ei.value)
+        # the context stays usable once the state is repaired
+        x[2, 5] = x[1, 5]
+        lib.pamd_set_state(ctx, x, np.zeros_like(x))
+        f, E = lib.pamd_forces(ctx)
+        assert np.all(np.isfinite(E))
+    finally:
+        lib.pamd_destroy(ctx)
+
+
+def test_checkpoint_resume_is_bit_identical(lib):
+    top = pi.make_chain(22, 2)
+    R, dt = 300, 0.001
+    a = lib.pamd_init(top, R, 900.0, 21)
+    b = lib.pamd_init(top, R, 900.0, 21)
+    c = lib.pamd_init(top, R, 900.0, 21)
+    try:
+        for ctx in (a, b):
+            lib.pamd_propagate(ctx, 25, dt, 900.0)
+        lib.pamd_resample(a, 900.0, 850.0)
+        lib.pamd_propagate(a, 25, dt, 850.0)
+        # checkpoint b, restore into c, continue there
+        x, v, E, fam = lib.pamd_get_state(b)
+        ctr = lib.pamd_get_counters(b)
+        lib.pamd_set_state(c, x, v, E, fam)
+        lib.pamd_set_counters(c, *ctr)
+        lib.pamd_resample(c, 900.0, 850.0)
+        lib.pamd_propagate(c, 25, dt, 850.0)
+        for u, w in zip(lib.pamd_get_state(a), lib.pamd_get_state(c)):
+            np.testing.assert_array_equal(u, w)
+        assert lib.pamd_get_counters(a) == lib.pamd_get_counters(c)
+    finally:
+        for ctx in (a, b, c):
+            lib.pamd_destroy(ctx)
+
+
+def test_torch_allocator_and_stream(lib):
+    import torch
+    top = pi.make_chain(22, 5)
+    temps = pi.geometric_schedule(800.0, 700.0, 2)
+    a = lib.Population(top, 128, temps[0], 8, lib.torch_options())
+    b = lib.Population(top, 128, temps[0], 8)
+    try:
+        before = torch.cuda.memory_allocated()
+        assert before > 0  # the population lives in PyTorch's allocator
+        oa = a.anneal(temps, 10, 0.001)
+        ob = b.anneal(temps, 10, 0.001)
+        assert oa == ob
+    finally:
+        a.close()
+        b.close()
+
+
+def test_full_size_sampled_parity(lib, orc):
+    """75-atom chain, R = 8192 (the benchmark shape): the full launch, checked on
+    sampled replicas against the oracle, and the full-size resampling bit-exact."""
+    top = pi.make_chain(75, 1)
+    R, T, dt, seed = 8192, 1000.0, 0.001, 12345
+    ctx = lib.pamd_init(top, R, T, seed)
+    try:
+        x0, v0, _, _ = lib.pamd_get_state(ctx)
+        lib.pamd_propagate(ctx, 10, dt, T)
+        x1, v1, E1, fam = lib.pamd_get_state(ctx)
+        cnt, lnq = lib.pamd_resample(ctx, T, 980.0)
+    finally:
+        lib.pamd_destroy(ctx)
+    sample = np.array([0, 1, 31, 32, 33, 1000, 4095, 4096, 8190, 8191])
+    xo, vo, eo = orc.propagate(top, x0[sample], v0[sample], 10, dt, T, 1.0, seed, 0, slots=sample)
+    assert np.abs(x1[sample] - xo).max() < 1e-4
+    assert np.abs(E1[sample] - eo).max() < 1e-4 * np.abs(eo).max()
+    lnq_o, W = orc.resample_weights(E1, T, 980.0)
+    np.testing.assert_array_equal(cnt, orc.multinomial_counts(W, seed, 1))
+    assert abs(lnq - lnq_o) <= 1e-12 * max(1.0, abs(lnq_o))
+
+
+def test_large_population_resample_bit_exact(lib, orc):
+    """R = 2^20 replicas of the 75-atom chain: copy counts bit-exact."""
+    top = pi.make_chain(75, 1)
+    R, seed = 1 << 20, 31
+    ctx = lib.pamd_init(top, R, 1000.0, seed)
+    try:
+        lib.pamd_propagate(ctx, 2, 0.001, 1000.0)
+        _, _, E, _ = lib.pamd_get_state(ctx, positions=False, velocities=False, families=False)
+        cnt, lnq = lib.pamd_resample(ctx, 1000.0, 975.0)
+    finally:
+        lib.pamd_destroy(ctx)
+    lnq_o, W = orc.resample_weights(E, 1000.0, 975.0)
+    np.testing.assert_array_equal(cnt, orc.multinomial_counts(W, seed, 1))
+    assert abs(lnq - lnq_o) <= 1e-11 * max(1.0, abs(lnq_o))
