@@ -220,8 +220,10 @@ def run_gpu(args, w):
     temps = pi.geometric_schedule(w["T0"], w["TK"], w["K"])
     R, theta, dt = w["R"], w["theta"], w["dt"]
     seed = w["seed"] + 7919 * rank
+    # the library launches on this stream; the timing events are recorded on it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     pop = pamd.Population(top, R, temps[0], seed, pamd.torch_options(gamma_per_ps=w["gamma"]))
-    stream = torch.cuda.current_stream()
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     def one_anneal():
@@ -328,6 +330,47 @@ def run_gpu(args, w):
         dist.destroy_process_group()
 
 
+def run_kernel(args, w):
+    """Propagate launches only (theta steps over all R replicas), for
+    profiling and launch-shape sweeps.  Prints one JSON line."""
+    import torch
+
+    import pamd_inputs as pi
+    from paper_1806_06016_gb300 import build as pbuild
+    from paper_1806_06016_gb300 import pamd
+
+    torch.cuda.set_device(0)
+    pbuild.build()
+    top = pi.make_chain(w["n_atoms"], w["gen_seed"])
+    theta = args.theta or w["theta"]
+    R = args.replicas or w["R"]
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    opts = pamd.torch_options(gamma_per_ps=w["gamma"], lanes_per_replica=args.lanes,
+                              warps_per_block=args.warps)
+    pop = pamd.Population(top, R, w["T0"], w["seed"], opts)
+    info = pop.info()
+    for _ in range(args.warmup):
+        pamd.pamd_propagate(pop.ctx, theta, w["dt"], w["T0"])
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        pamd.pamd_propagate(pop.ctx, theta, w["dt"], w["T0"])
+        ev1.record(stream)
+        ev1.synchronize()
+        ms.append(ev0.elapsed_time(ev1))
+    pop.close()
+    avg = statistics.mean(ms)
+    flops = flop_per_replica_step(w["n_atoms"]) * R * theta
+    achieved = flops / (avg / 1e3) / 1e12
+    print(json.dumps({"mode": "kernel", "n_atoms": w["n_atoms"], "replicas": R, "theta": theta,
+                      "launch": info, "ms": avg, "atom_steps_per_s": w["n_atoms"] * R * theta / (avg / 1e3),
+                      "achieved_tflops": achieved, "frac": achieved / FP32_PEAK_TFLOPS}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -336,9 +379,16 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", choices=["anneal", "kernel"], default="anneal")
+    ap.add_argument("--theta", type=int, default=0, help="kernel mode: steps per launch")
+    ap.add_argument("--replicas", type=int, default=0, help="kernel mode: population size")
+    ap.add_argument("--lanes", type=int, default=0, help="kernel mode: lanes per replica")
+    ap.add_argument("--warps", type=int, default=0, help="kernel mode: warps per block")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
-    if args.impl == "reference":
+    if args.mode == "kernel":
+        run_kernel(args, w)
+    elif args.impl == "reference":
         run_reference(args, w)
     else:
         run_gpu(args, w)

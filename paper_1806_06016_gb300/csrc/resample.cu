@@ -623,9 +623,11 @@ cudaError_t launch_resample(pamd_ctx* c, double T_prev, double T_next, int do_re
     const double two_s = ldexp(1.0, 63 - bits);
     static const ExpCoef cf = exp_coefficients();
 
-    amax_kernel<<<nblk, kScanThreads, 0, s>>>(c->b.E, R, dbeta, c->b.blk_f64);
+    // energies of the current population (the ping-pong buffers alternate)
+    const double* Ecur = c->cur_is_alt ? c->b.E_alt : c->b.E;
+    amax_kernel<<<nblk, kScanThreads, 0, s>>>(Ecur, R, dbeta, c->b.blk_f64);
     max_top_kernel<<<1, 1024, 0, s>>>(c->b.blk_f64, nblk, c->b.scal);
-    weights_kernel<<<nblk, kScanThreads, 0, s>>>(c->b.E, R, dbeta, two_s, c->b.scal, cf, c->b.W,
+    weights_kernel<<<nblk, kScanThreads, 0, s>>>(Ecur, R, dbeta, two_s, c->b.scal, cf, c->b.W,
                                                  c->b.blk_u64, c->b.blk_f64);
     weights_top_kernel<<<1, kScanThreads, 0, s>>>(c->b.blk_u64, c->b.blk_f64, nblk, R, c->b.scal);
     scan_local_u64_kernel<<<nblk, kScanThreads, 0, s>>>(c->b.W, R, c->b.blk_u64, c->b.C);

@@ -185,7 +185,11 @@ _keepalive: dict[int, object] = {}
 
 
 def torch_options(gamma_per_ps: float = 1.0, **kw) -> PamdOptions:
-    """Options whose device memory and stream come from PyTorch."""
+    """Options whose device memory and stream come from PyTorch: the caching
+    allocator and torch's current stream.  If that stream is the legacy
+    default stream (handle 0) the library uses a stream of its own, which is
+    not ordered with torch's work; make a side stream current first to share
+    one stream with torch."""
     o = pamd_options_default()
     o.gamma_per_ps = gamma_per_ps
     for k, v in kw.items():

@@ -172,6 +172,25 @@ def test_resample_bit_exact(lib, orc, R, spread):
     assert abs(obs["lnQ"] - lnq_o) <= 1e-12 * max(1.0, abs(lnq_o))
 
 
+def test_consecutive_resamplings_bit_exact(lib, orc):
+    """Every resampling of a sequence weighs the current population."""
+    top = pi.make_chain(12, 3)
+    R, seed, dt = 777, 5, 0.001
+    temps = [900.0, 850.0, 800.0, 760.0, 720.0]
+    ctx = lib.pamd_init(top, R, temps[0], seed)
+    try:
+        lib.pamd_propagate(ctx, 10, dt, temps[0])
+        for i in range(1, len(temps)):
+            _, _, E, _ = lib.pamd_get_state(ctx)
+            cnt, lnq = lib.pamd_resample(ctx, temps[i - 1], temps[i])
+            lnq_o, W = orc.resample_weights(E, temps[i - 1], temps[i])
+            np.testing.assert_array_equal(cnt, orc.multinomial_counts(W, seed, i))
+            assert abs(lnq - lnq_o) <= 1e-12 * max(1.0, abs(lnq_o))
+            lib.pamd_propagate(ctx, 10, dt, temps[i])
+    finally:
+        lib.pamd_destroy(ctx)
+
+
 def test_observables_match_oracle(lib, orc):
     top = pi.make_chain(22, 4)
     R = 3000
@@ -239,8 +258,12 @@ def test_c1_anneal_statistical_parity(lib, orc):
         o = np.array([o[key] for o in oo])
         s = np.sqrt(np.array([x[se] for x in og]) ** 2 + np.array([x[se] for x in oo]) ** 2)
         assert np.all(np.abs(g - o) <= 3 * s), (key, (g - o) / s)
-    tm = np.array([o["t_meas"] for o in og])
-    assert np.all(np.abs(tm / temps - 1) < 0.1)
+    # kinetic temperature: theta = 100 is too short to equilibrate (the
+    # paper's point about theta), so compare GPU with oracle, not with T
+    g = np.array([o["e_kin"] for o in og])
+    o = np.array([o["e_kin"] for o in oo])
+    s = np.sqrt(np.array([x["e_kin_se"] for x in og]) ** 2 + np.array([x["e_kin_se"] for x in oo]) ** 2)
+    assert np.all(np.abs(g - o) <= 3 * s), (g - o) / s
 
 
 def test_harmonic_chain_closed_forms_on_gpu(lib):
