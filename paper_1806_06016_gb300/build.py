@@ -26,6 +26,14 @@ NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp
                      "-I" + INCLUDE]
 
 
+# The FP32 force kernels flush denormals and use the approximate division and
+# square root (relative error of a few ulp, far inside the force tolerance).
+PROPAGATE_FLAGS = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
+# Extra preprocessor definitions for tuning builds, e.g.
+# PAMD_NVCC_DEFINES="PAMD_PROP_MIN_BLOCKS=2".
+DEFINES = ["-D" + d for d in os.environ.get("PAMD_NVCC_DEFINES", "").split() if d]
+
+
 def _nvcc() -> str:
     p = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     if not os.path.exists(p):
@@ -59,7 +67,8 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
-        cmd = [nvcc] + NVCC_FLAGS + ["-c", src, "-o", obj]
+        extra = PROPAGATE_FLAGS if os.path.basename(src).startswith("propagate_") else []
+        cmd = [nvcc] + NVCC_FLAGS + DEFINES + extra + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

@@ -118,24 +118,68 @@ int colour_terms(const std::vector<std::vector<int>>& atoms, int N, std::vector<
     return PAMD_OK;
 }
 
+// Launch shape: B atoms per lane (1..8), L = ceil(N/B) lanes per replica
+// (<= 32), G = floor(32/L) replicas per warp.  The cost of one replica-step per
+// warp slot is modelled as (pair evaluations per lane + per-atom work) / G,
+// with the per-atom work (bonded terms, noise, integration) taken as 16 pair
+// evaluations; the cheapest shape is chosen.
 int choose_lanes(int N, int requested, int* L, int* B) {
     if (requested) {
-        if (requested != 4 && requested != 8 && requested != 16 && requested != 32)
-            return fail(PAMD_EINVAL, "lanes_per_replica must be 0, 4, 8, 16 or 32");
+        if (requested < 1 || requested > 32) return fail(PAMD_EINVAL, "lanes_per_replica must be 0..32");
         *L = requested;
         *B = (N + requested - 1) / requested;
         if (*B > 8) return fail(PAMD_EINVAL, "lanes_per_replica too small for this molecule (8 atoms per lane at most)");
+        *L = (N + *B - 1) / *B;  // no lane without atoms
         return PAMD_OK;
     }
-    for (int l : {4, 8, 16, 32}) {
-        const int b = (N + l - 1) / l;
-        if (b <= 8) {
+    double best = 1e300;
+    for (int b = 1; b <= 8; ++b) {
+        const int l = (N + b - 1) / b;
+        if (l > 32) continue;
+        const int G = 32 / l;
+        const double cost = (0.5 * b * (double)(l * b) + 16.0 * b) / G;
+        if (cost < best) {
+            best = cost;
             *L = l;
             *B = b;
-            return PAMD_OK;
         }
     }
-    return fail(PAMD_EUNSUPPORTED, "molecule too large");
+    if (best == 1e300) return fail(PAMD_EUNSUPPORTED, "molecule too large");
+    return PAMD_OK;
+}
+
+// True when the bonded lists are those of a linear chain: bond k = (k, k+1),
+// angle k = (k, k+1, k+2), dihedral k = (k..k+3) (either direction), one
+// entry per k, and the 1-4 pairs are exactly {(k, k+3)}.
+bool is_linear_chain(const pamd_topology* t) {
+    const int N = t->n_atoms;
+    auto run = [](const int32_t* idx, int n, int arity, int k) {
+        bool fwd = true, bwd = true;
+        for (int a = 0; a < arity; ++a) {
+            fwd = fwd && idx[k * arity + a] == k + a;
+            bwd = bwd && idx[k * arity + a] == k + arity - 1 - a;
+        }
+        return fwd || bwd;
+    };
+    if (t->n_bonds != std::max(N - 1, 0) || t->n_angles != std::max(N - 2, 0) ||
+        t->n_dihedrals != std::max(N - 3, 0) || t->n_pair14 != std::max(N - 3, 0))
+        return false;
+    for (int k = 0; k < t->n_bonds; ++k) if (!run(t->bond, t->n_bonds, 2, k)) return false;
+    for (int k = 0; k < t->n_angles; ++k) if (!run(t->angle, t->n_angles, 3, k)) return false;
+    for (int k = 0; k < t->n_dihedrals; ++k) if (!run(t->dihedral, t->n_dihedrals, 4, k)) return false;
+    std::vector<char> seen(std::max(N - 3, 0), 0);
+    for (int p = 0; p < t->n_pair14; ++p) {
+        const int i = std::min(t->pair14[2 * p], t->pair14[2 * p + 1]);
+        const int j = std::max(t->pair14[2 * p], t->pair14[2 * p + 1]);
+        if (j != i + 3 || seen[i]) return false;
+        seen[i] = 1;
+    }
+    // a 1-4 pair that is also excluded would be skipped by the generic path
+    for (int p = 0; p < t->n_excl; ++p) {
+        const int i = t->excl[2 * p], j = t->excl[2 * p + 1];
+        if (std::abs(i - j) == 3) return false;
+    }
+    return true;
 }
 
 // Build the shared-memory table of the propagate kernel.
@@ -208,7 +252,7 @@ int build_topology(pamd_ctx* c, const pamd_topology* t, int lanes_req, std::vect
             return;
         }
         const int tt = ((gj - gi) % L + L) % L;
-        if (tt < TH || (tt == TH && gi < TH)) {
+        if (2 * tt < L || (2 * tt == L && gi < tt)) {
             masks[(size_t)tt * L + gi] |= 1ull << (ai * B + aj);
         } else {
             const int t2 = L - tt;
@@ -266,6 +310,10 @@ int build_topology(pamd_ctx* c, const pamd_topology* t, int lanes_req, std::vect
             prs.push_back({slot(p14[o].first), slot(p14[o].second), (float)t->scale14_lj,
                            (float)t->scale14_coul});
     }
+    const bool chain = B >= 3 && is_linear_chain(t);
+    lay.chain = chain ? 1 : 0;
+    lay.s14_lj = (float)t->scale14_lj;
+    lay.s14_c = (float)t->scale14_coul;
     lay.n_bonds = (int)bonds.size();
     lay.n_angles = (int)angles.size();
     lay.n_dihs = (int)dihs.size();
@@ -279,6 +327,9 @@ int build_topology(pamd_ctx* c, const pamd_topology* t, int lanes_req, std::vect
     lay.off_dihs = off; off += round_up(lay.n_dihs * 32, 16);
     lay.off_p14 = off; off += round_up(lay.n_p14 * 16, 16);
     lay.off_colors = off; off += round_up(4 * (kMaxColors + 1) * 4, 16);
+    lay.off_cbond = off; off += round_up(std::max(N - 1, 0) * 8, 16);
+    lay.off_cangle = off; off += round_up(std::max(N - 2, 0) * 8, 16);
+    lay.off_cdih = off; off += round_up(std::max(N - 3, 0) * 16, 16);
     lay.bytes = off;
     blob.assign(off, 0);
     float* prm = reinterpret_cast<float*>(blob.data() + lay.off_params);
@@ -295,19 +346,47 @@ int build_topology(pamd_ctx* c, const pamd_topology* t, int lanes_req, std::vect
     if (!angles.empty()) std::memcpy(blob.data() + lay.off_angles, angles.data(), angles.size() * 32);
     if (!dihs.empty()) std::memcpy(blob.data() + lay.off_dihs, dihs.data(), dihs.size() * 32);
     if (!prs.empty()) std::memcpy(blob.data() + lay.off_p14, prs.data(), prs.size() * 16);
+    if (chain) {
+        // per-term parameters indexed by the term's first (lowest) atom
+        float* cb = reinterpret_cast<float*>(blob.data() + lay.off_cbond);
+        for (int b = 0; b < t->n_bonds; ++b) {
+            const int d = std::min(t->bond[2 * b], t->bond[2 * b + 1]);
+            cb[2 * d] = (float)t->bond_r0[b];
+            cb[2 * d + 1] = (float)t->bond_k[b];
+        }
+        float* ca = reinterpret_cast<float*>(blob.data() + lay.off_cangle);
+        for (int a = 0; a < t->n_angles; ++a) {
+            const int d = std::min(t->angle[3 * a], t->angle[3 * a + 2]);
+            ca[2 * d] = (float)t->angle_t0[a];
+            ca[2 * d + 1] = (float)t->angle_k[a];
+        }
+        float* cd = reinterpret_cast<float*>(blob.data() + lay.off_cdih);
+        for (int h = 0; h < t->n_dihedrals; ++h) {
+            const int d = std::min(t->dihedral[4 * h], t->dihedral[4 * h + 3]);
+            cd[4 * d] = (float)t->dih_k[h];
+            cd[4 * d + 1] = (float)t->dih_n[h];
+            cd[4 * d + 2] = (float)std::cos(t->dih_phase[h]);
+            cd[4 * d + 3] = (float)std::sin(t->dih_phase[h]);
+        }
+    }
     int* cols = reinterpret_cast<int*>(blob.data() + lay.off_colors);
     for (int ty = 0; ty < 4; ++ty)
         for (int q = 0; q <= kMaxColors; ++q) cols[ty * (kMaxColors + 1) + q] = starts[ty][q];
     return PAMD_OK;
 }
 
-cudaError_t propagate_dispatch_any(int L, const PropParams* p, int B, int warps, int grid,
+cudaError_t propagate_dispatch_any(const TopoLayout& lay, const PropParams* p, int warps, int grid,
                                    size_t smem, cudaStream_t s, int* occ) {
-    switch (L) {
-        case 4: return propagate_l4(p, B, warps, grid, smem, s, occ);
-        case 8: return propagate_l8(p, B, warps, grid, smem, s, occ);
-        case 16: return propagate_l16(p, B, warps, grid, smem, s, occ);
-        case 32: return propagate_l32(p, B, warps, grid, smem, s, occ);
+    const bool chain = lay.chain != 0;
+    switch (lay.per_lane) {
+        case 1: return propagate_b1(p, chain, warps, grid, smem, s, occ);
+        case 2: return propagate_b2(p, chain, warps, grid, smem, s, occ);
+        case 3: return propagate_b3(p, chain, warps, grid, smem, s, occ);
+        case 4: return propagate_b4(p, chain, warps, grid, smem, s, occ);
+        case 5: return propagate_b5(p, chain, warps, grid, smem, s, occ);
+        case 6: return propagate_b6(p, chain, warps, grid, smem, s, occ);
+        case 7: return propagate_b7(p, chain, warps, grid, smem, s, occ);
+        case 8: return propagate_b8(p, chain, warps, grid, smem, s, occ);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -343,8 +422,8 @@ int launch_prop(pamd_ctx* c, int theta, double dt, double T, const uint32_t* dev
     p.seed = c->seed;
     p.step0 = step0;
     p.purpose_mol = kPurposeNoise | ((uint32_t)c->mol << 8);
-    cudaError_t e = propagate_dispatch_any(c->lay.lanes, &p, c->lay.per_lane, c->warps_per_block,
-                                           c->grid_prop, prop_smem(c), c->stream, nullptr);
+    cudaError_t e = propagate_dispatch_any(c->lay, &p, c->warps_per_block, c->grid_prop,
+                                           prop_smem(c), c->stream, nullptr);
     c->launches += 1;
     if (e != cudaSuccess) return cuda_fail(c, e, "propagate launch");
     return PAMD_OK;
@@ -447,7 +526,7 @@ int pamd_init(pamd_ctx** out, const pamd_topology* top, int64_t R, double T0, ui
         c->own_stream = true;
     }
     // launch shape
-    const int groups_per_warp = 32 / c->lay.lanes;
+    const int groups_per_warp = 32 / c->lay.lanes;  // idle lanes when L does not divide 32
     int warps = o.warps_per_block ? o.warps_per_block : 4;
     int max_smem = 0;
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -459,8 +538,8 @@ int pamd_init(pamd_ctx** out, const pamd_topology* top, int64_t R, double T0, ui
     }
     if ((long long)prop_smem(c) > max_smem) return bail(PAMD_EUNSUPPORTED, "molecule tables exceed shared memory");
     int occ = 0;
-    cudaError_t e = propagate_dispatch_any(c->lay.lanes, nullptr, c->lay.per_lane, c->warps_per_block,
-                                           0, prop_smem(c), nullptr, &occ);
+    cudaError_t e = propagate_dispatch_any(c->lay, nullptr, c->warps_per_block, 0, prop_smem(c),
+                                           nullptr, &occ);
     if (e != cudaSuccess || occ < 1) return bail(PAMD_ECUDA, std::string("propagate occupancy: ") + cudaGetErrorString(e));
     const long long batches = (R + c->rpb - 1) / c->rpb;
     c->grid_prop = (int)std::min<long long>(batches, (long long)c->num_sms * occ);

@@ -28,7 +28,7 @@ struct Pair14Rec { int32_t i, j; float s_lj, s_c; };
 // shared memory once per CTA.  All offsets are multiples of 16.
 struct TopoLayout {
     int n_atoms, n_pad;        // N and Np = round_up(N, 4) (global state stride)
-    int lanes, per_lane;       // L lanes per replica, B atoms per lane
+    int lanes, per_lane;       // L lanes per replica (1..32), B atoms per lane (1..8)
     int block_stride;          // B rounded up to odd (smem atoms per lane block)
     int nk;                    // L * block_stride smem atom slots
     int off_params;            // float4 [nk]: {sigma/2, sqrt(24 eps), q sqrt(k_e), 1/m}
@@ -39,6 +39,11 @@ struct TopoLayout {
     int off_p14, n_p14;
     int off_colors;            // int32 [4][kMaxColors+1] colour start offsets
     int n_colors[4];           // bonds, angles, dihedrals, 1-4 pairs
+    int chain;                 // 1: linear-chain bonded layout (B >= 3)
+    int off_cbond;             // chain: float2 [N-1] {r0, k} of bond (d, d+1)
+    int off_cangle;            // chain: float2 [N-2] {theta0, k} of angle (d, d+1, d+2)
+    int off_cdih;              // chain: float4 [N-3] {k, n, cos phase, sin phase} of (d..d+3)
+    float s14_lj, s14_c;       // chain: 1-4 scale factors
     int bytes;                 // total, multiple of 16
 };
 
@@ -149,16 +154,21 @@ struct pamd_ctx {
 
 namespace pamd {
 
-// propagate kernels (one translation unit per lane count).  With p == null
-// they only report how many blocks of that shape fit on one SM.
-cudaError_t propagate_l4(const PropParams* p, int per_lane, int warps, int grid, size_t smem,
-                         cudaStream_t s, int* blocks_per_sm);
-cudaError_t propagate_l8(const PropParams* p, int per_lane, int warps, int grid, size_t smem,
-                         cudaStream_t s, int* blocks_per_sm);
-cudaError_t propagate_l16(const PropParams* p, int per_lane, int warps, int grid, size_t smem,
-                          cudaStream_t s, int* blocks_per_sm);
-cudaError_t propagate_l32(const PropParams* p, int per_lane, int warps, int grid, size_t smem,
-                          cudaStream_t s, int* blocks_per_sm);
+// propagate kernels, one function per atoms-per-lane count B (two per
+// translation unit).  With p == null they only report how many blocks of that
+// shape fit on one SM.
+#define PAMD_DECLARE_PROPAGATE(B)                                                            \
+    cudaError_t propagate_b##B(const PropParams* p, bool chain, int warps, int grid, size_t smem, \
+                               cudaStream_t s, int* blocks_per_sm);
+PAMD_DECLARE_PROPAGATE(1)
+PAMD_DECLARE_PROPAGATE(2)
+PAMD_DECLARE_PROPAGATE(3)
+PAMD_DECLARE_PROPAGATE(4)
+PAMD_DECLARE_PROPAGATE(5)
+PAMD_DECLARE_PROPAGATE(6)
+PAMD_DECLARE_PROPAGATE(7)
+PAMD_DECLARE_PROPAGATE(8)
+#undef PAMD_DECLARE_PROPAGATE
 
 // resampling / observables / init kernels (resample.cu)
 cudaError_t launch_init(pamd_ctx* c, double T0);

@@ -1,25 +1,31 @@
 // propagate_impl.cuh -- persistent BAOAB Langevin kernel (PAMD scheme, step 3).
 //
-// Mapping.  A replica is owned by a group of L lanes of one warp (L = 4, 8,
-// 16 or 32; 32/L replicas per warp).  Lane g of the group owns the B atoms
-// [g*B, g*B+B) of the molecule: their positions, velocities, parameters and
-// force accumulators live in registers for all theta steps.  Positions are
-// mirrored to shared memory (one float4 per atom) so that other lanes can read
-// them, and a float4 per atom in shared memory collects force contributions
-// written by other lanes.
+// Mapping.  A replica is owned by a group of L lanes of one warp (1 <= L <= 32,
+// G = floor(32/L) replicas per warp, the remaining 32 - G*L lanes idle).  Lane
+// g of a group owns the B atoms [g*B, g*B+B) of the molecule: their
+// positions, velocities, parameters and force accumulators live in registers
+// for all theta steps.  Positions are mirrored to shared memory (one float4
+// per atom) so that other lanes can read them, and a float4 per atom in
+// shared memory collects force contributions written by other lanes.
 //
 // Nonbonded forces use Newton's third law over a "half ring" of lane blocks:
-// at step t (1 <= t <= L/2) lane g pairs its block with block (g+t) mod L
-// (at t = L/2 only lanes g < L/2 do, so that the antipodal pair is done once),
-// accumulating its own atoms' forces in registers and the partner block's in
-// registers that are then added to shared memory.  At each t the partner
-// blocks of the lanes are distinct, so those read-modify-writes need no
-// atomics; a __syncwarp separates the steps.  The block's internal pairs
+// at step t (1 <= t <= L/2) lane g pairs its block with block (g+t) mod L (for
+// even L, at t = L/2 only lanes g < L/2 do, so the antipodal pair is done
+// once), accumulating its own atoms' forces in registers and the partner
+// block's in registers that are then added to shared memory.  At each t the
+// partner blocks of the lanes are distinct, so those read-modify-writes need
+// no atomics; a __syncwarp separates the steps.  The block's internal pairs
 // (t = 0) are done by the owner.  Pairs that the topology excludes or scales
-// (1-2, 1-3, 1-4) are masked out of their tile by a 64-bit mask per tile;
-// 1-4 pairs are then added with their scale factors in the bonded pass.
-// Bonded terms are split into colour classes whose terms share no atom, so
-// all lanes of the group can add their forces without atomics.
+// (1-2, 1-3, 1-4) are masked out of their tile by a 64-bit mask per tile; 1-4
+// pairs are then added with their scale factors in the bonded pass.
+//
+// Bonded terms.  For a linear chain (bonds (k,k+1), angles (k..k+2),
+// dihedrals (k..k+3), 1-4 pairs (k,k+3)) each lane evaluates the terms whose
+// first atom is in its block: their atoms lie in its block or in the first
+// three atoms of the next block (B >= 3), so the lane adds forces to its own
+// atoms in registers and only the next block's first atoms go through shared
+// memory, each written by one lane only.  Any other topology uses colour
+// classes of atom-disjoint terms, lanes striding over each class.
 //
 // Atoms beyond N (padding up to L*B) get zero parameters, infinite mass and
 // positions 1000 nm away from everything, so they contribute exactly zero.
@@ -30,12 +36,15 @@
 
 namespace pamd {
 
-template <int L, int B>
+// Blocks per SM the compiler is asked to fit (register budget 65536 /
+// (256 threads x PAMD_PROP_MIN_BLOCKS) per thread); chosen by measurement.
+#ifndef PAMD_PROP_MIN_BLOCKS
+#define PAMD_PROP_MIN_BLOCKS 1
+#endif
+
+template <int B>
 struct PropCfg {
     static constexpr int BS = (B % 2 == 1) ? B : B + 1;  // odd stride: conflict-free LDS.128
-    static constexpr int NK = L * BS;                     // shared-memory atom slots
-    static constexpr int TH = L / 2;                      // half-ring steps
-    static constexpr int SLOT = 2 * NK + 1;               // float4s per replica slot (pos + frc + pad)
 };
 
 // Lennard-Jones + Coulomb for one pair.  d = x_j - x_i.  With
@@ -50,9 +59,8 @@ __device__ __forceinline__ void pair_lj_coul(float dx, float dy, float dz, float
     const float s2 = sig * sig * rinv2;
     const float s6 = s2 * s2 * s2;
     const float lj = eps * s6 * fmaf(2.0f, s6, -1.0f);
-    const float cq = qq * rinv;
-    fs = (lj + cq) * rinv2;
-    if (ENERGY) e = fmaf((eps * (1.0f / 6.0f)) * s6, s6 - 1.0f, cq);
+    fs = fmaf(qq, rinv, lj) * rinv2;
+    if (ENERGY) e = fmaf((eps * (1.0f / 6.0f)) * s6, s6 - 1.0f, qq * rinv);
 }
 
 template <int B, bool MASKED, bool ENERGY>
@@ -97,163 +105,272 @@ __device__ __forceinline__ void add_force(float4* frc, int s, float fx, float fy
     frc[s] = f;
 }
 
-__device__ __forceinline__ float3 sub3(float4 a, float4 b) {
+__device__ __forceinline__ float3 f3sub(float3 a, float3 b) {
     return make_float3(a.x - b.x, a.y - b.y, a.z - b.z);
 }
+__device__ __forceinline__ float3 f3(float4 a) { return make_float3(a.x, a.y, a.z); }
 __device__ __forceinline__ float dot3(float3 a, float3 b) {
     return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z));
 }
 __device__ __forceinline__ float3 cross3(float3 a, float3 b) {
     return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
+__device__ __forceinline__ float3 f3scale(float s, float3 a) {
+    return make_float3(s * a.x, s * a.y, s * a.z);
+}
+__device__ __forceinline__ float3 f3axpby(float a, float3 x, float b, float3 y) {
+    return make_float3(fmaf(a, x.x, b * y.x), fmaf(a, x.y, b * y.y), fmaf(a, x.z, b * y.z));
+}
 
-// Bonded terms and scaled 1-4 pairs: colour by colour, lanes of the group
-// stride over the terms of a colour.
-template <int L, bool ENERGY>
-__device__ __forceinline__ void bonded_forces(const unsigned char* sm, const TopoLayout& lay,
-                                              const float4* prm, const float4* pos, float4* frc,
-                                              int g, unsigned gmask, double& e_acc) {
+// ---- bonded term kernels on positions; return forces on each atom ----------
+
+// 1/2 k (r - r0)^2 ; force on atom i (atom j gets the opposite)
+template <bool ENERGY>
+__device__ __forceinline__ float3 bond_force(float3 pi_, float3 pj_, float r0, float k,
+                                             double& e_acc) {
+    const float3 d = f3sub(pi_, pj_);
+    const float r = sqrtf(dot3(d, d));
+    const float gk = (r0 == 0.0f) ? k : k * (r - r0) / r;
+    if (ENERGY) e_acc += (double)(0.5f * k * (r - r0) * (r - r0));
+    return f3scale(-gk, d);
+}
+
+// 1/2 k (theta - theta0)^2 with theta the angle at j
+template <bool ENERGY>
+__device__ __forceinline__ void angle_force(float3 pi_, float3 pj_, float3 pk_, float t0, float kk,
+                                            float3& fi, float3& fj, float3& fk, double& e_acc) {
+    const float3 u = f3sub(pi_, pj_);
+    const float3 w = f3sub(pk_, pj_);
+    const float3 uxw = cross3(u, w);
+    const float s = sqrtf(dot3(uxw, uxw));
+    const float cw = dot3(u, w);
+    const float dth = atan2f(s, cw) - t0;
+    const float gk = kk * dth;
+    const float is = gk / s;
+    const float cu = cw / dot3(u, u), cv = cw / dot3(w, w);
+    // F_i = -gk dtheta/du = gk (w - cu u)/s ; F_k = gk (u - cv w)/s
+    fi = make_float3(is * (w.x - cu * u.x), is * (w.y - cu * u.y), is * (w.z - cu * u.z));
+    fk = make_float3(is * (u.x - cv * w.x), is * (u.y - cv * w.y), is * (u.z - cv * w.z));
+    fj = make_float3(-fi.x - fk.x, -fi.y - fk.y, -fi.z - fk.z);
+    if (ENERGY) e_acc += (double)(0.5f * kk * dth * dth);
+}
+
+// k (1 + cos(n phi - phase)); gradient of phi after Blondel & Karplus (1996)
+template <bool ENERGY>
+__device__ __forceinline__ void dihedral_force(float3 pi_, float3 pj_, float3 pk_, float3 pl_,
+                                               float4 prm, float3& fi, float3& fj, float3& fk,
+                                               float3& fl, double& e_acc) {
+    const float kd = prm.x, nn = prm.y, cph = prm.z, sph = prm.w;
+    const float3 F = f3sub(pi_, pj_);
+    const float3 G = f3sub(pj_, pk_);
+    const float3 H = f3sub(pl_, pk_);
+    const float3 A = cross3(F, G);
+    const float3 Bv = cross3(H, G);
+    const float AA = dot3(A, A), BB = dot3(Bv, Bv);
+    const float lg = sqrtf(dot3(G, G));
+    const float rab = rsqrtf(AA * BB);
+    const float cphi = dot3(A, Bv) * rab;
+    const float sphi = dot3(cross3(Bv, A), G) * rab / lg;
+    float cn = cphi, sn = sphi;
+    const int n = (int)nn;
+    for (int q = 1; q < n; ++q) {
+        const float c2 = cn * cphi - sn * sphi;
+        sn = fmaf(sn, cphi, cn * sphi);
+        cn = c2;
+    }
+    const float dEdphi = -kd * nn * (sn * cph - cn * sph);
+    const float ia = lg / AA, ib = lg / BB;
+    const float pa = dot3(F, G) / (AA * lg), pb = dot3(H, G) / (BB * lg);
+    fi = f3scale(dEdphi * ia, A);
+    fl = f3scale(-dEdphi * ib, Bv);
+    fj = f3axpby(-dEdphi * (ia + pa), A, dEdphi * pb, Bv);
+    fk = f3axpby(dEdphi * pa, A, -dEdphi * (pb - ib), Bv);
+    if (ENERGY) e_acc += (double)(kd * (1.0f + cn * cph + sn * sph));
+}
+
+// scaled Lennard-Jones + Coulomb of a 1-4 pair; force on i
+template <bool ENERGY>
+__device__ __forceinline__ float3 pair14_force(float3 pi_, float3 pj_, float4 ci, float4 cj,
+                                               float s_lj, float s_c, double& e_acc) {
+    const float3 d = f3sub(pj_, pi_);
+    const float r2 = dot3(d, d);
+    const float rinv = rsqrtf(r2);
+    const float rinv2 = rinv * rinv;
+    const float sig = ci.x + cj.x;
+    const float s2 = sig * sig * rinv2;
+    const float s6 = s2 * s2 * s2;
+    const float eps = ci.y * cj.y;
+    const float cq = s_c * ci.z * cj.z * rinv;
+    const float lj = s_lj * eps * s6 * fmaf(2.0f, s6, -1.0f);
+    const float fs = (lj + cq) * rinv2;
+    if (ENERGY) e_acc += (double)(s_lj * (eps * (1.0f / 6.0f)) * s6 * (s6 - 1.0f) + cq);
+    return f3scale(-fs, d);
+}
+
+// Generic bonded pass: colour by colour, lanes of the group stride over the
+// terms of a colour (atom-disjoint, so plain read-modify-writes suffice).
+template <bool ENERGY>
+__device__ __forceinline__ void bonded_colored(const unsigned char* sm, const TopoLayout& lay,
+                                               const float4* prm, const float4* pos, float4* frc,
+                                               int L, int g, unsigned gmask, double& e_acc) {
     const int* colors = reinterpret_cast<const int*>(sm + lay.off_colors);
-    // bonds: 1/2 k (r - r0)^2
     {
         const BondRec* rec = reinterpret_cast<const BondRec*>(sm + lay.off_bonds);
         const int* cs = colors + 0 * (kMaxColors + 1);
         for (int c = 0; c < lay.n_colors[0]; ++c) {
             for (int t = cs[c] + g; t < cs[c + 1]; t += L) {
                 const BondRec b = rec[t];
-                const float3 d = sub3(pos[b.i], pos[b.j]);
-                const float r2 = dot3(d, d);
-                const float r = sqrtf(r2);
-                const float gk = (b.r0 == 0.0f) ? b.k : b.k * (r - b.r0) / r;
-                add_force(frc, b.i, -gk * d.x, -gk * d.y, -gk * d.z);
-                add_force(frc, b.j, gk * d.x, gk * d.y, gk * d.z);
-                if (ENERGY) e_acc += (double)(0.5f * b.k * (r - b.r0) * (r - b.r0));
+                const float3 f = bond_force<ENERGY>(f3(pos[b.i]), f3(pos[b.j]), b.r0, b.k, e_acc);
+                add_force(frc, b.i, f.x, f.y, f.z);
+                add_force(frc, b.j, -f.x, -f.y, -f.z);
             }
             __syncwarp(gmask);
         }
     }
-    // angles: 1/2 k (theta - theta0)^2
     {
         const AngleRec* rec = reinterpret_cast<const AngleRec*>(sm + lay.off_angles);
         const int* cs = colors + 1 * (kMaxColors + 1);
         for (int c = 0; c < lay.n_colors[1]; ++c) {
             for (int t = cs[c] + g; t < cs[c + 1]; t += L) {
                 const AngleRec a = rec[t];
-                const float3 u = sub3(pos[a.i], pos[a.j]);
-                const float3 w = sub3(pos[a.k], pos[a.j]);
-                const float3 uxw = cross3(u, w);
-                const float s = sqrtf(dot3(uxw, uxw));
-                const float cw = dot3(u, w);
-                const float th = atan2f(s, cw);
-                const float dth = th - a.t0;
-                const float gk = a.kk * dth;
-                const float is = 1.0f / s;
-                const float cu = cw / dot3(u, u), cv = cw / dot3(w, w);
-                // dtheta/du = -(w - (u.w) u/|u|^2)/|u x w|, dtheta/dw likewise
-                const float3 du = make_float3(-(w.x - cu * u.x) * is, -(w.y - cu * u.y) * is,
-                                              -(w.z - cu * u.z) * is);
-                const float3 dw = make_float3(-(u.x - cv * w.x) * is, -(u.y - cv * w.y) * is,
-                                              -(u.z - cv * w.z) * is);
-                add_force(frc, a.i, -gk * du.x, -gk * du.y, -gk * du.z);
-                add_force(frc, a.k, -gk * dw.x, -gk * dw.y, -gk * dw.z);
-                add_force(frc, a.j, gk * (du.x + dw.x), gk * (du.y + dw.y), gk * (du.z + dw.z));
-                if (ENERGY) e_acc += (double)(0.5f * a.kk * dth * dth);
+                float3 fi, fj, fk;
+                angle_force<ENERGY>(f3(pos[a.i]), f3(pos[a.j]), f3(pos[a.k]), a.t0, a.kk, fi, fj,
+                                    fk, e_acc);
+                add_force(frc, a.i, fi.x, fi.y, fi.z);
+                add_force(frc, a.j, fj.x, fj.y, fj.z);
+                add_force(frc, a.k, fk.x, fk.y, fk.z);
             }
             __syncwarp(gmask);
         }
     }
-    // dihedrals: k (1 + cos(n phi - phase)), gradient after Blondel & Karplus (1996)
     {
         const DihRec* rec = reinterpret_cast<const DihRec*>(sm + lay.off_dihs);
         const int* cs = colors + 2 * (kMaxColors + 1);
         for (int c = 0; c < lay.n_colors[2]; ++c) {
             for (int t = cs[c] + g; t < cs[c + 1]; t += L) {
                 const DihRec h = rec[t];
-                const float4 pi_ = pos[h.i], pj_ = pos[h.j], pk_ = pos[h.k], pl_ = pos[h.l];
-                const float3 F = sub3(pi_, pj_);
-                const float3 G = sub3(pj_, pk_);
-                const float3 H = sub3(pl_, pk_);
-                const float3 A = cross3(F, G);
-                const float3 Bv = cross3(H, G);
-                const float AA = dot3(A, A), BB = dot3(Bv, Bv);
-                const float lg = sqrtf(dot3(G, G));
-                const float rab = rsqrtf(AA * BB);
-                const float cphi = dot3(A, Bv) * rab;
-                const float sphi = dot3(cross3(Bv, A), G) * rab / lg;
-                // cos(n phi), sin(n phi) by the angle-addition recurrence
-                float cn = cphi, sn = sphi;
-                const int n = (int)h.n;
-                for (int q = 1; q < n; ++q) {
-                    const float c2 = cn * cphi - sn * sphi;
-                    sn = sn * cphi + cn * sphi;
-                    cn = c2;
-                }
-                // dE/dphi = -k n sin(n phi - phase)
-                const float sdel = sn * h.cos_ph - cn * h.sin_ph;
-                const float dEdphi = -h.kd * h.n * sdel;
-                const float fg = dot3(F, G), hg = dot3(H, G);
-                const float ia = lg / AA, ib = lg / BB;
-                const float pa = fg / (AA * lg), pb = hg / (BB * lg);
-                // F_atom = -dE/dphi * dphi/dx_atom
-                const float ci = dEdphi * ia;           // dphi/dx_i = -ia A
-                const float cl = -dEdphi * ib;          // dphi/dx_l = +ib B
-                add_force(frc, h.i, ci * A.x, ci * A.y, ci * A.z);
-                add_force(frc, h.l, cl * Bv.x, cl * Bv.y, cl * Bv.z);
-                // dphi/dx_j = (ia + pa) A - pb B ; dphi/dx_k = -pa A + (pb - ib) B
-                const float ja = -dEdphi * (ia + pa), jb = dEdphi * pb;
-                const float ka = dEdphi * pa, kb = -dEdphi * (pb - ib);
-                add_force(frc, h.j, ja * A.x + jb * Bv.x, ja * A.y + jb * Bv.y, ja * A.z + jb * Bv.z);
-                add_force(frc, h.k, ka * A.x + kb * Bv.x, ka * A.y + kb * Bv.y, ka * A.z + kb * Bv.z);
-                if (ENERGY) {
-                    const float cdel = cn * h.cos_ph + sn * h.sin_ph;
-                    e_acc += (double)(h.kd * (1.0f + cdel));
-                }
+                float3 fi, fj, fk, fl;
+                dihedral_force<ENERGY>(f3(pos[h.i]), f3(pos[h.j]), f3(pos[h.k]), f3(pos[h.l]),
+                                       make_float4(h.kd, h.n, h.cos_ph, h.sin_ph), fi, fj, fk, fl,
+                                       e_acc);
+                add_force(frc, h.i, fi.x, fi.y, fi.z);
+                add_force(frc, h.j, fj.x, fj.y, fj.z);
+                add_force(frc, h.k, fk.x, fk.y, fk.z);
+                add_force(frc, h.l, fl.x, fl.y, fl.z);
             }
             __syncwarp(gmask);
         }
     }
-    // 1-4 pairs with scaled Lennard-Jones and Coulomb
     {
         const Pair14Rec* rec = reinterpret_cast<const Pair14Rec*>(sm + lay.off_p14);
         const int* cs = colors + 3 * (kMaxColors + 1);
         for (int c = 0; c < lay.n_colors[3]; ++c) {
             for (int t = cs[c] + g; t < cs[c + 1]; t += L) {
                 const Pair14Rec q = rec[t];
-                const float4 ci = prm[q.i], cj = prm[q.j];
-                const float3 d = sub3(pos[q.j], pos[q.i]);
-                const float r2 = dot3(d, d);
-                const float rinv = rsqrtf(r2);
-                const float rinv2 = rinv * rinv;
-                const float sig = ci.x + cj.x;
-                const float s2 = sig * sig * rinv2;
-                const float s6 = s2 * s2 * s2;
-                const float eps = ci.y * cj.y;
-                const float cq = q.s_c * ci.z * cj.z * rinv;
-                const float lj = q.s_lj * eps * s6 * fmaf(2.0f, s6, -1.0f);
-                const float fs = (lj + cq) * rinv2;
-                add_force(frc, q.i, -fs * d.x, -fs * d.y, -fs * d.z);
-                add_force(frc, q.j, fs * d.x, fs * d.y, fs * d.z);
-                if (ENERGY)
-                    e_acc += (double)(q.s_lj * (eps * (1.0f / 6.0f)) * s6 * (s6 - 1.0f) + cq);
+                const float3 f = pair14_force<ENERGY>(f3(pos[q.i]), f3(pos[q.j]), prm[q.i], prm[q.j],
+                                                      q.s_lj, q.s_c, e_acc);
+                add_force(frc, q.i, f.x, f.y, f.z);
+                add_force(frc, q.j, -f.x, -f.y, -f.z);
             }
             __syncwarp(gmask);
         }
     }
 }
 
+// Chain bonded pass (B >= 3): the lane's terms start in its block; atom
+// offsets o = 0..B+2 relative to the block start, o >= B in the next block.
+template <int B, bool ENERGY>
+__device__ __forceinline__ void bonded_chain(const unsigned char* sm, const TopoLayout& lay,
+                                             const float4* prm, const float4* pos, float4* frc,
+                                             int L, int g, const float (&xi)[B],
+                                             const float (&yi)[B], const float (&zi)[B],
+                                             float (&fx)[B], float (&fy)[B], float (&fz)[B],
+                                             double& e_acc) {
+    static_assert(B >= 3, "chain pass needs three atoms per lane");
+    using C = PropCfg<B>;
+    const int i0 = g * B;
+    const int N = lay.n_atoms;
+    if (i0 + 1 >= N) return;  // no term starts here
+    const bool has_next = (g + 1 < L);
+    const int nbase = (g + 1) * C::BS;
+    float3 sp[3];
+    float3 sf[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        sp[m] = has_next ? f3(pos[nbase + m]) : make_float3(0.f, 0.f, 0.f);
+        sf[m] = make_float3(0.f, 0.f, 0.f);
+    }
+    auto P = [&](int o) -> float3 {
+        return (o < B) ? make_float3(xi[o < B ? o : 0], yi[o < B ? o : 0], zi[o < B ? o : 0])
+                       : sp[o >= B ? o - B : 0];
+    };
+    auto F = [&](int o, float3 f) {
+        if (o < B) {
+            fx[o < B ? o : 0] += f.x;
+            fy[o < B ? o : 0] += f.y;
+            fz[o < B ? o : 0] += f.z;
+        } else {
+            float3& s = sf[o >= B ? o - B : 0];
+            s.x += f.x;
+            s.y += f.y;
+            s.z += f.z;
+        }
+    };
+    const float2* cb = reinterpret_cast<const float2*>(sm + lay.off_cbond);
+    const float2* ca = reinterpret_cast<const float2*>(sm + lay.off_cangle);
+    const float4* cd = reinterpret_cast<const float4*>(sm + lay.off_cdih);
+#pragma unroll
+    for (int a = 0; a < B; ++a) {
+        const int d = i0 + a;
+        if (d + 1 < N) {  // bond (d, d+1)
+            const float2 q = cb[d];
+            const float3 f = bond_force<ENERGY>(P(a), P(a + 1), q.x, q.y, e_acc);
+            F(a, f);
+            F(a + 1, make_float3(-f.x, -f.y, -f.z));
+        }
+        if (d + 2 < N) {  // angle (d, d+1, d+2)
+            const float2 q = ca[d];
+            float3 fi, fj, fk;
+            angle_force<ENERGY>(P(a), P(a + 1), P(a + 2), q.x, q.y, fi, fj, fk, e_acc);
+            F(a, fi);
+            F(a + 1, fj);
+            F(a + 2, fk);
+        }
+        if (d + 3 < N) {  // dihedral (d..d+3) and 1-4 pair (d, d+3)
+            float3 fi, fj, fk, fl;
+            dihedral_force<ENERGY>(P(a), P(a + 1), P(a + 2), P(a + 3), cd[d], fi, fj, fk, fl,
+                                   e_acc);
+            F(a, fi);
+            F(a + 1, fj);
+            F(a + 2, fk);
+            F(a + 3, fl);
+            const int s0 = g * C::BS + a;
+            const int s3 = (a + 3 < B) ? (s0 + 3) : (nbase + a + 3 - B);
+            const float3 f = pair14_force<ENERGY>(P(a), P(a + 3), prm[s0], prm[s3], lay.s14_lj,
+                                                  lay.s14_c, e_acc);
+            F(a, f);
+            F(a + 3, make_float3(-f.x, -f.y, -f.z));
+        }
+    }
+    if (has_next) {
+#pragma unroll
+        for (int m = 0; m < 3; ++m) add_force(frc, nbase + m, sf[m].x, sf[m].y, sf[m].z);
+    }
+}
+
 // Forces on the lane's B atoms (registers fx, fy, fz); positions must already
 // be in shared memory and the lane's force slots zeroed, with a __syncwarp
 // after both.
-template <int L, int B, bool ENERGY>
+template <int B, bool CHAIN, bool ENERGY>
 __device__ __forceinline__ void compute_forces(const unsigned char* sm, const TopoLayout& lay,
                                                const float4* prm, const float4* pos, float4* frc,
-                                               const unsigned long long* masks, int g,
+                                               const unsigned long long* masks, int L, int g,
                                                unsigned gmask, const float (&xi)[B],
                                                const float (&yi)[B], const float (&zi)[B],
                                                const float (&hsi)[B], const float (&sei)[B],
                                                const float (&qi)[B], float (&fx)[B],
                                                float (&fy)[B], float (&fz)[B], double& e_acc) {
-    using C = PropCfg<L, B>;
+    using C = PropCfg<B>;
 #pragma unroll
     for (int a = 0; a < B; ++a) fx[a] = fy[a] = fz[a] = 0.0f;
     // pairs inside the lane's own block (always masked: 1-2/1-3/1-4 live here)
@@ -280,11 +397,13 @@ __device__ __forceinline__ void compute_forces(const unsigned char* sm, const To
         }
     }
     // half ring over partner blocks
+    const int TH = L / 2;
 #pragma unroll 1
-    for (int t = 1; t <= C::TH; ++t) {
-        const bool active = (t < C::TH) || (g < C::TH);
+    for (int t = 1; t <= TH; ++t) {
+        const bool active = !(2 * t == L && g >= t);
         if (active) {
-            const int J = (g + t) & (L - 1);
+            int J = g + t;
+            J = (J >= L) ? J - L : J;
             float4 pj[B], cj[B];
             float fxj[B], fyj[B], fzj[B];
 #pragma unroll
@@ -305,7 +424,11 @@ __device__ __forceinline__ void compute_forces(const unsigned char* sm, const To
         }
         __syncwarp(gmask);
     }
-    bonded_forces<L, ENERGY>(sm, lay, prm, pos, frc, g, gmask, e_acc);
+    if constexpr (CHAIN)
+        bonded_chain<B, ENERGY>(sm, lay, prm, pos, frc, L, g, xi, yi, zi, fx, fy, fz, e_acc);
+    else
+        bonded_colored<ENERGY>(sm, lay, prm, pos, frc, L, g, gmask, e_acc);
+    __syncwarp(gmask);
 #pragma unroll
     for (int a = 0; a < B; ++a) {
         const float4 f = frc[g * C::BS + a];
@@ -315,16 +438,16 @@ __device__ __forceinline__ void compute_forces(const unsigned char* sm, const To
     }
 }
 
-template <int L>
-__device__ __forceinline__ double group_sum(double v, unsigned gmask) {
-#pragma unroll
-    for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(gmask, v, o);
-    return v;
+// Sum over the L lanes of a group (any L), result in every lane.
+__device__ __forceinline__ double group_sum(double v, unsigned gmask, int base, int L) {
+    double s = 0.0;
+    for (int q = 0; q < L; ++q) s += __shfl_sync(gmask, v, base + q);
+    return s;
 }
 
-template <int L, int B>
-__global__ void __launch_bounds__(256, 1) propagate_kernel(const PropParams p) {
-    using C = PropCfg<L, B>;
+template <int B, bool CHAIN>
+__global__ void __launch_bounds__(256, PAMD_PROP_MIN_BLOCKS) propagate_kernel(const PropParams p) {
+    using C = PropCfg<B>;
     extern __shared__ float4 smem4[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(smem4);
     const TopoLayout& lay = p.lay;
@@ -337,15 +460,19 @@ __global__ void __launch_bounds__(256, 1) propagate_kernel(const PropParams p) {
     const unsigned long long* masks = reinterpret_cast<const unsigned long long*>(sm + lay.off_masks);
     float4* slots = smem4 + lay.bytes / 16;
 
+    const int L = lay.lanes;
+    const int G = 32 / L;
     const int lane = threadIdx.x & 31;
     const int grp = lane / L;
-    const int g = lane % L;
-    const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << (grp * L));
-    const int groups_per_warp = 32 / L;
-    const int slot_local = (threadIdx.x >> 5) * groups_per_warp + grp;
-    const int rpb = (blockDim.x >> 5) * groups_per_warp;
-    float4* pos = slots + slot_local * C::SLOT;
-    float4* frc = pos + C::NK;
+    if (grp >= G) return;  // idle lanes when L does not divide 32
+    const int g = lane - grp * L;
+    const int base = grp * L;
+    const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << base);
+    const int slot_local = (threadIdx.x >> 5) * G + grp;
+    const int rpb = (blockDim.x >> 5) * G;
+    const int slot_f4 = 2 * lay.nk + 1;
+    float4* pos = slots + slot_local * slot_f4;
+    float4* frc = pos + lay.nk;
 
     const int N = lay.n_atoms, Np = lay.n_pad;
     const uint32_t step_base = (p.dev_counters ? p.dev_counters[0] : 0u) + p.step0;
@@ -384,11 +511,11 @@ __global__ void __launch_bounds__(256, 1) propagate_kernel(const PropParams p) {
         float fx[B], fy[B], fz[B];
         double e_acc = 0.0;
         if (p.theta == 0)
-            compute_forces<L, B, true>(sm, lay, prm, pos, frc, masks, g, gmask, xi, yi, zi, hsi,
-                                       sei, qi, fx, fy, fz, e_acc);
+            compute_forces<B, CHAIN, true>(sm, lay, prm, pos, frc, masks, L, g, gmask, xi, yi, zi,
+                                           hsi, sei, qi, fx, fy, fz, e_acc);
         else
-            compute_forces<L, B, false>(sm, lay, prm, pos, frc, masks, g, gmask, xi, yi, zi, hsi,
-                                        sei, qi, fx, fy, fz, e_acc);
+            compute_forces<B, CHAIN, false>(sm, lay, prm, pos, frc, masks, L, g, gmask, xi, yi, zi,
+                                            hsi, sei, qi, fx, fy, fz, e_acc);
 
         for (int s = 0; s < p.theta; ++s) {
             const uint32_t step = step_base + (uint32_t)s;
@@ -416,11 +543,11 @@ __global__ void __launch_bounds__(256, 1) propagate_kernel(const PropParams p) {
             }
             __syncwarp(gmask);
             if (s == p.theta - 1)
-                compute_forces<L, B, true>(sm, lay, prm, pos, frc, masks, g, gmask, xi, yi, zi,
-                                           hsi, sei, qi, fx, fy, fz, e_acc);
+                compute_forces<B, CHAIN, true>(sm, lay, prm, pos, frc, masks, L, g, gmask, xi, yi,
+                                               zi, hsi, sei, qi, fx, fy, fz, e_acc);
             else
-                compute_forces<L, B, false>(sm, lay, prm, pos, frc, masks, g, gmask, xi, yi, zi,
-                                            hsi, sei, qi, fx, fy, fz, e_acc);
+                compute_forces<B, CHAIN, false>(sm, lay, prm, pos, frc, masks, L, g, gmask, xi, yi,
+                                                zi, hsi, sei, qi, fx, fy, fz, e_acc);
 #pragma unroll
             for (int a = 0; a < B; ++a) {                   // B
                 vx[a] = fmaf(p.hdt * im[a], fx[a], vx[a]);
@@ -457,11 +584,11 @@ __global__ void __launch_bounds__(256, 1) propagate_kernel(const PropParams p) {
                 cz += zi[a];
             }
         }
-        const double E = group_sum<L>(e_acc, gmask);
-        ek = group_sum<L>(ek, gmask);
-        cx = group_sum<L>(cx, gmask) / N;
-        cy = group_sum<L>(cy, gmask) / N;
-        cz = group_sum<L>(cz, gmask) / N;
+        const double E = group_sum(e_acc, gmask, base, L);
+        ek = group_sum(ek, gmask, base, L);
+        cx = group_sum(cx, gmask, base, L) / N;
+        cy = group_sum(cy, gmask, base, L) / N;
+        cz = group_sum(cz, gmask, base, L) / N;
         double r2 = 0.0;
 #pragma unroll
         for (int a = 0; a < B; ++a) {
@@ -471,7 +598,7 @@ __global__ void __launch_bounds__(256, 1) propagate_kernel(const PropParams p) {
                 r2 += dx * dx + dy * dy + dz * dz;
             }
         }
-        r2 = group_sum<L>(r2, gmask);
+        r2 = group_sum(r2, gmask, base, L);
         if (g == 0) {
             p.E[k] = E;
             p.ke[k] = ek;
@@ -483,10 +610,10 @@ __global__ void __launch_bounds__(256, 1) propagate_kernel(const PropParams p) {
     }
 }
 
-template <int L, int B>
+template <int B, bool CHAIN>
 cudaError_t propagate_launch_one(const PropParams* p, int warps, int grid, size_t smem,
                                  cudaStream_t s, int* blocks_per_sm) {
-    auto kern = propagate_kernel<L, B>;
+    auto kern = propagate_kernel<B, CHAIN>;
     static size_t configured = 0;
     if (smem > configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -499,20 +626,13 @@ cudaError_t propagate_launch_one(const PropParams* p, int warps, int grid, size_
     return cudaGetLastError();
 }
 
-template <int L>
-cudaError_t propagate_dispatch(const PropParams* p, int per_lane, int warps, int grid, size_t smem,
-                               cudaStream_t s, int* blocks_per_sm) {
-    switch (per_lane) {
-        case 1: return propagate_launch_one<L, 1>(p, warps, grid, smem, s, blocks_per_sm);
-        case 2: return propagate_launch_one<L, 2>(p, warps, grid, smem, s, blocks_per_sm);
-        case 3: return propagate_launch_one<L, 3>(p, warps, grid, smem, s, blocks_per_sm);
-        case 4: return propagate_launch_one<L, 4>(p, warps, grid, smem, s, blocks_per_sm);
-        case 5: return propagate_launch_one<L, 5>(p, warps, grid, smem, s, blocks_per_sm);
-        case 6: return propagate_launch_one<L, 6>(p, warps, grid, smem, s, blocks_per_sm);
-        case 7: return propagate_launch_one<L, 7>(p, warps, grid, smem, s, blocks_per_sm);
-        case 8: return propagate_launch_one<L, 8>(p, warps, grid, smem, s, blocks_per_sm);
-        default: return cudaErrorInvalidValue;
+template <int B>
+cudaError_t propagate_dispatch_b(const PropParams* p, bool chain, int warps, int grid, size_t smem,
+                                 cudaStream_t s, int* blocks_per_sm) {
+    if constexpr (B >= 3) {
+        if (chain) return propagate_launch_one<B, true>(p, warps, grid, smem, s, blocks_per_sm);
     }
+    return propagate_launch_one<B, false>(p, warps, grid, smem, s, blocks_per_sm);
 }
 
 }  // namespace pamd

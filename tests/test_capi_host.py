@@ -61,7 +61,8 @@ def test_argument_validation_before_device_use(lib):
     top = pi.make_chain(10, 1)
     assert _init_rc(top, R=0)[0] == pamd.PAMD_EINVAL
     assert _init_rc(top, T0=-1.0)[0] == pamd.PAMD_EINVAL
-    assert _init_rc(top, lanes_per_replica=5)[0] == pamd.PAMD_EINVAL
+    assert _init_rc(top, lanes_per_replica=33)[0] == pamd.PAMD_EINVAL
+    assert _init_rc(top, lanes_per_replica=-1)[0] == pamd.PAMD_EINVAL
     assert _init_rc(top, lanes_per_replica=4, warps_per_block=9)[0] == pamd.PAMD_EINVAL
     assert _init_rc(top, precision=7)[0] == pamd.PAMD_EUNSUPPORTED
     bad = pi.make_chain(10, 1)
