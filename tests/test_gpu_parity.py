@@ -82,6 +82,34 @@ def test_forces_and_energies(lib, orc, n, lanes):
         assert abs(eg[k] - eo[k]) <= 1e-5 * max(scale[k], 1e-3), (k, eg[k], eo[k])
 
 
+@pytest.mark.parametrize("n", [13, 40, 75])
+def test_forces_relabelled_chain(lib, orc, n):
+    """Atoms of a chain relabelled at random: the bonded terms are no longer a
+    chain in index order and exclusions fall in every tile (generic path)."""
+    base = pi.make_chain(n, 5)
+    perm = np.random.default_rng(n).permutation(n)   # new index of old atom i
+    inv = np.argsort(perm)
+    top = pi.make_chain(n, 5)
+    for name in ("mass", "charge", "sigma", "epsilon"):
+        setattr(top, name, getattr(base, name)[inv])
+    top.x0 = base.x0[inv]
+    for name in ("bond", "angle", "dihedral", "excl", "pair14"):
+        setattr(top, name, perm[getattr(base, name)].astype(np.int32))
+    R = 4
+    x = f32(pi.perturbed_positions(top, R, 0.01, 9))
+    ctx = lib.pamd_init(top, R, 300.0, 1)
+    try:
+        lib.pamd_set_state(ctx, x, np.zeros_like(x))
+        fg, eg = lib.pamd_forces(ctx)
+    finally:
+        lib.pamd_destroy(ctx)
+    fo, eo, scale = _oracle_forces(orc, top, x)
+    for k in range(R):
+        rms = math.sqrt(np.mean(fo[k] ** 2))
+        assert math.sqrt(np.mean((fg[k] - fo[k]) ** 2)) <= 1e-5 * rms
+        assert abs(eg[k] - eo[k]) <= 1e-5 * scale[k]
+
+
 def test_forces_excluded_overlapping_pairs(lib, orc):
     # bonds-only chain: every pair excluded, atoms may sit on top of each other
     top = pi.make_harmonic_chain(9, 400.0, 0.0, seed=3)
