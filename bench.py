@@ -224,6 +224,7 @@ def run_gpu(args, w):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     pop = pamd.Population(top, R, temps[0], seed, pamd.torch_options(gamma_per_ps=w["gamma"]))
+    tune = pamd.pamd_autotune(pop.ctx, 50)   # launch shape by measurement (untimed)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     def one_anneal():
@@ -322,7 +323,8 @@ def run_gpu(args, w):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": config_of(w, args), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+        "config": dict(config_of(w, args), launch_shape=tune), "roofline": roofline,
+        "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": int(launches), "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -349,6 +351,8 @@ def run_kernel(args, w):
     opts = pamd.torch_options(gamma_per_ps=w["gamma"], lanes_per_replica=args.lanes,
                               warps_per_block=args.warps)
     pop = pamd.Population(top, R, w["T0"], w["seed"], opts)
+    if args.autotune:
+        pop.autotune(50)
     info = pop.info()
     for _ in range(args.warmup):
         pamd.pamd_propagate(pop.ctx, theta, w["dt"], w["T0"])
@@ -384,6 +388,7 @@ def main():
     ap.add_argument("--replicas", type=int, default=0, help="kernel mode: population size")
     ap.add_argument("--lanes", type=int, default=0, help="kernel mode: lanes per replica")
     ap.add_argument("--warps", type=int, default=0, help="kernel mode: warps per block")
+    ap.add_argument("--autotune", action="store_true", help="kernel mode: tune the launch shape")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.mode == "kernel":

@@ -104,6 +104,7 @@ typedef struct pamd_options {
     int32_t lanes_per_replica;  /* 0 = choose; else 4, 8, 16 or 32 */
     int32_t warps_per_block;    /* 0 = choose (4); else 1..8 */
     int32_t mol_id;             /* molecule index mixed into the random counters */
+    int32_t autotune;           /* 1: pamd_autotune(ctx, 20, NULL) at the end of pamd_init */
     void* (*dev_alloc)(size_t bytes, void* user); /* NULL = cudaMalloc */
     void (*dev_free)(void* ptr, void* user);      /* NULL = cudaFree */
     void* alloc_user;
@@ -227,13 +228,37 @@ int pamd_set_state(pamd_ctx* ctx, const double* x, const double* v, const double
  */
 int pamd_forces(pamd_ctx* ctx, double* f, double* E);
 
+/* Launch shape of the propagate kernel. */
+typedef struct pamd_tune {
+    int32_t lanes_per_replica; /* L: lanes of one warp that share a replica */
+    int32_t atoms_per_lane;    /* B: atoms each lane owns */
+    int32_t warps_per_block;
+    int32_t from_cache;        /* 1 if the shape came from the cache */
+    double ms;                 /* probe time of the chosen shape (0 if cached) */
+} pamd_tune;
+
+/*
+ * Launch-shape autotuner (no counterpart in the paper; it picks how the
+ * replica-parallel work of step 3 maps onto the GPU).  For every feasible
+ * shape -- B = 1..8 atoms per lane with L = ceil(N/B) <= 32 lanes per replica
+ * (fixed to the requested lanes_per_replica if one was given), and 2, 4 or 8
+ * warps per block -- one propagate launch of theta_probe steps over the whole
+ * population is timed on a scratch copy; the fastest shape is kept.  The
+ * population, energies, counters and observables are left unchanged.  The
+ * choice is cached in the process per (N, R, chain layout) and, when the
+ * environment variable PAMD_TUNE_CACHE names a file, in that file.
+ * theta_probe: 1..1000.  out: chosen shape, or NULL.  Synchronises the
+ * stream; must not be called while the stream is being captured.
+ */
+int pamd_autotune(pamd_ctx* ctx, int32_t theta_probe, pamd_tune* out);
+
 /* Random-counter state: global MD step and resampling index.  A restarted
  * run that restores both (with the same seed and population) continues
  * bit-identically. */
 int pamd_get_counters(pamd_ctx* ctx, uint32_t* step, uint32_t* resample_index, double* sum_lnQ);
 int pamd_set_counters(pamd_ctx* ctx, uint32_t step, uint32_t resample_index, double sum_lnQ);
 
-/* Number of replicas and atoms; the launch shape picked for propagate. */
+/* Number of replicas and atoms; the launch shape in use for propagate. */
 int pamd_info(pamd_ctx* ctx, int64_t* R, int32_t* n_atoms, int32_t* lanes_per_replica,
               int32_t* atoms_per_lane, int32_t* replicas_per_block);
 

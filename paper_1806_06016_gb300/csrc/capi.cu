@@ -7,7 +7,10 @@
 // whole anneal into one CUDA graph.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -183,7 +186,8 @@ bool is_linear_chain(const pamd_topology* t) {
 }
 
 // Build the shared-memory table of the propagate kernel.
-int build_topology(pamd_ctx* c, const pamd_topology* t, int lanes_req, std::vector<unsigned char>& blob) {
+int build_topology(const pamd_topology* t, int lanes_req, TopoLayout* lay_out,
+                   std::vector<unsigned char>& blob) {
     const int N = t->n_atoms;
     if (N < 1) return fail(PAMD_EINVAL, "n_atoms must be >= 1");
     if (N > PAMD_MAX_ATOMS) return fail(PAMD_EUNSUPPORTED, "n_atoms exceeds PAMD_MAX_ATOMS");
@@ -220,7 +224,7 @@ int build_topology(pamd_ctx* c, const pamd_topology* t, int lanes_req, std::vect
 
     int L, B;
     if ((rc = choose_lanes(N, lanes_req, &L, &B))) return rc;
-    TopoLayout& lay = c->lay;
+    TopoLayout& lay = *lay_out;
     lay = TopoLayout{};
     lay.n_atoms = N;
     lay.n_pad = round_up(N, 4);
@@ -399,14 +403,14 @@ float* cur_state(pamd_ctx* c) { return c->cur_is_alt ? c->b.state_alt : c->b.sta
 double* cur_E(pamd_ctx* c) { return c->cur_is_alt ? c->b.E_alt : c->b.E; }
 int32_t* cur_fam(pamd_ctx* c) { return c->cur_is_alt ? c->b.fam_alt : c->b.fam; }
 
-int launch_prop(pamd_ctx* c, int theta, double dt, double T, const uint32_t* dev_ctr,
-                uint32_t step0, float* fout) {
+int launch_prop_on(pamd_ctx* c, float* state, double* E, double* ke, double* rg, int theta,
+                   double dt, double T, const uint32_t* dev_ctr, uint32_t step0, float* fout) {
     PropParams p{};
-    p.state_in = cur_state(c);
-    p.state_out = cur_state(c);
-    p.E = cur_E(c);
-    p.ke = c->b.ke;
-    p.rg = c->b.rg;
+    p.state_in = state;
+    p.state_out = state;
+    p.E = E;
+    p.ke = ke;
+    p.rg = rg;
     p.fout = fout;
     p.masses = c->b.masses;
     p.topo = c->b.topo;
@@ -426,6 +430,89 @@ int launch_prop(pamd_ctx* c, int theta, double dt, double T, const uint32_t* dev
                                            prop_smem(c), c->stream, nullptr);
     c->launches += 1;
     if (e != cudaSuccess) return cuda_fail(c, e, "propagate launch");
+    return PAMD_OK;
+}
+
+int launch_prop(pamd_ctx* c, int theta, double dt, double T, const uint32_t* dev_ctr,
+                uint32_t step0, float* fout) {
+    return launch_prop_on(c, cur_state(c), cur_E(c), c->b.ke, c->b.rg, theta, dt, T, dev_ctr,
+                          step0, fout);
+}
+
+// In-process cache of tuned shapes, mirrored to the file named by
+// PAMD_TUNE_CACHE ("N R chain lanes_req -> L warps" per line).
+struct TuneKey {
+    int N;
+    long long R;
+    int chain;
+    int lanes_req;
+};
+std::mutex g_tune_mu;
+std::vector<std::pair<TuneKey, std::pair<int, int>>> g_tune;
+
+bool tune_cache_lookup(const TuneKey& k, int* L, int* W) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto match = [&](const TuneKey& q) {
+        return q.N == k.N && q.R == k.R && q.chain == k.chain && q.lanes_req == k.lanes_req;
+    };
+    for (auto& e : g_tune)
+        if (match(e.first)) {
+            *L = e.second.first;
+            *W = e.second.second;
+            return true;
+        }
+    const char* path = std::getenv("PAMD_TUNE_CACHE");
+    if (!path || !*path) return false;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return false;
+    TuneKey q;
+    int l, w;
+    bool found = false;
+    while (std::fscanf(f, "%d %lld %d %d %d %d", &q.N, &q.R, &q.chain, &q.lanes_req, &l, &w) == 6) {
+        if (match(q) && l >= 1 && l <= 32 && (w == 2 || w == 4 || w == 8)) {
+            *L = l;
+            *W = w;
+            found = true;
+        }
+    }
+    std::fclose(f);
+    if (found) g_tune.push_back({k, {*L, *W}});
+    return found;
+}
+
+void tune_cache_store(const TuneKey& k, int L, int W) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.push_back({k, {L, W}});
+    const char* path = std::getenv("PAMD_TUNE_CACHE");
+    if (!path || !*path) return;
+    if (FILE* f = std::fopen(path, "a")) {
+        std::fprintf(f, "%d %lld %d %d %d %d\n", k.N, k.R, k.chain, k.lanes_req, L, W);
+        std::fclose(f);
+    }
+}
+
+// Warps per block (<= requested, shared memory permitting), replicas per
+// block and the persistent grid for layout `lay`.
+int set_launch_shape(pamd_ctx* c, const TopoLayout& lay, int warps_req) {
+    int dev = 0, max_smem = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int groups_per_warp = 32 / lay.lanes;  // idle lanes when L does not divide 32
+    int warps = warps_req ? warps_req : 4;
+    auto smem = [&](int w) {
+        return (long long)lay.bytes + (long long)w * groups_per_warp * (2 * lay.nk + 1) * 16;
+    };
+    while (smem(warps) > max_smem && warps > 1) --warps;
+    if (smem(warps) > max_smem) return fail(PAMD_EUNSUPPORTED, "molecule tables exceed shared memory");
+    int occ = 0;
+    cudaError_t e = propagate_dispatch_any(lay, nullptr, warps, 0, (size_t)smem(warps), nullptr, &occ);
+    if (e != cudaSuccess || occ < 1)
+        return fail(PAMD_ECUDA, std::string("propagate occupancy: ") + cudaGetErrorString(e));
+    c->lay = lay;
+    c->warps_per_block = warps;
+    c->rpb = warps * groups_per_warp;
+    const long long batches = (c->R + c->rpb - 1) / c->rpb;
+    c->grid_prop = (int)std::min<long long>(batches, (long long)c->num_sms * occ);
     return PAMD_OK;
 }
 
@@ -501,13 +588,16 @@ int pamd_init(pamd_ctx** out, const pamd_topology* top, int64_t R, double T0, ui
     c->dev_free = o.dev_free;
     c->alloc_user = o.alloc_user;
     std::vector<unsigned char> blob;
-    int rc = build_topology(c, top, o.lanes_per_replica, blob);
+    TopoLayout lay0;
+    int rc = build_topology(top, o.lanes_per_replica, &lay0, blob);
     if (rc) {
         delete c;
         return rc;
     }
-    c->N = c->lay.n_atoms;
-    c->Np = c->lay.n_pad;
+    c->host_top.assign(top);
+    c->lanes_req = o.lanes_per_replica;
+    c->N = lay0.n_atoms;
+    c->Np = lay0.n_pad;
     auto bail = [&](int code, const std::string& m) {
         free_all(c);
         if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -526,23 +616,10 @@ int pamd_init(pamd_ctx** out, const pamd_topology* top, int64_t R, double T0, ui
         c->own_stream = true;
     }
     // launch shape
-    const int groups_per_warp = 32 / c->lay.lanes;  // idle lanes when L does not divide 32
-    int warps = o.warps_per_block ? o.warps_per_block : 4;
-    int max_smem = 0;
-    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    for (;;) {
-        c->warps_per_block = warps;
-        c->rpb = warps * groups_per_warp;
-        if ((long long)prop_smem(c) <= max_smem || warps == 1) break;
-        --warps;
+    if ((rc = set_launch_shape(c, lay0, o.warps_per_block))) {
+        const std::string m = g_err;
+        return bail(rc, m);
     }
-    if ((long long)prop_smem(c) > max_smem) return bail(PAMD_EUNSUPPORTED, "molecule tables exceed shared memory");
-    int occ = 0;
-    cudaError_t e = propagate_dispatch_any(c->lay, nullptr, c->warps_per_block, 0, prop_smem(c),
-                                           nullptr, &occ);
-    if (e != cudaSuccess || occ < 1) return bail(PAMD_ECUDA, std::string("propagate occupancy: ") + cudaGetErrorString(e));
-    const long long batches = (R + c->rpb - 1) / c->rpb;
-    c->grid_prop = (int)std::min<long long>(batches, (long long)c->num_sms * occ);
 
     // host-side tables
     c->host_mass.assign(top->mass, top->mass + c->N);
@@ -570,6 +647,7 @@ int pamd_init(pamd_ctx** out, const pamd_topology* top, int64_t R, double T0, ui
     b.rg = (double*)dalloc(c, sizeof(double) * R);
     b.masses = (float*)dalloc(c, sizeof(float) * c->Np);
     b.topo = (unsigned char*)dalloc(c, blob.size());
+    c->topo_cap = blob.size();
     b.x0 = (float*)dalloc(c, sizeof(float) * 3 * c->Np);
     b.W = (unsigned long long*)dalloc(c, 8 * (size_t)R);
     b.C = (unsigned long long*)dalloc(c, 8 * (size_t)R);
@@ -597,6 +675,13 @@ int pamd_init(pamd_ctx** out, const pamd_topology* top, int64_t R, double T0, ui
               launch_set_counters(c, 0, 0) == cudaSuccess &&
               cudaStreamSynchronize(c->stream) == cudaSuccess;
     if (!ok) return bail(PAMD_ECUDA, std::string("initialisation: ") + cudaGetErrorString(cudaGetLastError()));
+    if (o.autotune) {
+        const int r = pamd_autotune(c, 20, nullptr);
+        if (r) {
+            const std::string m = g_err;
+            return bail(r, "autotune: " + m);
+        }
+    }
     *out = c;
     return PAMD_OK;
 }
@@ -805,6 +890,104 @@ int pamd_forces(pamd_ctx* c, double* f, double* E) {
             for (int q = 0; q < 3; ++q)
                 f[((size_t)k * N + i) * 3 + q] = fo[(size_t)k * 3 * Np + (size_t)q * Np + i];
     return read_status(c);
+}
+
+int pamd_autotune(pamd_ctx* c, int32_t theta_probe, pamd_tune* out) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (theta_probe < 1 || theta_probe > 1000) return fail(PAMD_EINVAL, "theta_probe must be 1..1000");
+    const pamd_topology t = c->host_top.view();
+    const int chain = (int)is_linear_chain(&t);
+    const TuneKey key{c->N, c->R, chain, c->lanes_req};
+    int L = 0, W = 0;
+    double best_ms = 0.0;
+    bool cached = tune_cache_lookup(key, &L, &W);
+    std::vector<unsigned char> blob;
+    TopoLayout lay;
+    auto apply = [&](int lanes, int warps) -> int {
+        int r = build_topology(&t, lanes, &lay, blob);
+        if (r) return r;
+        if (blob.size() > c->topo_cap) {
+            void* p = dalloc(c, blob.size());
+            if (!p) return fail(PAMD_ENOMEM, "topology table");
+            c->b.topo = (unsigned char*)p;
+            c->topo_cap = blob.size();
+        }
+        PAMD_CU(c, cudaMemcpyAsync(c->b.topo, blob.data(), blob.size(), cudaMemcpyHostToDevice, c->stream));
+        PAMD_CU(c, cudaStreamSynchronize(c->stream));
+        return set_launch_shape(c, lay, warps);
+    };
+    if (!cached) {
+        // scratch copy of the population; per-replica outputs go to scratch too
+        const size_t st_bytes = sizeof(float) * 6 * (size_t)c->Np * (size_t)c->R;
+        float* scratch = c->cur_is_alt ? c->b.state : c->b.state_alt;
+        double* e_scr = c->cur_is_alt ? c->b.E : c->b.E_alt;
+        double* ke_scr = reinterpret_cast<double*>(c->b.W);
+        double* rg_scr = reinterpret_cast<double*>(c->b.C);
+        cudaEvent_t e0, e1;
+        PAMD_CU(c, cudaEventCreate(&e0));
+        PAMD_CU(c, cudaEventCreate(&e1));
+        double best = 1e300;
+        std::vector<std::pair<int, int>> shapes;
+        for (int b = 1; b <= 8; ++b) {
+            int l = c->lanes_req ? c->lanes_req : (c->N + b - 1) / b;
+            if (l > 32) continue;
+            int bb = (c->N + l - 1) / l;
+            if (bb > 8) continue;
+            l = (c->N + bb - 1) / bb;
+            bool dup = false;
+            for (auto& s2 : shapes) dup = dup || s2.first == l;
+            if (!dup) shapes.emplace_back(l, bb);
+        }
+        int err = PAMD_OK;
+        for (auto& sh : shapes) {
+            for (int warps : {2, 4, 8}) {
+                if ((err = apply(sh.first, warps))) break;
+                if (c->warps_per_block != warps) continue;  // shared memory capped it
+                cudaMemcpyAsync(scratch, cur_state(c), st_bytes, cudaMemcpyDeviceToDevice, c->stream);
+                if ((err = launch_prop_on(c, scratch, e_scr, ke_scr, rg_scr, 1, 0.001, 300.0, nullptr,
+                                          c->step, nullptr)))
+                    break;
+                cudaEventRecord(e0, c->stream);
+                if ((err = launch_prop_on(c, scratch, e_scr, ke_scr, rg_scr, theta_probe, 0.001, 300.0,
+                                          nullptr, c->step, nullptr)))
+                    break;
+                cudaEventRecord(e1, c->stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    err = cuda_fail(c, cudaGetLastError(), "autotune");
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) {
+                    best = ms;
+                    L = sh.first;
+                    W = warps;
+                }
+            }
+            if (err) break;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (err) return err;
+        if (best == 1e300) return fail(PAMD_EUNSUPPORTED, "no feasible launch shape");
+        best_ms = best;
+        tune_cache_store(key, L, W);
+    }
+    if ((rc = apply(L, W))) return rc;
+    if (c->graph_exec) {  // captured launches carry the old shape
+        cudaGraphExecDestroy(c->graph_exec);
+        c->graph_exec = nullptr;
+        c->graph_key = GraphKey{};
+    }
+    if (out) {
+        out->lanes_per_replica = c->lay.lanes;
+        out->atoms_per_lane = c->lay.per_lane;
+        out->warps_per_block = c->warps_per_block;
+        out->from_cache = cached ? 1 : 0;
+        out->ms = best_ms;
+    }
+    return PAMD_OK;
 }
 
 int pamd_get_counters(pamd_ctx* c, uint32_t* step, uint32_t* ridx, double* sum_lnQ) {

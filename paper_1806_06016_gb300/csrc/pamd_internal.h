@@ -120,6 +120,51 @@ struct GraphKey {
 
 }  // namespace pamd
 
+namespace pamd {
+// Copy of the caller's topology, kept so that the launch shape can be
+// re-chosen (autotuning) after pamd_init returned.
+struct HostTopology {
+    int32_t n_atoms = 0;
+    std::vector<double> mass, charge, sigma, epsilon, x0, bond_r0, bond_k, angle_t0, angle_k,
+        dih_k, dih_phase;
+    std::vector<int32_t> bond, angle, dihedral, dih_n, excl, pair14;
+    double scale14_lj = 0, scale14_coul = 0;
+    void assign(const pamd_topology* t) {
+        auto cp = [](auto& v, const auto* p, size_t n) { v.assign(p, p + (p ? n : 0)); };
+        const size_t N = (size_t)t->n_atoms;
+        n_atoms = t->n_atoms;
+        cp(mass, t->mass, N); cp(charge, t->charge, N); cp(sigma, t->sigma, N);
+        cp(epsilon, t->epsilon, N); cp(x0, t->x0, 3 * N);
+        cp(bond, t->bond, 2 * (size_t)t->n_bonds); cp(bond_r0, t->bond_r0, (size_t)t->n_bonds);
+        cp(bond_k, t->bond_k, (size_t)t->n_bonds);
+        cp(angle, t->angle, 3 * (size_t)t->n_angles); cp(angle_t0, t->angle_t0, (size_t)t->n_angles);
+        cp(angle_k, t->angle_k, (size_t)t->n_angles);
+        cp(dihedral, t->dihedral, 4 * (size_t)t->n_dihedrals); cp(dih_n, t->dih_n, (size_t)t->n_dihedrals);
+        cp(dih_k, t->dih_k, (size_t)t->n_dihedrals); cp(dih_phase, t->dih_phase, (size_t)t->n_dihedrals);
+        cp(excl, t->excl, 2 * (size_t)t->n_excl); cp(pair14, t->pair14, 2 * (size_t)t->n_pair14);
+        scale14_lj = t->scale14_lj;
+        scale14_coul = t->scale14_coul;
+    }
+    pamd_topology view() const {
+        pamd_topology t{};
+        t.n_atoms = n_atoms;
+        t.mass = mass.data(); t.charge = charge.data(); t.sigma = sigma.data();
+        t.epsilon = epsilon.data(); t.x0 = x0.data();
+        t.n_bonds = (int32_t)bond_r0.size(); t.bond = bond.data(); t.bond_r0 = bond_r0.data();
+        t.bond_k = bond_k.data();
+        t.n_angles = (int32_t)angle_t0.size(); t.angle = angle.data(); t.angle_t0 = angle_t0.data();
+        t.angle_k = angle_k.data();
+        t.n_dihedrals = (int32_t)dih_k.size(); t.dihedral = dihedral.data(); t.dih_n = dih_n.data();
+        t.dih_k = dih_k.data(); t.dih_phase = dih_phase.data();
+        t.n_excl = (int32_t)(excl.size() / 2); t.excl = excl.data();
+        t.n_pair14 = (int32_t)(pair14.size() / 2); t.pair14 = pair14.data();
+        t.scale14_lj = scale14_lj;
+        t.scale14_coul = scale14_coul;
+        return t;
+    }
+};
+}  // namespace pamd
+
 struct pamd_ctx {
     long long R = 0;
     int N = 0, Np = 0;
@@ -150,6 +195,9 @@ struct pamd_ctx {
     pamd::GraphKey graph_key;
     bool cur_is_alt = false;   // population currently in state_alt
     std::vector<double> host_mass;
+    pamd::HostTopology host_top;
+    int lanes_req = 0;
+    size_t topo_cap = 0;          // bytes allocated for the device topology table
 };
 
 namespace pamd {

@@ -36,15 +36,18 @@
 
 namespace pamd {
 
-// Blocks per SM the compiler is asked to fit (register budget 65536 /
-// (256 threads x PAMD_PROP_MIN_BLOCKS) per thread); chosen by measurement.
-#ifndef PAMD_PROP_MIN_BLOCKS
-#define PAMD_PROP_MIN_BLOCKS 1
-#endif
-
+// Blocks of 256 threads per SM the compiler is asked to fit: 2 (128
+// registers per thread) for up to 3 atoms per lane, 1 (255) above, where the
+// cap would spill.  Chosen by measurement; a build may override it with
+// PAMD_PROP_MIN_BLOCKS.
 template <int B>
 struct PropCfg {
     static constexpr int BS = (B % 2 == 1) ? B : B + 1;  // odd stride: conflict-free LDS.128
+#ifdef PAMD_PROP_MIN_BLOCKS
+    static constexpr int MIN_BLOCKS = PAMD_PROP_MIN_BLOCKS;
+#else
+    static constexpr int MIN_BLOCKS = (B <= 3) ? 2 : 1;
+#endif
 };
 
 // Lennard-Jones + Coulomb for one pair.  d = x_j - x_i.  With
@@ -358,6 +361,67 @@ __device__ __forceinline__ void bonded_chain(const unsigned char* sm, const Topo
     }
 }
 
+// Bonded energies of a chain lane's terms (no forces written).
+template <int B>
+__device__ __forceinline__ void bonded_chain_energy(const unsigned char* sm, const TopoLayout& lay,
+                                                    const float4* prm, const float4* pos, int L,
+                                                    int g, const float (&xi)[B],
+                                                    const float (&yi)[B], const float (&zi)[B],
+                                                    double& e_acc) {
+    using C = PropCfg<B>;
+    const int i0 = g * B;
+    const int N = lay.n_atoms;
+    const int nbase = (g + 1) * C::BS;
+    const bool has_next = (g + 1 < L);
+    float3 sp[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) sp[m] = has_next ? f3(pos[nbase + m]) : make_float3(0.f, 0.f, 0.f);
+    auto P = [&](int o) -> float3 {
+        return (o < B) ? make_float3(xi[o < B ? o : 0], yi[o < B ? o : 0], zi[o < B ? o : 0])
+                       : sp[o >= B ? o - B : 0];
+    };
+    const float2* cb = reinterpret_cast<const float2*>(sm + lay.off_cbond);
+    const float2* ca = reinterpret_cast<const float2*>(sm + lay.off_cangle);
+    const float4* cd = reinterpret_cast<const float4*>(sm + lay.off_cdih);
+#pragma unroll
+    for (int a = 0; a < B; ++a) {
+        const int d = i0 + a;
+        float3 f1, f2, f3_, f4;
+        if (d + 1 < N) bond_force<true>(P(a), P(a + 1), cb[d].x, cb[d].y, e_acc);
+        if (d + 2 < N) angle_force<true>(P(a), P(a + 1), P(a + 2), ca[d].x, ca[d].y, f1, f2, f3_, e_acc);
+        if (d + 3 < N) {
+            dihedral_force<true>(P(a), P(a + 1), P(a + 2), P(a + 3), cd[d], f1, f2, f3_, f4, e_acc);
+            const int s0 = g * C::BS + a;
+            const int s3 = (a + 3 < B) ? (s0 + 3) : (nbase + a + 3 - B);
+            pair14_force<true>(P(a), P(a + 3), prm[s0], prm[s3], lay.s14_lj, lay.s14_c, e_acc);
+        }
+    }
+}
+
+// Bonded energies of the generic colour-class layout: lane g takes terms
+// g, g+L, ... of every list (no writes, so colours do not matter).
+__device__ __forceinline__ void bonded_colored_energy(const unsigned char* sm, const TopoLayout& lay,
+                                                      const float4* prm, const float4* pos, int L,
+                                                      int g, double& e_acc) {
+    float3 f1, f2, f3_, f4;
+    const BondRec* br = reinterpret_cast<const BondRec*>(sm + lay.off_bonds);
+    for (int t = g; t < lay.n_bonds; t += L)
+        bond_force<true>(f3(pos[br[t].i]), f3(pos[br[t].j]), br[t].r0, br[t].k, e_acc);
+    const AngleRec* ar = reinterpret_cast<const AngleRec*>(sm + lay.off_angles);
+    for (int t = g; t < lay.n_angles; t += L)
+        angle_force<true>(f3(pos[ar[t].i]), f3(pos[ar[t].j]), f3(pos[ar[t].k]), ar[t].t0, ar[t].kk,
+                          f1, f2, f3_, e_acc);
+    const DihRec* dr = reinterpret_cast<const DihRec*>(sm + lay.off_dihs);
+    for (int t = g; t < lay.n_dihs; t += L)
+        dihedral_force<true>(f3(pos[dr[t].i]), f3(pos[dr[t].j]), f3(pos[dr[t].k]), f3(pos[dr[t].l]),
+                             make_float4(dr[t].kd, dr[t].n, dr[t].cos_ph, dr[t].sin_ph), f1, f2,
+                             f3_, f4, e_acc);
+    const Pair14Rec* pr = reinterpret_cast<const Pair14Rec*>(sm + lay.off_p14);
+    for (int t = g; t < lay.n_p14; t += L)
+        pair14_force<true>(f3(pos[pr[t].i]), f3(pos[pr[t].j]), prm[pr[t].i], prm[pr[t].j],
+                           pr[t].s_lj, pr[t].s_c, e_acc);
+}
+
 // Forces on the lane's B atoms (registers fx, fy, fz); positions must already
 // be in shared memory and the lane's force slots zeroed, with a __syncwarp
 // after both.
@@ -438,6 +502,69 @@ __device__ __forceinline__ void compute_forces(const unsigned char* sm, const To
     }
 }
 
+// Potential energy of the lane's share of the replica (FP32 terms summed in
+// FP64): its own block's pairs, its half-ring tiles and its bonded terms.
+// Reads positions only, so no synchronisation is needed beyond the one that
+// published them.
+template <int B, bool CHAIN>
+__device__ __noinline__ double energy_pass(const unsigned char* sm, const TopoLayout& lay,
+                                           const float4* prm, const float4* pos,
+                                           const unsigned long long* masks, int L, int g) {
+    using C = PropCfg<B>;
+    double e_acc = 0.0;
+    float xi[B], yi[B], zi[B], hsi[B], sei[B], qi[B];
+#pragma unroll
+    for (int a = 0; a < B; ++a) {
+        const float4 p4 = pos[g * C::BS + a];
+        const float4 c4 = prm[g * C::BS + a];
+        xi[a] = p4.x; yi[a] = p4.y; zi[a] = p4.z;
+        hsi[a] = c4.x; sei[a] = c4.y; qi[a] = c4.z;
+    }
+    {
+        const unsigned long long m = masks[g];
+#pragma unroll
+        for (int a = 0; a < B; ++a) {
+#pragma unroll
+            for (int b = a + 1; b < B; ++b) {
+                if ((m >> (a * B + b)) & 1ull) continue;
+                float fs, e;
+                pair_lj_coul<true>(xi[b] - xi[a], yi[b] - yi[a], zi[b] - zi[a], hsi[a] + hsi[b],
+                                   sei[a] * sei[b], qi[a] * qi[b], fs, e);
+                e_acc += (double)e;
+            }
+        }
+    }
+    const int TH = L / 2;
+    for (int t = 1; t <= TH; ++t) {
+        if (2 * t == L && g >= t) continue;
+        int J = g + t;
+        J = (J >= L) ? J - L : J;
+        const unsigned long long m = masks[t * L + g];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const float4 pj = pos[J * C::BS + b];
+            const float4 cj = prm[J * C::BS + b];
+#pragma unroll
+            for (int a = 0; a < B; ++a) {
+                if ((m >> (a * B + b)) & 1ull) continue;
+                float fs, e;
+                pair_lj_coul<true>(pj.x - xi[a], pj.y - yi[a], pj.z - zi[a], hsi[a] + cj.x,
+                                   sei[a] * cj.y, qi[a] * cj.z, fs, e);
+                e_acc += (double)e;
+            }
+        }
+    }
+    // bonded terms: reuse the force routines (their force outputs are unused)
+    if constexpr (CHAIN) {
+        float fx[B], fy[B], fz[B];
+        bonded_chain_energy<B>(sm, lay, prm, pos, L, g, xi, yi, zi, e_acc);
+        (void)fx; (void)fy; (void)fz;
+    } else {
+        bonded_colored_energy(sm, lay, prm, pos, L, g, e_acc);
+    }
+    return e_acc;
+}
+
 // Sum over the L lanes of a group (any L), result in every lane.
 __device__ __forceinline__ double group_sum(double v, unsigned gmask, int base, int L) {
     double s = 0.0;
@@ -446,7 +573,7 @@ __device__ __forceinline__ double group_sum(double v, unsigned gmask, int base, 
 }
 
 template <int B, bool CHAIN>
-__global__ void __launch_bounds__(256, PAMD_PROP_MIN_BLOCKS) propagate_kernel(const PropParams p) {
+__global__ void __launch_bounds__(256, PropCfg<B>::MIN_BLOCKS) propagate_kernel(const PropParams p) {
     using C = PropCfg<B>;
     extern __shared__ float4 smem4[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(smem4);
@@ -510,51 +637,47 @@ __global__ void __launch_bounds__(256, PAMD_PROP_MIN_BLOCKS) propagate_kernel(co
         __syncwarp(gmask);
         float fx[B], fy[B], fz[B];
         double e_acc = 0.0;
-        if (p.theta == 0)
-            compute_forces<B, CHAIN, true>(sm, lay, prm, pos, frc, masks, L, g, gmask, xi, yi, zi,
-                                           hsi, sei, qi, fx, fy, fz, e_acc);
-        else
+        // s = -1 evaluates the forces of the incoming state; s >= 0 are BAOAB steps
+        for (int s = -1; s < p.theta; ++s) {
+            if (s >= 0) {
+                const uint32_t step = step_base + (uint32_t)s;
+#pragma unroll
+                for (int a = 0; a < B; ++a) {
+                    const int i = g * B + a;
+                    vx[a] = fmaf(p.hdt * im[a], fx[a], vx[a]);  // B
+                    vy[a] = fmaf(p.hdt * im[a], fy[a], vy[a]);
+                    vz[a] = fmaf(p.hdt * im[a], fz[a], vz[a]);
+                    xi[a] = fmaf(p.hdt, vx[a], xi[a]);          // A
+                    yi[a] = fmaf(p.hdt, vy[a], yi[a]);
+                    zi[a] = fmaf(p.hdt, vz[a], zi[a]);
+                    if (i < N) {                                // O
+                        const float3 z = normal3(p.seed, (uint32_t)i, (uint32_t)k, step, p.purpose_mol);
+                        vx[a] = fmaf(p.c1, vx[a], sd[a] * z.x);
+                        vy[a] = fmaf(p.c1, vy[a], sd[a] * z.y);
+                        vz[a] = fmaf(p.c1, vz[a], sd[a] * z.z);
+                    }
+                    xi[a] = fmaf(p.hdt, vx[a], xi[a]);          // A
+                    yi[a] = fmaf(p.hdt, vy[a], yi[a]);
+                    zi[a] = fmaf(p.hdt, vz[a], zi[a]);
+                    const int sl = g * C::BS + a;
+                    pos[sl] = make_float4(xi[a], yi[a], zi[a], 0.0f);
+                    frc[sl] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                }
+                __syncwarp(gmask);
+            }
             compute_forces<B, CHAIN, false>(sm, lay, prm, pos, frc, masks, L, g, gmask, xi, yi, zi,
                                             hsi, sei, qi, fx, fy, fz, e_acc);
-
-        for (int s = 0; s < p.theta; ++s) {
-            const uint32_t step = step_base + (uint32_t)s;
+            if (s >= 0) {
 #pragma unroll
-            for (int a = 0; a < B; ++a) {
-                const int i = g * B + a;
-                vx[a] = fmaf(p.hdt * im[a], fx[a], vx[a]);  // B
-                vy[a] = fmaf(p.hdt * im[a], fy[a], vy[a]);
-                vz[a] = fmaf(p.hdt * im[a], fz[a], vz[a]);
-                xi[a] = fmaf(p.hdt, vx[a], xi[a]);          // A
-                yi[a] = fmaf(p.hdt, vy[a], yi[a]);
-                zi[a] = fmaf(p.hdt, vz[a], zi[a]);
-                if (i < N) {                                // O
-                    const float3 z = normal3(p.seed, (uint32_t)i, (uint32_t)k, step, p.purpose_mol);
-                    vx[a] = fmaf(p.c1, vx[a], sd[a] * z.x);
-                    vy[a] = fmaf(p.c1, vy[a], sd[a] * z.y);
-                    vz[a] = fmaf(p.c1, vz[a], sd[a] * z.z);
+                for (int a = 0; a < B; ++a) {                   // B
+                    vx[a] = fmaf(p.hdt * im[a], fx[a], vx[a]);
+                    vy[a] = fmaf(p.hdt * im[a], fy[a], vy[a]);
+                    vz[a] = fmaf(p.hdt * im[a], fz[a], vz[a]);
                 }
-                xi[a] = fmaf(p.hdt, vx[a], xi[a]);          // A
-                yi[a] = fmaf(p.hdt, vy[a], yi[a]);
-                zi[a] = fmaf(p.hdt, vz[a], zi[a]);
-                const int sl = g * C::BS + a;
-                pos[sl] = make_float4(xi[a], yi[a], zi[a], 0.0f);
-                frc[sl] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            }
-            __syncwarp(gmask);
-            if (s == p.theta - 1)
-                compute_forces<B, CHAIN, true>(sm, lay, prm, pos, frc, masks, L, g, gmask, xi, yi,
-                                               zi, hsi, sei, qi, fx, fy, fz, e_acc);
-            else
-                compute_forces<B, CHAIN, false>(sm, lay, prm, pos, frc, masks, L, g, gmask, xi, yi,
-                                                zi, hsi, sei, qi, fx, fy, fz, e_acc);
-#pragma unroll
-            for (int a = 0; a < B; ++a) {                   // B
-                vx[a] = fmaf(p.hdt * im[a], fx[a], vx[a]);
-                vy[a] = fmaf(p.hdt * im[a], fy[a], vy[a]);
-                vz[a] = fmaf(p.hdt * im[a], fz[a], vz[a]);
             }
         }
+        // positions in shared memory are those of the last step
+        e_acc = energy_pass<B, CHAIN>(sm, lay, prm, pos, masks, L, g);
 
         // write back and per-replica observables
         float* so = p.state_out + (size_t)k * 6 * Np;

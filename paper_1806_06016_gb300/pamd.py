@@ -54,11 +54,20 @@ class PamdOptions(C.Structure):
         ("lanes_per_replica", C.c_int32),
         ("warps_per_block", C.c_int32),
         ("mol_id", C.c_int32),
+        ("autotune", C.c_int32),
         ("dev_alloc", ALLOC_FN),
         ("dev_free", FREE_FN),
         ("alloc_user", C.c_void_p),
         ("stream", C.c_void_p),
     ]
+
+
+class PamdTune(C.Structure):
+    _fields_ = [("lanes_per_replica", C.c_int32), ("atoms_per_lane", C.c_int32),
+                ("warps_per_block", C.c_int32), ("from_cache", C.c_int32), ("ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class PamdObs(C.Structure):
@@ -77,7 +86,7 @@ class PamdObs(C.Structure):
 EXPORTS = [
     "pamd_options_default", "pamd_init", "pamd_reset", "pamd_propagate", "pamd_resample", "pamd_observables",
     "pamd_anneal", "pamd_get_state", "pamd_set_state", "pamd_forces", "pamd_get_counters",
-    "pamd_set_counters", "pamd_info", "pamd_launch_count", "pamd_sync", "pamd_destroy",
+    "pamd_set_counters", "pamd_autotune", "pamd_info", "pamd_launch_count", "pamd_sync", "pamd_destroy",
     "pamd_last_error",
 ]
 
@@ -110,6 +119,7 @@ def load(path: str | None = None):
             "pamd_forces": (C.c_int, [P, P, P]),
             "pamd_get_counters": (C.c_int, [P, C.POINTER(U32), C.POINTER(U32), C.POINTER(D)]),
             "pamd_set_counters": (C.c_int, [P, U32, U32, D]),
+            "pamd_autotune": (C.c_int, [P, I32, C.POINTER(PamdTune)]),
             "pamd_info": (C.c_int, [P, C.POINTER(I64), C.POINTER(I32), C.POINTER(I32),
                                     C.POINTER(I32), C.POINTER(I32)]),
             "pamd_launch_count": (I64, [P]),
@@ -292,6 +302,12 @@ def pamd_set_counters(ctx, step: int, resample_index: int, sum_lnQ: float) -> No
     _check(load().pamd_set_counters(ctx, int(step), int(resample_index), float(sum_lnQ)))
 
 
+def pamd_autotune(ctx, theta_probe: int = 20) -> dict:
+    t = PamdTune()
+    _check(load().pamd_autotune(ctx, int(theta_probe), C.byref(t)))
+    return t.as_dict()
+
+
 def pamd_launch_count(ctx) -> int:
     return int(load().pamd_launch_count(ctx))
 
@@ -345,6 +361,9 @@ class Population:
 
     def info(self):
         return pamd_info(self.ctx)
+
+    def autotune(self, theta_probe=20):
+        return pamd_autotune(self.ctx, theta_probe)
 
     def close(self):
         if self.ctx is not None:

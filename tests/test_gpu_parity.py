@@ -409,3 +409,31 @@ def test_large_population_resample_bit_exact(lib, orc):
     lnq_o, W = orc.resample_weights(E, 1000.0, 975.0)
     np.testing.assert_array_equal(cnt, orc.multinomial_counts(W, seed, 1))
     assert abs(lnq - lnq_o) <= 1e-11 * max(1.0, abs(lnq_o))
+
+
+def test_autotune_keeps_state_and_parity(lib, orc):
+    top = pi.make_chain(75, 1)
+    R = 600
+    ctx = lib.pamd_init(top, R, 800.0, 3)
+    try:
+        lib.pamd_propagate(ctx, 5, 0.001, 800.0)
+        before = lib.pamd_get_state(ctx)
+        ctr = lib.pamd_get_counters(ctx)
+        tune = lib.pamd_autotune(ctx, 5)
+        assert tune["from_cache"] == 0 and tune["ms"] > 0
+        assert tune["lanes_per_replica"] * tune["atoms_per_lane"] >= 75
+        for u, w in zip(before, lib.pamd_get_state(ctx)):
+            np.testing.assert_array_equal(u, w)
+        assert lib.pamd_get_counters(ctx) == ctr
+        info = lib.pamd_info(ctx)
+        assert info["lanes_per_replica"] == tune["lanes_per_replica"]
+        # the tuned shape computes the same forces
+        x = before[0][:4]
+        fg, eg = lib.pamd_forces(ctx)
+        fo, eo, scale = _oracle_forces(orc, top, before[0][:4])
+        for k in range(4):
+            rms = math.sqrt(np.mean(fo[k] ** 2))
+            assert math.sqrt(np.mean((fg[k] - fo[k]) ** 2)) <= 1e-5 * rms
+        assert lib.pamd_autotune(ctx, 5)["from_cache"] == 1
+    finally:
+        lib.pamd_destroy(ctx)
