@@ -252,6 +252,38 @@ typedef struct pamd_tune {
  */
 int pamd_autotune(pamd_ctx* ctx, int32_t theta_probe, pamd_tune* out);
 
+/*
+ * Copy counts and ln Q of one resampling, allocating no memory.  The paper
+ * has no counterpart: this is a service for callers that cannot allocate
+ * device memory -- code running under a framework that owns the whole device
+ * pool (a custom operator whose memory must come from the host framework),
+ * code that must not trigger the device-wide synchronisation cudaFree can
+ * cause, or a loop with a fixed, pre-reserved memory budget.
+ *
+ * Computes exactly what pamd_resample computes for copies_out and lnQ_out
+ * (same integer weights, prefix sums, Philox targets and ancestors; copy
+ * counts identical bit for bit) from R energies already on the device, but
+ * does not gather a population.  E_dev: device [R] FP64 potential energies;
+ * non-finite energies get weight 0.  resample_index and mol_id select the
+ * Philox stream as in pamd_resample (its k-th call on a context uses index
+ * k).  counts_dev: device [R] int32 output, n_j by ancestor.  lnQ_dev: device
+ * double output or NULL.  stream: cudaStream_t (NULL = legacy default).
+ * Asynchronous: returns after queuing the work.
+ *
+ * Its scratch is one static device array of 2.1 MiB inside the library,
+ * which every GPU that loads the library holds until the process exits; R
+ * is therefore limited to 262144 (PAMD_EINVAL above).  No cudaMalloc, cudaFree
+ * or allocating library routine is called.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the array: calls that overlap
+ * on the GPU (different streams, or different host threads on one device)
+ * race with each other and must be serialised by the caller.
+ * Errors: PAMD_EINVAL (null pointer, R, temperatures, mol_id), PAMD_ECUDA.
+ */
+int pamd_resample_counts_noalloc(const double* E_dev, int64_t R, double T_prev, double T_next,
+                                 uint64_t seed, uint32_t resample_index, int32_t mol_id,
+                                 int32_t* counts_dev, double* lnQ_dev, void* stream);
+
 /* Random-counter state: global MD step and resampling index.  A restarted
  * run that restores both (with the same seed and population) continues
  * bit-identically. */

@@ -547,6 +547,10 @@ int ensure_obs_cap(pamd_ctx* c, int n) {
 
 }  // namespace
 
+namespace pamd {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace pamd
+
 extern "C" {
 
 void pamd_options_default(pamd_options* o) {

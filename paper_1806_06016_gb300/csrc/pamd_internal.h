@@ -218,6 +218,21 @@ PAMD_DECLARE_PROPAGATE(7)
 PAMD_DECLARE_PROPAGATE(8)
 #undef PAMD_DECLARE_PROPAGATE
 
+// message returned by pamd_last_error() on this thread (capi.cu)
+void set_last_error(const std::string& msg);
+
+// resampling kernels defined in resample.cu, also launched by noalloc.cu
+__global__ void reset_scalars_kernel(DevScalars* s);
+__global__ void amax_kernel(const double* E, long long R, double dbeta, double* blk_max);
+__global__ void max_top_kernel(const double* blk_max, int nblk, DevScalars* s);
+__global__ void weights_top_kernel(unsigned long long* blk_w, const double* blk_e, int nblk,
+                                   long long R, DevScalars* s);
+__global__ void scan_local_u64_kernel(unsigned long long* W, long long R,
+                                      const unsigned long long* blk_off, unsigned long long* C);
+__global__ void counts_kernel(const unsigned long long* C, long long R, const DevScalars* s,
+                              unsigned long long seed, const uint32_t* dev_counters,
+                              uint32_t ridx_off, uint32_t purpose, int do_resample, int32_t* cnt);
+
 // resampling / observables / init kernels (resample.cu)
 cudaError_t launch_init(pamd_ctx* c, double T0);
 cudaError_t launch_resample(pamd_ctx* c, double T_prev, double T_next, int do_resample,

@@ -86,7 +86,7 @@ class PamdObs(C.Structure):
 EXPORTS = [
     "pamd_options_default", "pamd_init", "pamd_reset", "pamd_propagate", "pamd_resample", "pamd_observables",
     "pamd_anneal", "pamd_get_state", "pamd_set_state", "pamd_forces", "pamd_get_counters",
-    "pamd_set_counters", "pamd_autotune", "pamd_info", "pamd_launch_count", "pamd_sync", "pamd_destroy",
+    "pamd_set_counters", "pamd_autotune", "pamd_resample_counts_noalloc", "pamd_info", "pamd_launch_count", "pamd_sync", "pamd_destroy",
     "pamd_last_error",
 ]
 
@@ -120,6 +120,7 @@ def load(path: str | None = None):
             "pamd_get_counters": (C.c_int, [P, C.POINTER(U32), C.POINTER(U32), C.POINTER(D)]),
             "pamd_set_counters": (C.c_int, [P, U32, U32, D]),
             "pamd_autotune": (C.c_int, [P, I32, C.POINTER(PamdTune)]),
+            "pamd_resample_counts_noalloc": (C.c_int, [P, I64, D, D, U64, U32, I32, P, P, P]),
             "pamd_info": (C.c_int, [P, C.POINTER(I64), C.POINTER(I32), C.POINTER(I32),
                                     C.POINTER(I32), C.POINTER(I32)]),
             "pamd_launch_count": (I64, [P]),
@@ -306,6 +307,16 @@ def pamd_autotune(ctx, theta_probe: int = 20) -> dict:
     t = PamdTune()
     _check(load().pamd_autotune(ctx, int(theta_probe), C.byref(t)))
     return t.as_dict()
+
+
+def pamd_resample_counts_noalloc(E_dev: int, R: int, T_prev: float, T_next: float, seed: int,
+                                 resample_index: int, counts_dev: int, lnQ_dev: int = 0,
+                                 mol_id: int = 0, stream: int = 0) -> None:
+    """Copy counts and ln Q from device energies into device outputs without
+    allocating (pointers are device addresses, e.g. ``tensor.data_ptr()``)."""
+    _check(load().pamd_resample_counts_noalloc(
+        C.c_void_p(E_dev), int(R), float(T_prev), float(T_next), int(seed), int(resample_index),
+        int(mol_id), C.c_void_p(counts_dev), C.c_void_p(lnQ_dev or None), C.c_void_p(stream or None)))
 
 
 def pamd_launch_count(ctx) -> int:
