@@ -105,6 +105,8 @@ typedef struct pamd_options {
     int32_t warps_per_block;    /* 0 = choose (4); else 1..8 */
     int32_t mol_id;             /* molecule index mixed into the random counters */
     int32_t autotune;           /* 1: pamd_autotune(ctx, 20, NULL) at the end of pamd_init */
+    int32_t replicas_per_lane;  /* 0 or 1: one replica per lane group; 2: two replicas per
+                                   group in packed FP32x2 arithmetic (2..4 atoms per lane) */
     void* (*dev_alloc)(size_t bytes, void* user); /* NULL = cudaMalloc */
     void (*dev_free)(void* ptr, void* user);      /* NULL = cudaFree */
     void* alloc_user;
@@ -233,6 +235,7 @@ typedef struct pamd_tune {
     int32_t lanes_per_replica; /* L: lanes of one warp that share a replica */
     int32_t atoms_per_lane;    /* B: atoms each lane owns */
     int32_t warps_per_block;
+    int32_t replicas_per_lane; /* 1, or 2 for the packed two-replica kernels */
     int32_t from_cache;        /* 1 if the shape came from the cache */
     double ms;                 /* probe time of the chosen shape (0 if cached) */
 } pamd_tune;
@@ -241,8 +244,9 @@ typedef struct pamd_tune {
  * Launch-shape autotuner (no counterpart in the paper; it picks how the
  * replica-parallel work of step 3 maps onto the GPU).  For every feasible
  * shape -- B = 1..8 atoms per lane with L = ceil(N/B) <= 32 lanes per replica
- * (fixed to the requested lanes_per_replica if one was given), and 2, 4 or 8
- * warps per block -- one propagate launch of theta_probe steps over the whole
+ * (fixed to the requested lanes_per_replica if one was given), one or two
+ * replicas per lane group (two only for B = 2..4), and 2, 4 or 8 warps per
+ * block -- one propagate launch of theta_probe steps over the whole
  * population is timed on a scratch copy; the fastest shape is kept.  The
  * population, energies, counters and observables are left unchanged.  The
  * choice is cached in the process per (N, R, chain layout) and, when the

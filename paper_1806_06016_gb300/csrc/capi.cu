@@ -382,6 +382,14 @@ int build_topology(const pamd_topology* t, int lanes_req, TopoLayout* lay_out,
 cudaError_t propagate_dispatch_any(const TopoLayout& lay, const PropParams* p, int warps, int grid,
                                    size_t smem, cudaStream_t s, int* occ) {
     const bool chain = lay.chain != 0;
+    if (lay.paired) {
+        switch (lay.per_lane) {
+            case 2: return propagate2_b2(p, chain, warps, grid, smem, s, occ);
+            case 3: return propagate2_b3(p, chain, warps, grid, smem, s, occ);
+            case 4: return propagate2_b4(p, chain, warps, grid, smem, s, occ);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (lay.per_lane) {
         case 1: return propagate_b1(p, chain, warps, grid, smem, s, occ);
         case 2: return propagate_b2(p, chain, warps, grid, smem, s, occ);
@@ -395,8 +403,12 @@ cudaError_t propagate_dispatch_any(const TopoLayout& lay, const PropParams* p, i
     }
 }
 
+// float4s of shared memory per replica slot (single) or replica-pair slot (paired)
+int slot_f4(const TopoLayout& lay) { return lay.paired ? 3 * lay.nk + 1 : 2 * lay.nk + 1; }
+
 size_t prop_smem(const pamd_ctx* c) {
-    return (size_t)c->lay.bytes + (size_t)c->rpb * (2 * c->lay.nk + 1) * 16;
+    const int units = c->lay.paired ? c->rpb / 2 : c->rpb;
+    return (size_t)c->lay.bytes + (size_t)units * slot_f4(c->lay) * 16;
 }
 
 float* cur_state(pamd_ctx* c) { return c->cur_is_alt ? c->b.state_alt : c->b.state; }
@@ -447,18 +459,20 @@ struct TuneKey {
     int chain;
     int lanes_req;
 };
+struct TuneShape {
+    int L, W, paired;
+};
 std::mutex g_tune_mu;
-std::vector<std::pair<TuneKey, std::pair<int, int>>> g_tune;
+std::vector<std::pair<TuneKey, TuneShape>> g_tune;
 
-bool tune_cache_lookup(const TuneKey& k, int* L, int* W) {
+bool tune_cache_lookup(const TuneKey& k, TuneShape* out) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto match = [&](const TuneKey& q) {
         return q.N == k.N && q.R == k.R && q.chain == k.chain && q.lanes_req == k.lanes_req;
     };
     for (auto& e : g_tune)
         if (match(e.first)) {
-            *L = e.second.first;
-            *W = e.second.second;
+            *out = e.second;
             return true;
         }
     const char* path = std::getenv("PAMD_TUNE_CACHE");
@@ -466,41 +480,47 @@ bool tune_cache_lookup(const TuneKey& k, int* L, int* W) {
     FILE* f = std::fopen(path, "r");
     if (!f) return false;
     TuneKey q;
-    int l, w;
+    TuneShape t;
     bool found = false;
-    while (std::fscanf(f, "%d %lld %d %d %d %d", &q.N, &q.R, &q.chain, &q.lanes_req, &l, &w) == 6) {
-        if (match(q) && l >= 1 && l <= 32 && (w == 2 || w == 4 || w == 8)) {
-            *L = l;
-            *W = w;
+    while (std::fscanf(f, "%d %lld %d %d %d %d %d", &q.N, &q.R, &q.chain, &q.lanes_req, &t.L, &t.W,
+                       &t.paired) == 7) {
+        if (match(q) && t.L >= 1 && t.L <= 32 && (t.W == 2 || t.W == 4 || t.W == 8) &&
+            (t.paired == 0 || t.paired == 1)) {
+            *out = t;
             found = true;
         }
     }
     std::fclose(f);
-    if (found) g_tune.push_back({k, {*L, *W}});
+    if (found) g_tune.push_back({k, *out});
     return found;
 }
 
-void tune_cache_store(const TuneKey& k, int L, int W) {
+void tune_cache_store(const TuneKey& k, const TuneShape& t) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune.push_back({k, {L, W}});
+    g_tune.push_back({k, t});
     const char* path = std::getenv("PAMD_TUNE_CACHE");
     if (!path || !*path) return;
     if (FILE* f = std::fopen(path, "a")) {
-        std::fprintf(f, "%d %lld %d %d %d %d\n", k.N, k.R, k.chain, k.lanes_req, L, W);
+        std::fprintf(f, "%d %lld %d %d %d %d %d\n", k.N, k.R, k.chain, k.lanes_req, t.L, t.W,
+                     t.paired);
         std::fclose(f);
     }
 }
 
 // Warps per block (<= requested, shared memory permitting), replicas per
 // block and the persistent grid for layout `lay`.
-int set_launch_shape(pamd_ctx* c, const TopoLayout& lay, int warps_req) {
+int set_launch_shape(pamd_ctx* c, const TopoLayout& lay_in, int warps_req, int paired) {
+    TopoLayout lay = lay_in;
+    lay.paired = paired ? 1 : 0;
+    if (lay.paired && (lay.per_lane < 2 || lay.per_lane > 4))
+        return fail(PAMD_EUNSUPPORTED, "two replicas per lane need 2..4 atoms per lane");
     int dev = 0, max_smem = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int groups_per_warp = 32 / lay.lanes;  // idle lanes when L does not divide 32
     int warps = warps_req ? warps_req : 4;
     auto smem = [&](int w) {
-        return (long long)lay.bytes + (long long)w * groups_per_warp * (2 * lay.nk + 1) * 16;
+        return (long long)lay.bytes + (long long)w * groups_per_warp * slot_f4(lay) * 16;
     };
     while (smem(warps) > max_smem && warps > 1) --warps;
     if (smem(warps) > max_smem) return fail(PAMD_EUNSUPPORTED, "molecule tables exceed shared memory");
@@ -510,7 +530,7 @@ int set_launch_shape(pamd_ctx* c, const TopoLayout& lay, int warps_req) {
         return fail(PAMD_ECUDA, std::string("propagate occupancy: ") + cudaGetErrorString(e));
     c->lay = lay;
     c->warps_per_block = warps;
-    c->rpb = warps * groups_per_warp;
+    c->rpb = warps * groups_per_warp * (lay.paired ? 2 : 1);
     const long long batches = (c->R + c->rpb - 1) / c->rpb;
     c->grid_prop = (int)std::min<long long>(batches, (long long)c->num_sms * occ);
     return PAMD_OK;
@@ -579,6 +599,8 @@ int pamd_init(pamd_ctx** out, const pamd_topology* top, int64_t R, double T0, ui
     if (o.warps_per_block < 0 || o.warps_per_block > 8)
         return fail(PAMD_EINVAL, "warps_per_block must be 0..8");
     if (o.mol_id < 0 || o.mol_id > 0xffffff) return fail(PAMD_EINVAL, "mol_id must be 0..2^24-1");
+    if (o.replicas_per_lane < 0 || o.replicas_per_lane > 2)
+        return fail(PAMD_EINVAL, "replicas_per_lane must be 0, 1 or 2");
     if ((o.dev_alloc == nullptr) != (o.dev_free == nullptr))
         return fail(PAMD_EINVAL, "dev_alloc and dev_free must both be set or both be NULL");
 
@@ -620,7 +642,8 @@ int pamd_init(pamd_ctx** out, const pamd_topology* top, int64_t R, double T0, ui
         c->own_stream = true;
     }
     // launch shape
-    if ((rc = set_launch_shape(c, lay0, o.warps_per_block))) {
+    if ((rc = set_launch_shape(c, lay0, o.warps_per_block,
+                               o.replicas_per_lane == 2 ? 1 : 0))) {
         const std::string m = g_err;
         return bail(rc, m);
     }
@@ -903,13 +926,13 @@ int pamd_autotune(pamd_ctx* c, int32_t theta_probe, pamd_tune* out) {
     const pamd_topology t = c->host_top.view();
     const int chain = (int)is_linear_chain(&t);
     const TuneKey key{c->N, c->R, chain, c->lanes_req};
-    int L = 0, W = 0;
+    TuneShape best_shape{0, 0, 0};
     double best_ms = 0.0;
-    bool cached = tune_cache_lookup(key, &L, &W);
+    bool cached = tune_cache_lookup(key, &best_shape);
     std::vector<unsigned char> blob;
     TopoLayout lay;
-    auto apply = [&](int lanes, int warps) -> int {
-        int r = build_topology(&t, lanes, &lay, blob);
+    auto apply = [&](const TuneShape& sh) -> int {
+        int r = build_topology(&t, sh.L, &lay, blob);
         if (r) return r;
         if (blob.size() > c->topo_cap) {
             void* p = dalloc(c, blob.size());
@@ -919,7 +942,7 @@ int pamd_autotune(pamd_ctx* c, int32_t theta_probe, pamd_tune* out) {
         }
         PAMD_CU(c, cudaMemcpyAsync(c->b.topo, blob.data(), blob.size(), cudaMemcpyHostToDevice, c->stream));
         PAMD_CU(c, cudaStreamSynchronize(c->stream));
-        return set_launch_shape(c, lay, warps);
+        return set_launch_shape(c, lay, sh.W, sh.paired);
     };
     if (!cached) {
         // scratch copy of the population; per-replica outputs go to scratch too
@@ -932,53 +955,57 @@ int pamd_autotune(pamd_ctx* c, int32_t theta_probe, pamd_tune* out) {
         PAMD_CU(c, cudaEventCreate(&e0));
         PAMD_CU(c, cudaEventCreate(&e1));
         double best = 1e300;
-        std::vector<std::pair<int, int>> shapes;
+        std::vector<TuneShape> shapes;
         for (int b = 1; b <= 8; ++b) {
             int l = c->lanes_req ? c->lanes_req : (c->N + b - 1) / b;
             if (l > 32) continue;
-            int bb = (c->N + l - 1) / l;
+            const int bb = (c->N + l - 1) / l;
             if (bb > 8) continue;
             l = (c->N + bb - 1) / bb;
-            bool dup = false;
-            for (auto& s2 : shapes) dup = dup || s2.first == l;
-            if (!dup) shapes.emplace_back(l, bb);
+            for (int paired = 0; paired <= 1; ++paired) {
+                if (paired && (bb < 2 || bb > 4)) continue;
+                for (int w : {2, 4, 8}) {
+                    bool dup = false;
+                    for (auto& s2 : shapes) dup = dup || (s2.L == l && s2.W == w && s2.paired == paired);
+                    if (!dup) shapes.push_back({l, w, paired});
+                }
+            }
         }
         int err = PAMD_OK;
         for (auto& sh : shapes) {
-            for (int warps : {2, 4, 8}) {
-                if ((err = apply(sh.first, warps))) break;
-                if (c->warps_per_block != warps) continue;  // shared memory capped it
-                cudaMemcpyAsync(scratch, cur_state(c), st_bytes, cudaMemcpyDeviceToDevice, c->stream);
-                if ((err = launch_prop_on(c, scratch, e_scr, ke_scr, rg_scr, 1, 0.001, 300.0, nullptr,
-                                          c->step, nullptr)))
-                    break;
-                cudaEventRecord(e0, c->stream);
-                if ((err = launch_prop_on(c, scratch, e_scr, ke_scr, rg_scr, theta_probe, 0.001, 300.0,
-                                          nullptr, c->step, nullptr)))
-                    break;
-                cudaEventRecord(e1, c->stream);
-                if (cudaEventSynchronize(e1) != cudaSuccess) {
-                    err = cuda_fail(c, cudaGetLastError(), "autotune");
-                    break;
-                }
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best) {
-                    best = ms;
-                    L = sh.first;
-                    W = warps;
-                }
+            if ((err = apply(sh))) {
+                if (err == PAMD_EUNSUPPORTED) { err = PAMD_OK; continue; }
+                break;
             }
-            if (err) break;
+            if (c->warps_per_block != sh.W) continue;  // shared memory capped it
+            cudaMemcpyAsync(scratch, cur_state(c), st_bytes, cudaMemcpyDeviceToDevice, c->stream);
+            if ((err = launch_prop_on(c, scratch, e_scr, ke_scr, rg_scr, 1, 0.001, 300.0, nullptr,
+                                      c->step, nullptr)))
+                break;
+            cudaEventRecord(e0, c->stream);
+            if ((err = launch_prop_on(c, scratch, e_scr, ke_scr, rg_scr, theta_probe, 0.001, 300.0,
+                                      nullptr, c->step, nullptr)))
+                break;
+            cudaEventRecord(e1, c->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                err = cuda_fail(c, cudaGetLastError(), "autotune");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                best_shape = sh;
+            }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         if (err) return err;
         if (best == 1e300) return fail(PAMD_EUNSUPPORTED, "no feasible launch shape");
         best_ms = best;
-        tune_cache_store(key, L, W);
+        tune_cache_store(key, best_shape);
     }
-    if ((rc = apply(L, W))) return rc;
+    if ((rc = apply(best_shape))) return rc;
     if (c->graph_exec) {  // captured launches carry the old shape
         cudaGraphExecDestroy(c->graph_exec);
         c->graph_exec = nullptr;
@@ -988,6 +1015,7 @@ int pamd_autotune(pamd_ctx* c, int32_t theta_probe, pamd_tune* out) {
         out->lanes_per_replica = c->lay.lanes;
         out->atoms_per_lane = c->lay.per_lane;
         out->warps_per_block = c->warps_per_block;
+        out->replicas_per_lane = c->lay.paired ? 2 : 1;
         out->from_cache = cached ? 1 : 0;
         out->ms = best_ms;
     }

@@ -44,6 +44,7 @@ struct TopoLayout {
     int off_cangle;            // chain: float2 [N-2] {theta0, k} of angle (d, d+1, d+2)
     int off_cdih;              // chain: float4 [N-3] {k, n, cos phase, sin phase} of (d..d+3)
     float s14_lj, s14_c;       // chain: 1-4 scale factors
+    int paired;                // launch: 1 = two replicas per lane group (packed FP32x2)
     int bytes;                 // total, multiple of 16
 };
 
@@ -217,6 +218,13 @@ PAMD_DECLARE_PROPAGATE(6)
 PAMD_DECLARE_PROPAGATE(7)
 PAMD_DECLARE_PROPAGATE(8)
 #undef PAMD_DECLARE_PROPAGATE
+// paired kernels (two replicas per lane group), 2..4 atoms per lane
+cudaError_t propagate2_b2(const PropParams* p, bool chain, int warps, int grid, size_t smem,
+                          cudaStream_t s, int* blocks_per_sm);
+cudaError_t propagate2_b3(const PropParams* p, bool chain, int warps, int grid, size_t smem,
+                          cudaStream_t s, int* blocks_per_sm);
+cudaError_t propagate2_b4(const PropParams* p, bool chain, int warps, int grid, size_t smem,
+                          cudaStream_t s, int* blocks_per_sm);
 
 // message returned by pamd_last_error() on this thread (capi.cu)
 void set_last_error(const std::string& msg);

@@ -55,6 +55,7 @@ class PamdOptions(C.Structure):
         ("warps_per_block", C.c_int32),
         ("mol_id", C.c_int32),
         ("autotune", C.c_int32),
+        ("replicas_per_lane", C.c_int32),
         ("dev_alloc", ALLOC_FN),
         ("dev_free", FREE_FN),
         ("alloc_user", C.c_void_p),
@@ -64,7 +65,8 @@ class PamdOptions(C.Structure):
 
 class PamdTune(C.Structure):
     _fields_ = [("lanes_per_replica", C.c_int32), ("atoms_per_lane", C.c_int32),
-                ("warps_per_block", C.c_int32), ("from_cache", C.c_int32), ("ms", C.c_double)]
+                ("warps_per_block", C.c_int32), ("replicas_per_lane", C.c_int32),
+                ("from_cache", C.c_int32), ("ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -82,6 +82,70 @@ def test_forces_and_energies(lib, orc, n, lanes):
         assert abs(eg[k] - eo[k]) <= 1e-5 * max(scale[k], 1e-3), (k, eg[k], eo[k])
 
 
+PAIRED_CASES = [(13, 7, 6), (13, 7, 5), (22, 8, 7), (75, 25, 4), (75, 25, 3), (75, 19, 2),
+                (40, 20, 5)]
+
+
+@pytest.mark.parametrize("n,lanes,R", PAIRED_CASES)
+def test_paired_kernel_forces(lib, orc, n, lanes, R):
+    """Two replicas per lane group (packed FP32x2), including an odd R whose
+    last group runs one replica twice."""
+    top = pi.make_chain(n, 200 + n)
+    top.dih_phase = np.linspace(0.2, 1.7, len(top.dih_phase))
+    x = f32(pi.perturbed_positions(top, R, 0.01, n + 1))
+    ctx = lib.pamd_init(top, R, 300.0, 1, _opts(lib, lanes_per_replica=lanes, replicas_per_lane=2))
+    try:
+        assert lib.pamd_info(ctx)["replicas_per_block"] % 2 == 0
+        lib.pamd_set_state(ctx, x, np.zeros_like(x))
+        fg, eg = lib.pamd_forces(ctx)
+    finally:
+        lib.pamd_destroy(ctx)
+    fo, eo, scale = _oracle_forces(orc, top, x)
+    for k in range(R):
+        rms = math.sqrt(np.mean(fo[k] ** 2))
+        assert math.sqrt(np.mean((fg[k] - fo[k]) ** 2)) <= 1e-5 * rms, (k, n)
+        assert abs(eg[k] - eo[k]) <= 1e-5 * scale[k], (k, eg[k], eo[k])
+
+
+@pytest.mark.parametrize("n,lanes,R", [(22, 8, 5), (75, 25, 3)])
+def test_paired_kernel_trajectory(lib, orc, n, lanes, R):
+    top = pi.make_chain(n, 7)
+    T, dt, gamma, seed = 400.0, 0.001, 1.0, 4242
+    x = f32(pi.perturbed_positions(top, R, 0.005, 1))
+    x = f32(x - x.mean(axis=1, keepdims=True))
+    v = f32(pi.gaussian_velocities(R, n, math.sqrt(KB * T / 12.0), 2))
+    ctx = lib.pamd_init(top, R, T, seed, _opts(lib, gamma_per_ps=gamma, lanes_per_replica=lanes,
+                                                replicas_per_lane=2))
+    try:
+        lib.pamd_set_state(ctx, x, v)
+        xo, vo = x.copy(), v.copy()
+        for s in range(10):
+            lib.pamd_propagate(ctx, 1, dt, T)
+            xg, vg, eg, _ = lib.pamd_get_state(ctx)
+            xo, vo, eo = orc.propagate(top, xo, vo, 1, dt, T, gamma, seed, s)
+            assert np.abs(xg - xo).max() < 1e-4, (s, np.abs(xg - xo).max())
+        assert np.abs(eg - eo).max() < 1e-4 * max(np.abs(eo).max(), 1.0)
+    finally:
+        lib.pamd_destroy(ctx)
+
+
+def test_paired_and_single_kernels_agree_statistically(lib):
+    """The two kernel families run the same anneal (same seed): the FP32
+    rounding differs, so compare averages within combined errors."""
+    top = pi.make_chain(22, 1)
+    temps = pi.geometric_schedule(1000.0, 500.0, 6)
+    out = []
+    for rpl in (1, 2):
+        ctx = lib.pamd_init(top, 512, temps[0], 9, _opts(lib, lanes_per_replica=8, replicas_per_lane=rpl))
+        try:
+            out.append(lib.pamd_anneal(ctx, temps, 50, 0.001))
+        finally:
+            lib.pamd_destroy(ctx)
+    for a, b in zip(*out):
+        s = math.hypot(a["e_pot_se"], b["e_pot_se"])
+        assert abs(a["e_pot"] - b["e_pot"]) <= 4 * s + 1e-9
+
+
 @pytest.mark.parametrize("n", [13, 40, 75])
 def test_forces_relabelled_chain(lib, orc, n):
     """Atoms of a chain relabelled at random: the bonded terms are no longer a
@@ -97,7 +161,9 @@ def test_forces_relabelled_chain(lib, orc, n):
         setattr(top, name, perm[getattr(base, name)].astype(np.int32))
     R = 4
     x = f32(pi.perturbed_positions(top, R, 0.01, 9))
-    ctx = lib.pamd_init(top, R, 300.0, 1)
+    paired = 2 if n in (13, 75) else 1   # generic path of both kernel families
+    lanes = {13: 5, 40: 0, 75: 25}[n]
+    ctx = lib.pamd_init(top, R, 300.0, 1, _opts(lib, lanes_per_replica=lanes, replicas_per_lane=paired))
     try:
         lib.pamd_set_state(ctx, x, np.zeros_like(x))
         fg, eg = lib.pamd_forces(ctx)
