@@ -349,7 +349,8 @@ def run_kernel(args, w):
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     opts = pamd.torch_options(gamma_per_ps=w["gamma"], lanes_per_replica=args.lanes,
-                              warps_per_block=args.warps, replicas_per_lane=args.rpl)
+                              warps_per_block=args.warps, replicas_per_lane=args.rpl,
+                              precision=1 if args.fp64 else 0)
     pop = pamd.Population(top, R, w["T0"], w["seed"], opts)
     if args.autotune:
         pop.autotune(50)
@@ -371,7 +372,7 @@ def run_kernel(args, w):
     flops = flop_per_replica_step(w["n_atoms"]) * R * theta
     achieved = flops / (avg / 1e3) / 1e12
     print(json.dumps({"mode": "kernel", "n_atoms": w["n_atoms"], "replicas": R, "theta": theta,
-                      "launch": info, "rpl": args.rpl, "ms": avg, "atom_steps_per_s": w["n_atoms"] * R * theta / (avg / 1e3),
+                      "launch": info, "rpl": args.rpl, "fp64": args.fp64, "ms": avg, "atom_steps_per_s": w["n_atoms"] * R * theta / (avg / 1e3),
                       "achieved_tflops": achieved, "frac": achieved / FP32_PEAK_TFLOPS}), flush=True)
 
 
@@ -390,6 +391,7 @@ def main():
     ap.add_argument("--warps", type=int, default=0, help="kernel mode: warps per block")
     ap.add_argument("--autotune", action="store_true", help="kernel mode: tune the launch shape")
     ap.add_argument("--rpl", type=int, default=0, help="kernel mode: replicas per lane group (1, 2)")
+    ap.add_argument("--fp64", action="store_true", help="kernel mode: all-FP64 propagate")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.mode == "kernel":

@@ -412,11 +412,22 @@ size_t prop_smem(const pamd_ctx* c) {
 }
 
 float* cur_state(pamd_ctx* c) { return c->cur_is_alt ? c->b.state_alt : c->b.state; }
+bool is_f64(const pamd_ctx* c) { return c->precision == PAMD_PREC_FP64; }
+// bytes of one population buffer: 6 Np values per replica, FP32 or FP64
+size_t state_bytes(const pamd_ctx* c) {
+    return (is_f64(c) ? sizeof(double) : sizeof(float)) * 6 * (size_t)c->Np * (size_t)c->R;
+}
 double* cur_E(pamd_ctx* c) { return c->cur_is_alt ? c->b.E_alt : c->b.E; }
 int32_t* cur_fam(pamd_ctx* c) { return c->cur_is_alt ? c->b.fam_alt : c->b.fam; }
 
 int launch_prop_on(pamd_ctx* c, float* state, double* E, double* ke, double* rg, int theta,
                    double dt, double T, const uint32_t* dev_ctr, uint32_t step0, float* fout) {
+    if (is_f64(c)) {
+        cudaError_t e = launch_propagate_f64(c, reinterpret_cast<double*>(state), E, ke, rg, theta,
+                                             dt, T, dev_ctr, step0, reinterpret_cast<double*>(fout));
+        if (e != cudaSuccess) return cuda_fail(c, e, "propagate launch (FP64)");
+        return PAMD_OK;
+    }
     PropParams p{};
     p.state_in = state;
     p.state_out = state;
@@ -449,6 +460,77 @@ int launch_prop(pamd_ctx* c, int theta, double dt, double T, const uint32_t* dev
                 uint32_t step0, float* fout) {
     return launch_prop_on(c, cur_state(c), cur_E(c), c->b.ke, c->b.rg, theta, dt, T, dev_ctr,
                           step0, fout);
+}
+
+// Device tables of the all-FP64 mode: one allocation, laid out on the host.
+int build_topo_f64(pamd_ctx* c, const pamd_topology* t, std::vector<unsigned char>& blob) {
+    const int N = t->n_atoms, Np = c->Np;
+    std::vector<double> sh(N), ep(N), q(N), im(N), x0(3 * (size_t)Np, 0.0);
+    double com[3] = {0, 0, 0}, mt = 0;
+    for (int i = 0; i < N; ++i) {
+        sh[i] = 0.5 * t->sigma[i];
+        ep[i] = t->epsilon[i];
+        q[i] = t->charge[i];
+        im[i] = 1.0 / t->mass[i];
+        for (int k = 0; k < 3; ++k) com[k] += t->mass[i] * t->x0[3 * i + k];
+        mt += t->mass[i];
+    }
+    for (int i = 0; i < N; ++i)
+        for (int k = 0; k < 3; ++k) x0[(size_t)k * Np + i] = t->x0[3 * i + k] - com[k] / mt;
+    std::vector<unsigned char> kind((size_t)N * N, 0);
+    for (int p = 0; p < t->n_pair14; ++p) {
+        const int i = t->pair14[2 * p], j = t->pair14[2 * p + 1];
+        kind[(size_t)i * N + j] = kind[(size_t)j * N + i] = 2;
+    }
+    for (int p = 0; p < t->n_excl; ++p) {
+        const int i = t->excl[2 * p], j = t->excl[2 * p + 1];
+        kind[(size_t)i * N + j] = kind[(size_t)j * N + i] = 1;
+    }
+    std::vector<double> bp(2 * (size_t)t->n_bonds), ap(2 * (size_t)t->n_angles), dp(4 * (size_t)t->n_dihedrals);
+    for (int b = 0; b < t->n_bonds; ++b) { bp[2 * b] = t->bond_r0[b]; bp[2 * b + 1] = t->bond_k[b]; }
+    for (int a = 0; a < t->n_angles; ++a) { ap[2 * a] = t->angle_t0[a]; ap[2 * a + 1] = t->angle_k[a]; }
+    for (int d = 0; d < t->n_dihedrals; ++d) {
+        dp[4 * d] = t->dih_k[d];
+        dp[4 * d + 1] = (double)t->dih_n[d];
+        dp[4 * d + 2] = std::cos(t->dih_phase[d]);
+        dp[4 * d + 3] = std::sin(t->dih_phase[d]);
+    }
+    // append each array 16-byte aligned and remember its offset
+    std::vector<size_t> off;
+    auto put = [&](const void* src, size_t bytes) {
+        const size_t o = (blob.size() + 15) & ~size_t(15);
+        blob.resize(o + bytes);
+        if (bytes) std::memcpy(blob.data() + o, src, bytes);
+        off.push_back(o);
+    };
+    put(sh.data(), 8 * sh.size()); put(ep.data(), 8 * ep.size()); put(q.data(), 8 * q.size());
+    put(im.data(), 8 * im.size()); put(x0.data(), 8 * x0.size()); put(kind.data(), kind.size());
+    put(t->bond, 8 * (size_t)t->n_bonds); put(bp.data(), 8 * bp.size());
+    put(t->angle, 12 * (size_t)t->n_angles); put(ap.data(), 8 * ap.size());
+    put(t->dihedral, 16 * (size_t)t->n_dihedrals); put(dp.data(), 8 * dp.size());
+    unsigned char* d = (unsigned char*)dalloc(c, blob.size() + 16);
+    if (!d) return fail(PAMD_ENOMEM, "FP64 tables");
+    c->top64_blob = d;
+    TopoF64& T = c->top64;
+    T.n_atoms = N;
+    T.sigma_half = (const double*)(d + off[0]);
+    T.epsilon = (const double*)(d + off[1]);
+    T.charge = (const double*)(d + off[2]);
+    T.inv_mass = (const double*)(d + off[3]);
+    T.x0 = (const double*)(d + off[4]);
+    T.kind = d + off[5];
+    T.s14_lj = t->scale14_lj;
+    T.s14_c = t->scale14_coul;
+    T.n_bonds = t->n_bonds;
+    T.n_angles = t->n_angles;
+    T.n_dihs = t->n_dihedrals;
+    T.bond = (const int*)(d + off[6]);
+    T.bond_p = (const double*)(d + off[7]);
+    T.angle = (const int*)(d + off[8]);
+    T.angle_p = (const double*)(d + off[9]);
+    T.dih = (const int*)(d + off[10]);
+    T.dih_p = (const double*)(d + off[11]);
+    return PAMD_OK;
 }
 
 // In-process cache of tuned shapes, mirrored to the file named by
@@ -594,8 +676,8 @@ int pamd_init(pamd_ctx** out, const pamd_topology* top, int64_t R, double T0, ui
     if (opt) o = *opt;
     if (!(o.gamma_per_ps >= 0) || !std::isfinite(o.gamma_per_ps))
         return fail(PAMD_EINVAL, "gamma must be >= 0");
-    if (o.precision != PAMD_PREC_MIXED)
-        return fail(PAMD_EUNSUPPORTED, "only PAMD_PREC_MIXED is built");
+    if (o.precision != PAMD_PREC_MIXED && o.precision != PAMD_PREC_FP64)
+        return fail(PAMD_EUNSUPPORTED, "precision must be PAMD_PREC_MIXED or PAMD_PREC_FP64");
     if (o.warps_per_block < 0 || o.warps_per_block > 8)
         return fail(PAMD_EINVAL, "warps_per_block must be 0..8");
     if (o.mol_id < 0 || o.mol_id > 0xffffff) return fail(PAMD_EINVAL, "mol_id must be 0..2^24-1");
@@ -607,6 +689,7 @@ int pamd_init(pamd_ctx** out, const pamd_topology* top, int64_t R, double T0, ui
     pamd_ctx* c = new (std::nothrow) pamd_ctx();
     if (!c) return fail(PAMD_ENOMEM, "host allocation");
     c->R = R;
+    c->precision = o.precision;
     c->gamma = o.gamma_per_ps;
     c->seed = seed;
     c->mol = o.mol_id;
@@ -661,7 +744,7 @@ int pamd_init(pamd_ctx** out, const pamd_topology* top, int64_t R, double T0, ui
         for (int q = 0; q < 3; ++q) x0[(size_t)q * c->Np + i] = (float)(top->x0[3 * i + q] - com[q] / mt);
     }
     // buffers
-    const size_t st_bytes = sizeof(float) * 6 * (size_t)c->Np * (size_t)R;
+    const size_t st_bytes = state_bytes(c);
     c->n_blk = (int)((R + 1023) / 1024);
     Buffers& b = c->b;
     b.state = (float*)dalloc(c, st_bytes);
@@ -692,12 +775,21 @@ int pamd_init(pamd_ctx** out, const pamd_topology* top, int64_t R, double T0, ui
         !b.blk_f64 || !b.blk_i32 || !b.flags || !b.obs_part || !b.scal || !b.counters)
         return bail(PAMD_ENOMEM, "device allocation failed");
     if (ensure_obs_cap(c, 2)) return bail(PAMD_ENOMEM, "device allocation failed");
+    std::vector<unsigned char> t64;
+    if (is_f64(c)) {
+        if ((rc = build_topo_f64(c, top, t64))) {
+            const std::string m = g_err;
+            return bail(rc, m);
+        }
+    }
     bool ok = cudaMemcpyAsync(b.masses, masses.data(), sizeof(float) * c->Np, cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
               cudaMemcpyAsync(b.topo, blob.data(), blob.size(), cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
               cudaMemcpyAsync(b.x0, x0.data(), sizeof(float) * 3 * c->Np, cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
               cudaMemsetAsync(b.state_alt, 0, st_bytes, c->stream) == cudaSuccess &&
               cudaMemsetAsync(b.ke, 0, sizeof(double) * R, c->stream) == cudaSuccess &&
               cudaMemsetAsync(b.rg, 0, sizeof(double) * R, c->stream) == cudaSuccess &&
+              (t64.empty() || cudaMemcpyAsync(c->top64_blob, t64.data(), t64.size(),
+                                              cudaMemcpyHostToDevice, c->stream) == cudaSuccess) &&
               launch_init(c, T0) == cudaSuccess &&
               launch_set_counters(c, 0, 0) == cudaSuccess &&
               cudaStreamSynchronize(c->stream) == cudaSuccess;
@@ -784,7 +876,7 @@ int pamd_anneal(pamd_ctx* c, int32_t K, const double* T, int32_t theta, double d
     key.T.assign(T, T + K + 1);
     // the captured graph starts from the main buffers
     if (c->cur_is_alt) {
-        const size_t st_bytes = sizeof(float) * 6 * (size_t)c->Np * (size_t)c->R;
+        const size_t st_bytes = state_bytes(c);
         PAMD_CU(c, cudaMemcpyAsync(c->b.state, c->b.state_alt, st_bytes, cudaMemcpyDeviceToDevice, c->stream));
         PAMD_CU(c, cudaMemcpyAsync(c->b.E, c->b.E_alt, 8 * (size_t)c->R, cudaMemcpyDeviceToDevice, c->stream));
         PAMD_CU(c, cudaMemcpyAsync(c->b.fam, c->b.fam_alt, 4 * (size_t)c->R, cudaMemcpyDeviceToDevice, c->stream));
@@ -810,7 +902,7 @@ int pamd_anneal(pamd_ctx* c, int32_t K, const double* T, int32_t theta, double d
             if (!err && launch_observe(c, T[i], c->b.obs + i) != cudaSuccess) err = PAMD_ECUDA;
         }
         if (!err && c->cur_is_alt) {
-            const size_t st_bytes = sizeof(float) * 6 * (size_t)c->Np * (size_t)c->R;
+            const size_t st_bytes = state_bytes(c);
             if (cudaMemcpyAsync(c->b.state, c->b.state_alt, st_bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
                 cudaMemcpyAsync(c->b.E, c->b.E_alt, 8 * (size_t)c->R, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
                 cudaMemcpyAsync(c->b.fam, c->b.fam_alt, 4 * (size_t)c->R, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
@@ -852,7 +944,11 @@ int pamd_get_state(pamd_ctx* c, double* x, double* v, double* E, int32_t* fam) {
     const int N = c->N, Np = c->Np;
     const long long R = c->R;
     std::vector<float> st;
-    if (x || v) {
+    std::vector<double> st64;
+    if ((x || v) && is_f64(c)) {
+        st64.resize((size_t)R * 6 * Np);
+        PAMD_CU(c, cudaMemcpyAsync(st64.data(), cur_state(c), st64.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+    } else if (x || v) {
         st.resize((size_t)R * 6 * Np);
         PAMD_CU(c, cudaMemcpyAsync(st.data(), cur_state(c), st.size() * 4, cudaMemcpyDeviceToHost, c->stream));
     }
@@ -860,11 +956,12 @@ int pamd_get_state(pamd_ctx* c, double* x, double* v, double* E, int32_t* fam) {
     if (fam) PAMD_CU(c, cudaMemcpyAsync(fam, cur_fam(c), 4 * (size_t)R, cudaMemcpyDeviceToHost, c->stream));
     PAMD_CU(c, cudaStreamSynchronize(c->stream));
     for (long long k = 0; k < R && (x || v); ++k) {
-        const float* s = st.data() + (size_t)k * 6 * Np;
         for (int i = 0; i < N; ++i)
             for (int q = 0; q < 3; ++q) {
-                if (x) x[((size_t)k * N + i) * 3 + q] = s[(size_t)q * Np + i];
-                if (v) v[((size_t)k * N + i) * 3 + q] = s[(size_t)(3 + q) * Np + i];
+                const size_t ix = (size_t)k * 6 * Np + (size_t)q * Np + i;
+                const size_t iv = ix + 3 * (size_t)Np;
+                if (x) x[((size_t)k * N + i) * 3 + q] = st64.empty() ? (double)st[ix] : st64[ix];
+                if (v) v[((size_t)k * N + i) * 3 + q] = st64.empty() ? (double)st[iv] : st64[iv];
             }
     }
     return PAMD_OK;
@@ -879,16 +976,31 @@ int pamd_set_state(pamd_ctx* c, const double* x, const double* v, const double* 
     if (!finite_all(x, (int)std::min<long long>(R * N * 3, 0x7fffffff)) ||
         !finite_all(v, (int)std::min<long long>(R * N * 3, 0x7fffffff)))
         return fail(PAMD_EINVAL, "non-finite state");
-    std::vector<float> st((size_t)R * 6 * Np, 0.0f);
-    for (long long k = 0; k < R; ++k) {
-        float* s = st.data() + (size_t)k * 6 * Np;
-        for (int i = 0; i < N; ++i)
-            for (int q = 0; q < 3; ++q) {
-                s[(size_t)q * Np + i] = (float)x[((size_t)k * N + i) * 3 + q];
-                s[(size_t)(3 + q) * Np + i] = (float)v[((size_t)k * N + i) * 3 + q];
-            }
+    if (is_f64(c)) {
+        std::vector<double> st((size_t)R * 6 * Np, 0.0);
+        for (long long k = 0; k < R; ++k) {
+            double* s = st.data() + (size_t)k * 6 * Np;
+            for (int i = 0; i < N; ++i)
+                for (int q = 0; q < 3; ++q) {
+                    s[(size_t)q * Np + i] = x[((size_t)k * N + i) * 3 + q];
+                    s[(size_t)(3 + q) * Np + i] = v[((size_t)k * N + i) * 3 + q];
+                }
+        }
+        PAMD_CU(c, cudaMemcpyAsync(cur_state(c), st.data(), st.size() * 8, cudaMemcpyHostToDevice, c->stream));
+        PAMD_CU(c, cudaStreamSynchronize(c->stream));
+    } else {
+        std::vector<float> st((size_t)R * 6 * Np, 0.0f);
+        for (long long k = 0; k < R; ++k) {
+            float* s = st.data() + (size_t)k * 6 * Np;
+            for (int i = 0; i < N; ++i)
+                for (int q = 0; q < 3; ++q) {
+                    s[(size_t)q * Np + i] = (float)x[((size_t)k * N + i) * 3 + q];
+                    s[(size_t)(3 + q) * Np + i] = (float)v[((size_t)k * N + i) * 3 + q];
+                }
+        }
+        PAMD_CU(c, cudaMemcpyAsync(cur_state(c), st.data(), st.size() * 4, cudaMemcpyHostToDevice, c->stream));
+        PAMD_CU(c, cudaStreamSynchronize(c->stream));
     }
-    PAMD_CU(c, cudaMemcpyAsync(cur_state(c), st.data(), st.size() * 4, cudaMemcpyHostToDevice, c->stream));
     if (E) PAMD_CU(c, cudaMemcpyAsync(cur_E(c), E, 8 * (size_t)R, cudaMemcpyHostToDevice, c->stream));
     if (fam) PAMD_CU(c, cudaMemcpyAsync(cur_fam(c), fam, 4 * (size_t)R, cudaMemcpyHostToDevice, c->stream));
     PAMD_CU(c, cudaStreamSynchronize(c->stream));
@@ -900,13 +1012,18 @@ int pamd_forces(pamd_ctx* c, double* f, double* E) {
     if (rc) return rc;
     const int N = c->N, Np = c->Np;
     const long long R = c->R;
+    const size_t es = is_f64(c) ? 8 : 4;
     if (!c->b.fout) {
-        c->b.fout = (float*)dalloc(c, sizeof(float) * 3 * (size_t)Np * (size_t)R);
+        c->b.fout = (float*)dalloc(c, es * 3 * (size_t)Np * (size_t)R);
         if (!c->b.fout) return fail(PAMD_ENOMEM, "force buffer");
     }
     if ((rc = launch_prop(c, 0, 0.001, 300.0, nullptr, c->step, c->b.fout))) return rc;
     std::vector<float> fo;
-    if (f) {
+    std::vector<double> fo64;
+    if (f && is_f64(c)) {
+        fo64.resize((size_t)R * 3 * Np);
+        PAMD_CU(c, cudaMemcpyAsync(fo64.data(), c->b.fout, fo64.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+    } else if (f) {
         fo.resize((size_t)R * 3 * Np);
         PAMD_CU(c, cudaMemcpyAsync(fo.data(), c->b.fout, fo.size() * 4, cudaMemcpyDeviceToHost, c->stream));
     }
@@ -915,7 +1032,8 @@ int pamd_forces(pamd_ctx* c, double* f, double* E) {
     for (long long k = 0; k < R && f; ++k)
         for (int i = 0; i < N; ++i)
             for (int q = 0; q < 3; ++q)
-                f[((size_t)k * N + i) * 3 + q] = fo[(size_t)k * 3 * Np + (size_t)q * Np + i];
+                f[((size_t)k * N + i) * 3 + q] = fo64.empty() ? (double)fo[(size_t)k * 3 * Np + (size_t)q * Np + i]
+                                                               : fo64[(size_t)k * 3 * Np + (size_t)q * Np + i];
     return read_status(c);
 }
 
@@ -923,6 +1041,10 @@ int pamd_autotune(pamd_ctx* c, int32_t theta_probe, pamd_tune* out) {
     int rc = check_ctx(c);
     if (rc) return rc;
     if (theta_probe < 1 || theta_probe > 1000) return fail(PAMD_EINVAL, "theta_probe must be 1..1000");
+    if (is_f64(c)) {  // one fixed shape (a warp per replica)
+        if (out) *out = pamd_tune{32, (c->N + 31) / 32, 4, 1, 0, 0.0};
+        return PAMD_OK;
+    }
     const pamd_topology t = c->host_top.view();
     const int chain = (int)is_linear_chain(&t);
     const TuneKey key{c->N, c->R, chain, c->lanes_req};
@@ -946,7 +1068,7 @@ int pamd_autotune(pamd_ctx* c, int32_t theta_probe, pamd_tune* out) {
     };
     if (!cached) {
         // scratch copy of the population; per-replica outputs go to scratch too
-        const size_t st_bytes = sizeof(float) * 6 * (size_t)c->Np * (size_t)c->R;
+        const size_t st_bytes = state_bytes(c);
         float* scratch = c->cur_is_alt ? c->b.state : c->b.state_alt;
         double* e_scr = c->cur_is_alt ? c->b.E : c->b.E_alt;
         double* ke_scr = reinterpret_cast<double*>(c->b.W);

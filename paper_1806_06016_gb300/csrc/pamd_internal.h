@@ -70,6 +70,44 @@ struct PropParams {
     uint32_t purpose_mol;      // mol << 8
 };
 
+// Device tables of the all-FP64 mode (PAMD_PREC_FP64); pointers into one
+// device allocation.
+struct TopoF64 {
+    int n_atoms;
+    const double* sigma_half;   // [N]
+    const double* epsilon;      // [N]
+    const double* charge;       // [N]
+    const double* inv_mass;     // [N]
+    const double* x0;           // [3][Np] recentred start geometry
+    const unsigned char* kind;  // [N][N]: 0 full, 1 excluded, 2 scaled 1-4 pair
+    double s14_lj, s14_c;
+    int n_bonds, n_angles, n_dihs;
+    const int* bond;            // [nb][2]
+    const double* bond_p;       // [nb][2] r0, k
+    const int* angle;           // [na][3]
+    const double* angle_p;      // [na][2] theta0, k
+    const int* dih;             // [nd][4]
+    const double* dih_p;        // [nd][4] k, n, cos phase, sin phase
+};
+
+struct PropF64Params {
+    double* state;              // [R][6][Np], updated in place
+    double* E;
+    double* ke;
+    double* rg;
+    double* fout;               // [R][3][Np] or null
+    int* status;
+    const uint32_t* dev_counters;
+    TopoF64 top;
+    int n_pad;
+    long long R;
+    int theta;
+    double dt, T, gamma;
+    unsigned long long seed;
+    uint32_t step0;
+    uint32_t purpose_mol;
+};
+
 struct DevScalars {
     double m;                  // max a_j
     double S;                  // sum exp(a_j - m)
@@ -199,6 +237,8 @@ struct pamd_ctx {
     pamd::HostTopology host_top;
     int lanes_req = 0;
     size_t topo_cap = 0;          // bytes allocated for the device topology table
+    pamd::TopoF64 top64{};        // all-FP64 mode tables (precision == PAMD_PREC_FP64)
+    unsigned char* top64_blob = nullptr;
 };
 
 namespace pamd {
@@ -247,6 +287,14 @@ cudaError_t launch_resample(pamd_ctx* c, double T_prev, double T_next, int do_re
                             const uint32_t* dev_counters, uint32_t resample_offset);
 cudaError_t launch_observe(pamd_ctx* c, double T, pamd_obs* dst);
 cudaError_t launch_set_counters(pamd_ctx* c, uint32_t step, uint32_t ridx);
+
+// all-FP64 mode (propagate_f64.cu)
+cudaError_t launch_propagate_f64(pamd_ctx* c, double* state, double* E, double* ke, double* rg,
+                                 int theta, double dt, double T, const uint32_t* dev_ctr,
+                                 uint32_t step0, double* fout);
+cudaError_t launch_init_f64(pamd_ctx* c, double T0);
+cudaError_t launch_gather_f64(pamd_ctx* c, const double* src, double* dst, const double* Ein,
+                              double* Eout, const int32_t* fin, int32_t* fout, double vscale);
 
 
 }  // namespace pamd

@@ -587,6 +587,13 @@ static int grid_for(long long n, int threads, int cap) {
 }
 
 cudaError_t launch_init(pamd_ctx* c, double T0) {
+    if (c->precision == PAMD_PREC_FP64) {
+        const cudaError_t e = launch_init_f64(c, T0);
+        if (e != cudaSuccess) return e;
+        reset_scalars_kernel<<<1, 1, 0, c->stream>>>(c->b.scal);
+        c->launches += 1;
+        return cudaGetLastError();
+    }
     const long long total = c->R * c->Np;
     init_kernel<<<grid_for(total, 256, c->num_sms * 16), 256, 0, c->stream>>>(
         c->b.state, c->b.E, c->b.fam, c->b.x0, c->b.masses, c->R, c->N, c->Np,
@@ -647,6 +654,13 @@ cudaError_t launch_resample(pamd_ctx* c, double T_prev, double T_next, int do_re
     double* Eout = c->cur_is_alt ? c->b.E : c->b.E_alt;
     const int32_t* fin = c->cur_is_alt ? c->b.fam_alt : c->b.fam;
     int32_t* fout = c->cur_is_alt ? c->b.fam : c->b.fam_alt;
+    if (c->precision == PAMD_PREC_FP64) {
+        const cudaError_t e = launch_gather_f64(
+            c, reinterpret_cast<const double*>(src), reinterpret_cast<double*>(dst), Ein, Eout, fin,
+            fout, sqrt(T_next / T_prev));
+        c->launches += 9;
+        return e != cudaSuccess ? e : cudaGetLastError();
+    }
     const long long warps_needed = R;
     gather_kernel<<<grid_for(warps_needed * 32, 256, c->num_sms * 32), 256, 0, s>>>(
         src, dst, Ein, Eout, fin, fout, c->b.ke, c->b.rg, c->b.cnt_incl, c->b.masses, R, c->N,
