@@ -376,6 +376,93 @@ def run_kernel(args, w):
                       "achieved_tflops": achieved, "frac": achieved / FP32_PEAK_TFLOPS}), flush=True)
 
 
+def run_precision(args):
+    """Large-population precision study (75-atom chain, 60 geometric steps
+    1000 -> 250 K, theta = 200): the mixed FP32/FP64 path against the all-FP64
+    GPU path at the same seeds, force errors against the FP64 oracle, and the
+    resampling throughput at R = 2^20.  Prints one JSON line."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import pamd_inputs as pi
+    from paper_1806_06016_gb300 import build as pbuild
+    from paper_1806_06016_gb300 import pamd
+
+    torch.cuda.set_device(0)
+    pbuild.build()
+    oracle.build()
+    N, theta, K, dt, seed = 75, 200, 60, 0.001, 12345
+    R = args.replicas or 2048
+    top = pi.make_chain(N, 1)
+    temps = pi.geometric_schedule(1000.0, 250.0, K)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    out = {"mode": "precision", "n_atoms": N, "replicas": R, "theta": theta, "temperature_steps": K}
+
+    def anneal(precision):
+        o = pamd.torch_options(precision=precision)
+        pop = pamd.Population(top, R, temps[0], seed, o)
+        if precision == 0:
+            pop.autotune(20)
+        if precision == 0:
+            # warm-up anneal (graph capture); the FP64 anneal runs for tens of
+            # seconds, where the capture is negligible
+            pop.anneal(temps, theta, dt)
+            pop.reset(temps[0], seed)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        obs = pop.anneal(temps, theta, dt)
+        ev1.record(stream)
+        ev1.synchronize()
+        x, _, _, _ = pop.state()
+        f, _ = pop.forces()
+        pop.close()
+        return obs, ev0.elapsed_time(ev1), x, f
+
+    obs32, ms32, x32, f32 = anneal(0)
+    obs64, ms64, x64, f64 = anneal(1)
+    e32 = np.array([o["e_pot"] for o in obs32]); e64 = np.array([o["e_pot"] for o in obs64])
+    s32 = np.array([o["e_pot_se"] for o in obs32]); s64 = np.array([o["e_pot_se"] for o in obs64])
+    g32 = np.array([o["rg"] for o in obs32]); g64 = np.array([o["rg"] for o in obs64])
+    q32 = np.array([o["rg_se"] for o in obs32]); q64 = np.array([o["rg_se"] for o in obs64])
+    comb = np.sqrt(s32 ** 2 + s64 ** 2)
+    out["e_bias_kJmol_max"] = float(np.max(np.abs(e32 - e64)))
+    out["e_bias_in_se_max"] = float(np.max(np.abs(e32 - e64) / comb))
+    out["rg_bias_in_se_max"] = float(np.max(np.abs(g32 - g64) / np.sqrt(q32 ** 2 + q64 ** 2)))
+    out["sum_lnQ_final"] = {"mixed": obs32[-1]["sum_lnQ"], "fp64": obs64[-1]["sum_lnQ"]}
+    out["anneal_ms"] = {"mixed": ms32, "fp64": ms64}
+    # force errors on the final configurations (64 replicas) against the oracle
+    t = oracle.Topo(top)
+    num32 = num64 = den = 0.0
+    for k in range(0, R, max(1, R // 64)):
+        _, fo, _ = oracle.energy_forces(t, x32[k])
+        num32 += float(np.sum((f32[k] - fo) ** 2)); den += float(np.sum(fo ** 2))
+        _, fo64, _ = oracle.energy_forces(t, x64[k])
+        num64 += float(np.sum((f64[k] - fo64) ** 2))
+    out["force_rel_rmse"] = {"mixed": math.sqrt(num32 / den), "fp64": math.sqrt(num64 / den)}
+    # resampling at R = 2^20: whole chain (weights, scans, counts, gather)
+    big = 1 << 20
+    pop = pamd.Population(top, big, 1000.0, seed, pamd.torch_options())
+    pamd.pamd_propagate(pop.ctx, 2, dt, 1000.0)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    ms = []
+    for i in range(4):
+        flush.zero_()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        pamd.pamd_resample(pop.ctx, 1000.0 - 5 * i, 995.0 - 5 * i, want_copies=False)
+        ev1.record(stream)
+        ev1.synchronize()
+        ms.append(ev0.elapsed_time(ev1))
+    pop.close()
+    gather_bytes = 2 * big * 6 * ((N + 3) // 4 * 4) * 4
+    chain_ms = statistics.mean(ms[1:])
+    out["resample_R2p20"] = {"chain_ms": chain_ms, "gather_bytes": gather_bytes,
+                             "gather_GBps_lower_bound": gather_bytes / (chain_ms / 1e3) / 1e9}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -384,7 +471,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["anneal", "kernel"], default="anneal")
+    ap.add_argument("--mode", choices=["anneal", "kernel", "precision"], default="anneal")
     ap.add_argument("--theta", type=int, default=0, help="kernel mode: steps per launch")
     ap.add_argument("--replicas", type=int, default=0, help="kernel mode: population size")
     ap.add_argument("--lanes", type=int, default=0, help="kernel mode: lanes per replica")
@@ -396,6 +483,8 @@ def main():
     w = WORKLOADS[args.workload]
     if args.mode == "kernel":
         run_kernel(args, w)
+    elif args.mode == "precision":
+        run_precision(args)
     elif args.impl == "reference":
         run_reference(args, w)
     else:
