@@ -400,16 +400,15 @@ def run_precision(args):
     torch.cuda.set_stream(stream)
     out = {"mode": "precision", "n_atoms": N, "replicas": R, "theta": theta, "temperature_steps": K}
 
-    def anneal(precision):
+    def anneal(precision, sd):
         o = pamd.torch_options(precision=precision)
-        pop = pamd.Population(top, R, temps[0], seed, o)
+        pop = pamd.Population(top, R, temps[0], sd, o)
         if precision == 0:
             pop.autotune(20)
-        if precision == 0:
             # warm-up anneal (graph capture); the FP64 anneal runs for tens of
             # seconds, where the capture is negligible
             pop.anneal(temps, theta, dt)
-            pop.reset(temps[0], seed)
+            pop.reset(temps[0], sd)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         obs = pop.anneal(temps, theta, dt)
@@ -420,18 +419,34 @@ def run_precision(args):
         pop.close()
         return obs, ev0.elapsed_time(ev1), x, f
 
-    obs32, ms32, x32, f32 = anneal(0)
-    obs64, ms64, x64, f64 = anneal(1)
-    e32 = np.array([o["e_pot"] for o in obs32]); e64 = np.array([o["e_pot"] for o in obs64])
-    s32 = np.array([o["e_pot_se"] for o in obs32]); s64 = np.array([o["e_pot_se"] for o in obs64])
-    g32 = np.array([o["rg"] for o in obs32]); g64 = np.array([o["rg"] for o in obs64])
-    q32 = np.array([o["rg_se"] for o in obs32]); q64 = np.array([o["rg_se"] for o in obs64])
+    # independent anneals (different seeds) of each mode: the two modes are
+    # compared through the spread of their run means, since FP32 rounding
+    # makes even same-seed runs independent realisations
+    seeds = [seed + 1000 * s_ for s_ in range(args.seeds)]
+    runs = {0: [], 1: []}
+    for prec in (0, 1):
+        for s_ in seeds[: (args.seeds if prec == 0 else max(2, args.seeds // 2))]:
+            runs[prec].append(anneal(prec, s_))
+    obs32, ms32, x32, f32 = runs[0][0]
+    obs64, ms64, x64, f64 = runs[1][0]
+
+    def stat(prec, key):
+        a = np.array([[o[key] for o in r[0]] for r in runs[prec]])
+        return a.mean(0), a.std(0, ddof=1) / math.sqrt(a.shape[0]), a
+    e32, s32, _ = stat(0, "e_pot"); e64, s64, _ = stat(1, "e_pot")
+    g32, q32, _ = stat(0, "rg"); g64, q64, _ = stat(1, "rg")
+    f32q, _, _ = stat(0, "sum_lnQ"); f64q, _, _ = stat(1, "sum_lnQ")
     comb = np.sqrt(s32 ** 2 + s64 ** 2)
-    out["e_bias_kJmol_max"] = float(np.max(np.abs(e32 - e64)))
+    out["seeds"] = {"mixed": len(runs[0]), "fp64": len(runs[1])}
+    out["e_bias_kJmol"] = [float(v) for v in (e32 - e64)[::10]]
+    out["e_se_kJmol"] = [float(v) for v in comb[::10]]
+    out["T_K"] = [float(v) for v in temps[::10]]
     out["e_bias_in_se_max"] = float(np.max(np.abs(e32 - e64) / comb))
     out["rg_bias_in_se_max"] = float(np.max(np.abs(g32 - g64) / np.sqrt(q32 ** 2 + q64 ** 2)))
-    out["sum_lnQ_final"] = {"mixed": obs32[-1]["sum_lnQ"], "fp64": obs64[-1]["sum_lnQ"]}
+    out["sum_lnQ_final"] = {"mixed": float(f32q[-1]), "fp64": float(f64q[-1])}
     out["anneal_ms"] = {"mixed": ms32, "fp64": ms64}
+    out["families_final"] = {"mixed": [r[0][-1]["n_families"] for r in runs[0]],
+                             "fp64": [r[0][-1]["n_families"] for r in runs[1]]}
     # force errors on the final configurations (64 replicas) against the oracle
     t = oracle.Topo(top)
     num32 = num64 = den = 0.0
@@ -479,6 +494,7 @@ def main():
     ap.add_argument("--autotune", action="store_true", help="kernel mode: tune the launch shape")
     ap.add_argument("--rpl", type=int, default=0, help="kernel mode: replicas per lane group (1, 2)")
     ap.add_argument("--fp64", action="store_true", help="kernel mode: all-FP64 propagate")
+    ap.add_argument("--seeds", type=int, default=8, help="precision mode: independent anneals")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.mode == "kernel":
