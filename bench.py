@@ -478,6 +478,45 @@ def run_precision(args):
     print(json.dumps(out), flush=True)
 
 
+def run_resample(args):
+    """Resampling of a large population (75-atom chain, R = 2^20 by default):
+    the whole chain (weights, scans, copy counts, gather) timed with events
+    on its stream, and the gather's algorithmic bytes (state read + written,
+    2 x 6 Np x 4 B per replica).  Prints one JSON line."""
+    import torch
+
+    import pamd_inputs as pi
+    from paper_1806_06016_gb300 import build as pbuild
+    from paper_1806_06016_gb300 import pamd
+
+    torch.cuda.set_device(0)
+    pbuild.build()
+    N = 75
+    R = args.replicas or (1 << 20)
+    top = pi.make_chain(N, 1)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    pop = pamd.Population(top, R, 1000.0, 12345, pamd.torch_options())
+    pamd.pamd_propagate(pop.ctx, 2, 0.001, 1000.0)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    ms = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        pamd.pamd_resample(pop.ctx, 1000.0 - 2 * i, 998.0 - 2 * i, want_copies=False)
+        ev1.record(stream)
+        ev1.synchronize()
+        if i >= args.warmup:
+            ms.append(ev0.elapsed_time(ev1))
+    pop.close()
+    gather_bytes = 2 * R * 6 * ((N + 3) // 4 * 4) * 4
+    chain = statistics.mean(ms)
+    print(json.dumps({"mode": "resample", "n_atoms": N, "replicas": R, "chain_ms": chain,
+                      "gather_bytes": gather_bytes,
+                      "chain_GBps": gather_bytes / (chain / 1e3) / 1e9}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -486,7 +525,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["anneal", "kernel", "precision"], default="anneal")
+    ap.add_argument("--mode", choices=["anneal", "kernel", "precision", "resample"], default="anneal")
     ap.add_argument("--theta", type=int, default=0, help="kernel mode: steps per launch")
     ap.add_argument("--replicas", type=int, default=0, help="kernel mode: population size")
     ap.add_argument("--lanes", type=int, default=0, help="kernel mode: lanes per replica")
@@ -501,6 +540,8 @@ def main():
         run_kernel(args, w)
     elif args.mode == "precision":
         run_precision(args)
+    elif args.mode == "resample":
+        run_resample(args)
     elif args.impl == "reference":
         run_reference(args, w)
     else:
