@@ -351,46 +351,61 @@ __global__ void cnt_local_kernel(const int32_t* cnt, long long R, const int32_t*
 
 // ------------------------------------------------------------------ gather
 
-// One warp per new slot k: ancestor j = first index with incl_j > k; the
-// replica's state (6 Np floats, Np % 4 == 0) is moved as float4s.  Positions
-// are shifted to the centre of mass, velocities scaled by vscale, and the new
-// replica's kinetic energy and radius of gyration are recomputed from the
-// moved state.
-__global__ void gather_kernel(const float* __restrict__ st_in, float* __restrict__ st_out,
-                              const double* E_in, double* E_out, const int32_t* fam_in,
-                              int32_t* fam_out, double* ke_out, double* rg_out,
-                              const int32_t* incl, const float* masses, long long R, int N,
-                              int Np, float vscale, float inv_mtot) {
-    const int lane = threadIdx.x & 31;
-    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    const int q4 = Np / 4;          // float4s per component
-    const int nq = 6 * q4;          // float4s per replica
-    for (long long k = warp; k < R; k += nwarps) {
+// Ancestor of every new slot: anc[k] = first j with incl_j > k (copies of j
+// fill slots incl_{j-1} .. incl_j - 1).  One thread per slot.
+__global__ void ancestor_kernel(const int32_t* __restrict__ incl, long long R, int32_t* anc) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < R;
+         k += (long long)gridDim.x * blockDim.x) {
         long long lo = 0, hi = R;
         while (lo < hi) {
             const long long mid = lo + ((hi - lo) >> 1);
             if (incl[mid] > k) hi = mid;
             else lo = mid + 1;
         }
-        const long long j = lo < R ? lo : R - 1;
+        anc[k] = (int32_t)(lo < R ? lo : R - 1);
+    }
+}
+
+// One warp per new slot k copies the ancestor's state (6 Np floats, Np % 4 ==
+// 0) as P float4s per lane: positions shifted to the centre of mass,
+// velocities scaled by vscale, and the new replica's kinetic energy and
+// radius of gyration recomputed from the moved state (FP32 sums: GB300's FP64
+// rate is a small fraction of its FP32 rate, and every propagate launch
+// recomputes these values in FP64).
+template <int P>
+__global__ void __launch_bounds__(256) gather_kernel(
+    const float* __restrict__ st_in, float* __restrict__ st_out, const double* E_in,
+    double* E_out, const int32_t* fam_in, int32_t* fam_out, double* ke_out, double* rg_out,
+    const int32_t* __restrict__ anc, const float* __restrict__ masses, long long R, int N, int Np,
+    float vscale, float inv_mtot) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int q4 = Np / 4;          // float4s per component
+    const int nq = 6 * q4;          // float4s per replica
+    const float4* m4 = reinterpret_cast<const float4*>(masses);
+    for (long long k = warp; k < R; k += nwarps) {
+        const long long j = anc[k];
         const float4* src = reinterpret_cast<const float4*>(st_in + (size_t)j * 6 * Np);
         float4* dst = reinterpret_cast<float4*>(st_out + (size_t)k * 6 * Np);
-        constexpr int kMaxPer = 12;  // float4s per lane: 6 Np / 4 <= 384 for Np <= 256
-        float4 v[kMaxPer];
+        float4 v[P];
+#pragma unroll
+        for (int r = 0; r < P; ++r) {
+            const int q = lane + 32 * r;
+            if (q < nq) v[r] = __ldcs(src + q);  // read once: streaming load
+        }
         float sx = 0.f, sy = 0.f, sz = 0.f;
 #pragma unroll
-        for (int r = 0; r < kMaxPer; ++r) {
+        for (int r = 0; r < P; ++r) {
             const int q = lane + 32 * r;
             if (q < nq) {
-                v[r] = src[q];
                 const int comp = q / q4;
                 if (comp < 3) {
-                    const float4 m = reinterpret_cast<const float4*>(masses)[q - comp * q4];
+                    const float4 m = m4[q - comp * q4];
                     const float s = m.x * v[r].x + m.y * v[r].y + m.z * v[r].z + m.w * v[r].w;
-                    if (comp == 0) sx += s;
-                    else if (comp == 1) sy += s;
-                    else sz += s;
+                    sx += comp == 0 ? s : 0.f;
+                    sy += comp == 1 ? s : 0.f;
+                    sz += comp == 2 ? s : 0.f;
                 }
             }
         }
@@ -401,36 +416,31 @@ __global__ void gather_kernel(const float* __restrict__ st_in, float* __restrict
             sz += __shfl_xor_sync(0xffffffffu, sz, o);
         }
         const float cx = sx * inv_mtot, cy = sy * inv_mtot, cz = sz * inv_mtot;
-        double mv2 = 0.0, ux = 0.0, uy = 0.0, uz = 0.0, u2 = 0.0;
+        float mv2 = 0.f, ux = 0.f, uy = 0.f, uz = 0.f, u2 = 0.f;
 #pragma unroll
-        for (int r = 0; r < kMaxPer; ++r) {
+        for (int r = 0; r < P; ++r) {
             const int q = lane + 32 * r;
             if (q < nq) {
                 const int comp = q / q4;
                 const int i0 = (q - comp * q4) * 4;
                 float4 w = v[r];
+                const float4 m = m4[q - comp * q4];  // 0 for padding atoms
+                // padding atoms (i >= N) are kept out of the sums
+                const float4 real = make_float4(i0 < N ? 1.f : 0.f, i0 + 1 < N ? 1.f : 0.f,
+                                                i0 + 2 < N ? 1.f : 0.f, i0 + 3 < N ? 1.f : 0.f);
                 if (comp < 3) {
                     const float c = (comp == 0) ? cx : (comp == 1) ? cy : cz;
                     w.x -= c; w.y -= c; w.z -= c; w.w -= c;
-                    const float e[4] = {w.x, w.y, w.z, w.w};
-                    double s1 = 0.0;
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        if (i0 + t < N) {
-                            s1 += e[t];
-                            u2 += (double)e[t] * e[t];
-                        }
-                    }
-                    if (comp == 0) ux += s1;
-                    else if (comp == 1) uy += s1;
-                    else uz += s1;
+                    const float s1 = real.x * w.x + real.y * w.y + real.z * w.z + real.w * w.w;
+                    u2 += real.x * w.x * w.x + real.y * w.y * w.y + real.z * w.z * w.z + real.w * w.w * w.w;
+                    ux += comp == 0 ? s1 : 0.f;
+                    uy += comp == 1 ? s1 : 0.f;
+                    uz += comp == 2 ? s1 : 0.f;
                 } else {
                     w.x *= vscale; w.y *= vscale; w.z *= vscale; w.w *= vscale;
-                    const float4 m = reinterpret_cast<const float4*>(masses)[q - comp * q4];
-                    mv2 += (double)m.x * w.x * w.x + (double)m.y * w.y * w.y +
-                           (double)m.z * w.z * w.z + (double)m.w * w.w * w.w;
+                    mv2 += m.x * w.x * w.x + m.y * w.y * w.y + m.z * w.z * w.z + m.w * w.w * w.w;
                 }
-                dst[q] = w;
+                __stcs(dst + q, w);  // written once: streaming store
             }
         }
 #pragma unroll
@@ -444,10 +454,9 @@ __global__ void gather_kernel(const float* __restrict__ st_in, float* __restrict
         if (lane == 0) {
             E_out[k] = E_in[j];
             fam_out[k] = fam_in[j];
-            ke_out[k] = 0.5 * mv2;
-            const double mx = ux / N, my = uy / N, mz = uz / N;
-            const double r2 = u2 / N - (mx * mx + my * my + mz * mz);
-            rg_out[k] = sqrt(fmax(r2, 0.0));
+            ke_out[k] = 0.5 * (double)mv2;
+            const float mx = ux / N, my = uy / N, mz = uz / N;
+            rg_out[k] = (double)sqrtf(fmaxf(u2 / N - (mx * mx + my * my + mz * mz), 0.f));
         }
     }
 }
@@ -661,11 +670,24 @@ cudaError_t launch_resample(pamd_ctx* c, double T_prev, double T_next, int do_re
         c->launches += 9;
         return e != cudaSuccess ? e : cudaGetLastError();
     }
-    const long long warps_needed = R;
-    gather_kernel<<<grid_for(warps_needed * 32, 256, c->num_sms * 32), 256, 0, s>>>(
-        src, dst, Ein, Eout, fin, fout, c->b.ke, c->b.rg, c->b.cnt_incl, c->b.masses, R, c->N,
-        c->Np, (float)sqrt(T_next / T_prev), (float)(1.0 / mt));
-    c->launches += 10;
+    // ancestors of the new slots (into the weight buffer, no longer needed)
+    int32_t* anc = reinterpret_cast<int32_t*>(c->b.W);
+    ancestor_kernel<<<grid_for(R, 256, c->num_sms * 16), 256, 0, s>>>(c->b.cnt_incl, R, anc);
+    const int gridg = grid_for(R * 32, 256, c->num_sms * 64);
+    const float vs = (float)sqrt(T_next / T_prev), imt = (float)(1.0 / mt);
+    switch ((6 * (c->Np / 4) + 31) / 32) {
+#define PAMD_GATHER_CASE(P)                                                                     \
+    case P:                                                                                     \
+        gather_kernel<P><<<gridg, 256, 0, s>>>(src, dst, Ein, Eout, fin, fout, c->b.ke, c->b.rg, \
+                                               anc, c->b.masses, R, c->N, c->Np, vs, imt);      \
+        break;
+        PAMD_GATHER_CASE(1) PAMD_GATHER_CASE(2) PAMD_GATHER_CASE(3) PAMD_GATHER_CASE(4)
+        PAMD_GATHER_CASE(5) PAMD_GATHER_CASE(6) PAMD_GATHER_CASE(7) PAMD_GATHER_CASE(8)
+        PAMD_GATHER_CASE(9) PAMD_GATHER_CASE(10) PAMD_GATHER_CASE(11) PAMD_GATHER_CASE(12)
+#undef PAMD_GATHER_CASE
+        default: return cudaErrorInvalidValue;
+    }
+    c->launches += 11;
     return cudaGetLastError();
 }
 
