@@ -149,6 +149,31 @@ int pamd_init(pamd_ctx** out, const pamd_topology* top, int64_t R, double T0, ui
               const pamd_options* opt);
 
 /*
+ * Batched independent anneals: n_mol molecules (1..64) of uneven size, each
+ * with its own population R[m], start temperature T0[m] and Philox stream
+ * (molecule index m mixed into the counters), advanced by ONE persistent
+ * launch per pamd_propagate (a device work queue of (molecule, replica
+ * batch) items, largest molecules first; each molecule keeps its own launch
+ * shape with 3..7 atoms per lane).  On a batch context pamd_reset,
+ * pamd_propagate, pamd_resample (copies_out: [sum R] in molecule order, lnQ_out:
+ * [n_mol]), pamd_observables (out: [n_mol]) and pamd_anneal (per_step_out:
+ * [(K+1) * n_mol], temperature-major; one CUDA graph for the whole batch) act
+ * on every molecule with a common temperature schedule; state access goes
+ * through pamd_batch_sub.  Mixed precision only.  opt: as for pamd_init
+ * (lanes_per_replica, warps_per_block, mol_id and autotune are chosen per
+ * molecule and ignored).
+ */
+int pamd_init_batch(pamd_ctx** out, int32_t n_mol, const pamd_topology* tops, const int64_t* R,
+                    const double* T0, uint64_t seed, const pamd_options* opt);
+
+/* Number of molecules of a batch context (0 for an ordinary context). */
+int32_t pamd_batch_size(pamd_ctx* ctx);
+
+/* The ordinary context of molecule m of a batch (owned by the batch: valid
+ * until pamd_destroy of the batch, not to be destroyed separately), or NULL. */
+pamd_ctx* pamd_batch_sub(pamd_ctx* ctx, int32_t m);
+
+/*
  * PAMD scheme, step 1 again on an existing context: the population is reset
  * exactly as pamd_init left it for (T0, seed) -- start geometry, fresh
  * Maxwell-Boltzmann velocities, family id = slot -- and the random counters

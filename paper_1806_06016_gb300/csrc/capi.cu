@@ -420,6 +420,10 @@ size_t state_bytes(const pamd_ctx* c) {
 double* cur_E(pamd_ctx* c) { return c->cur_is_alt ? c->b.E_alt : c->b.E; }
 int32_t* cur_fam(pamd_ctx* c) { return c->cur_is_alt ? c->b.fam_alt : c->b.fam; }
 
+void fill_prop_params(pamd_ctx* c, PropParams& p, float* state, double* E, double* ke, double* rg,
+                      int theta, double dt, double T, const uint32_t* dev_ctr, uint32_t step0,
+                      float* fout);
+
 int launch_prop_on(pamd_ctx* c, float* state, double* E, double* ke, double* rg, int theta,
                    double dt, double T, const uint32_t* dev_ctr, uint32_t step0, float* fout) {
     if (is_f64(c)) {
@@ -429,6 +433,17 @@ int launch_prop_on(pamd_ctx* c, float* state, double* E, double* ke, double* rg,
         return PAMD_OK;
     }
     PropParams p{};
+    fill_prop_params(c, p, state, E, ke, rg, theta, dt, T, dev_ctr, step0, fout);
+    cudaError_t e = propagate_dispatch_any(c->lay, &p, c->warps_per_block, c->grid_prop,
+                                           prop_smem(c), c->stream, nullptr);
+    c->launches += 1;
+    if (e != cudaSuccess) return cuda_fail(c, e, "propagate launch");
+    return PAMD_OK;
+}
+
+void fill_prop_params(pamd_ctx* c, PropParams& p, float* state, double* E, double* ke, double* rg,
+                      int theta, double dt, double T, const uint32_t* dev_ctr, uint32_t step0,
+                      float* fout) {
     p.state_in = state;
     p.state_out = state;
     p.E = E;
@@ -449,11 +464,6 @@ int launch_prop_on(pamd_ctx* c, float* state, double* E, double* ke, double* rg,
     p.seed = c->seed;
     p.step0 = step0;
     p.purpose_mol = kPurposeNoise | ((uint32_t)c->mol << 8);
-    cudaError_t e = propagate_dispatch_any(c->lay, &p, c->warps_per_block, c->grid_prop,
-                                           prop_smem(c), c->stream, nullptr);
-    c->launches += 1;
-    if (e != cudaSuccess) return cuda_fail(c, e, "propagate launch");
-    return PAMD_OK;
 }
 
 int launch_prop(pamd_ctx* c, int theta, double dt, double T, const uint32_t* dev_ctr,
@@ -618,6 +628,36 @@ int set_launch_shape(pamd_ctx* c, const TopoLayout& lay_in, int warps_req, int p
     return PAMD_OK;
 }
 
+bool is_batch(const pamd_ctx* c) { return !c->subs.empty(); }
+
+// One launch of the batched kernel over every molecule of a batch context.
+// graph: counters come from each molecule's device counters plus step_off.
+int launch_prop_batch(pamd_ctx* c, int theta, double dt, double T, bool graph, uint32_t step_off) {
+    BatchParams bp{};
+    bp.n_items = c->n_items;
+    bp.items = c->items;
+    bp.queue = c->queue;
+    for (size_t m = 0; m < c->subs.size(); ++m) {
+        pamd_ctx* s = c->subs[m];
+        fill_prop_params(s, bp.mol[m], cur_state(s), cur_E(s), s->b.ke, s->b.rg, theta, dt, T,
+                         graph ? s->b.counters : nullptr, graph ? step_off : s->step, nullptr);
+    }
+    PAMD_CU(c, cudaMemsetAsync(c->queue, 0, sizeof(int), c->stream));
+    const cudaError_t e = launch_propagate_batch(bp, c->batch_grid, c->batch_smem, c->stream);
+    c->launches += 1;
+    if (e != cudaSuccess) return cuda_fail(c, e, "batched propagate launch");
+    return PAMD_OK;
+}
+
+// Atoms per lane of a molecule in a batch: the cost-model choice kept in the
+// batched kernel's range 3..7.
+int batch_lanes(int N) {
+    int L = 0, B = 0;
+    if (choose_lanes(N, 0, &L, &B)) return 0;
+    B = std::min(7, std::max(3, B));
+    return (N + B - 1) / B;
+}
+
 int check_ctx(pamd_ctx* c) {
     if (!c) return fail(PAMD_EINVAL, "null context");
     if (c->broken) return fail(PAMD_ESTATE, "context broken by an earlier CUDA failure");
@@ -652,6 +692,113 @@ int ensure_obs_cap(pamd_ctx* c, int n) {
 namespace pamd {
 void set_last_error(const std::string& msg) { g_err = msg; }
 }  // namespace pamd
+
+namespace {
+
+// Whole batched anneal as one CUDA graph: the batched propagate launch, then
+// per molecule its resampling and measurement, for every temperature step.
+int anneal_batch(pamd_ctx* c, int32_t K, const double* T, int32_t theta, double dt_ps,
+                 int32_t resample, pamd_obs* per_step_out) {
+    if (K < 0 || !T) return fail(PAMD_EINVAL, "K must be >= 0 and T non-null");
+    if (theta < 0 || !(dt_ps > 0) || !std::isfinite(dt_ps)) return fail(PAMD_EINVAL, "theta / dt");
+    for (int i = 0; i <= K; ++i)
+        if (!(T[i] > 0) || !std::isfinite(T[i])) return fail(PAMD_EINVAL, "temperatures must be > 0");
+    int rc;
+    for (pamd_ctx* sub : c->subs) {
+        if ((rc = ensure_obs_cap(sub, K + 1))) return rc;
+        if (sub->cur_is_alt) {
+            const size_t st = state_bytes(sub);
+            PAMD_CU(c, cudaMemcpyAsync(sub->b.state, sub->b.state_alt, st, cudaMemcpyDeviceToDevice, c->stream));
+            PAMD_CU(c, cudaMemcpyAsync(sub->b.E, sub->b.E_alt, 8 * (size_t)sub->R, cudaMemcpyDeviceToDevice, c->stream));
+            PAMD_CU(c, cudaMemcpyAsync(sub->b.fam, sub->b.fam_alt, 4 * (size_t)sub->R, cudaMemcpyDeviceToDevice, c->stream));
+            sub->cur_is_alt = false;
+        }
+    }
+    GraphKey key;
+    key.K = K;
+    key.theta = theta;
+    key.resample = resample ? 1 : 0;
+    key.dt = dt_ps;
+    key.T.assign(T, T + K + 1);
+    if (!c->graph_exec || !(c->graph_key == key)) {
+        if (c->graph_exec) {
+            cudaGraphExecDestroy(c->graph_exec);
+            c->graph_exec = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        PAMD_CU(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        long long before = c->launches;
+        for (pamd_ctx* sub : c->subs) before += sub->launches;
+        int err = launch_prop_batch(c, theta, dt_ps, T[0], true, 0u);
+        for (pamd_ctx* sub : c->subs)
+            if (!err && launch_observe(sub, T[0], sub->b.obs) != cudaSuccess) err = PAMD_ECUDA;
+        for (int i = 1; i <= K && !err; ++i) {
+            for (pamd_ctx* sub : c->subs) {
+                if (launch_resample(sub, T[i - 1], T[i], resample ? 1 : 0, sub->b.counters, (uint32_t)i) != cudaSuccess) {
+                    err = PAMD_ECUDA;
+                    break;
+                }
+                sub->cur_is_alt = !sub->cur_is_alt;
+            }
+            if (!err) err = launch_prop_batch(c, theta, dt_ps, T[i], true, (uint32_t)i * (uint32_t)theta);
+            for (pamd_ctx* sub : c->subs)
+                if (!err && launch_observe(sub, T[i], sub->b.obs + i) != cudaSuccess) err = PAMD_ECUDA;
+        }
+        for (pamd_ctx* sub : c->subs) {
+            if (!err && sub->cur_is_alt) {
+                const size_t st = state_bytes(sub);
+                if (cudaMemcpyAsync(sub->b.state, sub->b.state_alt, st, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
+                    cudaMemcpyAsync(sub->b.E, sub->b.E_alt, 8 * (size_t)sub->R, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
+                    cudaMemcpyAsync(sub->b.fam, sub->b.fam_alt, 4 * (size_t)sub->R, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+                    err = PAMD_ECUDA;
+            }
+            sub->cur_is_alt = false;
+        }
+        long long after = c->launches;
+        for (pamd_ctx* sub : c->subs) after += sub->launches;
+        c->graph_kernels = after - before;
+        // the captured launches are counted when the graph runs, not now
+        c->launches -= c->graph_kernels;
+        cudaError_t ec = cudaStreamEndCapture(c->stream, &g);
+        if (err || ec != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            c->broken = true;
+            return fail(PAMD_ECUDA, std::string("batched anneal capture failed: ") + cudaGetErrorString(ec));
+        }
+        cudaError_t ei = cudaGraphInstantiate(&c->graph_exec, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) return cuda_fail(c, ei, "graph instantiate");
+        c->graph_key = key;
+    }
+    for (pamd_ctx* sub : c->subs) {
+        cudaError_t e = launch_set_counters(sub, sub->step, sub->resample_index);
+        if (e != cudaSuccess) return cuda_fail(c, e, "set counters");
+    }
+    PAMD_CU(c, cudaGraphLaunch(c->graph_exec, c->stream));
+    c->launches += c->graph_kernels;
+    for (pamd_ctx* sub : c->subs) {
+        sub->step += (uint32_t)(K + 1) * (uint32_t)theta;
+        sub->resample_index += (uint32_t)K;
+    }
+    const int M = (int)c->subs.size();
+    std::vector<pamd_obs> tmp((size_t)(K + 1));
+    for (int m = 0; m < M; ++m) {
+        pamd_ctx* sub = c->subs[m];
+        if (per_step_out) {
+            PAMD_CU(c, cudaMemcpyAsync(tmp.data(), sub->b.obs, sizeof(pamd_obs) * (size_t)(K + 1),
+                                       cudaMemcpyDeviceToHost, c->stream));
+            PAMD_CU(c, cudaStreamSynchronize(c->stream));
+            for (int i = 0; i <= K; ++i) {
+                per_step_out[(size_t)i * M + m] = tmp[i];
+                per_step_out[(size_t)i * M + m].pad_ = 0;
+            }
+        }
+        if ((rc = read_status(sub))) return rc;
+    }
+    return PAMD_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -805,9 +952,117 @@ int pamd_init(pamd_ctx** out, const pamd_topology* top, int64_t R, double T0, ui
     return PAMD_OK;
 }
 
+int pamd_init_batch(pamd_ctx** out, int32_t n_mol, const pamd_topology* tops, const int64_t* R,
+                    const double* T0, uint64_t seed, const pamd_options* opt) {
+    g_err.clear();
+    if (!out || !tops || !R || !T0) return fail(PAMD_EINVAL, "null argument");
+    *out = nullptr;
+    if (n_mol < 1 || n_mol > kMaxBatchMols) return fail(PAMD_EINVAL, "n_mol must be 1..64");
+    pamd_options o;
+    pamd_options_default(&o);
+    if (opt) o = *opt;
+    if (o.precision != PAMD_PREC_MIXED)
+        return fail(PAMD_EUNSUPPORTED, "the batched kernel runs the mixed-precision path only");
+    if (o.replicas_per_lane > 1) return fail(PAMD_EUNSUPPORTED, "the batched kernel runs one replica per lane group");
+    if ((o.dev_alloc == nullptr) != (o.dev_free == nullptr))
+        return fail(PAMD_EINVAL, "dev_alloc and dev_free must both be set or both be NULL");
+    for (int m = 0; m < n_mol; ++m)
+        if (R[m] < 1 || R[m] > 0x7fffffffLL) return fail(PAMD_EINVAL, "every R must be in 1 .. 2^31-1");
+    pamd_ctx* c = new (std::nothrow) pamd_ctx();
+    if (!c) return fail(PAMD_ENOMEM, "host allocation");
+    c->dev_alloc = o.dev_alloc;
+    c->dev_free = o.dev_free;
+    c->alloc_user = o.alloc_user;
+    c->seed = seed;
+    auto bail = [&](int code, const std::string& m) {
+        for (pamd_ctx* s : c->subs) pamd_destroy(s);
+        c->subs.clear();
+        free_all(c);
+        if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+        delete c;
+        return fail(code, m);
+    };
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return bail(PAMD_ECUDA, "no CUDA device");
+    if (o.stream) {
+        c->stream = (cudaStream_t)o.stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(PAMD_ECUDA, "stream creation");
+        c->own_stream = true;
+    }
+    // one ordinary context per molecule, sharing the stream
+    std::vector<std::pair<int, int>> order;  // (N, m)
+    for (int m = 0; m < n_mol; ++m) {
+        pamd_options so = o;
+        so.mol_id = m;
+        so.stream = c->stream;
+        so.warps_per_block = kBatchThreads / 32;
+        so.autotune = 0;
+        so.replicas_per_lane = 1;
+        so.lanes_per_replica = tops[m].n_atoms >= 1 && tops[m].n_atoms <= PAMD_MAX_ATOMS
+                                   ? batch_lanes(tops[m].n_atoms) : 0;
+        pamd_ctx* sub = nullptr;
+        const int rc = pamd_init(&sub, &tops[m], R[m], T0[m], seed, &so);
+        if (rc) {
+            const std::string msg = "molecule " + std::to_string(m) + ": " + g_err;
+            return bail(rc, msg);
+        }
+        c->subs.push_back(sub);
+        if (sub->warps_per_block != kBatchThreads / 32 || sub->lay.per_lane < 3 || sub->lay.per_lane > 7)
+            return bail(PAMD_EUNSUPPORTED, "molecule " + std::to_string(m) + " does not fit the batched kernel");
+        c->R += R[m];
+        c->N = std::max(c->N, sub->N);
+        order.push_back({sub->N, m});
+    }
+    // work list: molecules by decreasing size, each cut into one CTA's worth of replicas
+    std::stable_sort(order.begin(), order.end(), [](auto a, auto b) { return a.first > b.first; });
+    std::vector<int4> items;
+    size_t smem = 0;
+    for (auto& om : order) {
+        pamd_ctx* sub = c->subs[om.second];
+        for (long long k0 = 0; k0 < sub->R; k0 += sub->rpb)
+            items.push_back(make_int4(om.second, (int)k0, (int)std::min<long long>(k0 + sub->rpb, sub->R), 0));
+        smem = std::max(smem, prop_smem(sub));
+    }
+    c->n_items = (int)items.size();
+    c->items = (int4*)dalloc(c, sizeof(int4) * items.size());
+    c->queue = (int*)dalloc(c, sizeof(int));
+    if (!c->items || !c->queue) return bail(PAMD_ENOMEM, "work list");
+    int occ = 0;
+    const cudaError_t e = propagate_batch_occupancy(smem, &occ);
+    if (e != cudaSuccess || occ < 1)
+        return bail(PAMD_ECUDA, std::string("batched kernel occupancy: ") + cudaGetErrorString(e));
+    c->batch_smem = smem;
+    c->batch_grid = std::min(c->n_items, c->num_sms * occ);
+    if (cudaMemcpyAsync(c->items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice,
+                        c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return bail(PAMD_ECUDA, "work list upload");
+    *out = c;
+    return PAMD_OK;
+}
+
+int32_t pamd_batch_size(pamd_ctx* c) { return c ? (int32_t)c->subs.size() : -1; }
+
+pamd_ctx* pamd_batch_sub(pamd_ctx* c, int32_t m) {
+    if (!c || m < 0 || m >= (int32_t)c->subs.size()) {
+        g_err = "no such molecule in this batch";
+        return nullptr;
+    }
+    return c->subs[m];
+}
+
 int pamd_reset(pamd_ctx* c, double T0, uint64_t seed) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if (is_batch(c)) {
+        for (pamd_ctx* sub : c->subs)
+            if ((rc = pamd_reset(sub, T0, seed))) return rc;
+        return PAMD_OK;
+    }
     if (!(T0 > 0) || !std::isfinite(T0)) return fail(PAMD_EINVAL, "T0 must be > 0");
     c->seed = seed;
     c->cur_is_alt = false;
@@ -821,6 +1076,13 @@ int pamd_reset(pamd_ctx* c, double T0, uint64_t seed) {
 int pamd_propagate(pamd_ctx* c, int32_t theta, double dt_ps, double T) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if (is_batch(c)) {
+        if (theta < 0 || !(dt_ps > 0) || !(T > 0) || !std::isfinite(dt_ps) || !std::isfinite(T))
+            return fail(PAMD_EINVAL, "theta >= 0, dt > 0 and T > 0 required");
+        if ((rc = launch_prop_batch(c, theta, dt_ps, T, false, 0))) return rc;
+        for (pamd_ctx* sub : c->subs) sub->step += (uint32_t)theta;
+        return PAMD_OK;
+    }
     if (theta < 0) return fail(PAMD_EINVAL, "theta must be >= 0");
     if (!(dt_ps > 0) || !std::isfinite(dt_ps)) return fail(PAMD_EINVAL, "dt must be > 0");
     if (!(T > 0) || !std::isfinite(T)) return fail(PAMD_EINVAL, "T must be > 0");
@@ -833,6 +1095,19 @@ int pamd_propagate(pamd_ctx* c, int32_t theta, double dt_ps, double T) {
 int pamd_resample(pamd_ctx* c, double T_prev, double T_next, int32_t* copies_out, double* lnQ_out) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if (is_batch(c)) {
+        if (!(T_prev > 0) || !(T_next > 0) || !std::isfinite(T_prev) || !std::isfinite(T_next))
+            return fail(PAMD_EINVAL, "temperatures must be > 0");
+        long long off = 0;
+        for (size_t m = 0; m < c->subs.size(); ++m) {
+            pamd_ctx* sub = c->subs[m];
+            if ((rc = pamd_resample(sub, T_prev, T_next, copies_out ? copies_out + off : nullptr,
+                                    lnQ_out ? lnQ_out + m : nullptr)))
+                return rc;
+            off += sub->R;
+        }
+        return PAMD_OK;
+    }
     if (!(T_prev > 0) || !(T_next > 0) || !std::isfinite(T_prev) || !std::isfinite(T_next))
         return fail(PAMD_EINVAL, "temperatures must be > 0");
     c->resample_index += 1;
@@ -850,6 +1125,12 @@ int pamd_resample(pamd_ctx* c, double T_prev, double T_next, int32_t* copies_out
 int pamd_observables(pamd_ctx* c, double T, pamd_obs* out) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if (is_batch(c)) {
+        if (!out) return fail(PAMD_EINVAL, "null output");
+        for (size_t m = 0; m < c->subs.size(); ++m)
+            if ((rc = pamd_observables(c->subs[m], T, out + m))) return rc;
+        return PAMD_OK;
+    }
     if (!out) return fail(PAMD_EINVAL, "null output");
     cudaError_t e = launch_observe(c, T, c->b.obs);
     if (e != cudaSuccess) return cuda_fail(c, e, "observables launch");
@@ -863,6 +1144,7 @@ int pamd_anneal(pamd_ctx* c, int32_t K, const double* T, int32_t theta, double d
                 int32_t resample, pamd_obs* per_step_out) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if (is_batch(c)) return anneal_batch(c, K, T, theta, dt_ps, resample, per_step_out);
     if (K < 0 || !T) return fail(PAMD_EINVAL, "K must be >= 0 and T non-null");
     if (theta < 0 || !(dt_ps > 0) || !std::isfinite(dt_ps)) return fail(PAMD_EINVAL, "theta / dt");
     for (int i = 0; i <= K; ++i)
@@ -941,6 +1223,7 @@ int pamd_anneal(pamd_ctx* c, int32_t K, const double* T, int32_t theta, double d
 int pamd_get_state(pamd_ctx* c, double* x, double* v, double* E, int32_t* fam) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if (is_batch(c)) return fail(PAMD_EINVAL, "batch context: call this on pamd_batch_sub(ctx, m)");
     const int N = c->N, Np = c->Np;
     const long long R = c->R;
     std::vector<float> st;
@@ -970,6 +1253,7 @@ int pamd_get_state(pamd_ctx* c, double* x, double* v, double* E, int32_t* fam) {
 int pamd_set_state(pamd_ctx* c, const double* x, const double* v, const double* E, const int32_t* fam) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if (is_batch(c)) return fail(PAMD_EINVAL, "batch context: call this on pamd_batch_sub(ctx, m)");
     if (!x || !v) return fail(PAMD_EINVAL, "x and v are required");
     const int N = c->N, Np = c->Np;
     const long long R = c->R;
@@ -1010,6 +1294,7 @@ int pamd_set_state(pamd_ctx* c, const double* x, const double* v, const double* 
 int pamd_forces(pamd_ctx* c, double* f, double* E) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if (is_batch(c)) return fail(PAMD_EINVAL, "batch context: call this on pamd_batch_sub(ctx, m)");
     const int N = c->N, Np = c->Np;
     const long long R = c->R;
     const size_t es = is_f64(c) ? 8 : 4;
@@ -1040,6 +1325,7 @@ int pamd_forces(pamd_ctx* c, double* f, double* E) {
 int pamd_autotune(pamd_ctx* c, int32_t theta_probe, pamd_tune* out) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if (is_batch(c)) return fail(PAMD_EINVAL, "batch context: call this on pamd_batch_sub(ctx, m)");
     if (theta_probe < 1 || theta_probe > 1000) return fail(PAMD_EINVAL, "theta_probe must be 1..1000");
     if (is_f64(c)) {  // one fixed shape (a warp per replica)
         if (out) *out = pamd_tune{32, (c->N + 31) / 32, 4, 1, 0, 0.0};
@@ -1147,6 +1433,7 @@ int pamd_autotune(pamd_ctx* c, int32_t theta_probe, pamd_tune* out) {
 int pamd_get_counters(pamd_ctx* c, uint32_t* step, uint32_t* ridx, double* sum_lnQ) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if (is_batch(c)) return fail(PAMD_EINVAL, "batch context: call this on pamd_batch_sub(ctx, m)");
     if (step) *step = c->step;
     if (ridx) *ridx = c->resample_index;
     if (sum_lnQ) {
@@ -1159,6 +1446,7 @@ int pamd_get_counters(pamd_ctx* c, uint32_t* step, uint32_t* ridx, double* sum_l
 int pamd_set_counters(pamd_ctx* c, uint32_t step, uint32_t ridx, double sum_lnQ) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if (is_batch(c)) return fail(PAMD_EINVAL, "batch context: call this on pamd_batch_sub(ctx, m)");
     if (!std::isfinite(sum_lnQ)) return fail(PAMD_EINVAL, "sum_lnQ must be finite");
     c->step = step;
     c->resample_index = ridx;
@@ -1169,6 +1457,14 @@ int pamd_set_counters(pamd_ctx* c, uint32_t step, uint32_t ridx, double sum_lnQ)
 
 int pamd_info(pamd_ctx* c, int64_t* R, int32_t* n_atoms, int32_t* lanes, int32_t* per_lane, int32_t* rpb) {
     if (!c) return fail(PAMD_EINVAL, "null context");
+    if (is_batch(c)) {  // total replicas, largest molecule; shapes are per molecule
+        if (R) *R = c->R;
+        if (n_atoms) *n_atoms = c->N;
+        if (lanes) *lanes = 0;
+        if (per_lane) *per_lane = 0;
+        if (rpb) *rpb = 0;
+        return PAMD_OK;
+    }
     if (R) *R = c->R;
     if (n_atoms) *n_atoms = c->N;
     if (lanes) *lanes = c->lay.lanes;
@@ -1177,7 +1473,12 @@ int pamd_info(pamd_ctx* c, int64_t* R, int32_t* n_atoms, int32_t* lanes, int32_t
     return PAMD_OK;
 }
 
-int64_t pamd_launch_count(pamd_ctx* c) { return c ? c->launches : -1; }
+int64_t pamd_launch_count(pamd_ctx* c) {
+    if (!c) return -1;
+    long long n = c->launches;
+    for (pamd_ctx* sub : c->subs) n += sub->launches;
+    return n;
+}
 
 int pamd_sync(pamd_ctx* c) {
     int rc = check_ctx(c);
@@ -1189,6 +1490,8 @@ int pamd_sync(pamd_ctx* c) {
 void pamd_destroy(pamd_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
+    for (pamd_ctx* sub : c->subs) pamd_destroy(sub);
+    c->subs.clear();
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     free_all(c);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

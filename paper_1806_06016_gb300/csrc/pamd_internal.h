@@ -108,6 +108,16 @@ struct PropF64Params {
     uint32_t purpose_mol;
 };
 
+// Batched propagate (propagate_batch.cu): one launch for many molecules.
+constexpr int kBatchThreads = 128;  // 4 warps per block
+constexpr int kMaxBatchMols = 64;
+struct BatchParams {
+    int n_items;
+    const int4* items;  // {molecule, first replica, end replica, 0}
+    int* queue;         // work counter, zero at launch
+    PropParams mol[kMaxBatchMols];
+};
+
 struct DevScalars {
     double m;                  // max a_j
     double S;                  // sum exp(a_j - m)
@@ -238,6 +248,13 @@ struct pamd_ctx {
     int lanes_req = 0;
     size_t topo_cap = 0;          // bytes allocated for the device topology table
     pamd::TopoF64 top64{};        // all-FP64 mode tables (precision == PAMD_PREC_FP64)
+    // batch context (pamd_init_batch): one sub-context per molecule
+    std::vector<pamd_ctx*> subs;
+    int4* items = nullptr;        // device work list of the batched propagate
+    int n_items = 0;
+    int* queue = nullptr;         // device work counter
+    size_t batch_smem = 0;
+    int batch_grid = 0;
     unsigned char* top64_blob = nullptr;
 };
 
@@ -287,6 +304,9 @@ cudaError_t launch_resample(pamd_ctx* c, double T_prev, double T_next, int do_re
                             const uint32_t* dev_counters, uint32_t resample_offset);
 cudaError_t launch_observe(pamd_ctx* c, double T, pamd_obs* dst);
 cudaError_t launch_set_counters(pamd_ctx* c, uint32_t step, uint32_t ridx);
+
+cudaError_t launch_propagate_batch(const BatchParams& bp, int grid, size_t smem, cudaStream_t s);
+cudaError_t propagate_batch_occupancy(size_t smem, int* blocks_per_sm);
 
 // all-FP64 mode (propagate_f64.cu)
 cudaError_t launch_propagate_f64(pamd_ctx* c, double* state, double* E, double* ke, double* rg,

@@ -572,6 +572,146 @@ __device__ __forceinline__ double group_sum(double v, unsigned gmask, int base, 
     return s;
 }
 
+// theta BAOAB steps of replica k by the L lanes of one group (lane g of the
+// group, lanes base .. base+L-1 of the warp, mask gmask); pos / frc are the
+// group's shared-memory slots.  Used by the single-molecule kernel and by the
+// batched kernel.
+template <int B, bool CHAIN>
+__device__ __forceinline__ void advance_replica(const PropParams& p, const unsigned char* sm,
+                                                const float4* prm,
+                                                const unsigned long long* masks, float4* pos,
+                                                float4* frc, long long k, int L, int g, int base,
+                                                unsigned gmask) {
+    using C = PropCfg<B>;
+    const TopoLayout& lay = p.lay;
+    const int N = lay.n_atoms, Np = lay.n_pad;
+    const uint32_t step_base = (p.dev_counters ? p.dev_counters[0] : 0u) + p.step0;
+    const float* st = p.state_in + (size_t)k * 6 * Np;
+    float xi[B], yi[B], zi[B], vx[B], vy[B], vz[B];
+    float hsi[B], sei[B], qi[B], im[B], sd[B];
+#pragma unroll
+    for (int a = 0; a < B; ++a) {
+        const int i = g * B + a;
+        const int s = g * C::BS + a;
+        if (i < N) {
+            xi[a] = st[i];
+            yi[a] = st[Np + i];
+            zi[a] = st[2 * Np + i];
+            vx[a] = st[3 * Np + i];
+            vy[a] = st[4 * Np + i];
+            vz[a] = st[5 * Np + i];
+        } else {
+            xi[a] = 1000.0f + 4.0f * (float)i;
+            yi[a] = zi[a] = 0.0f;
+            vx[a] = vy[a] = vz[a] = 0.0f;
+        }
+        const float4 c = prm[s];
+        hsi[a] = c.x;
+        sei[a] = c.y;
+        qi[a] = c.z;
+        im[a] = c.w;
+        sd[a] = p.c2kT * sqrtf(c.w);
+        pos[s] = make_float4(xi[a], yi[a], zi[a], 0.0f);
+        frc[s] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    }
+    __syncwarp(gmask);
+    float fx[B], fy[B], fz[B];
+    double e_acc = 0.0;
+    // s = -1 evaluates the forces of the incoming state; s >= 0 are BAOAB steps
+    for (int s = -1; s < p.theta; ++s) {
+        if (s >= 0) {
+            const uint32_t step = step_base + (uint32_t)s;
+#pragma unroll
+            for (int a = 0; a < B; ++a) {
+                const int i = g * B + a;
+                vx[a] = fmaf(p.hdt * im[a], fx[a], vx[a]);  // B
+                vy[a] = fmaf(p.hdt * im[a], fy[a], vy[a]);
+                vz[a] = fmaf(p.hdt * im[a], fz[a], vz[a]);
+                xi[a] = fmaf(p.hdt, vx[a], xi[a]);          // A
+                yi[a] = fmaf(p.hdt, vy[a], yi[a]);
+                zi[a] = fmaf(p.hdt, vz[a], zi[a]);
+                if (i < N) {                                // O
+                    const float3 z = normal3(p.seed, (uint32_t)i, (uint32_t)k, step, p.purpose_mol);
+                    vx[a] = fmaf(p.c1, vx[a], sd[a] * z.x);
+                    vy[a] = fmaf(p.c1, vy[a], sd[a] * z.y);
+                    vz[a] = fmaf(p.c1, vz[a], sd[a] * z.z);
+                }
+                xi[a] = fmaf(p.hdt, vx[a], xi[a]);          // A
+                yi[a] = fmaf(p.hdt, vy[a], yi[a]);
+                zi[a] = fmaf(p.hdt, vz[a], zi[a]);
+                const int sl = g * C::BS + a;
+                pos[sl] = make_float4(xi[a], yi[a], zi[a], 0.0f);
+                frc[sl] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+            __syncwarp(gmask);
+        }
+        compute_forces<B, CHAIN, false>(sm, lay, prm, pos, frc, masks, L, g, gmask, xi, yi, zi,
+                                        hsi, sei, qi, fx, fy, fz, e_acc);
+        if (s >= 0) {
+#pragma unroll
+            for (int a = 0; a < B; ++a) {                   // B
+                vx[a] = fmaf(p.hdt * im[a], fx[a], vx[a]);
+                vy[a] = fmaf(p.hdt * im[a], fy[a], vy[a]);
+                vz[a] = fmaf(p.hdt * im[a], fz[a], vz[a]);
+            }
+        }
+    }
+    // positions in shared memory are those of the last step
+    e_acc = energy_pass<B, CHAIN>(sm, lay, prm, pos, masks, L, g);
+
+    // write back and per-replica observables
+    float* so = p.state_out + (size_t)k * 6 * Np;
+    double ek = 0.0, cx = 0.0, cy = 0.0, cz = 0.0;
+#pragma unroll
+    for (int a = 0; a < B; ++a) {
+        const int i = g * B + a;
+        if (i < N) {
+            if (p.theta > 0) {
+                so[i] = xi[a];
+                so[Np + i] = yi[a];
+                so[2 * Np + i] = zi[a];
+                so[3 * Np + i] = vx[a];
+                so[4 * Np + i] = vy[a];
+                so[5 * Np + i] = vz[a];
+            }
+            if (p.fout) {
+                float* fo = p.fout + (size_t)k * 3 * Np;
+                fo[i] = fx[a];
+                fo[Np + i] = fy[a];
+                fo[2 * Np + i] = fz[a];
+            }
+            const double m = (double)p.masses[i];
+            ek += 0.5 * m * ((double)vx[a] * vx[a] + (double)vy[a] * vy[a] + (double)vz[a] * vz[a]);
+            cx += xi[a];
+            cy += yi[a];
+            cz += zi[a];
+        }
+    }
+    const double E = group_sum(e_acc, gmask, base, L);
+    ek = group_sum(ek, gmask, base, L);
+    cx = group_sum(cx, gmask, base, L) / N;
+    cy = group_sum(cy, gmask, base, L) / N;
+    cz = group_sum(cz, gmask, base, L) / N;
+    double r2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < B; ++a) {
+        const int i = g * B + a;
+        if (i < N) {
+            const double dx = xi[a] - cx, dy = yi[a] - cy, dz = zi[a] - cz;
+            r2 += dx * dx + dy * dy + dz * dz;
+        }
+    }
+    r2 = group_sum(r2, gmask, base, L);
+    if (g == 0) {
+        p.E[k] = E;
+        p.ke[k] = ek;
+        p.rg[k] = sqrt(r2 / N);
+        if (!isfinite(E) && atomicCAS(&p.status[0], 0, PAMD_ENONFINITE) == 0)
+            p.status[1] = (int)k;
+    }
+    __syncwarp(gmask);
+}
+
 template <int B, bool CHAIN>
 __global__ void __launch_bounds__(256, PropCfg<B>::MIN_BLOCKS) propagate_kernel(const PropParams p) {
     using C = PropCfg<B>;
@@ -601,136 +741,9 @@ __global__ void __launch_bounds__(256, PropCfg<B>::MIN_BLOCKS) propagate_kernel(
     float4* pos = slots + slot_local * slot_f4;
     float4* frc = pos + lay.nk;
 
-    const int N = lay.n_atoms, Np = lay.n_pad;
-    const uint32_t step_base = (p.dev_counters ? p.dev_counters[0] : 0u) + p.step0;
-
     for (long long k = (long long)blockIdx.x * rpb + slot_local; k < p.R;
-         k += (long long)gridDim.x * rpb) {
-        const float* st = p.state_in + (size_t)k * 6 * Np;
-        float xi[B], yi[B], zi[B], vx[B], vy[B], vz[B];
-        float hsi[B], sei[B], qi[B], im[B], sd[B];
-#pragma unroll
-        for (int a = 0; a < B; ++a) {
-            const int i = g * B + a;
-            const int s = g * C::BS + a;
-            if (i < N) {
-                xi[a] = st[i];
-                yi[a] = st[Np + i];
-                zi[a] = st[2 * Np + i];
-                vx[a] = st[3 * Np + i];
-                vy[a] = st[4 * Np + i];
-                vz[a] = st[5 * Np + i];
-            } else {
-                xi[a] = 1000.0f + 4.0f * (float)i;
-                yi[a] = zi[a] = 0.0f;
-                vx[a] = vy[a] = vz[a] = 0.0f;
-            }
-            const float4 c = prm[s];
-            hsi[a] = c.x;
-            sei[a] = c.y;
-            qi[a] = c.z;
-            im[a] = c.w;
-            sd[a] = p.c2kT * sqrtf(c.w);
-            pos[s] = make_float4(xi[a], yi[a], zi[a], 0.0f);
-            frc[s] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        }
-        __syncwarp(gmask);
-        float fx[B], fy[B], fz[B];
-        double e_acc = 0.0;
-        // s = -1 evaluates the forces of the incoming state; s >= 0 are BAOAB steps
-        for (int s = -1; s < p.theta; ++s) {
-            if (s >= 0) {
-                const uint32_t step = step_base + (uint32_t)s;
-#pragma unroll
-                for (int a = 0; a < B; ++a) {
-                    const int i = g * B + a;
-                    vx[a] = fmaf(p.hdt * im[a], fx[a], vx[a]);  // B
-                    vy[a] = fmaf(p.hdt * im[a], fy[a], vy[a]);
-                    vz[a] = fmaf(p.hdt * im[a], fz[a], vz[a]);
-                    xi[a] = fmaf(p.hdt, vx[a], xi[a]);          // A
-                    yi[a] = fmaf(p.hdt, vy[a], yi[a]);
-                    zi[a] = fmaf(p.hdt, vz[a], zi[a]);
-                    if (i < N) {                                // O
-                        const float3 z = normal3(p.seed, (uint32_t)i, (uint32_t)k, step, p.purpose_mol);
-                        vx[a] = fmaf(p.c1, vx[a], sd[a] * z.x);
-                        vy[a] = fmaf(p.c1, vy[a], sd[a] * z.y);
-                        vz[a] = fmaf(p.c1, vz[a], sd[a] * z.z);
-                    }
-                    xi[a] = fmaf(p.hdt, vx[a], xi[a]);          // A
-                    yi[a] = fmaf(p.hdt, vy[a], yi[a]);
-                    zi[a] = fmaf(p.hdt, vz[a], zi[a]);
-                    const int sl = g * C::BS + a;
-                    pos[sl] = make_float4(xi[a], yi[a], zi[a], 0.0f);
-                    frc[sl] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                }
-                __syncwarp(gmask);
-            }
-            compute_forces<B, CHAIN, false>(sm, lay, prm, pos, frc, masks, L, g, gmask, xi, yi, zi,
-                                            hsi, sei, qi, fx, fy, fz, e_acc);
-            if (s >= 0) {
-#pragma unroll
-                for (int a = 0; a < B; ++a) {                   // B
-                    vx[a] = fmaf(p.hdt * im[a], fx[a], vx[a]);
-                    vy[a] = fmaf(p.hdt * im[a], fy[a], vy[a]);
-                    vz[a] = fmaf(p.hdt * im[a], fz[a], vz[a]);
-                }
-            }
-        }
-        // positions in shared memory are those of the last step
-        e_acc = energy_pass<B, CHAIN>(sm, lay, prm, pos, masks, L, g);
-
-        // write back and per-replica observables
-        float* so = p.state_out + (size_t)k * 6 * Np;
-        double ek = 0.0, cx = 0.0, cy = 0.0, cz = 0.0;
-#pragma unroll
-        for (int a = 0; a < B; ++a) {
-            const int i = g * B + a;
-            if (i < N) {
-                if (p.theta > 0) {
-                    so[i] = xi[a];
-                    so[Np + i] = yi[a];
-                    so[2 * Np + i] = zi[a];
-                    so[3 * Np + i] = vx[a];
-                    so[4 * Np + i] = vy[a];
-                    so[5 * Np + i] = vz[a];
-                }
-                if (p.fout) {
-                    float* fo = p.fout + (size_t)k * 3 * Np;
-                    fo[i] = fx[a];
-                    fo[Np + i] = fy[a];
-                    fo[2 * Np + i] = fz[a];
-                }
-                const double m = (double)p.masses[i];
-                ek += 0.5 * m * ((double)vx[a] * vx[a] + (double)vy[a] * vy[a] + (double)vz[a] * vz[a]);
-                cx += xi[a];
-                cy += yi[a];
-                cz += zi[a];
-            }
-        }
-        const double E = group_sum(e_acc, gmask, base, L);
-        ek = group_sum(ek, gmask, base, L);
-        cx = group_sum(cx, gmask, base, L) / N;
-        cy = group_sum(cy, gmask, base, L) / N;
-        cz = group_sum(cz, gmask, base, L) / N;
-        double r2 = 0.0;
-#pragma unroll
-        for (int a = 0; a < B; ++a) {
-            const int i = g * B + a;
-            if (i < N) {
-                const double dx = xi[a] - cx, dy = yi[a] - cy, dz = zi[a] - cz;
-                r2 += dx * dx + dy * dy + dz * dz;
-            }
-        }
-        r2 = group_sum(r2, gmask, base, L);
-        if (g == 0) {
-            p.E[k] = E;
-            p.ke[k] = ek;
-            p.rg[k] = sqrt(r2 / N);
-            if (!isfinite(E) && atomicCAS(&p.status[0], 0, PAMD_ENONFINITE) == 0)
-                p.status[1] = (int)k;
-        }
-        __syncwarp(gmask);
-    }
+         k += (long long)gridDim.x * rpb)
+        advance_replica<B, CHAIN>(p, sm, prm, masks, pos, frc, k, L, g, base, gmask);
 }
 
 template <int B, bool CHAIN>

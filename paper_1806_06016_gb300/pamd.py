@@ -86,7 +86,8 @@ class PamdObs(C.Structure):
 
 
 EXPORTS = [
-    "pamd_options_default", "pamd_init", "pamd_reset", "pamd_propagate", "pamd_resample", "pamd_observables",
+    "pamd_options_default", "pamd_init", "pamd_init_batch", "pamd_batch_size", "pamd_batch_sub",
+    "pamd_reset", "pamd_propagate", "pamd_resample", "pamd_observables",
     "pamd_anneal", "pamd_get_state", "pamd_set_state", "pamd_forces", "pamd_get_counters",
     "pamd_set_counters", "pamd_autotune", "pamd_resample_counts_noalloc", "pamd_info", "pamd_launch_count", "pamd_sync", "pamd_destroy",
     "pamd_last_error",
@@ -111,6 +112,10 @@ def load(path: str | None = None):
             "pamd_options_default": (None, [C.POINTER(PamdOptions)]),
             "pamd_init": (C.c_int, [C.POINTER(P), C.POINTER(PamdTopology), I64, D, U64,
                                     C.POINTER(PamdOptions)]),
+            "pamd_init_batch": (C.c_int, [C.POINTER(P), I32, C.POINTER(PamdTopology), P, P, U64,
+                                          C.POINTER(PamdOptions)]),
+            "pamd_batch_size": (I32, [P]),
+            "pamd_batch_sub": (P, [P, I32]),
             "pamd_reset": (C.c_int, [P, D, U64]),
             "pamd_propagate": (C.c_int, [P, I32, D, D]),
             "pamd_resample": (C.c_int, [P, D, D, P, P]),
@@ -225,6 +230,33 @@ def pamd_init(top, R: int, T0: float, seed: int, options: PamdOptions | None = N
     return ctx
 
 
+def pamd_init_batch(tops, R, T0, seed: int, options: PamdOptions | None = None):
+    """Batch context over several molecules (one persistent launch per propagate)."""
+    lib = load()
+    n = len(tops)
+    args = [_TopologyArgs(t) for t in tops]
+    arr = (PamdTopology * n)(*[a.s for a in args])
+    Rv = np.ascontiguousarray(R, dtype=np.int64)
+    Tv = np.ascontiguousarray(T0, dtype=np.float64)
+    ctx = C.c_void_p()
+    opt = options if options is not None else pamd_options_default()
+    _check(lib.pamd_init_batch(C.byref(ctx), n, arr, _ptr(Rv), _ptr(Tv), int(seed), C.byref(opt)))
+    _keepalive[ctx.value] = getattr(opt, "_allocator", None)
+    return ctx
+
+
+def pamd_batch_size(ctx) -> int:
+    return int(load().pamd_batch_size(ctx))
+
+
+def pamd_batch_sub(ctx, m: int):
+    """Context of molecule m of a batch (owned by the batch)."""
+    h = load().pamd_batch_sub(ctx, int(m))
+    if not h:
+        raise PamdError(PAMD_EINVAL, pamd_last_error())
+    return C.c_void_p(h)
+
+
 def pamd_reset(ctx, T0: float, seed: int) -> None:
     _check(load().pamd_reset(ctx, float(T0), int(seed)))
 
@@ -234,25 +266,35 @@ def pamd_propagate(ctx, theta: int, dt_ps: float, T: float) -> None:
 
 
 def pamd_resample(ctx, T_prev: float, T_next: float, want_copies: bool = True):
-    """Returns (copies[R] int32 or None, lnQ)."""
+    """Returns (copies[R] int32 or None, lnQ); for a batch context lnQ is a
+    list over molecules and copies spans all molecules in order."""
     R = pamd_info(ctx)["R"]
+    nb = pamd_batch_size(ctx)
     cnt = np.zeros(R, np.int32) if want_copies else None
-    lnq = C.c_double(0.0)
-    _check(load().pamd_resample(ctx, float(T_prev), float(T_next), _ptr(cnt), C.byref(lnq)))
-    return cnt, lnq.value
+    lnq = np.zeros(max(nb, 1))
+    _check(load().pamd_resample(ctx, float(T_prev), float(T_next), _ptr(cnt), _ptr(lnq)))
+    return cnt, (list(lnq) if nb > 0 else float(lnq[0]))
 
 
-def pamd_observables(ctx, T: float) -> dict:
-    o = PamdObs()
-    _check(load().pamd_observables(ctx, float(T), C.byref(o)))
-    return o.as_dict()
+def pamd_observables(ctx, T: float):
+    """dict, or a list of dicts (one per molecule) for a batch context."""
+    nb = pamd_batch_size(ctx)
+    out = (PamdObs * max(nb, 1))()
+    _check(load().pamd_observables(ctx, float(T), out))
+    return [o.as_dict() for o in out] if nb > 0 else out[0].as_dict()
 
 
-def pamd_anneal(ctx, temps, theta: int, dt_ps: float, resample: bool = True) -> list[dict]:
+def pamd_anneal(ctx, temps, theta: int, dt_ps: float, resample: bool = True):
+    """Per-temperature observables: a list of dicts, or for a batch context a
+    list (per temperature) of lists (per molecule)."""
     t = np.ascontiguousarray(temps, dtype=np.float64)
     K = len(t) - 1
-    out = (PamdObs * (K + 1))()
+    nb = pamd_batch_size(ctx)
+    M = max(nb, 1)
+    out = (PamdObs * ((K + 1) * M))()
     _check(load().pamd_anneal(ctx, K, _ptr(t), int(theta), float(dt_ps), int(bool(resample)), out))
+    if nb > 0:
+        return [[out[i * M + m].as_dict() for m in range(M)] for i in range(K + 1)]
     return [o.as_dict() for o in out]
 
 
