@@ -34,6 +34,12 @@ WORKLOADS = {
                  "100 geometric temperature steps 1000->250 K",
         n_atoms=75, gen_seed=1, R=8192, theta=1000, K=100, T0=1000.0, TK=250.0, dt=0.001,
         gamma=1.0, seed=12345),
+    "c3": dict(
+        workload="batched uneven anneals: 16 chains N~U{20..200} (seed 7), R=4096 each, "
+                 "theta=500, dt=1 fs, 50 geometric temperature steps 800->300 K, one persistent "
+                 "launch per temperature step",
+        n_atoms=0, gen_seed=1, R=4096, theta=500, K=50, T0=800.0, TK=300.0, dt=0.001,
+        gamma=1.0, seed=12345, batch=16),
     "c1": dict(
         workload="plain PAMD: 22-atom chain, R=256, theta=100, dt=1 fs, "
                  "20 geometric temperature steps 1000->300 K",
@@ -70,8 +76,14 @@ def kernel_source_hash():
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
 
+def batch_sizes(w):
+    import pamd_inputs as pi
+    return pi.batched_chain_sizes(w["batch"])
+
+
 def atom_steps(w, replicas):
-    return w["n_atoms"] * replicas * w["theta"] * (w["K"] + 1)
+    n = sum(batch_sizes(w)) if w.get("batch") else w["n_atoms"]
+    return n * replicas * w["theta"] * (w["K"] + 1)
 
 
 # ----------------------------------------------------------------- clocks
@@ -181,7 +193,8 @@ def run_reference(args, w):
 
 
 def config_of(w, args):
-    return {"workload": w["workload"], "n_atoms": w["n_atoms"], "replicas_per_gpu": w["R"],
+    return {"workload": w["workload"], "n_atoms": w["n_atoms"],
+            "replicas_per_gpu": w["R"] * w.get("batch", 1),
             "theta": w["theta"], "temperature_steps": w["K"], "T_first_K": w["T0"],
             "T_last_K": w["TK"], "dt_fs": w["dt"] * 1e3, "gamma_per_ps": w["gamma"],
             "precision": "FP32 forces/integration, FP64 energies/weights/lnQ",
@@ -216,15 +229,25 @@ def run_gpu(args, w):
         dist.barrier()
     pamd.load()
 
-    top = pi.make_chain(w["n_atoms"], w["gen_seed"])
     temps = pi.geometric_schedule(w["T0"], w["TK"], w["K"])
     R, theta, dt = w["R"], w["theta"], w["dt"]
     seed = w["seed"] + 7919 * rank
     # the library launches on this stream; the timing events are recorded on it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    pop = pamd.Population(top, R, temps[0], seed, pamd.torch_options(gamma_per_ps=w["gamma"]))
-    tune = pamd.pamd_autotune(pop.ctx, 50)   # launch shape by measurement (untimed)
+    if w.get("batch"):
+        sizes = batch_sizes(w)
+        tops = [pi.make_chain(n, m + 1) for m, n in enumerate(sizes)]
+        top = tops[int(np.argmax(sizes))]
+        ctx = pamd.pamd_init_batch(tops, [R] * len(tops), [temps[0]] * len(tops), seed,
+                                   pamd.torch_options(gamma_per_ps=w["gamma"]))
+        pop = pamd.Population.__new__(pamd.Population)
+        pop.ctx, pop.top, pop.R = ctx, top, R * len(tops)
+        tune = {"per_molecule": [pamd.pamd_info(pamd.pamd_batch_sub(ctx, m)) for m in range(len(tops))]}
+    else:
+        top = pi.make_chain(w["n_atoms"], w["gen_seed"])
+        pop = pamd.Population(top, R, temps[0], seed, pamd.torch_options(gamma_per_ps=w["gamma"]))
+        tune = pamd.pamd_autotune(pop.ctx, 50)   # launch shape by measurement (untimed)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
     def one_anneal():
@@ -261,6 +284,20 @@ def run_gpu(args, w):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     max_ms = float(t.item())
     total_units = atom_steps(w, R) * args.steps * world
+    if w.get("batch"):
+        # one batched launch advances all molecules; no single-kernel roofline
+        pop.close()
+        line = {"metric": METRIC, "value": total_units / (max_ms / 1e3), "unit": UNIT,
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": dict(config_of(w, args), launch_shape=tune, atoms=batch_sizes(w)),
+                "gpu_launches": int(launches), "clocks": clocks}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return
     value = total_units / (max_ms / 1e3)
 
     # dominant kernel: the persistent propagate launch, timed alone in the
