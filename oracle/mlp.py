@@ -159,3 +159,30 @@ def pair_jacobian_apply_T(x, u):
     r = np.sqrt(np.sum(d * d, axis=-1))
     dgi = -d / r[..., None] ** 3
     return np.sum(dgi * (u[:, i, :] - u[:, j, :]), axis=-1)
+
+
+def propagate(p, x, v, masses, theta, dt, T, gamma, seed, step0, mol=0, slots=None):
+    """theta BAOAB Langevin steps of configurations x, v [R, N, 3] with the
+    surrogate's forces (FP64): the integrator and noise stream of the exact
+    oracle (B, A, O, A, new forces, B; noise from Philox(seed; atom, slot,
+    step0 + s, NOISE | mol << 8)).  Returns (x, v, E)."""
+    from . import normal3
+    kB = 0.008314462618
+    x = np.array(x, dtype=np.float64)
+    v = np.array(v, dtype=np.float64)
+    R, n = x.shape[0], x.shape[1]
+    slots = np.arange(R) if slots is None else np.asarray(slots)
+    im = 1.0 / np.asarray(masses, dtype=np.float64)
+    c1 = np.exp(-gamma * dt)
+    sdv = np.sqrt((1.0 - c1 * c1) * kB * T * im)
+    E, F = energy_forces(p, x)
+    for s in range(theta):
+        z = np.array([[normal3(seed, i, int(slots[r]), step0 + s, mol << 8) for i in range(n)]
+                      for r in range(R)])
+        v += 0.5 * dt * F * im[None, :, None]          # B
+        x += 0.5 * dt * v                               # A
+        v = c1 * v + sdv[None, :, None] * z             # O
+        x += 0.5 * dt * v                               # A
+        E, F = energy_forces(p, x)
+        v += 0.5 * dt * F * im[None, :, None]          # B
+    return x, v, E

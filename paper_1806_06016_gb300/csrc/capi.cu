@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "mlp_internal.h"
 #include "pamd_internal.h"
 
 using namespace pamd;
@@ -432,6 +433,13 @@ int launch_prop_on(pamd_ctx* c, float* state, double* E, double* ke, double* rg,
         if (e != cudaSuccess) return cuda_fail(c, e, "propagate launch (FP64)");
         return PAMD_OK;
     }
+    if (c->mlp) {
+        const int rc = mlp_propagate(c->mlp, state, E, ke, rg, fout, c->b.masses, &c->b.scal->status,
+                                     dev_ctr, c->R, c->Np, theta, dt, T, c->gamma, c->seed, step0,
+                                     kPurposeNoise | ((uint32_t)c->mol << 8), c->stream, &c->launches);
+        if (rc == PAMD_ECUDA) c->broken = true;
+        return rc;
+    }
     PropParams p{};
     fill_prop_params(c, p, state, E, ke, rg, theta, dt, T, dev_ctr, step0, fout);
     cudaError_t e = propagate_dispatch_any(c->lay, &p, c->warps_per_block, c->grid_prop,
@@ -720,7 +728,33 @@ int anneal_batch(pamd_ctx* c, int32_t K, const double* T, int32_t theta, double 
     key.resample = resample ? 1 : 0;
     key.dt = dt_ps;
     key.T.assign(T, T + K + 1);
-    if (!c->graph_exec || !(c->graph_key == key)) {
+    if (c->mlp) {
+        // A force model issues five launches per MD step: queue the anneal
+        // directly instead of capturing a graph of that size.
+        PAMD_CU(c, launch_set_counters(c, c->step, c->resample_index));
+        int err = launch_prop(c, theta, dt_ps, T[0], c->b.counters, 0u, nullptr);
+        if (!err && launch_observe(c, T[0], c->b.obs) != cudaSuccess) err = PAMD_ECUDA;
+        for (int i = 1; i <= K && !err; ++i) {
+            if (launch_resample(c, T[i - 1], T[i], resample ? 1 : 0, c->b.counters, (uint32_t)i) != cudaSuccess) {
+                err = PAMD_ECUDA;
+                break;
+            }
+            c->cur_is_alt = !c->cur_is_alt;
+            err = launch_prop(c, theta, dt_ps, T[i], c->b.counters, (uint32_t)i * (uint32_t)theta, nullptr);
+            if (!err && launch_observe(c, T[i], c->b.obs + i) != cudaSuccess) err = PAMD_ECUDA;
+        }
+        if (err) {
+            c->broken = true;
+            return err == PAMD_ECUDA ? fail(PAMD_ECUDA, "anneal with force model: " + g_err) : err;
+        }
+        if (c->cur_is_alt) {
+            const size_t st_bytes = state_bytes(c);
+            PAMD_CU(c, cudaMemcpyAsync(c->b.state, c->b.state_alt, st_bytes, cudaMemcpyDeviceToDevice, c->stream));
+            PAMD_CU(c, cudaMemcpyAsync(c->b.E, c->b.E_alt, 8 * (size_t)c->R, cudaMemcpyDeviceToDevice, c->stream));
+            PAMD_CU(c, cudaMemcpyAsync(c->b.fam, c->b.fam_alt, 4 * (size_t)c->R, cudaMemcpyDeviceToDevice, c->stream));
+            c->cur_is_alt = false;
+        }
+    } else if (!c->graph_exec || !(c->graph_key == key)) {
         if (c->graph_exec) {
             cudaGraphExecDestroy(c->graph_exec);
             c->graph_exec = nullptr;
@@ -1164,7 +1198,33 @@ int pamd_anneal(pamd_ctx* c, int32_t K, const double* T, int32_t theta, double d
         PAMD_CU(c, cudaMemcpyAsync(c->b.fam, c->b.fam_alt, 4 * (size_t)c->R, cudaMemcpyDeviceToDevice, c->stream));
         c->cur_is_alt = false;
     }
-    if (!c->graph_exec || !(c->graph_key == key)) {
+    if (c->mlp) {
+        // A force model issues five launches per MD step: queue the anneal
+        // directly instead of capturing a graph of that size.
+        PAMD_CU(c, launch_set_counters(c, c->step, c->resample_index));
+        int err = launch_prop(c, theta, dt_ps, T[0], c->b.counters, 0u, nullptr);
+        if (!err && launch_observe(c, T[0], c->b.obs) != cudaSuccess) err = PAMD_ECUDA;
+        for (int i = 1; i <= K && !err; ++i) {
+            if (launch_resample(c, T[i - 1], T[i], resample ? 1 : 0, c->b.counters, (uint32_t)i) != cudaSuccess) {
+                err = PAMD_ECUDA;
+                break;
+            }
+            c->cur_is_alt = !c->cur_is_alt;
+            err = launch_prop(c, theta, dt_ps, T[i], c->b.counters, (uint32_t)i * (uint32_t)theta, nullptr);
+            if (!err && launch_observe(c, T[i], c->b.obs + i) != cudaSuccess) err = PAMD_ECUDA;
+        }
+        if (err) {
+            c->broken = true;
+            return err == PAMD_ECUDA ? fail(PAMD_ECUDA, "anneal with force model: " + g_err) : err;
+        }
+        if (c->cur_is_alt) {
+            const size_t st_bytes = state_bytes(c);
+            PAMD_CU(c, cudaMemcpyAsync(c->b.state, c->b.state_alt, st_bytes, cudaMemcpyDeviceToDevice, c->stream));
+            PAMD_CU(c, cudaMemcpyAsync(c->b.E, c->b.E_alt, 8 * (size_t)c->R, cudaMemcpyDeviceToDevice, c->stream));
+            PAMD_CU(c, cudaMemcpyAsync(c->b.fam, c->b.fam_alt, 4 * (size_t)c->R, cudaMemcpyDeviceToDevice, c->stream));
+            c->cur_is_alt = false;
+        }
+    } else if (!c->graph_exec || !(c->graph_key == key)) {
         if (c->graph_exec) {
             cudaGraphExecDestroy(c->graph_exec);
             c->graph_exec = nullptr;
@@ -1204,10 +1264,12 @@ int pamd_anneal(pamd_ctx* c, int32_t K, const double* T, int32_t theta, double d
         if (ei != cudaSuccess) return cuda_fail(c, ei, "graph instantiate");
         c->graph_key = key;
     }
-    cudaError_t e = launch_set_counters(c, c->step, c->resample_index);
-    if (e != cudaSuccess) return cuda_fail(c, e, "set counters");
-    PAMD_CU(c, cudaGraphLaunch(c->graph_exec, c->stream));
-    c->launches += c->graph_kernels;
+    if (!c->mlp) {
+        cudaError_t e = launch_set_counters(c, c->step, c->resample_index);
+        if (e != cudaSuccess) return cuda_fail(c, e, "set counters");
+        PAMD_CU(c, cudaGraphLaunch(c->graph_exec, c->stream));
+        c->launches += c->graph_kernels;
+    }
     c->step += (uint32_t)(K + 1) * (uint32_t)theta;
     c->resample_index += (uint32_t)K;
     if (per_step_out) {
@@ -1327,6 +1389,13 @@ int pamd_autotune(pamd_ctx* c, int32_t theta_probe, pamd_tune* out) {
     if (rc) return rc;
     if (is_batch(c)) return fail(PAMD_EINVAL, "batch context: call this on pamd_batch_sub(ctx, m)");
     if (theta_probe < 1 || theta_probe > 1000) return fail(PAMD_EINVAL, "theta_probe must be 1..1000");
+    // the shapes tuned are those of the exact-force kernel
+    struct ModelDetach {
+        pamd_ctx* c;
+        pamd_mlp* m;
+        ~ModelDetach() { c->mlp = m; }
+    } detach{c, c->mlp};
+    c->mlp = nullptr;
     if (is_f64(c)) {  // one fixed shape (a warp per replica)
         if (out) *out = pamd_tune{32, (c->N + 31) / 32, 4, 1, 0, 0.0};
         return PAMD_OK;
@@ -1484,6 +1553,22 @@ int pamd_sync(pamd_ctx* c) {
     int rc = check_ctx(c);
     if (rc) return rc;
     PAMD_CU(c, cudaStreamSynchronize(c->stream));
+    return PAMD_OK;
+}
+
+int pamd_set_force_model(pamd_ctx* c, pamd_mlp* m) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (is_batch(c) || is_f64(c))
+        return fail(PAMD_EUNSUPPORTED, "force models need a single-molecule mixed-precision context");
+    if (m) {
+        if (m->N != c->N) return fail(PAMD_EINVAL, "force model is for another atom count");
+        if (m->broken) return fail(PAMD_ESTATE, "force model unusable after an earlier CUDA error");
+        PAMD_CU(c, cudaStreamSynchronize(c->stream));
+        if ((rc = mlp_ensure_work(m, c->R, false))) return rc;
+        PAMD_CU(c, cudaStreamSynchronize(m->stream));
+    }
+    c->mlp = m;
     return PAMD_OK;
 }
 

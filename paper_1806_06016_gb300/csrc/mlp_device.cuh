@@ -1,0 +1,100 @@
+// mlp_device.cuh -- block-level device helpers of the MLP energy surrogate:
+// loading one configuration, its normalised inverse-distance features, and
+// the force sum that maps de/dg back onto the atoms.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "mlp_internal.h"
+
+namespace pamd {
+
+constexpr int kXs = PAMD_MAX_ATOMS;  // stride of a coordinate row in shared memory
+
+// index of pair (i, j), i < j, in row order
+__device__ __forceinline__ int pair_id(int i, int j, int N) {
+    return i * (2 * N - i - 1) / 2 + (j - i - 1);
+}
+
+__device__ __forceinline__ long long config_index(const ConfigView& cv, int m) {
+    return cv.idx ? (long long)cv.idx[m] : (long long)m;
+}
+
+// xs[c * kXs + i] = coordinate c of atom i of configuration m (whole block)
+__device__ __forceinline__ void load_config(const ConfigView& cv, int m, int N, float* xs) {
+    const float* x = cv.x + config_index(cv, m) * cv.s_cfg;
+    for (int t = threadIdx.x; t < 3 * N; t += blockDim.x) {
+        int i, c;
+        if (cv.s_coord == 1) {  // [N][3]: consecutive threads read consecutive floats
+            i = t / 3;
+            c = t - 3 * i;
+        } else {
+            c = t / N;
+            i = t - c * N;
+        }
+        xs[c * kXs + i] = x[(long long)i * cv.s_atom + (long long)c * cv.s_coord];
+    }
+}
+
+// a_p = (1 / r_ij - mu_p) / sd_p rounded to BF16, zero for the padding
+// columns P <= p < Pp (whole block)
+__device__ __forceinline__ void block_features(const float* xs, const ushort2* __restrict__ pairs,
+                                               const float* __restrict__ mu,
+                                               const float* __restrict__ inv_sd, int P, int Pp,
+                                               __nv_bfloat16* a_row, __nv_bfloat16* aT, int ldt,
+                                               int m) {
+    for (int p = threadIdx.x; p < Pp; p += blockDim.x) {
+        float v = 0.0f;
+        if (p < P) {
+            const ushort2 ij = pairs[p];
+            const float dx = xs[ij.x] - xs[ij.y];
+            const float dy = xs[kXs + ij.x] - xs[kXs + ij.y];
+            const float dz = xs[2 * kXs + ij.x] - xs[2 * kXs + ij.y];
+            const float g = rsqrtf(dx * dx + dy * dy + dz * dz);
+            v = (g - mu[p]) * inv_sd[p];
+        }
+        const __nv_bfloat16 b = __float2bfloat16(v);
+        a_row[p] = b;
+        if (aT) aT[(size_t)p * ldt + m] = b;
+    }
+}
+
+// sum over j != k of gam_p(k,j) (x_k - x_j) / r_kj^3, i.e. minus the
+// derivative of sum_p gam_p g_p with respect to x_k
+__device__ __forceinline__ float3 atom_force(int k, const float* xs, const float* gam, int N) {
+    const float xk = xs[k], yk = xs[kXs + k], zk = xs[2 * kXs + k];
+    float fx = 0.0f, fy = 0.0f, fz = 0.0f;
+    for (int j = 0; j < N; ++j) {
+        if (j == k) continue;
+        const int p = k < j ? pair_id(k, j, N) : pair_id(j, k, N);
+        const float dx = xk - xs[j], dy = yk - xs[kXs + j], dz = zk - xs[2 * kXs + j];
+        const float ir = rsqrtf(dx * dx + dy * dy + dz * dz);
+        const float c = gam[p] * ir * ir * ir;
+        fx = fmaf(c, dx, fx);
+        fy = fmaf(c, dy, fy);
+        fz = fmaf(c, dz, fz);
+    }
+    return make_float3(fx, fy, fz);
+}
+
+// normalised energy e = b3 + sum of the layer-2 partial sums
+__device__ __forceinline__ double head_energy(const float* part, int nparts, int m, const float* b3) {
+    double e = (double)*b3;
+    for (int q = 0; q < nparts; ++q) e += (double)part[(size_t)m * nparts + q];
+    return e;
+}
+
+// sum of v over the block (blockDim.x a multiple of 32, <= 1024); every
+// thread receives the total.  red: >= 32 doubles of shared memory.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int i = 0; i < nw; ++i) t += red[i];
+    return t;
+}
+
+}  // namespace pamd

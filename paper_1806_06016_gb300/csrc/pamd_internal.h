@@ -214,6 +214,8 @@ struct HostTopology {
 };
 }  // namespace pamd
 
+struct pamd_mlp;
+
 struct pamd_ctx {
     long long R = 0;
     int N = 0, Np = 0;
@@ -256,6 +258,7 @@ struct pamd_ctx {
     size_t batch_smem = 0;
     int batch_grid = 0;
     unsigned char* top64_blob = nullptr;
+    pamd_mlp* mlp = nullptr;      // force model replacing the exact forces (pamd_set_force_model)
 };
 
 namespace pamd {
@@ -282,6 +285,31 @@ cudaError_t propagate2_b3(const PropParams* p, bool chain, int warps, int grid, 
                           cudaStream_t s, int* blocks_per_sm);
 cudaError_t propagate2_b4(const PropParams* p, bool chain, int warps, int grid, size_t smem,
                           cudaStream_t s, int* blocks_per_sm);
+
+// BF16 tensor-core GEMM (mlp_gemm.cu): C = A . B^T with A [M x K], B [N x K]
+// row-major BF16 (K contiguous), FP32 accumulation, and a fused epilogue on
+// z = acc (+ bias[n]):
+//   kEpiStore  C = z, Cb = bf16(z)                       (each output optional)
+//   kEpiSilu   C = z, Cs = silu'(z), Cb = bf16(silu(z)), CbT = Cb transposed
+//   kEpiHead   C = z, Cs = silu'(z), Cb = bf16(vec[n] silu'(z)), CbT, and
+//              part[m * gridDim.x + tile] = sum over the tile's n of vec[n] silu(z)
+//   kEpiMul    C = z, Cb = bf16(z * mul[m, n]) (mul FP32, leading dim ldc), CbT
+enum GemmEpi { kEpiStore = 0, kEpiSilu = 1, kEpiHead = 2, kEpiMul = 3 };
+struct GemmArgs {
+    const void* A;             // __nv_bfloat16 [M][lda]
+    const void* B;             // __nv_bfloat16 [N][ldb]
+    float* C;                  // [M][ldc] or null
+    float* Cs;                 // [M][ldc] or null
+    void* Cb;                  // __nv_bfloat16 [M][ldcb] or null
+    void* CbT;                 // __nv_bfloat16 [N][ldt] or null
+    const float* bias;         // [N] or null
+    const float* vec;          // [N] (kEpiHead)
+    const float* mul;          // [M][ldc] (kEpiMul)
+    float* part;               // [M][gridDim.x] (kEpiHead)
+    int* status;               // PAMD status word (timeouts)
+    int M, N, K, lda, ldb, ldc, ldcb, ldt, epi;
+};
+cudaError_t launch_gemm_bf16(const GemmArgs& g, cudaStream_t s);
 
 // message returned by pamd_last_error() on this thread (capi.cu)
 void set_last_error(const std::string& msg);

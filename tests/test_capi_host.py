@@ -1,6 +1,6 @@
 """CPU-only checks of the C-ABI library: it builds, loads, exports every
-function include/pamd.h declares, and rejects bad arguments before touching
-the GPU."""
+function include/pamd.h and include/pamd_mlp.h declare, and rejects bad
+arguments before touching the GPU."""
 import ctypes as C
 import os
 import re
@@ -14,9 +14,12 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _header_functions():
-    txt = open(os.path.join(ROOT, "include", "pamd.h")).read()
-    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(pamd_[a-z0-9_]+)\s*\(", txt)))
+    names = set()
+    for h in ("pamd.h", "pamd_mlp.h"):
+        txt = open(os.path.join(ROOT, "include", h)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        names |= set(re.findall(r"\b(pamd_[a-z0-9_]+)\s*\(", txt))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -90,3 +93,27 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.pamd_sync(None) == pamd.PAMD_EINVAL
     assert lib.pamd_launch_count(None) == -1
     lib.pamd_destroy(None)
+
+
+def test_surrogate_argument_validation(lib):
+    """The surrogate's entry points reject bad shapes and null pointers
+    before any device work."""
+    from paper_1806_06016_gb300 import pamd
+    h = C.c_void_p()
+    for n_atoms, hidden in [(1, 128), (pamd.PAMD_MAX_ATOMS + 1, 128), (22, 0), (22, 100), (22, 2048)]:
+        assert lib.pamd_mlp_create(C.byref(h), n_atoms, hidden, 0, None) == pamd.PAMD_EINVAL
+        assert not h.value
+    assert "n_atoms" in pamd.pamd_last_error() or "hidden" in pamd.pamd_last_error()
+    assert lib.pamd_mlp_create(None, 22, 128, 0, None) == pamd.PAMD_EINVAL
+    dummy = C.c_void_p(16)
+    for M, N, K, lda, ldb, ldc in [(0, 8, 8, 8, 8, 8), (8, 8, 12, 16, 16, 8), (8, 8, 8, 4, 8, 8),
+                                   (8, 16, 8, 8, 8, 8)]:
+        assert lib.pamd_gemm_bf16(dummy, dummy, dummy, M, N, K, lda, ldb, ldc, None) == pamd.PAMD_EINVAL
+    assert lib.pamd_gemm_bf16(None, dummy, dummy, 8, 8, 8, 8, 8, 8, None) == pamd.PAMD_EINVAL
+    for fn in ("pamd_mlp_info", "pamd_mlp_sync", "pamd_mlp_get_params", "pamd_mlp_get_grads"):
+        args = [None] * (4 if fn == "pamd_mlp_info" else (1 if fn == "pamd_mlp_sync" else 2))
+        assert getattr(lib, fn)(*args) == pamd.PAMD_EINVAL
+    assert lib.pamd_mlp_energy_forces(None, None, 4, None, None) == pamd.PAMD_EINVAL
+    assert lib.pamd_mlp_loss_grads(None, None, None, None, None, 4, 1.0, None) == pamd.PAMD_EINVAL
+    assert lib.pamd_mlp_launch_count(None) == 0
+    lib.pamd_mlp_destroy(None)

@@ -100,3 +100,44 @@ def test_special_cases():
     for k in g0:
         np.testing.assert_allclose(np.asarray(g2[k]) - np.asarray(g1[k]),
                                    np.asarray(g1[k]) - np.asarray(g0[k]), rtol=1e-9, atol=1e-12)
+
+
+def test_surrogate_dynamics_reduces_to_exact_oracle_without_forces(orc):
+    """With W1 = 0 the surrogate exerts no force; a bonds-only chain with k = 0
+    has none either, so both integrators must produce the same trajectory from
+    the same noise stream (pins the B-A-O-A-B order, the O coefficients and the
+    Philox counters of the surrogate integrator)."""
+    n, R = 5, 3
+    p = _small(n=n, hidden=4)
+    p["W1"][:] = 0.0
+    top = pi.make_harmonic_chain(n, 0.0, 0.0)
+    rng = np.random.default_rng(4)
+    x0 = top.x0[None] + rng.normal(0, 0.02, (R, n, 3))
+    v0 = rng.normal(0, 0.5, (R, n, 3))
+    slots = np.array([0, 5, 9])
+    xs, vs, _ = mlp.propagate(p, x0, v0, top.mass, 4, 0.002, 400.0, 2.0, 99, 7, mol=1, slots=slots)
+    xo, vo, _ = orc.propagate(top, x0, v0, 4, 0.002, 400.0, 2.0, 99, 7, mol=1, slots=slots)
+    np.testing.assert_allclose(xs, xo, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(vs, vo, rtol=0, atol=1e-12)
+
+
+def test_surrogate_nve_energy_error_scales_with_dt_squared():
+    """gamma = 0: velocity Verlet on the surrogate surface; the total-energy
+    error after a fixed time shrinks ~4x when dt halves (second order)."""
+    n = 6
+    x0 = _configs(n, 1, 12)
+    p = mlp.init_params(n, 8, 11)
+    p["mu"] = mlp.features(x0)[0]
+    p["sd"] = np.full(n * (n - 1) // 2, 0.5)
+    masses = np.full(n, 12.0)
+    v0 = np.random.default_rng(3).normal(0, 0.3, (1, n, 3))
+
+    def drift(dt, steps):
+        E0, _ = mlp.energy_forces(p, x0)
+        x, v, E = mlp.propagate(p, x0, v0, masses, steps, dt, 300.0, 0.0, 1, 0)
+        k0 = 0.5 * np.sum(masses[None, :, None] * v0 ** 2)
+        k1 = 0.5 * np.sum(masses[None, :, None] * v ** 2)
+        return abs((E[0] + k1) - (E0[0] + k0))
+
+    d1, d2 = drift(0.004, 25), drift(0.002, 50)
+    assert d1 > 0 and 2.5 < d1 / d2 < 6.0, (d1, d2)
