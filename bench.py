@@ -45,6 +45,13 @@ WORKLOADS = {
                  "20 geometric temperature steps 1000->300 K",
         n_atoms=22, gen_seed=1, R=256, theta=100, K=20, T0=1000.0, TK=300.0, dt=0.001,
         gamma=1.0, seed=12345),
+    "c5": dict(
+        workload="learned surrogate: 75-atom chain, R=65536, theta=1000, dt=1 fs, 100 geometric "
+                 "temperature steps 1000->250 K; MLP 2775 inverse distances -> 512 -> 512 -> 1 "
+                 "(SiLU, BF16 tensor cores, FP32 accumulation) trained on ~2M exact samples from "
+                 "runs shaped like the 75-atom R=8192 workload",
+        n_atoms=75, gen_seed=1, R=65536, theta=1000, K=100, T0=1000.0, TK=250.0, dt=0.001,
+        gamma=1.0, seed=12345, hidden=512),
 }
 
 METRIC = "atom-steps/sec over all replicas (full anneal)"
@@ -554,6 +561,208 @@ def run_resample(args):
                       "chain_GBps": gather_bytes / (chain / 1e3) / 1e9}), flush=True)
 
 
+def gemm_shapes(M, n_atoms=75, hidden=512):
+    """The four tensor-core products of one surrogate force evaluation of M
+    configurations: (name, rows, cols, depth)."""
+    P = n_atoms * (n_atoms - 1) // 2
+    Pp = (P + 7) // 8 * 8
+    return [("layer1 a.W1^T", M, hidden, Pp), ("layer2 h1.W2^T", M, hidden, hidden),
+            ("backward d2.W2", M, hidden, hidden), ("backward d1.W1", M, Pp, hidden)]
+
+
+def time_gemms(torch, S, stream, M, reps=10, n_atoms=75, hidden=512):
+    """CUDA-event time (ms, mean of reps after 2 warm-ups) of each surrogate GEMM shape."""
+    res = []
+    g = torch.Generator(device="cuda").manual_seed(0)
+    for name, m, n, k in gemm_shapes(M, n_atoms, hidden):
+        A = torch.randn(m, k, generator=g, device="cuda").to(torch.bfloat16)
+        B = torch.randn(n, k, generator=g, device="cuda").to(torch.bfloat16)
+        for _ in range(2):
+            S.gemm_bf16(A, B)
+        ms = []
+        for _ in range(reps):
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            S.gemm_bf16(A, B)
+            ev1.record(stream)
+            ev1.synchronize()
+            ms.append(ev0.elapsed_time(ev1))
+        t = statistics.mean(ms)
+        flop = 2.0 * m * n * k
+        res.append({"gemm": name, "M": m, "N": n, "K": k, "ms": t, "tflops": flop / (t / 1e3) / 1e12})
+        del A, B
+    return res
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def run_gemm(args):
+    """The surrogate's four GEMM shapes at M = R (65536 by default), each
+    timed alone with events on its stream.  Prints one JSON line."""
+    import torch
+
+    from paper_1806_06016_gb300 import build as pbuild
+    from paper_1806_06016_gb300 import surrogate as S
+
+    torch.cuda.set_device(0)
+    pbuild.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    M = args.replicas or 65536
+    res = time_gemms(torch, S, stream, M, reps=max(3, args.steps))
+    peak = measured_peaks().get("bf16_tflops")
+    for r in res:
+        r["frac_of_measured_bf16"] = r["tflops"] / peak if peak else None
+    print(json.dumps({"mode": "gemm", "M": M, "gemms": res, "bf16_peak_tflops": peak}), flush=True)
+
+
+def run_surrogate(args, w):
+    """Learned-surrogate workload: harvest exact data, train, compare.
+
+    1. Training data: exact anneals shaped like the 75-atom R = 8192
+       workload (theta = 1000, 100 geometric steps 1000 -> 250 K), each
+       population recorded with its exact energies and forces after every
+       temperature block; the first ``--harvest-runs`` runs (different seeds)
+       are training data (2^21 samples drawn), one more run is held out.
+    2. Training: force matching (lam = 1) with Adam on the GPU kernels.
+    3. Held-out energy and force errors against the exact force field.
+    4. Full anneals at R = 65536 with the exact force field and with the
+       surrogate: time (CUDA events on the anneal stream) and the per-
+       temperature <E> and <R_g> of the two.
+    Prints one JSON line; its value is the surrogate anneal's atom-steps/s.
+    """
+    import numpy as np
+    import torch
+
+    import pamd_inputs as pi
+    from paper_1806_06016_gb300 import build as pbuild
+    from paper_1806_06016_gb300 import pamd
+    from paper_1806_06016_gb300 import surrogate as S
+
+    torch.cuda.set_device(0)
+    pbuild.build()
+    pamd.load()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    N, theta, dt = w["n_atoms"], w["theta"], w["dt"]
+    R = args.replicas or w["R"]
+    K = args.temps or w["K"]
+    temps = pi.geometric_schedule(w["T0"], w["TK"], K)
+    top = pi.make_chain(N, w["gen_seed"])
+    out = {"mode": "surrogate", "config": dict(config_of(w, args), replicas_per_gpu=R,
+                                               temperature_steps=K, hidden=w["hidden"])}
+    # 1. data
+    t0 = time.perf_counter()
+    temps_h = pi.geometric_schedule(1000.0, 250.0, 100)
+    runs = [S.harvest(top, 8192, temps_h, 1000, dt, 1000 + r, pamd.torch_options())
+            for r in range(args.harvest_runs + 1)]
+    harvest_s = time.perf_counter() - t0
+    x_tr = np.concatenate([r[0] for r in runs[:-1]])
+    E_tr = np.concatenate([r[1] for r in runs[:-1]])
+    F_tr = np.concatenate([r[2] for r in runs[:-1]])
+    rng = np.random.default_rng(0)
+    n_train = min(len(x_tr), args.train_samples)
+    pick = rng.choice(len(x_tr), n_train, replace=False)
+    x_tr, E_tr, F_tr = x_tr[pick], E_tr[pick], F_tr[pick]
+    x_te, E_te, F_te = runs[-1]
+    sel = rng.choice(len(x_te), min(len(x_te), 65536), replace=False)
+    x_te, E_te, F_te = x_te[sel], E_te[sel], F_te[sel]
+    del runs
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    xt, Et, Ft = dev(x_tr), dev(E_tr), dev(F_tr)
+    out["data"] = {"train_samples": int(n_train), "test_samples": int(len(x_te)),
+                   "harvest_runs": args.harvest_runs, "harvest_s": harvest_s,
+                   "E_train_mean_sd": [float(E_tr.mean()), float(E_tr.std())],
+                   "F_train_rms": float(np.sqrt(np.mean(F_tr.astype(np.float64) ** 2)))}
+    # 2. training
+    model = S.MLP(N, w["hidden"], seed=7)
+    model.fit_normalization(xt[:262144], Et[:262144])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = model.train(xt, Et, Ft, epochs=args.epochs, batch=args.batch, lam=1.0, lr=1e-3,
+                       lr_final=1e-5, report_every=500)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    steps = args.epochs * (n_train // args.batch)
+    out["training"] = {"epochs": args.epochs, "batch": args.batch, "steps": steps, "s": train_s,
+                       "samples_per_s": steps * args.batch / train_s,
+                       "loss": [[int(a), float(b)] for a, b in hist]}
+    del xt, Et, Ft
+    # 3. held-out errors
+    xe = dev(x_te)
+    Ep, Fp = model.energy_forces(xe)
+    Ep, Fp = Ep.cpu().numpy(), Fp.cpu().numpy().astype(np.float64)
+    out["held_out"] = {
+        "force_rmse_kJmol_nm": float(np.sqrt(np.mean((Fp - F_te) ** 2))),
+        "force_rel_rmse": float(np.sqrt(np.mean((Fp - F_te) ** 2) / np.mean(F_te.astype(np.float64) ** 2))),
+        "energy_rmse_kJmol": float(np.sqrt(np.mean((Ep - E_te) ** 2))),
+        "energy_sd_kJmol": float(E_te.std())}
+    del xe
+    # 4. anneals
+    gemms = time_gemms(torch, S, stream, R)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def anneal(with_model):
+        pop = pamd.Population(top, R, temps[0], w["seed"], pamd.torch_options(gamma_per_ps=w["gamma"]))
+        if with_model:
+            S.attach(pop.ctx, model)
+        else:
+            pop.autotune(50)
+        # warm-up: a short anneal at the first two temperatures
+        for _ in range(args.warmup):
+            pamd.pamd_anneal(pop.ctx, temps[:2], min(theta, 50), dt)
+        pamd.pamd_reset(pop.ctx, temps[0], w["seed"])
+        l0 = pamd.pamd_launch_count(pop.ctx)
+        flush.zero_()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        obs = pamd.pamd_anneal(pop.ctx, temps, theta, dt)
+        ev1.record(stream)
+        ev1.synchronize()
+        launches = pamd.pamd_launch_count(pop.ctx) - l0
+        pop.close()
+        return obs, ev0.elapsed_time(ev1), launches
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    obs_x, ms_x, l_x = anneal(False)
+    obs_s, ms_s, l_s = anneal(True)
+    clocks = sampler.stop()
+    model.close()
+
+    def cmp(key, se):
+        a = np.array([o[key] for o in obs_s]); b = np.array([o[key] for o in obs_x])
+        s = np.sqrt(np.array([o[se] for o in obs_s]) ** 2 + np.array([o[se] for o in obs_x]) ** 2)
+        return {"max_abs": float(np.max(np.abs(a - b))), "max_in_se": float(np.max(np.abs(a - b) / s)),
+                "mean_abs": float(np.mean(np.abs(a - b))),
+                "T_K": [float(t) for t in temps[::10]], "surrogate": [float(v) for v in a[::10]],
+                "exact": [float(v) for v in b[::10]]}
+
+    units = N * R * theta * (K + 1)
+    out["anneal"] = {"exact_ms": ms_x, "surrogate_ms": ms_s, "speedup_surrogate_over_exact": ms_x / ms_s,
+                     "exact_atom_steps_per_s": units / (ms_x / 1e3),
+                     "surrogate_atom_steps_per_s": units / (ms_s / 1e3),
+                     "launches": {"exact": int(l_x), "surrogate": int(l_s)},
+                     "e_pot": cmp("e_pot", "e_pot_se"), "rg": cmp("rg", "rg_se"),
+                     "sum_lnQ_final": {"surrogate": obs_s[-1]["sum_lnQ"], "exact": obs_x[-1]["sum_lnQ"]}}
+    peak = measured_peaks().get("bf16_tflops_sustained")
+    top_g = max(gemms, key=lambda r: r["ms"])
+    out["gemms"] = gemms
+    out["roofline"] = {"bound": "tensor", "achieved": top_g["tflops"], "peak": peak, "unit": "TFLOP/s",
+                       "frac": top_g["tflops"] / peak if peak else None, "traffic": None,
+                       "kernel": "gemm_bf16_kernel " + top_g["gemm"],
+                       "peak_basis": "measured sustained cuBLAS bf16 (MEASURED_PEAKS.json)"}
+    out["clocks"] = clocks
+    out["value"] = units / (ms_s / 1e3)
+    out["unit"] = UNIT
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -562,7 +771,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["anneal", "kernel", "precision", "resample"], default="anneal")
+    ap.add_argument("--mode", choices=["anneal", "kernel", "precision", "resample", "gemm", "surrogate"],
+                    default="anneal")
     ap.add_argument("--theta", type=int, default=0, help="kernel mode: steps per launch")
     ap.add_argument("--replicas", type=int, default=0, help="kernel mode: population size")
     ap.add_argument("--lanes", type=int, default=0, help="kernel mode: lanes per replica")
@@ -571,6 +781,11 @@ def main():
     ap.add_argument("--rpl", type=int, default=0, help="kernel mode: replicas per lane group (1, 2)")
     ap.add_argument("--fp64", action="store_true", help="kernel mode: all-FP64 propagate")
     ap.add_argument("--seeds", type=int, default=8, help="precision mode: independent anneals")
+    ap.add_argument("--temps", type=int, default=0, help="surrogate mode: temperature steps")
+    ap.add_argument("--harvest-runs", type=int, default=3, help="surrogate mode: exact training runs")
+    ap.add_argument("--train-samples", type=int, default=1 << 21, help="surrogate mode")
+    ap.add_argument("--epochs", type=int, default=6, help="surrogate mode: training epochs")
+    ap.add_argument("--batch", type=int, default=1024, help="surrogate mode: minibatch")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.mode == "kernel":
@@ -579,6 +794,10 @@ def main():
         run_precision(args)
     elif args.mode == "resample":
         run_resample(args)
+    elif args.mode == "gemm":
+        run_gemm(args)
+    elif args.mode == "surrogate" or args.workload == "c5":
+        run_surrogate(args, WORKLOADS["c5"])
     elif args.impl == "reference":
         run_reference(args, w)
     else:

@@ -2,18 +2,29 @@
 // for the dense layers of the MLP energy surrogate.
 //
 // C[M x N] (FP32) = A[M x K] . B[N x K]^T, A and B row-major BF16 (both
-// "K-major").  One CTA computes a 128 x 128 tile: 4 warps copy 128 x 64 tiles
-// of A and B into shared memory in the 128-byte-swizzled K-major layout
-// (two stages), one thread issues four tcgen05.mma (M 128, N 128, K 16) per
-// stage with the accumulator in tensor memory (128 columns of FP32), and a
-// tcgen05.commit signals an mbarrier when the stage may be overwritten.  The
-// epilogue reads the accumulator with tcgen05.ld (warp w owns rows 32w..32w+31)
-// and applies an optional bias and output transform.
+// "K-major").  One CTA computes a 128 x 128 tile with 4 warps:
+//   * one thread of warp 0 streams 128 x 64 tiles of A and B into a ring of
+//     kStages shared-memory stages with TMA (cp.async.bulk.tensor, 128-byte
+//     swizzle, out-of-range rows and columns zero-filled), completing a
+//     transaction-count mbarrier per stage;
+//   * one thread of warp 1 waits for each stage, issues four tcgen05.mma
+//     (M 128, N 128, K 16) with the FP32 accumulator in tensor memory, and
+//     frees the stage with tcgen05.commit;
+//   * after the last commit all four warps run the epilogue: tcgen05.ld of
+//     32 columns at a time (warp w owns rows 32w..32w+31), bias and the
+//     layer's output transform, 16-byte vector stores.
+// Shared memory (3 stages x 32 KiB) lets two CTAs share an SM, so one CTA's
+// epilogue overlaps the other's main loop.
 //
-// Every wait on an mbarrier is bounded: after kWaitLimit polls the kernel
-// records PAMD_ETIMEOUT, waits a bounded time more for its own MMAs, frees its
+// Every wait on an mbarrier is bounded: after kWaitLimit polls the waiting
+// role records PAMD_ETIMEOUT, the others stop at their next wait, the CTA
+// waits (bounded) for its own copies and products in flight, frees its
 // tensor memory and returns.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
 
 #include "pamd_internal.h"
 
@@ -21,8 +32,9 @@ namespace pamd {
 
 namespace {
 
-constexpr int kBM = 128, kBN = 128, kBK = 64, kThreads = 128;
+constexpr int kBM = 128, kBN = 128, kBK = 64, kThreads = 128, kStages = 3;
 constexpr int kTileBytes = kBM * kBK * 2;  // 16 KiB per operand tile
+constexpr int kStageBytes = 2 * kTileBytes;
 constexpr int kTmemCols = 128;
 constexpr uint32_t kWaitLimit = 1u << 22;
 
@@ -64,11 +76,28 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// bounded wait; returns false on timeout
+// bounded wait (polls, then polls with a short sleep); false on timeout
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kWaitLimit; ++i)
+    for (uint32_t i = 0; i < kWaitLimit; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (i >= 1024) __nanosleep(64);
+    }
     return false;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+// TMA: tile of a 2-D tensor map at element coordinates (x = column, y = row)
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() {
@@ -93,14 +122,6 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
                  : "memory");
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
-}
-
-__device__ __forceinline__ void st_shared_zero16(uint32_t dst) {
-    asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" ::"r"(dst), "r"(0u) : "memory");
-}
-
 // 32 columns of FP32 accumulator for this thread's row (TMEM lane)
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     uint32_t r[32];
@@ -119,38 +140,56 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// Copy a 128-row x 64-column BF16 tile (rows r0.., columns k0..) of a
-// row-major matrix into the swizzled layout; rows or columns outside the
-// matrix are zero.  K (and ld) must be multiples of 8.
-__device__ __forceinline__ void load_tile(uint32_t tile, const __nv_bfloat16* __restrict__ X,
-                                          int rows, int K, int ld, int r0, int k0) {
-    for (int idx = threadIdx.x; idx < kBM * 8; idx += kThreads) {
-        const int r = idx >> 3, c = idx & 7;
-        const uint32_t dst = tile + (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4));
-        const int gr = r0 + r, gk = k0 + c * 8;
-        if (gr < rows && gk < K)
-            cp_async16(dst, X + (size_t)gr * ld + gk);
-        else
-            st_shared_zero16(dst);
-    }
-}
-
-}  // namespace
 
 __device__ __forceinline__ float sigmoid(float z) { return 1.0f / (1.0f + __expf(-z)); }
 
-__global__ void __launch_bounds__(kThreads, 1) gemm_bf16_kernel(const __grid_constant__ GemmArgs g) {
+// 32 consecutive FP32 values of one row: vector stores when the whole chunk
+// is inside the matrix and 16-byte aligned, else element by element
+__device__ __forceinline__ void store_row32(float* dst, const float (&v)[32], int n, bool vec) {
+    if (vec && n == 32) {
+        float4* d = reinterpret_cast<float4*>(dst);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) d[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (j < n) dst[j] = v[j];
+    }
+}
+
+__device__ __forceinline__ void store_row32_bf16(__nv_bfloat16* dst, const float (&v)[32], int n,
+                                                 bool vec) {
+    if (vec && n == 32) {
+        uint4* d = reinterpret_cast<uint4*>(dst);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t w[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const __nv_bfloat162 h = __floats2bfloat162_rn(v[8 * q + 2 * t], v[8 * q + 2 * t + 1]);
+                w[t] = *reinterpret_cast<const uint32_t*>(&h);
+            }
+            d[q] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (j < n) dst[j] = __float2bfloat16(v[j]);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                             const __grid_constant__ CUtensorMap tmB,
+                                                             const __grid_constant__ GemmArgs g) {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long mbar[2];
+    __shared__ __align__(8) unsigned long long full_bar[kStages], empty_bar[kStages], accum_bar;
     __shared__ uint32_t tmem_slot;
-    // 1024-byte aligned operand tiles: [A0 | B0 | A1 | B1]
-    const uint32_t raw = smem_u32(smem_raw);
-    const uint32_t base = (raw + 1023u) & ~1023u;
+    __shared__ int s_abort, s_issued, s_consumed;
+    // 1024-byte aligned stages: [A0 | B0 | A1 | B1 | ...]
+    const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
-    const uint32_t bar[2] = {smem_u32(&mbar[0]), smem_u32(&mbar[1])};
-    const __nv_bfloat16* A = static_cast<const __nv_bfloat16*>(g.A);
-    const __nv_bfloat16* B = static_cast<const __nv_bfloat16*>(g.B);
+    const int KB = (g.K + kBK - 1) / kBK;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -160,54 +199,73 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_bf16_kernel(const __grid_con
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        mbar_init(bar[0], 1);
-        mbar_init(bar[1], 1);
+        for (int st = 0; st < kStages; ++st) {
+            mbar_init(smem_u32(&full_bar[st]), 1);
+            mbar_init(smem_u32(&empty_bar[st]), 1);
+        }
+        mbar_init(smem_u32(&accum_bar), 1);
+        s_abort = 0;
+        s_issued = 0;
+        s_consumed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
+    volatile int* abort_flag = &s_abort;
 
-    // Mainloop.  Control flow is uniform across the block: every thread sees
-    // the same k-block count and the same (block-reduced) timeout flag.
-    const int KB = (g.K + kBK - 1) / kBK;
-    uint32_t phase[2] = {0u, 0u};
-    bool ok = true;
-    int committed = 0;
-    for (int kb = 0; kb < KB; ++kb) {
-        const int s = kb & 1;
-        if (kb >= 2) {  // the MMAs of k-block kb-2 have finished reading stage s
-            if (!mbar_wait(bar[s], phase[s])) ok = false;
-            phase[s] ^= 1u;
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        int kb = 0;
+        for (; kb < KB; ++kb) {
+            const int st = kb % kStages;
+            if (kb >= kStages &&
+                !mbar_wait(smem_u32(&empty_bar[st]), (uint32_t)((kb / kStages - 1) & 1))) {
+                *abort_flag = 1;
+                break;
+            }
+            if (*abort_flag) break;
+            const uint32_t fb = smem_u32(&full_bar[st]);
+            const uint32_t ta = base + (uint32_t)(st * kStageBytes);
+            mbar_expect_tx(fb, (uint32_t)kStageBytes);
+            tma_load_2d(ta, &tmA, kb * kBK, m0, fb);
+            tma_load_2d(ta + kTileBytes, &tmB, kb * kBK, n0, fb);
         }
-        if (!__syncthreads_and(ok)) break;
-        const uint32_t ta = base + (uint32_t)(s * 2 * kTileBytes);
-        const uint32_t tb = ta + kTileBytes;
-        load_tile(ta, A, g.M, g.K, g.lda, m0, kb * kBK);
-        load_tile(tb, B, g.N, g.K, g.ldb, n0, kb * kBK);
-        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
+        s_issued = kb;
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        int kb = 0;
+        for (; kb < KB; ++kb) {
+            const int st = kb % kStages;
+            if (!mbar_wait(smem_u32(&full_bar[st]), (uint32_t)((kb / kStages) & 1))) {
+                *abort_flag = 1;
+                break;
+            }
+            if (*abort_flag) break;
             tc_fence_after();
+            const uint32_t ta = base + (uint32_t)(st * kStageBytes);
 #pragma unroll
             for (int k = 0; k < kBK / 16; ++k)
-                mma_bf16(tmem, sw128_desc(ta + k * 32), sw128_desc(tb + k * 32),
+                mma_bf16(tmem, sw128_desc(ta + k * 32), sw128_desc(ta + kTileBytes + k * 32),
                          (kb > 0 || k > 0) ? 1u : 0u);
-            mma_commit(bar[s]);
+            mma_commit(smem_u32(&empty_bar[st]));
         }
-        committed = kb + 1;
+        s_consumed = kb;
+        // tracks every product issued before it, also on the abort path
+        mma_commit(smem_u32(&accum_bar));
     }
-    // The last commit tracks every MMA issued before it: wait for it (on the
-    // error path too, so that no MMA still writes the tensor memory we free).
-    if (committed > 0) {
-        const int s = (committed - 1) & 1;
-        if (!mbar_wait(bar[s], phase[s])) ok = false;
-    }
-    ok = __syncthreads_and(ok);
+    __syncwarp();
+    bool ok = mbar_wait(smem_u32(&accum_bar), 0u);
+    ok = __syncthreads_and(ok && !*abort_flag);
     if (!ok) {
         if (tid == 0) atomicCAS(g.status, 0, PAMD_ETIMEOUT);
+        // copies issued but never consumed must land before the CTA exits
+        if (tid == 0) {
+            for (int kb = s_consumed; kb < s_issued; ++kb)
+                mbar_wait(smem_u32(&full_bar[kb % kStages]), (uint32_t)((kb / kStages) & 1));
+            mbar_wait(smem_u32(&accum_bar), 0u);  // products in flight
+        }
     } else {
         tc_fence_after();
         const int row = m0 + warp * 32 + lane;
@@ -215,35 +273,58 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_bf16_kernel(const __grid_con
         float head = 0.0f;
         __nv_bfloat16* Cb = static_cast<__nv_bfloat16*>(g.Cb);
         __nv_bfloat16* CbT = static_cast<__nv_bfloat16*>(g.CbT);
+        const bool vf = (g.vec_ok & 1) != 0, vb = (g.vec_ok & 2) != 0;
 #pragma unroll 1
         for (int cc = 0; cc < kBN / 32; ++cc) {
             float v[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), v);
-            if (!row_ok) continue;
+            const int col0 = n0 + cc * 32;
+            const int n = min(32, g.N - col0);
+            if (!row_ok || n <= 0) continue;
+            if (g.bias) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const int col = n0 + cc * 32 + j;
-                if (col >= g.N) continue;
-                const float z = v[j] + (g.bias ? g.bias[col] : 0.0f);
-                const size_t o = (size_t)row * g.ldc + col;
-                if (g.C) g.C[o] = z;
-                float out = z;
-                if (g.epi == kEpiSilu || g.epi == kEpiHead) {
-                    const float sg = sigmoid(z);
-                    const float ds = sg * (1.0f + z * (1.0f - sg));
-                    if (g.Cs) g.Cs[o] = ds;
-                    if (g.epi == kEpiSilu) {
-                        out = z * sg;
-                    } else {
-                        head += g.vec[col] * (z * sg);
-                        out = g.vec[col] * ds;
-                    }
-                } else if (g.epi == kEpiMul) {
-                    out = z * g.mul[o];
+                for (int j = 0; j < 32; ++j) v[j] += (j < n) ? g.bias[col0 + j] : 0.0f;
+            }
+            const size_t o = (size_t)row * g.ldc + col0;
+            if (g.C) store_row32(g.C + o, v, n, vf);
+            if (g.epi == kEpiSilu || g.epi == kEpiHead) {
+                float ds[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float sg = sigmoid(v[j]);
+                    ds[j] = sg * (1.0f + v[j] * (1.0f - sg));
+                    v[j] *= sg;  // silu
                 }
-                const __nv_bfloat16 ob = __float2bfloat16(out);
-                if (Cb) Cb[(size_t)row * g.ldcb + col] = ob;
-                if (CbT) CbT[(size_t)col * g.ldt + row] = ob;
+                if (g.Cs) store_row32(g.Cs + o, ds, n, vf);
+                if (g.epi == kEpiHead) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float w = (j < n) ? g.vec[col0 + j] : 0.0f;
+                        head = fmaf(w, v[j], head);
+                        v[j] = w * ds[j];
+                    }
+                }
+            } else if (g.epi == kEpiMul) {
+                const float* mr = g.mul + o;
+                if (vf && n == 32) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const float4 t = reinterpret_cast<const float4*>(mr)[q];
+                        v[4 * q] *= t.x;
+                        v[4 * q + 1] *= t.y;
+                        v[4 * q + 2] *= t.z;
+                        v[4 * q + 3] *= t.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[j] *= (j < n) ? mr[j] : 0.0f;
+                }
+            }
+            if (Cb) store_row32_bf16(Cb + (size_t)row * g.ldcb + col0, v, n, vb);
+            if (CbT) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (j < n) CbT[(size_t)(col0 + j) * g.ldt + row] = __float2bfloat16(v[j]);
             }
         }
         if (g.epi == kEpiHead && row_ok) g.part[(size_t)row * gridDim.x + blockIdx.x] = head;
@@ -256,19 +337,57 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_bf16_kernel(const __grid_con
                      : "memory");
 }
 
-cudaError_t launch_gemm_bf16(const GemmArgs& g, cudaStream_t s) {
-    if (g.M <= 0 || g.N <= 0 || g.K <= 0 || (g.K & 7) || (g.lda & 7) || (g.ldb & 7))
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// Tensor map of a row-major BF16 matrix [rows][ld] read in 128-row x 64-column
+// boxes with the 128-byte swizzle; columns >= cols and rows >= rows read as 0.
+bool encode_operand(CUtensorMap* map, const void* ptr, int rows, int cols, int ld) {
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+cudaError_t launch_gemm_bf16(const GemmArgs& ga, cudaStream_t s) {
+    if (ga.M <= 0 || ga.N <= 0 || ga.K <= 0 || (ga.K & 7) || (ga.lda & 7) || (ga.ldb & 7) ||
+        (reinterpret_cast<uintptr_t>(ga.A) & 15) || (reinterpret_cast<uintptr_t>(ga.B) & 15))
         return cudaErrorInvalidValue;
-    const size_t smem = 4 * (size_t)kTileBytes + 1024;
-    static bool configured = false;
-    if (!configured) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    CUtensorMap tmA, tmB;
+    if (!encode_operand(&tmA, ga.A, ga.M, ga.K, ga.lda) || !encode_operand(&tmB, ga.B, ga.N, ga.K, ga.ldb))
+        return cudaErrorInvalidValue;
+    GemmArgs g = ga;
+    auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+    const bool f_ok = (g.ldc % 4 == 0) && al16(g.C) && al16(g.Cs) && al16(g.mul);
+    const bool b_ok = (g.ldcb % 8 == 0) && al16(g.Cb);
+    g.vec_ok = (f_ok ? 1 : 0) | (b_ok ? 2 : 0);
+    const size_t smem = (size_t)kStages * kStageBytes + 1024;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [&] {
+        attr = cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    if (attr != cudaSuccess) return attr;
     const dim3 grid((g.N + kBN - 1) / kBN, (g.M + kBM - 1) / kBM);
-    gemm_bf16_kernel<<<grid, kThreads, smem, s>>>(g);
+    gemm_bf16_kernel<<<grid, kThreads, smem, s>>>(tmA, tmB, g);
     return cudaGetLastError();
 }
 

@@ -308,6 +308,7 @@ struct GemmArgs {
     float* part;               // [M][gridDim.x] (kEpiHead)
     int* status;               // PAMD status word (timeouts)
     int M, N, K, lda, ldb, ldc, ldcb, ldt, epi;
+    int vec_ok;                // set by the launcher: 1 FP32 rows, 2 BF16 rows 16-byte aligned
 };
 cudaError_t launch_gemm_bf16(const GemmArgs& g, cudaStream_t s);
 
