@@ -621,6 +621,54 @@ def run_gemm(args):
     print(json.dumps({"mode": "gemm", "M": M, "gemms": res, "bf16_peak_tflops": peak}), flush=True)
 
 
+def run_surrogate_kernel(args):
+    """Surrogate-driven propagate launches only: a randomly initialised model
+    (identity normalisation fitted to the start geometry) drives R replicas
+    of the 75-atom chain for theta steps per pamd_propagate call, timed with
+    events on the population's stream.  Prints one JSON line (ms per MD step
+    and the effective tensor throughput of the four GEMMs per step)."""
+    import numpy as np
+    import torch
+
+    import pamd_inputs as pi
+    from paper_1806_06016_gb300 import build as pbuild
+    from paper_1806_06016_gb300 import pamd
+    from paper_1806_06016_gb300 import surrogate as S
+
+    torch.cuda.set_device(0)
+    pbuild.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    w = WORKLOADS["c5"]
+    N, R = w["n_atoms"], args.replicas or w["R"]
+    theta = args.theta or 20
+    top = pi.make_chain(N, w["gen_seed"])
+    x = torch.from_numpy(pi.perturbed_positions(top, 4096, 0.01, 3).astype(np.float32)).cuda()
+    model = S.MLP(N, w["hidden"], seed=7)
+    model.fit_normalization(x, torch.linspace(-1.0, 1.0, 4096, dtype=torch.float64, device="cuda"))
+    pop = pamd.Population(top, R, 300.0, w["seed"], pamd.torch_options())
+    S.attach(pop.ctx, model)
+    for _ in range(args.warmup):
+        pamd.pamd_propagate(pop.ctx, theta, w["dt"], 300.0)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.steps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        pamd.pamd_propagate(pop.ctx, theta, w["dt"], 300.0)
+        ev1.record(stream)
+        ev1.synchronize()
+        ms.append(ev0.elapsed_time(ev1))
+    pop.close()
+    model.close()
+    per_step = statistics.mean(ms) / (theta + 1)
+    flop = sum(2.0 * m * n * k for _, m, n, k in gemm_shapes(R, N, w["hidden"]))
+    print(json.dumps({"mode": "surrogate_kernel", "replicas": R, "theta": theta,
+                      "ms_per_launch": statistics.mean(ms), "ms_per_force_evaluation": per_step,
+                      "gemm_tflops_effective": flop / (per_step / 1e3) / 1e12,
+                      "atom_steps_per_s": N * R * theta / (statistics.mean(ms) / 1e3)}), flush=True)
+
+
 def run_surrogate(args, w):
     """Learned-surrogate workload: harvest exact data, train, compare.
 
@@ -771,7 +819,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", choices=["anneal", "kernel", "precision", "resample", "gemm", "surrogate"],
+    ap.add_argument("--mode", choices=["anneal", "kernel", "precision", "resample", "gemm", "surrogate",
+                                       "surrogate_kernel"],
                     default="anneal")
     ap.add_argument("--theta", type=int, default=0, help="kernel mode: steps per launch")
     ap.add_argument("--replicas", type=int, default=0, help="kernel mode: population size")
@@ -784,8 +833,8 @@ def main():
     ap.add_argument("--temps", type=int, default=0, help="surrogate mode: temperature steps")
     ap.add_argument("--harvest-runs", type=int, default=3, help="surrogate mode: exact training runs")
     ap.add_argument("--train-samples", type=int, default=1 << 21, help="surrogate mode")
-    ap.add_argument("--epochs", type=int, default=6, help="surrogate mode: training epochs")
-    ap.add_argument("--batch", type=int, default=1024, help="surrogate mode: minibatch")
+    ap.add_argument("--epochs", type=int, default=40, help="surrogate mode: training epochs")
+    ap.add_argument("--batch", type=int, default=2048, help="surrogate mode: minibatch")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.mode == "kernel":
@@ -796,6 +845,8 @@ def main():
         run_resample(args)
     elif args.mode == "gemm":
         run_gemm(args)
+    elif args.mode == "surrogate_kernel":
+        run_surrogate_kernel(args)
     elif args.mode == "surrogate" or args.workload == "c5":
         run_surrogate(args, WORKLOADS["c5"])
     elif args.impl == "reference":

@@ -193,17 +193,18 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_forces_kernel(const ForceArgs
     extern __shared__ float fsm[];
     float* xs = fsm;
     float* gam = fsm + 3 * kXs;
+    init_gamma(f.N, gam);
     for (int m = blockIdx.x; m < f.M; m += gridDim.x) {
         __syncthreads();
         load_config(f.cv, m, f.N, xs);
-        const float* gr = f.ga + (size_t)m * f.Pp;
-        for (int p = threadIdx.x; p < f.P; p += blockDim.x) gam[p] = gr[p] * f.inv_sd[p];
+        __syncthreads();
+        if (f.F) load_gamma(xs, f.ga + (size_t)m * f.Pp, f.inv_sd, f.pairs, f.P, f.N, gam);
         __syncthreads();
         if (f.F) {
             const float sE = (float)f.sigma_E;
             float* Fo = f.F + (size_t)m * 3 * f.N;
             for (int k = threadIdx.x; k < f.N; k += blockDim.x) {
-                const float3 a = atom_force(k, xs, gam, f.N);
+                const float3 a = atom_force_any(k, xs, gam, f.N);
                 Fo[3 * k] = sE * a.x;
                 Fo[3 * k + 1] = sE * a.y;
                 Fo[3 * k + 2] = sE * a.z;
@@ -225,17 +226,18 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_loss_kernel(const LossArgs L)
     float* gam = lsm + 6 * kXs;
     const double inv_sE = 1.0 / L.sigma_E;
     const float cu = (float)(2.0 * L.lam / (3.0 * L.N * (double)L.M));
+    init_gamma(L.N, gam);
     for (int m = blockIdx.x; m < L.M; m += gridDim.x) {
         __syncthreads();
         load_config(L.cv, m, L.N, xs);
-        const float* gr = L.ga + (size_t)m * L.Pp;
-        for (int p = threadIdx.x; p < L.P; p += blockDim.x) gam[p] = gr[p] * L.inv_sd[p];
+        __syncthreads();
+        load_gamma(xs, L.ga + (size_t)m * L.Pp, L.inv_sd, L.pairs, L.P, L.N, gam);
         __syncthreads();
         const long long src = config_index(L.cv, m);
         const float* Fr = L.F_ref + src * 3 * L.N;
         double sq = 0.0;
         for (int k = threadIdx.x; k < L.N; k += blockDim.x) {
-            const float3 a = atom_force(k, xs, gam, L.N);
+            const float3 a = atom_force_any(k, xs, gam, L.N);
             const float dfx = a.x - (float)(Fr[3 * k] * inv_sE);
             const float dfy = a.y - (float)(Fr[3 * k + 1] * inv_sE);
             const float dfz = a.z - (float)(Fr[3 * k + 2] * inv_sE);
@@ -368,8 +370,8 @@ int pack(pamd_mlp* m) {
     return launch_check(m, "weight pack");
 }
 
-size_t forces_smem(const pamd_mlp* m) { return sizeof(float) * (3 * kXs + (size_t)m->Pp); }
-size_t loss_smem(const pamd_mlp* m) { return sizeof(float) * (6 * kXs + (size_t)m->Pp); }
+size_t forces_smem(const pamd_mlp* m) { return sizeof(float) * (3 * kXs + (size_t)gamma_floats(m->N, m->Pp)); }
+size_t loss_smem(const pamd_mlp* m) { return sizeof(float) * (6 * kXs + (size_t)gamma_floats(m->N, m->Pp)); }
 
 int set_smem_attrs(const pamd_mlp* m) {
     cudaError_t e = cudaFuncSetAttribute(mlp_forces_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -377,10 +379,6 @@ int set_smem_attrs(const pamd_mlp* m) {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(mlp_loss_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)loss_smem(m));
-    if (e == cudaSuccess) {
-        const size_t ss = mlp_step_smem(m->Pp);
-        (void)ss;  // the step kernel sets its own attribute when launched
-    }
     return e == cudaSuccess ? PAMD_OK : mfail(PAMD_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
 }
 
@@ -733,6 +731,7 @@ int pamd_mlp_energy_forces(pamd_mlp* m, const float* x_dev, int64_t M, double* E
     f.Pp = m->Pp;
     f.nparts = m->nparts;
     f.ga = m->w.ga;
+    f.pairs = m->pairs;
     f.part = m->w.part;
     f.inv_sd = m->inv_sd;
     f.b3 = m->params + m->ob3;

@@ -43,6 +43,7 @@ __device__ __forceinline__ void block_features(const float* xs, const ushort2* _
                                                const float* __restrict__ inv_sd, int P, int Pp,
                                                __nv_bfloat16* a_row, __nv_bfloat16* aT, int ldt,
                                                int m) {
+#pragma unroll 4
     for (int p = threadIdx.x; p < Pp; p += blockDim.x) {
         float v = 0.0f;
         if (p < P) {
@@ -73,6 +74,67 @@ __device__ __forceinline__ float3 atom_force(int k, const float* xs, const float
         fx = fmaf(c, dx, fx);
         fy = fmaf(c, dy, fy);
         fz = fmaf(c, dz, fz);
+    }
+    return make_float3(fx, fy, fz);
+}
+
+// Molecules of up to kGammaMatrixMax atoms use a symmetric N x N shared-
+// memory matrix (odd row stride: the atoms of a warp hit distinct banks)
+// holding c_ij = gam_ij / r_ij^3, filled by one pass over the pairs (one
+// rsqrt per pair), so that the force of atom k is the plain row sum
+// F_k = sum_j c_kj (x_k - x_j).  Larger molecules keep gam per pair and use
+// atom_force.  The diagonal is zero (set once per block, never written by
+// the pair pass).
+constexpr int kGammaMatrixMax = 128;
+
+__host__ __device__ __forceinline__ bool gamma_matrix(int N) { return N <= kGammaMatrixMax; }
+__host__ __device__ __forceinline__ int gamma_stride(int N) { return N | 1; }
+
+// floats of shared memory the table of an N-atom molecule takes
+__host__ __device__ __forceinline__ int gamma_floats(int N, int Pp) {
+    return gamma_matrix(N) ? N * gamma_stride(N) : Pp;
+}
+
+// zero diagonal of the matrix (whole block; once per block)
+__device__ __forceinline__ void init_gamma(int N, float* gam) {
+    if (gamma_matrix(N))
+        for (int k = threadIdx.x; k < N; k += blockDim.x) gam[k * gamma_stride(N) + k] = 0.0f;
+}
+
+// fill the table from de/da of one configuration (whole block)
+__device__ __forceinline__ void load_gamma(const float* xs, const float* __restrict__ ga_row,
+                                           const float* __restrict__ inv_sd,
+                                           const ushort2* __restrict__ pairs, int P, int N, float* gam) {
+    if (gamma_matrix(N)) {
+        const int S = gamma_stride(N);
+#pragma unroll 4
+        for (int p = threadIdx.x; p < P; p += blockDim.x) {
+            const ushort2 ij = pairs[p];
+            const float dx = xs[ij.x] - xs[ij.y];
+            const float dy = xs[kXs + ij.x] - xs[kXs + ij.y];
+            const float dz = xs[2 * kXs + ij.x] - xs[2 * kXs + ij.y];
+            const float ir = rsqrtf(dx * dx + dy * dy + dz * dz);
+            const float c = ga_row[p] * inv_sd[p] * ir * ir * ir;
+            gam[ij.x * S + ij.y] = c;
+            gam[ij.y * S + ij.x] = c;
+        }
+    } else {
+        for (int p = threadIdx.x; p < P; p += blockDim.x) gam[p] = ga_row[p] * inv_sd[p];
+    }
+}
+
+// sum over j != k of gam_kj (x_k - x_j) / r_kj^3 with the table of load_gamma
+__device__ __forceinline__ float3 atom_force_any(int k, const float* xs, const float* gam, int N) {
+    if (!gamma_matrix(N)) return atom_force(k, xs, gam, N);
+    const float xk = xs[k], yk = xs[kXs + k], zk = xs[2 * kXs + k];
+    const float* row = gam + k * gamma_stride(N);
+    float fx = 0.0f, fy = 0.0f, fz = 0.0f;
+#pragma unroll 4
+    for (int j = 0; j < N; ++j) {
+        const float c = row[j];
+        fx = fmaf(c, xk - xs[j], fx);
+        fy = fmaf(c, yk - xs[kXs + j], fy);
+        fz = fmaf(c, zk - xs[2 * kXs + j], fz);
     }
     return make_float3(fx, fy, fz);
 }

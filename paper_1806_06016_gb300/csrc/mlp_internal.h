@@ -68,6 +68,7 @@ struct FeatArgs {
 struct ForceArgs {
     ConfigView cv;
     int M, N, P, Pp, nparts;
+    const ushort2* pairs;    // [Pp] (i, j)
     const float* ga;         // [M][Pp]
     const float* part;       // [M][nparts]
     const float* inv_sd;
@@ -125,7 +126,7 @@ struct MlpStepParams {
     uint32_t purpose_mol;
 };
 cudaError_t launch_mlp_step(const MlpStepParams& p, cudaStream_t s);
-size_t mlp_step_smem(int Pp);
+size_t mlp_step_smem(int N, int Pp);
 
 }  // namespace pamd
 

@@ -22,10 +22,11 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_step_kernel(const MlpStepPara
     extern __shared__ float ssm[];
     __shared__ double red[32];
     float* xs = ssm;             // [3][kXs]
-    float* gam = ssm + 3 * kXs;  // [Pp]
+    float* gam = ssm + 3 * kXs;  // gamma_floats(N, Pp)
     const int N = p.N, Np = p.Np;
     const uint32_t step = (p.dev_counters ? p.dev_counters[0] : 0u) + p.step0 + (uint32_t)p.step_index;
     const float sE = (float)p.sigma_E;
+    init_gamma(N, gam);
     for (long long k = blockIdx.x; k < p.R; k += gridDim.x) {
         float* st = p.state + (size_t)k * 6 * Np;
         __syncthreads();
@@ -33,15 +34,13 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_step_kernel(const MlpStepPara
             const int c = t / N, i = t - c * N;
             xs[c * kXs + i] = st[c * Np + i];
         }
-        if (p.mode != 0) {
-            const float* gr = p.ga + (size_t)k * p.Pp;
-            for (int q = threadIdx.x; q < p.P; q += blockDim.x) gam[q] = gr[q] * p.inv_sd[q];
-        }
         __syncthreads();
         if (p.mode == 0) {
             block_features(xs, p.pairs, p.mu, p.inv_sd, p.P, p.Pp, p.a + (size_t)k * p.Pp, nullptr, 0, 0);
             continue;
         }
+        load_gamma(xs, p.ga + (size_t)k * p.Pp, p.inv_sd, p.pairs, p.P, N, gam);
+        __syncthreads();
         // forces of the current positions, F = -dE/dx
         float fx[kAtomsPerThread], fy[kAtomsPerThread], fz[kAtomsPerThread];
 #pragma unroll
@@ -49,7 +48,7 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_step_kernel(const MlpStepPara
             const int i = threadIdx.x + q * kMlpThreads;
             fx[q] = fy[q] = fz[q] = 0.0f;
             if (i < N) {
-                const float3 f = atom_force(i, xs, gam, N);
+                const float3 f = atom_force_any(i, xs, gam, N);
                 fx[q] = sE * f.x;
                 fy[q] = sE * f.y;
                 fz[q] = sE * f.z;
@@ -142,11 +141,13 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_step_kernel(const MlpStepPara
 
 }  // namespace
 
-size_t mlp_step_smem(int Pp) { return sizeof(float) * (3 * (size_t)kXs + (size_t)Pp); }
+size_t mlp_step_smem(int N, int Pp) {
+    return sizeof(float) * (3 * (size_t)kXs + (size_t)gamma_floats(N, Pp));
+}
 
 cudaError_t launch_mlp_step(const MlpStepParams& p, cudaStream_t s) {
     static size_t configured = 0;
-    const size_t smem = mlp_step_smem(p.Pp);
+    const size_t smem = mlp_step_smem(p.N, p.Pp);
     if (smem > configured) {
         const cudaError_t e =
             cudaFuncSetAttribute(mlp_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
