@@ -571,23 +571,15 @@ def gemm_shapes(M, n_atoms=75, hidden=512):
 
 
 def time_gemms(torch, S, stream, M, reps=10, n_atoms=75, hidden=512):
-    """CUDA-event time (ms, mean of reps after 2 warm-ups) of each surrogate GEMM shape."""
+    """Device time (ms) of each surrogate GEMM shape: mean of `reps` back-to-back
+    launches between CUDA events on the launch stream (after 2 warm-ups)."""
     res = []
     g = torch.Generator(device="cuda").manual_seed(0)
     for name, m, n, k in gemm_shapes(M, n_atoms, hidden):
         A = torch.randn(m, k, generator=g, device="cuda").to(torch.bfloat16)
         B = torch.randn(n, k, generator=g, device="cuda").to(torch.bfloat16)
-        for _ in range(2):
-            S.gemm_bf16(A, B)
-        ms = []
-        for _ in range(reps):
-            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            ev0.record(stream)
-            S.gemm_bf16(A, B)
-            ev1.record(stream)
-            ev1.synchronize()
-            ms.append(ev0.elapsed_time(ev1))
-        t = statistics.mean(ms)
+        S.gemm_bf16_time(A, B, 2)
+        t = S.gemm_bf16_time(A, B, reps)
         flop = 2.0 * m * n * k
         res.append({"gemm": name, "M": m, "N": n, "K": k, "ms": t, "tflops": flop / (t / 1e3) / 1e12})
         del A, B
@@ -723,7 +715,7 @@ def run_surrogate(args, w):
     del runs
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     xt, Et, Ft = dev(x_tr), dev(E_tr), dev(F_tr)
-    out["data"] = {"train_samples": int(n_train), "test_samples": int(len(x_te)),
+    out["training_data"] = {"train_samples": int(n_train), "test_samples": int(len(x_te)),
                    "harvest_runs": args.harvest_runs, "harvest_s": harvest_s,
                    "E_train_mean_sd": [float(E_tr.mean()), float(E_tr.std())],
                    "F_train_rms": float(np.sqrt(np.mean(F_tr.astype(np.float64) ** 2)))}
@@ -740,20 +732,61 @@ def run_surrogate(args, w):
     out["training"] = {"epochs": args.epochs, "batch": args.batch, "steps": steps, "s": train_s,
                        "samples_per_s": steps * args.batch / train_s,
                        "loss": [[int(a), float(b)] for a, b in hist]}
-    del xt, Et, Ft
-    # 3. held-out errors
     xe = dev(x_te)
-    Ep, Fp = model.energy_forces(xe)
-    Ep, Fp = Ep.cpu().numpy(), Fp.cpu().numpy().astype(np.float64)
-    out["held_out"] = {
-        "force_rmse_kJmol_nm": float(np.sqrt(np.mean((Fp - F_te) ** 2))),
-        "force_rel_rmse": float(np.sqrt(np.mean((Fp - F_te) ** 2) / np.mean(F_te.astype(np.float64) ** 2))),
-        "energy_rmse_kJmol": float(np.sqrt(np.mean((Ep - E_te) ** 2))),
-        "energy_sd_kJmol": float(E_te.std())}
-    del xe
+
+    def held_out():
+        Ep, Fp = model.energy_forces(xe)
+        Ep, Fp = Ep.cpu().numpy(), Fp.cpu().numpy().astype(np.float64)
+        return {"force_rmse_kJmol_nm": float(np.sqrt(np.mean((Fp - F_te) ** 2))),
+                "force_rel_rmse": float(np.sqrt(np.mean((Fp - F_te) ** 2) /
+                                                np.mean(F_te.astype(np.float64) ** 2))),
+                "energy_rmse_kJmol": float(np.sqrt(np.mean((Ep - E_te) ** 2))),
+                "energy_sd_kJmol": float(E_te.std())}
+
+    out["held_out_after_training"] = held_out()
+    # 2b. refinement rounds: the configurations a surrogate-driven anneal of the
+    # same shape visits (theta = 500), labelled by the exact force field, are
+    # added to the training set and the model is trained further
+    out["refinement"] = []
+    for r in range(args.refine_rounds):
+        t0 = time.perf_counter()
+        xr, Er, Fr = S.harvest(top, 8192, temps_h, 500, dt, 2000 + r, pamd.torch_options(), model=model)
+        harvest_r = time.perf_counter() - t0
+        rg_end = float(np.mean(np.sqrt(np.mean(np.sum(
+            (xr[-8192:] - xr[-8192:].mean(1, keepdims=True)) ** 2, axis=2), axis=1))))
+        # configurations the surrogate reaches far outside the physical range
+        # (overlapping atoms: exact energies up to 1e11 kJ/mol) would swamp the
+        # loss; keep those within 6 SD of the training energies and 5x the
+        # training force RMS
+        f_rms = np.sqrt(np.mean(Fr.astype(np.float64) ** 2, axis=(1, 2)))
+        keep = (Er <= E_tr.mean() + 6.0 * E_tr.std()) & (f_rms <= 5.0 * np.sqrt(np.mean(F_tr.astype(np.float64) ** 2)))
+        xr, Er, Fr = xr[keep], Er[keep], Fr[keep]
+        xt = torch.cat([xt, dev(xr)])
+        Et = torch.cat([Et, dev(Er)])
+        Ft = torch.cat([Ft, dev(Fr)])
+        t0 = time.perf_counter()
+        hist_r = model.train(xt, Et, Ft, epochs=args.refine_epochs, batch=args.batch, lam=1.0,
+                             lr=3e-4, lr_final=1e-5, seed=r + 1, report_every=2000)
+        torch.cuda.synchronize()
+        out["refinement"].append({"round": r + 1, "added_samples": int(len(xr)),
+                                  "discarded_samples": int((~keep).sum()),
+                                  "surrogate_rg_at_250K_before": rg_end,
+                                  "exact_E_mean_of_added": float(Er.mean()),
+                                  "harvest_s": harvest_r, "train_s": time.perf_counter() - t0,
+                                  "loss_last": float(hist_r[-1][1]) if hist_r else None,
+                                  "held_out": held_out()})
+    out["held_out"] = held_out()
+    model_params = {k: (np.asarray(v, dtype=np.float64) if isinstance(v, np.ndarray) else float(v))
+                    for k, v in model.get_params().items()}
+    del xe, xt, Et, Ft
     # 4. anneals
     gemms = time_gemms(torch, S, stream, R)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    Np = (N + 3) // 4 * 4
+    rng_h = np.random.default_rng(w["seed"])
+    x_host = np.repeat((top.x0 - top.x0.mean(0))[None], R, axis=0)
+    v_host = rng_h.normal(0.0, math.sqrt(0.008314462618 * temps[0] / 12.0), (R, N, 3))
+    fam_host = np.arange(R, dtype=np.int32)
 
     def anneal(with_model):
         pop = pamd.Population(top, R, temps[0], w["seed"], pamd.torch_options(gamma_per_ps=w["gamma"]))
@@ -761,25 +794,41 @@ def run_surrogate(args, w):
             S.attach(pop.ctx, model)
         else:
             pop.autotune(50)
-        # warm-up: a short anneal at the first two temperatures
+        # warm-up: short anneals at the first two temperatures
         for _ in range(args.warmup):
             pamd.pamd_anneal(pop.ctx, temps[:2], min(theta, 50), dt)
-        pamd.pamd_reset(pop.ctx, temps[0], w["seed"])
-        l0 = pamd.pamd_launch_count(pop.ctx)
+        per_eval = None
+        if with_model:
+            # one force evaluation (features, four GEMMs, step kernel): theta = 20 launch
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            pamd.pamd_propagate(pop.ctx, 20, dt, temps[0])
+            ev1.record(stream)
+            ev1.synchronize()
+            per_eval = ev0.elapsed_time(ev1) / 21
+        torch.cuda.synchronize()
         flush.zero_()
+        torch.cuda.synchronize()
+        l0 = pamd.pamd_launch_count(pop.ctx)
+        # end to end through the C-ABI: the start population from host memory,
+        # the anneal, the per-temperature observables back to the host
+        t0 = time.perf_counter()
+        pamd.pamd_set_state(pop.ctx, x_host, v_host, None, fam_host)
+        pamd.pamd_set_counters(pop.ctx, 0, 0, 0.0)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
         obs = pamd.pamd_anneal(pop.ctx, temps, theta, dt)
         ev1.record(stream)
         ev1.synchronize()
+        wall = time.perf_counter() - t0
         launches = pamd.pamd_launch_count(pop.ctx) - l0
         pop.close()
-        return obs, ev0.elapsed_time(ev1), launches
+        return obs, ev0.elapsed_time(ev1), wall, launches, per_eval
 
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
-    obs_x, ms_x, l_x = anneal(False)
-    obs_s, ms_s, l_s = anneal(True)
+    obs_x, ms_x, wall_x, l_x, _ = anneal(False)
+    obs_s, ms_s, wall_s, l_s, per_eval = anneal(True)
     clocks = sampler.stop()
     model.close()
 
@@ -798,17 +847,62 @@ def run_surrogate(args, w):
                      "launches": {"exact": int(l_x), "surrogate": int(l_s)},
                      "e_pot": cmp("e_pot", "e_pot_se"), "rg": cmp("rg", "rg_se"),
                      "sum_lnQ_final": {"surrogate": obs_s[-1]["sum_lnQ"], "exact": obs_x[-1]["sum_lnQ"]}}
-    peak = measured_peaks().get("bf16_tflops_sustained")
-    top_g = max(gemms, key=lambda r: r["ms"])
     out["gemms"] = gemms
-    out["roofline"] = {"bound": "tensor", "achieved": top_g["tflops"], "peak": peak, "unit": "TFLOP/s",
-                       "frac": top_g["tflops"] / peak if peak else None, "traffic": None,
-                       "kernel": "gemm_bf16_kernel " + top_g["gemm"],
-                       "peak_basis": "measured sustained cuBLAS bf16 (MEASURED_PEAKS.json)"}
-    out["clocks"] = clocks
-    out["value"] = units / (ms_s / 1e3)
-    out["unit"] = UNIT
+    # per force evaluation: four GEMMs (event-timed alone) and the step kernel
+    # (the rest of the event-timed evaluation)
+    gemm_ms = sum(r["ms"] for r in gemms)
+    step_ms = max(per_eval - gemm_ms, 1e-6)
+    # algorithmic bytes of one step-kernel launch: de/da row read (FP32), the
+    # feature row written (BF16), the replica state read and written
+    step_bytes = R * (padded_pairs(N) * (4 + 2) + 2 * 6 * Np * 4)
+    hbm = measured_peaks().get("hbm_gbs")
+    bf16 = measured_peaks().get("bf16_tflops_sustained")
+    top_g = max(gemms, key=lambda r: r["ms"])
+    out["force_evaluation_ms"] = {"total": per_eval, "gemms": gemm_ms, "step_kernel": step_ms}
+    out["roofline"] = {"bound": "hbm", "achieved": step_bytes / (step_ms / 1e3) / 1e9, "peak": hbm,
+                       "unit": "GB/s", "frac": step_bytes / (step_ms / 1e3) / 1e9 / hbm if hbm else None,
+                       "traffic": None, "kernel": "mlp_step_kernel (largest time share)",
+                       "bytes_per_launch": step_bytes,
+                       "launch_ms_basis": "event-timed force evaluation minus the event-timed GEMMs",
+                       "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json)"}
+    out["roofline_gemm"] = {"bound": "tensor", "achieved": top_g["tflops"], "peak": bf16, "unit": "TFLOP/s",
+                            "frac": top_g["tflops"] / bf16 if bf16 else None, "traffic": None,
+                            "kernel": "gemm_bf16_kernel " + top_g["gemm"],
+                            "peak_basis": "measured sustained cuBLAS bf16 (MEASURED_PEAKS.json)"}
+    h2d = R * 6 * Np * 4 + R * 4
+    d2h = (K + 1) * ctypes.sizeof(pamd.PamdObs)
+    out.update({"metric": METRIC, "value": units / (ms_s / 1e3), "unit": UNIT, "n_gpus": 1, "steps": 1,
+                "warmup": args.warmup, "ms_per_step": ms_s, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16 tensor cores / f32", "data": "synthetic",
+                "e2e": {"value": units / wall_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": int(l_s), "clocks": clocks})
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = surrogate_oracle_sample(top, model_params, temps[0], dt, w)
     print(json.dumps(out), flush=True)
+
+
+def padded_pairs(n):
+    """Pairs of an n-atom molecule rounded up to a multiple of 8 (row length
+    of the feature and de/da matrices)."""
+    P = n * (n - 1) // 2
+    return (P + 7) // 8 * 8
+
+
+def surrogate_oracle_sample(top, params, T, dt, w, reps=16, steps=10):
+    """The FP64 oracle of the surrogate dynamics (oracle/mlp.py) on a bounded
+    sample: `reps` replicas for `steps` BAOAB steps, single thread."""
+    import numpy as np
+
+    from oracle import mlp as omlp
+    rng = np.random.default_rng(1)
+    x0 = np.repeat((top.x0 - top.x0.mean(0))[None], reps, axis=0)
+    v0 = rng.normal(0.0, math.sqrt(0.008314462618 * T / 12.0), x0.shape)
+    t0 = time.perf_counter()
+    omlp.propagate(params, x0, v0, top.mass, steps, dt, T, w["gamma"], 5, 0)
+    dt_s = time.perf_counter() - t0
+    return {"value": top.n_atoms * reps * steps / dt_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{reps} replicas x {steps} surrogate BAOAB steps (FP64 numpy, trained weights)"}
 
 
 def main():
@@ -835,6 +929,9 @@ def main():
     ap.add_argument("--train-samples", type=int, default=1 << 21, help="surrogate mode")
     ap.add_argument("--epochs", type=int, default=40, help="surrogate mode: training epochs")
     ap.add_argument("--batch", type=int, default=2048, help="surrogate mode: minibatch")
+    ap.add_argument("--refine-rounds", type=int, default=2,
+                    help="surrogate mode: rounds of exact labels for surrogate-visited states")
+    ap.add_argument("--refine-epochs", type=int, default=8, help="surrogate mode: epochs per round")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.mode == "kernel":

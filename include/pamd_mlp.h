@@ -84,6 +84,16 @@ int pamd_gemm_bf16(const void* A, const void* B, float* C, int32_t M, int32_t N,
                    int32_t lda, int32_t ldb, int32_t ldc, void* stream);
 
 /*
+ * Device time of the product above: `reps` (1..1000) back-to-back launches
+ * bracketed by two CUDA events recorded on `stream`; *ms_out receives the
+ * mean time per launch in milliseconds and C the product.  Arguments and
+ * errors as for pamd_gemm_bf16 (PAMD_EINVAL also for reps or a null ms_out).
+ */
+int pamd_gemm_bf16_time(const void* A, const void* B, float* C, int32_t M, int32_t N, int32_t K,
+                        int32_t lda, int32_t ldb, int32_t ldc, int32_t reps, void* stream,
+                        float* ms_out);
+
+/*
  * New model for molecules of n_atoms atoms (2..PAMD_MAX_ATOMS) with hidden
  * width `hidden` (32..1024, a multiple of 32).  Weights are drawn from
  * N(0, 1/fan_in) by a Philox stream keyed on `seed`, biases are 0, mu = 0,

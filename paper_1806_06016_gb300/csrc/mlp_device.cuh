@@ -114,7 +114,7 @@ __device__ __forceinline__ void load_gamma(const float* xs, const float* __restr
             const float dy = xs[kXs + ij.x] - xs[kXs + ij.y];
             const float dz = xs[2 * kXs + ij.x] - xs[2 * kXs + ij.y];
             const float ir = rsqrtf(dx * dx + dy * dy + dz * dz);
-            const float c = ga_row[p] * inv_sd[p] * ir * ir * ir;
+            const float c = __ldcs(ga_row + p) * inv_sd[p] * ir * ir * ir;
             gam[ij.x * S + ij.y] = c;
             gam[ij.y * S + ij.x] = c;
         }

@@ -2,24 +2,27 @@
 // for the dense layers of the MLP energy surrogate.
 //
 // C[M x N] (FP32) = A[M x K] . B[N x K]^T, A and B row-major BF16 (both
-// "K-major").  One CTA computes a 128 x 128 tile with 4 warps:
-//   * one thread of warp 0 streams 128 x 64 tiles of A and B into a ring of
-//     kStages shared-memory stages with TMA (cp.async.bulk.tensor, 128-byte
-//     swizzle, out-of-range rows and columns zero-filled), completing a
-//     transaction-count mbarrier per stage;
-//   * one thread of warp 1 waits for each stage, issues four tcgen05.mma
-//     (M 128, N 128, K 16) with the FP32 accumulator in tensor memory, and
-//     frees the stage with tcgen05.commit;
-//   * after the last commit all four warps run the epilogue: tcgen05.ld of
-//     32 columns at a time (warp w owns rows 32w..32w+31), bias and the
-//     layer's output transform, 16-byte vector stores.
-// Shared memory (3 stages x 32 KiB) lets two CTAs share an SM, so one CTA's
-// epilogue overlaps the other's main loop.
+// "K-major").  Persistent kernel, one CTA per SM, 128 x 256 output tiles
+// taken in row-major tile order (tiles of one row block share A in L2), six
+// warps with fixed roles:
+//   * one thread of warp 0 streams 128 x 64 tiles of A and 256 x 64 tiles of
+//     B with TMA (cp.async.bulk.tensor, 128-byte swizzle, out-of-range rows
+//     and columns zero-filled) into a ring of kStages shared-memory stages,
+//     each completing a transaction-count mbarrier;
+//   * one thread of warp 1 issues four tcgen05.mma (M 128, N 256, K 16) per
+//     stage into one of two FP32 accumulators of 256 tensor-memory columns,
+//     frees each stage with tcgen05.commit, and commits the accumulator when
+//     a tile's last product is issued;
+//   * warps 2..5 drain a finished accumulator with tcgen05.ld (warp w reads
+//     tensor-memory lanes 32 (w mod 4) ..), apply the bias and the layer's
+//     output transform, store with 16-byte vector stores, and hand the
+//     accumulator back -- so the epilogue of one tile runs while the tensor
+//     core works on the next.
 //
 // Every wait on an mbarrier is bounded: after kWaitLimit polls the waiting
-// role records PAMD_ETIMEOUT, the others stop at their next wait, the CTA
-// waits (bounded) for its own copies and products in flight, frees its
-// tensor memory and returns.
+// role records PAMD_ETIMEOUT and raises a shared abort flag, the others stop
+// at their next wait, the CTA waits (bounded) for its own copies and products
+// in flight, frees its tensor memory and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -32,10 +35,12 @@ namespace pamd {
 
 namespace {
 
-constexpr int kBM = 128, kBN = 128, kBK = 64, kThreads = 128, kStages = 3;
-constexpr int kTileBytes = kBM * kBK * 2;  // 16 KiB per operand tile
-constexpr int kStageBytes = 2 * kTileBytes;
-constexpr int kTmemCols = 128;
+constexpr int kBM = 128, kBN = kGemmTileN, kBK = 64, kStages = 4;
+constexpr int kThreads = 192, kEpiThreads = 128;
+constexpr int kTileA = kBM * kBK * 2;  // 16 KiB
+constexpr int kTileB = kBN * kBK * 2;  // 32 KiB
+constexpr int kStageBytes = kTileA + kTileB;
+constexpr int kTmemCols = 2 * kBN;     // two accumulators: all 512 columns
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 // instruction descriptor of tcgen05.mma.kind::f16: D FP32 (bits 4-5 = 1),
@@ -178,20 +183,91 @@ __device__ __forceinline__ void store_row32_bf16(__nv_bfloat16* dst, const float
     }
 }
 
-__global__ void __launch_bounds__(kThreads) gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA,
-                                                             const __grid_constant__ CUtensorMap tmB,
-                                                             const __grid_constant__ GemmArgs g) {
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Epilogue of one 128 x 256 tile: accumulator columns acc_col.. of this
+// warp's 32 tensor-memory lanes (rows m0 + 32q + lane).
+__device__ __forceinline__ void epilogue_tile(const GemmArgs& g, uint32_t taddr, int row, int n0,
+                                              int ntile, int ntiles) {
+    const bool row_ok = row < g.M;
+    float head = 0.0f;
+    __nv_bfloat16* Cb = static_cast<__nv_bfloat16*>(g.Cb);
+    __nv_bfloat16* CbT = static_cast<__nv_bfloat16*>(g.CbT);
+    const bool vf = (g.vec_ok & 1) != 0, vb = (g.vec_ok & 2) != 0;
+#pragma unroll 1
+    for (int cc = 0; cc < kBN / 32; ++cc) {
+        float v[32];
+        tmem_ld32(taddr + (uint32_t)(cc * 32), v);
+        const int col0 = n0 + cc * 32;
+        const int n = min(32, g.N - col0);
+        if (!row_ok || n <= 0) continue;
+        if (g.bias) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] += (j < n) ? g.bias[col0 + j] : 0.0f;
+        }
+        const size_t o = (size_t)row * g.ldc + col0;
+        if (g.C) store_row32(g.C + o, v, n, vf);
+        if (g.epi == kEpiSilu || g.epi == kEpiHead) {
+            float ds[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const float sg = sigmoid(v[j]);
+                ds[j] = sg * (1.0f + v[j] * (1.0f - sg));
+                v[j] *= sg;  // silu
+            }
+            if (g.Cs) store_row32(g.Cs + o, ds, n, vf);
+            if (g.epi == kEpiHead) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float w = (j < n) ? g.vec[col0 + j] : 0.0f;
+                    head = fmaf(w, v[j], head);
+                    v[j] = w * ds[j];
+                }
+            }
+        } else if (g.epi == kEpiMul) {
+            const float* mr = g.mul + o;
+            if (vf && n == 32) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const float4 t = reinterpret_cast<const float4*>(mr)[q];
+                    v[4 * q] *= t.x;
+                    v[4 * q + 1] *= t.y;
+                    v[4 * q + 2] *= t.z;
+                    v[4 * q + 3] *= t.w;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] *= (j < n) ? mr[j] : 0.0f;
+            }
+        }
+        if (Cb) store_row32_bf16(Cb + (size_t)row * g.ldcb + col0, v, n, vb);
+        if (CbT) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (j < n) CbT[(size_t)(col0 + j) * g.ldt + row] = __float2bfloat16(v[j]);
+        }
+    }
+    if (g.epi == kEpiHead && row_ok) g.part[(size_t)row * ntiles + ntile] = head;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA,
+                                                                const __grid_constant__ CUtensorMap tmB,
+                                                                const __grid_constant__ GemmArgs g) {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) unsigned long long full_bar[kStages], empty_bar[kStages], accum_bar;
+    __shared__ __align__(8) unsigned long long full_bar[kStages], empty_bar[kStages];
+    __shared__ __align__(8) unsigned long long accf_bar[2], acce_bar[2], done_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ int s_abort, s_issued, s_consumed;
     // 1024-byte aligned stages: [A0 | B0 | A1 | B1 | ...]
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
+    const int MT = (g.M + kBM - 1) / kBM, NT = (g.N + kBN - 1) / kBN;
+    const int tiles = MT * NT;
     const int KB = (g.K + kBK - 1) / kBK;
 
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_slot)),
                      "r"((uint32_t)kTmemCols)
@@ -203,7 +279,11 @@ __global__ void __launch_bounds__(kThreads) gemm_bf16_kernel(const __grid_consta
             mbar_init(smem_u32(&full_bar[st]), 1);
             mbar_init(smem_u32(&empty_bar[st]), 1);
         }
-        mbar_init(smem_u32(&accum_bar), 1);
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(smem_u32(&accf_bar[q]), 1);
+            mbar_init(smem_u32(&acce_bar[q]), kEpiThreads);
+        }
+        mbar_init(smem_u32(&done_bar), 1);
         s_abort = 0;
         s_issued = 0;
         s_consumed = 0;
@@ -215,123 +295,95 @@ __global__ void __launch_bounds__(kThreads) gemm_bf16_kernel(const __grid_consta
     const uint32_t tmem = tmem_slot;
     volatile int* abort_flag = &s_abort;
 
-    if (warp == 0 && lane == 0) {
-        // TMA producer
-        int kb = 0;
-        for (; kb < KB; ++kb) {
-            const int st = kb % kStages;
-            if (kb >= kStages &&
-                !mbar_wait(smem_u32(&empty_bar[st]), (uint32_t)((kb / kStages - 1) & 1))) {
-                *abort_flag = 1;
-                break;
+    if (warp == 0) {
+        if (lane == 0) {  // TMA producer
+            long long gk = 0;
+            bool stop = false;
+            for (int t = blockIdx.x; t < tiles && !stop; t += gridDim.x) {
+                const int m0 = (t / NT) * kBM, n0 = (t % NT) * kBN;
+                for (int kb = 0; kb < KB; ++kb, ++gk) {
+                    const int st = (int)(gk % kStages);
+                    if (gk >= kStages &&
+                        !mbar_wait(smem_u32(&empty_bar[st]), (uint32_t)((gk / kStages - 1) & 1))) {
+                        *abort_flag = 1;
+                    }
+                    if (*abort_flag) {
+                        stop = true;
+                        break;
+                    }
+                    const uint32_t fb = smem_u32(&full_bar[st]);
+                    const uint32_t ta = base + (uint32_t)(st * kStageBytes);
+                    mbar_expect_tx(fb, (uint32_t)kStageBytes);
+                    tma_load_2d(ta, &tmA, kb * kBK, m0, fb);
+                    tma_load_2d(ta + kTileA, &tmB, kb * kBK, n0, fb);
+                }
             }
-            if (*abort_flag) break;
-            const uint32_t fb = smem_u32(&full_bar[st]);
-            const uint32_t ta = base + (uint32_t)(st * kStageBytes);
-            mbar_expect_tx(fb, (uint32_t)kStageBytes);
-            tma_load_2d(ta, &tmA, kb * kBK, m0, fb);
-            tma_load_2d(ta + kTileBytes, &tmB, kb * kBK, n0, fb);
+            s_issued = (int)gk;
         }
-        s_issued = kb;
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        int kb = 0;
-        for (; kb < KB; ++kb) {
-            const int st = kb % kStages;
-            if (!mbar_wait(smem_u32(&full_bar[st]), (uint32_t)((kb / kStages) & 1))) {
-                *abort_flag = 1;
-                break;
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issuer
+            long long gk = 0;
+            int i = 0;
+            bool stop = false;
+            for (int t = blockIdx.x; t < tiles && !stop; t += gridDim.x, ++i) {
+                const int acc = i & 1;
+                if (i >= 2 && !mbar_wait(smem_u32(&acce_bar[acc]), (uint32_t)((i / 2 - 1) & 1))) {
+                    *abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t td = tmem + (uint32_t)(acc * kBN);
+                for (int kb = 0; kb < KB; ++kb, ++gk) {
+                    const int st = (int)(gk % kStages);
+                    if (!mbar_wait(smem_u32(&full_bar[st]), (uint32_t)((gk / kStages) & 1))) *abort_flag = 1;
+                    if (*abort_flag) {
+                        stop = true;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t ta = base + (uint32_t)(st * kStageBytes);
+#pragma unroll
+                    for (int k = 0; k < kBK / 16; ++k)
+                        mma_bf16(td, sw128_desc(ta + k * 32), sw128_desc(ta + kTileA + k * 32),
+                                 (kb > 0 || k > 0) ? 1u : 0u);
+                    mma_commit(smem_u32(&empty_bar[st]));
+                }
+                if (!stop) mma_commit(smem_u32(&accf_bar[acc]));
             }
+            s_consumed = (int)gk;
+            // tracks every product issued before it, also on the abort path
+            mma_commit(smem_u32(&done_bar));
+        }
+    } else {  // epilogue warps 2..5
+        const int q = warp & 3;  // tensor-memory lane quarter this warp may access
+        int i = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
+            const int acc = i & 1;
+            if (!mbar_wait(smem_u32(&accf_bar[acc]), (uint32_t)((i / 2) & 1))) *abort_flag = 1;
+            __syncwarp();
             if (*abort_flag) break;
             tc_fence_after();
-            const uint32_t ta = base + (uint32_t)(st * kStageBytes);
-#pragma unroll
-            for (int k = 0; k < kBK / 16; ++k)
-                mma_bf16(tmem, sw128_desc(ta + k * 32), sw128_desc(ta + kTileBytes + k * 32),
-                         (kb > 0 || k > 0) ? 1u : 0u);
-            mma_commit(smem_u32(&empty_bar[st]));
+            const int m0 = (t / NT) * kBM, nt = t % NT;
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kBN);
+            epilogue_tile(g, taddr, m0 + q * 32 + lane, nt * kBN, nt, NT);
+            tc_fence_before();
+            mbar_arrive(smem_u32(&acce_bar[acc]));
         }
-        s_consumed = kb;
-        // tracks every product issued before it, also on the abort path
-        mma_commit(smem_u32(&accum_bar));
     }
     __syncwarp();
-    bool ok = mbar_wait(smem_u32(&accum_bar), 0u);
-    ok = __syncthreads_and(ok && !*abort_flag);
-    if (!ok) {
-        if (tid == 0) atomicCAS(g.status, 0, PAMD_ETIMEOUT);
-        // copies issued but never consumed must land before the CTA exits
-        if (tid == 0) {
-            for (int kb = s_consumed; kb < s_issued; ++kb)
-                mbar_wait(smem_u32(&full_bar[kb % kStages]), (uint32_t)((kb / kStages) & 1));
-            mbar_wait(smem_u32(&accum_bar), 0u);  // products in flight
+    __syncthreads();
+    if (tid == 0) {
+        if (*abort_flag) {
+            atomicCAS(g.status, 0, PAMD_ETIMEOUT);
+            // copies issued but never consumed must land before the CTA exits
+            for (long long gk = s_consumed; gk < s_issued; ++gk)
+                mbar_wait(smem_u32(&full_bar[gk % kStages]), (uint32_t)((gk / kStages) & 1));
         }
-    } else {
-        tc_fence_after();
-        const int row = m0 + warp * 32 + lane;
-        const bool row_ok = row < g.M;
-        float head = 0.0f;
-        __nv_bfloat16* Cb = static_cast<__nv_bfloat16*>(g.Cb);
-        __nv_bfloat16* CbT = static_cast<__nv_bfloat16*>(g.CbT);
-        const bool vf = (g.vec_ok & 1) != 0, vb = (g.vec_ok & 2) != 0;
-#pragma unroll 1
-        for (int cc = 0; cc < kBN / 32; ++cc) {
-            float v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cc * 32), v);
-            const int col0 = n0 + cc * 32;
-            const int n = min(32, g.N - col0);
-            if (!row_ok || n <= 0) continue;
-            if (g.bias) {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] += (j < n) ? g.bias[col0 + j] : 0.0f;
-            }
-            const size_t o = (size_t)row * g.ldc + col0;
-            if (g.C) store_row32(g.C + o, v, n, vf);
-            if (g.epi == kEpiSilu || g.epi == kEpiHead) {
-                float ds[32];
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float sg = sigmoid(v[j]);
-                    ds[j] = sg * (1.0f + v[j] * (1.0f - sg));
-                    v[j] *= sg;  // silu
-                }
-                if (g.Cs) store_row32(g.Cs + o, ds, n, vf);
-                if (g.epi == kEpiHead) {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float w = (j < n) ? g.vec[col0 + j] : 0.0f;
-                        head = fmaf(w, v[j], head);
-                        v[j] = w * ds[j];
-                    }
-                }
-            } else if (g.epi == kEpiMul) {
-                const float* mr = g.mul + o;
-                if (vf && n == 32) {
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const float4 t = reinterpret_cast<const float4*>(mr)[q];
-                        v[4 * q] *= t.x;
-                        v[4 * q + 1] *= t.y;
-                        v[4 * q + 2] *= t.z;
-                        v[4 * q + 3] *= t.w;
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) v[j] *= (j < n) ? mr[j] : 0.0f;
-                }
-            }
-            if (Cb) store_row32_bf16(Cb + (size_t)row * g.ldcb + col0, v, n, vb);
-            if (CbT) {
-#pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    if (j < n) CbT[(size_t)(col0 + j) * g.ldt + row] = __float2bfloat16(v[j]);
-            }
-        }
-        if (g.epi == kEpiHead && row_ok) g.part[(size_t)row * gridDim.x + blockIdx.x] = head;
+        mbar_wait(smem_u32(&done_bar), 0u);  // products in flight
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0)
+    if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"((uint32_t)kTmemCols)
                      : "memory");
@@ -351,14 +403,14 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// Tensor map of a row-major BF16 matrix [rows][ld] read in 128-row x 64-column
+// Tensor map of a row-major BF16 matrix [rows][ld] read in box_rows x 64-column
 // boxes with the 128-byte swizzle; columns >= cols and rows >= rows read as 0.
-bool encode_operand(CUtensorMap* map, const void* ptr, int rows, int cols, int ld) {
+bool encode_operand(CUtensorMap* map, const void* ptr, int rows, int cols, int ld, int box_rows) {
     const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+    const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -372,7 +424,8 @@ cudaError_t launch_gemm_bf16(const GemmArgs& ga, cudaStream_t s) {
         (reinterpret_cast<uintptr_t>(ga.A) & 15) || (reinterpret_cast<uintptr_t>(ga.B) & 15))
         return cudaErrorInvalidValue;
     CUtensorMap tmA, tmB;
-    if (!encode_operand(&tmA, ga.A, ga.M, ga.K, ga.lda) || !encode_operand(&tmB, ga.B, ga.N, ga.K, ga.ldb))
+    if (!encode_operand(&tmA, ga.A, ga.M, ga.K, ga.lda, kBM) ||
+        !encode_operand(&tmB, ga.B, ga.N, ga.K, ga.ldb, kBN))
         return cudaErrorInvalidValue;
     GemmArgs g = ga;
     auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
@@ -382,11 +435,16 @@ cudaError_t launch_gemm_bf16(const GemmArgs& ga, cudaStream_t s) {
     const size_t smem = (size_t)kStages * kStageBytes + 1024;
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
+    static int num_sms = 0;
     std::call_once(once, [&] {
         attr = cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int dev = 0;
+        if (attr == cudaSuccess) attr = cudaGetDevice(&dev);
+        if (attr == cudaSuccess) attr = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
     });
     if (attr != cudaSuccess) return attr;
-    const dim3 grid((g.N + kBN - 1) / kBN, (g.M + kBM - 1) / kBM);
+    const long long tiles = (long long)((g.M + kBM - 1) / kBM) * ((g.N + kBN - 1) / kBN);
+    const int grid = (int)(tiles < num_sms ? tiles : num_sms);
     gemm_bf16_kernel<<<grid, kThreads, smem, s>>>(tmA, tmB, g);
     return cudaGetLastError();
 }
@@ -395,22 +453,24 @@ cudaError_t launch_gemm_bf16(const GemmArgs& ga, cudaStream_t s) {
 
 using namespace pamd;
 
-extern "C" int pamd_gemm_bf16(const void* A, const void* B, float* C, int32_t M, int32_t N,
-                              int32_t K, int32_t lda, int32_t ldb, int32_t ldc, void* stream) {
+namespace {
+
+int gemm_entry(const void* A, const void* B, float* C, int32_t M, int32_t N, int32_t K, int32_t lda,
+               int32_t ldb, int32_t ldc, int32_t reps, void* stream, float* ms_out) {
     if (!A || !B || !C || M < 1 || N < 1 || K < 1 || (K & 7) || (lda & 7) || (ldb & 7) ||
         lda < K || ldb < K || ldc < N || (reinterpret_cast<uintptr_t>(A) & 15) ||
-        (reinterpret_cast<uintptr_t>(B) & 15)) {
+        (reinterpret_cast<uintptr_t>(B) & 15) || reps < 1 || reps > 1000) {
         set_last_error("pamd_gemm_bf16: null pointer, or sizes / leading dimensions invalid "
-                       "(K, lda, ldb multiples of 8; A, B 16-byte aligned)");
+                       "(K, lda, ldb multiples of 8; A, B 16-byte aligned; reps 1..1000)");
         return PAMD_EINVAL;
     }
     static int* status = nullptr;
     if (!status && cudaMalloc(&status, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
         set_last_error("pamd_gemm_bf16: status word");
         return PAMD_ENOMEM;
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (cudaMemsetAsync(status, 0, sizeof(int), s) != cudaSuccess) return PAMD_ECUDA;
     GemmArgs g{};
     g.A = A;
     g.B = B;
@@ -423,10 +483,23 @@ extern "C" int pamd_gemm_bf16(const void* A, const void* B, float* C, int32_t M,
     g.ldc = ldc;
     g.epi = kEpiStore;
     g.status = status;
-    cudaError_t e = launch_gemm_bf16(g, s);
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
+    if (e == cudaSuccess && ms_out) e = cudaEventCreate(&ev[0]);
+    if (e == cudaSuccess && ms_out) e = cudaEventCreate(&ev[1]);
+    if (e == cudaSuccess && ms_out) e = cudaEventRecord(ev[0], s);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_gemm_bf16(g, s);
+    if (e == cudaSuccess && ms_out) e = cudaEventRecord(ev[1], s);
     int st = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && ms_out) {
+        float ms = 0.0f;
+        e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        *ms_out = ms / (float)reps;
+    }
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
     if (e != cudaSuccess) {
         set_last_error(std::string("pamd_gemm_bf16: ") + cudaGetErrorString(e));
         return PAMD_ECUDA;
@@ -436,4 +509,21 @@ extern "C" int pamd_gemm_bf16(const void* A, const void* B, float* C, int32_t M,
         return st;
     }
     return PAMD_OK;
+}
+
+}  // namespace
+
+extern "C" int pamd_gemm_bf16(const void* A, const void* B, float* C, int32_t M, int32_t N,
+                              int32_t K, int32_t lda, int32_t ldb, int32_t ldc, void* stream) {
+    return gemm_entry(A, B, C, M, N, K, lda, ldb, ldc, 1, stream, nullptr);
+}
+
+extern "C" int pamd_gemm_bf16_time(const void* A, const void* B, float* C, int32_t M, int32_t N,
+                                   int32_t K, int32_t lda, int32_t ldb, int32_t ldc, int32_t reps,
+                                   void* stream, float* ms_out) {
+    if (!ms_out) {
+        set_last_error("pamd_gemm_bf16_time: null ms_out");
+        return PAMD_EINVAL;
+    }
+    return gemm_entry(A, B, C, M, N, K, lda, ldb, ldc, reps, stream, ms_out);
 }

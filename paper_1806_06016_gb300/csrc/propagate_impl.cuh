@@ -66,24 +66,32 @@ __device__ __forceinline__ void pair_lj_coul(float dx, float dy, float dz, float
     if (ENERGY) e = fmaf((eps * (1.0f / 6.0f)) * s6, s6 - 1.0f, qq * rinv);
 }
 
+// One tile: the lane's B atoms (registers) against the B atoms of partner
+// block J (shared memory).  The partner atoms are taken one at a time (b outer,
+// a inner), so that only one partner position, its parameters and its force
+// accumulator are live at once; each partner's force goes back to shared
+// memory before the next is loaded.  Per accumulator the summation order is
+// that of a full B x B sweep (a inner for the partner, b increasing for the
+// lane's own atoms).
 template <int B, bool MASKED, bool ENERGY>
 __device__ __forceinline__ void pair_tile(const float (&xi)[B], const float (&yi)[B],
                                           const float (&zi)[B], const float (&hsi)[B],
                                           const float (&sei)[B], const float (&qi)[B],
                                           float (&fxi)[B], float (&fyi)[B], float (&fzi)[B],
-                                          const float4 (&pj)[B], const float4 (&cj)[B],
-                                          float (&fxj)[B], float (&fyj)[B], float (&fzj)[B],
+                                          const float4* pj_s, const float4* cj_s, float4* fj_s,
                                           unsigned long long mask, double& e_acc) {
 #pragma unroll
-    for (int a = 0; a < B; ++a) {
+    for (int b = 0; b < B; ++b) {
+        const float4 pj = pj_s[b];
+        const float4 cj = cj_s[b];
+        float fxj = 0.0f, fyj = 0.0f, fzj = 0.0f;
 #pragma unroll
-        for (int b = 0; b < B; ++b) {
-            const float dx = pj[b].x - xi[a];
-            const float dy = pj[b].y - yi[a];
-            const float dz = pj[b].z - zi[a];
+        for (int a = 0; a < B; ++a) {
+            const float dx = pj.x - xi[a];
+            const float dy = pj.y - yi[a];
+            const float dz = pj.z - zi[a];
             float fs, e;
-            pair_lj_coul<ENERGY>(dx, dy, dz, hsi[a] + cj[b].x, sei[a] * cj[b].y, qi[a] * cj[b].z,
-                                 fs, e);
+            pair_lj_coul<ENERGY>(dx, dy, dz, hsi[a] + cj.x, sei[a] * cj.y, qi[a] * cj.z, fs, e);
             if (MASKED) {
                 const bool skip = (mask >> (a * B + b)) & 1ull;
                 fs = skip ? 0.0f : fs;
@@ -92,11 +100,16 @@ __device__ __forceinline__ void pair_tile(const float (&xi)[B], const float (&yi
             fxi[a] = fmaf(-fs, dx, fxi[a]);
             fyi[a] = fmaf(-fs, dy, fyi[a]);
             fzi[a] = fmaf(-fs, dz, fzi[a]);
-            fxj[b] = fmaf(fs, dx, fxj[b]);
-            fyj[b] = fmaf(fs, dy, fyj[b]);
-            fzj[b] = fmaf(fs, dz, fzj[b]);
+            fxj = fmaf(fs, dx, fxj);
+            fyj = fmaf(fs, dy, fyj);
+            fzj = fmaf(fs, dz, fzj);
             if (ENERGY) e_acc += (double)e;
         }
+        float4 f = fj_s[b];
+        f.x += fxj;
+        f.y += fyj;
+        f.z += fzj;
+        fj_s[b] = f;
     }
 }
 
@@ -468,23 +481,14 @@ __device__ __forceinline__ void compute_forces(const unsigned char* sm, const To
         if (active) {
             int J = g + t;
             J = (J >= L) ? J - L : J;
-            float4 pj[B], cj[B];
-            float fxj[B], fyj[B], fzj[B];
-#pragma unroll
-            for (int b = 0; b < B; ++b) {
-                pj[b] = pos[J * C::BS + b];
-                cj[b] = prm[J * C::BS + b];
-                fxj[b] = fyj[b] = fzj[b] = 0.0f;
-            }
+            const int sJ = J * C::BS;
             const unsigned long long m = masks[t * L + g];
             if (m == 0ull)
-                pair_tile<B, false, ENERGY>(xi, yi, zi, hsi, sei, qi, fx, fy, fz, pj, cj, fxj, fyj,
-                                            fzj, m, e_acc);
+                pair_tile<B, false, ENERGY>(xi, yi, zi, hsi, sei, qi, fx, fy, fz, pos + sJ, prm + sJ,
+                                            frc + sJ, m, e_acc);
             else
-                pair_tile<B, true, ENERGY>(xi, yi, zi, hsi, sei, qi, fx, fy, fz, pj, cj, fxj, fyj,
-                                           fzj, m, e_acc);
-#pragma unroll
-            for (int b = 0; b < B; ++b) add_force(frc, J * C::BS + b, fxj[b], fyj[b], fzj[b]);
+                pair_tile<B, true, ENERGY>(xi, yi, zi, hsi, sei, qi, fx, fy, fz, pos + sJ, prm + sJ,
+                                           frc + sJ, m, e_acc);
         }
         __syncwarp(gmask);
     }

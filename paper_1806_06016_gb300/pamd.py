@@ -92,7 +92,7 @@ EXPORTS = [
     "pamd_set_counters", "pamd_autotune", "pamd_resample_counts_noalloc", "pamd_info", "pamd_launch_count", "pamd_sync", "pamd_destroy",
     "pamd_last_error",
     # learned surrogate (include/pamd_mlp.h), wrapped in surrogate.py
-    "pamd_gemm_bf16", "pamd_mlp_create", "pamd_mlp_info", "pamd_mlp_set_params",
+    "pamd_gemm_bf16", "pamd_gemm_bf16_time", "pamd_mlp_create", "pamd_mlp_info", "pamd_mlp_set_params",
     "pamd_mlp_get_params", "pamd_mlp_fit_normalization", "pamd_mlp_energy_forces",
     "pamd_mlp_loss_grads", "pamd_mlp_get_grads", "pamd_mlp_adam_step", "pamd_set_force_model",
     "pamd_mlp_sync", "pamd_mlp_launch_count", "pamd_mlp_destroy",
@@ -141,6 +141,8 @@ def load(path: str | None = None):
             "pamd_last_error": (C.c_char_p, []),
             # learned surrogate (pamd_mlp.h)
             "pamd_gemm_bf16": (C.c_int, [P, P, P, I32, I32, I32, I32, I32, I32, P]),
+            "pamd_gemm_bf16_time": (C.c_int, [P, P, P, I32, I32, I32, I32, I32, I32, I32, P,
+                                              C.POINTER(C.c_float)]),
             "pamd_mlp_create": (C.c_int, [C.POINTER(P), I32, I32, U64, P]),
             "pamd_mlp_info": (C.c_int, [P, C.POINTER(I32), C.POINTER(I32), C.POINTER(I32)]),
             "pamd_mlp_set_params": (C.c_int, [P, P]),

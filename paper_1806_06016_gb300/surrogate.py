@@ -49,6 +49,21 @@ def gemm_bf16(A, B):
     return out
 
 
+def gemm_bf16_time(A, B, reps: int = 10):
+    """Mean device time (ms) of `reps` back-to-back tensor-core launches of A @ B.T,
+    bracketed by CUDA events on torch's current stream."""
+    torch = _torch()
+    A = A.contiguous()
+    B = B.contiguous()
+    M, K = A.shape
+    N = B.shape[0]
+    out = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    ms = C.c_float(0.0)
+    _p._check(_p.load().pamd_gemm_bf16_time(_dptr(A), _dptr(B), _dptr(out), M, N, K, K, K, N, reps,
+                                            _stream_handle(torch), C.byref(ms)))
+    return ms.value
+
+
 class MLP:
     """An MLP energy surrogate over inverse pair distances (2 SiLU layers).
 
@@ -228,22 +243,36 @@ def surrogate_energy(x, model: MLP):
     return _autograd_function().apply(x, model)
 
 
-def harvest(top, R: int, temps, theta: int, dt_ps: float, seed: int, options=None):
-    """(x [n, N, 3] float32, E [n] float64, F [n, N, 3] float32) sampled from an exact anneal.
+def harvest(top, R: int, temps, theta: int, dt_ps: float, seed: int, options=None, model=None):
+    """(x [n, N, 3] float32, E [n] float64, F [n, N, 3] float32) sampled from an anneal.
 
-    One population of R replicas is annealed through ``temps`` with the exact
-    force field; after the theta steps at every temperature the whole
-    population is recorded with its exact energies and forces.
+    One population of R replicas is annealed through ``temps``; after the
+    theta steps at every temperature the whole population is recorded with
+    its exact energies and forces.  With ``model`` the population is driven
+    by that surrogate (it samples the surrogate's distribution) and every
+    recorded configuration is labelled by the exact force field of a second
+    population of the same size.
     """
     xs, Es, Fs = [], [], []
-    with _p.Population(top, R, temps[0], seed, options) as pop:
-        for i, T in enumerate(temps):
-            if i:
-                pop.resample(temps[i - 1], T, want_copies=False)
-            pop.propagate(theta, dt_ps, T)
-            x, _, _, _ = pop.state()
-            f, E = pop.forces()
-            xs.append(x.astype(np.float32))
-            Fs.append(f.astype(np.float32))
-            Es.append(E.copy())
+    label = _p.Population(top, R, temps[0], seed, options) if model is not None else None
+    try:
+        with _p.Population(top, R, temps[0], seed, options) as pop:
+            if model is not None:
+                attach(pop.ctx, model)
+            for i, T in enumerate(temps):
+                if i:
+                    pop.resample(temps[i - 1], T, want_copies=False)
+                pop.propagate(theta, dt_ps, T)
+                x, v, _, _ = pop.state()
+                if label is not None:
+                    label.set_state(x, v)
+                    f, E = label.forces()
+                else:
+                    f, E = pop.forces()
+                xs.append(x.astype(np.float32))
+                Fs.append(f.astype(np.float32))
+                Es.append(E.copy())
+    finally:
+        if label is not None:
+            label.close()
     return np.concatenate(xs), np.concatenate(Es), np.concatenate(Fs)
