@@ -642,18 +642,21 @@ bool is_batch(const pamd_ctx* c) { return !c->subs.empty(); }
 // graph: counters come from each molecule's device counters plus step_off.
 int launch_prop_batch(pamd_ctx* c, int theta, double dt, double T, bool graph, uint32_t step_off) {
     BatchParams bp{};
-    bp.n_items = c->n_items;
-    bp.items = c->items;
-    bp.queue = c->queue;
     for (size_t m = 0; m < c->subs.size(); ++m) {
         pamd_ctx* s = c->subs[m];
         fill_prop_params(s, bp.mol[m], cur_state(s), cur_E(s), s->b.ke, s->b.rg, theta, dt, T,
                          graph ? s->b.counters : nullptr, graph ? step_off : s->step, nullptr);
     }
-    PAMD_CU(c, cudaMemsetAsync(c->queue, 0, sizeof(int), c->stream));
-    const cudaError_t e = launch_propagate_batch(bp, c->batch_grid, c->batch_smem, c->stream);
-    c->launches += 1;
-    if (e != cudaSuccess) return cuda_fail(c, e, "batched propagate launch");
+    PAMD_CU(c, cudaMemsetAsync(c->queue, 0, sizeof(int) * c->groups.size(), c->stream));
+    for (size_t q = 0; q < c->groups.size(); ++q) {
+        const pamd_ctx::BatchGroup& gr = c->groups[q];
+        bp.n_items = gr.n_items;
+        bp.items = c->items + gr.first_item;
+        bp.queue = c->queue + q;
+        const cudaError_t e = launch_propagate_batch(bp, gr.B, gr.grid, gr.smem, c->stream);
+        c->launches += 1;
+        if (e != cudaSuccess) return cuda_fail(c, e, "batched propagate launch");
+    }
     return PAMD_OK;
 }
 
@@ -1051,26 +1054,38 @@ int pamd_init_batch(pamd_ctx** out, int32_t n_mol, const pamd_topology* tops, co
         c->N = std::max(c->N, sub->N);
         order.push_back({sub->N, m});
     }
-    // work list: molecules by decreasing size, each cut into one CTA's worth of replicas
+    // work lists: molecules grouped by atoms per lane (one launch per group,
+    // largest total work first), by decreasing size within a group, each cut
+    // into one CTA's worth of replicas
     std::stable_sort(order.begin(), order.end(), [](auto a, auto b) { return a.first > b.first; });
     std::vector<int4> items;
-    size_t smem = 0;
-    for (auto& om : order) {
-        pamd_ctx* sub = c->subs[om.second];
-        for (long long k0 = 0; k0 < sub->R; k0 += sub->rpb)
-            items.push_back(make_int4(om.second, (int)k0, (int)std::min<long long>(k0 + sub->rpb, sub->R), 0));
-        smem = std::max(smem, prop_smem(sub));
+    std::vector<std::pair<double, pamd_ctx::BatchGroup>> groups;
+    for (int Bg = 3; Bg <= 7; ++Bg) {
+        pamd_ctx::BatchGroup gr{Bg, (int)items.size(), 0, 0, 0};
+        double work = 0.0;
+        for (auto& om : order) {
+            pamd_ctx* sub = c->subs[om.second];
+            if (sub->lay.per_lane != Bg) continue;
+            for (long long k0 = 0; k0 < sub->R; k0 += sub->rpb)
+                items.push_back(make_int4(om.second, (int)k0, (int)std::min<long long>(k0 + sub->rpb, sub->R), 0));
+            gr.smem = std::max(gr.smem, prop_smem(sub));
+            work += (double)sub->R * sub->N * sub->N;
+        }
+        gr.n_items = (int)items.size() - gr.first_item;
+        if (gr.n_items == 0) continue;
+        int occ = 0;
+        const cudaError_t e = propagate_batch_occupancy(Bg, gr.smem, &occ);
+        if (e != cudaSuccess || occ < 1)
+            return bail(PAMD_ECUDA, std::string("batched kernel occupancy: ") + cudaGetErrorString(e));
+        gr.grid = std::min(gr.n_items, c->num_sms * occ);
+        groups.push_back({work, gr});
     }
+    std::stable_sort(groups.begin(), groups.end(), [](auto a, auto b) { return a.first > b.first; });
+    for (auto& wg : groups) c->groups.push_back(wg.second);
     c->n_items = (int)items.size();
     c->items = (int4*)dalloc(c, sizeof(int4) * items.size());
-    c->queue = (int*)dalloc(c, sizeof(int));
+    c->queue = (int*)dalloc(c, sizeof(int) * c->groups.size());
     if (!c->items || !c->queue) return bail(PAMD_ENOMEM, "work list");
-    int occ = 0;
-    const cudaError_t e = propagate_batch_occupancy(smem, &occ);
-    if (e != cudaSuccess || occ < 1)
-        return bail(PAMD_ECUDA, std::string("batched kernel occupancy: ") + cudaGetErrorString(e));
-    c->batch_smem = smem;
-    c->batch_grid = std::min(c->n_items, c->num_sms * occ);
     if (cudaMemcpyAsync(c->items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice,
                         c->stream) != cudaSuccess ||
         cudaStreamSynchronize(c->stream) != cudaSuccess)

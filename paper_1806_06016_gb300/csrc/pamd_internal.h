@@ -252,11 +252,14 @@ struct pamd_ctx {
     pamd::TopoF64 top64{};        // all-FP64 mode tables (precision == PAMD_PREC_FP64)
     // batch context (pamd_init_batch): one sub-context per molecule
     std::vector<pamd_ctx*> subs;
-    int4* items = nullptr;        // device work list of the batched propagate
+    int4* items = nullptr;        // device work lists of the batched propagate, group by group
     int n_items = 0;
-    int* queue = nullptr;         // device work counter
-    size_t batch_smem = 0;
-    int batch_grid = 0;
+    int* queue = nullptr;         // device work counters, one per group
+    struct BatchGroup {           // molecules sharing one atoms-per-lane count B
+        int B, first_item, n_items, grid;
+        size_t smem;
+    };
+    std::vector<BatchGroup> groups;
     unsigned char* top64_blob = nullptr;
     pamd_mlp* mlp = nullptr;      // force model replacing the exact forces (pamd_set_force_model)
 };
@@ -336,8 +339,9 @@ cudaError_t launch_resample(pamd_ctx* c, double T_prev, double T_next, int do_re
 cudaError_t launch_observe(pamd_ctx* c, double T, pamd_obs* dst);
 cudaError_t launch_set_counters(pamd_ctx* c, uint32_t step, uint32_t ridx);
 
-cudaError_t launch_propagate_batch(const BatchParams& bp, int grid, size_t smem, cudaStream_t s);
-cudaError_t propagate_batch_occupancy(size_t smem, int* blocks_per_sm);
+// one launch of the batched kernel for atoms-per-lane B (3..7)
+cudaError_t launch_propagate_batch(const BatchParams& bp, int B, int grid, size_t smem, cudaStream_t s);
+cudaError_t propagate_batch_occupancy(int B, size_t smem, int* blocks_per_sm);
 
 // all-FP64 mode (propagate_f64.cu)
 cudaError_t launch_propagate_f64(pamd_ctx* c, double* state, double* E, double* ke, double* rg,

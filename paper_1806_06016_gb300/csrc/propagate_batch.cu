@@ -1,36 +1,33 @@
-// propagate_batch.cu -- one persistent launch for many molecules of uneven
+// propagate_batch.cu -- persistent launches for many molecules of uneven
 // size (batched independent anneals).
 //
 // Each molecule m has its own population, topology table and launch shape
-// (L_m lanes per replica, B_m atoms per lane, 3 <= B_m <= 7).  The host cuts
-// every population into work items of one CTA's worth of replicas and sorts
-// them by cost (N_m^2 per replica, largest first).  CTAs take items from a
-// device counter (atomicAdd; no CTA ever waits on another) until the list is
-// exhausted.  When a CTA moves to an item of another molecule it reloads that
-// molecule's table into shared memory; items of one molecule are contiguous in
-// the list, so that happens about once per molecule per CTA.
+// (L_m lanes per replica, B_m atoms per lane, 3 <= B_m <= 7).  Molecules are
+// grouped by B; each group is one launch of a kernel compiled for that B, so
+// the register allocation fits the group instead of the largest shape.  The
+// host cuts every population into work items of one CTA's worth of replicas
+// and sorts a group's items by cost (N_m^2 per replica, largest first).  CTAs
+// take items from the group's device counter (atomicAdd; no CTA ever waits on
+// another) until the list is exhausted.  When a CTA moves to an item of
+// another molecule it reloads that molecule's table into shared memory; items
+// of one molecule are contiguous in the list, so that happens about once per
+// molecule per CTA.
 #include "propagate_impl.cuh"
 
 namespace pamd {
 
 namespace {
 
-template <bool CHAIN>
-__device__ __forceinline__ void advance_any(int B, const PropParams& p, const unsigned char* sm,
-                                            const float4* prm, const unsigned long long* masks,
-                                            float4* pos, float4* frc, long long k, int L, int g,
-                                            int base, unsigned gmask) {
-    switch (B) {
-        case 3: advance_replica<3, CHAIN>(p, sm, prm, masks, pos, frc, k, L, g, base, gmask); break;
-        case 4: advance_replica<4, CHAIN>(p, sm, prm, masks, pos, frc, k, L, g, base, gmask); break;
-        case 5: advance_replica<5, CHAIN>(p, sm, prm, masks, pos, frc, k, L, g, base, gmask); break;
-        case 6: advance_replica<6, CHAIN>(p, sm, prm, masks, pos, frc, k, L, g, base, gmask); break;
-        case 7: advance_replica<7, CHAIN>(p, sm, prm, masks, pos, frc, k, L, g, base, gmask); break;
-        default: break;
-    }
-}
+// blocks of kBatchThreads per SM the compiler is asked to fit: 128 registers
+// for B = 3 (no spills there), otherwise what the shape needs
+template <int B>
+struct BatchCfg {
+    static constexpr int MIN_BLOCKS = (B <= 3) ? 4 : 2;
+};
 
-__global__ void __launch_bounds__(kBatchThreads, 1) propagate_batch_kernel(const __grid_constant__ BatchParams bp) {
+template <int B>
+__global__ void __launch_bounds__(kBatchThreads, BatchCfg<B>::MIN_BLOCKS)
+    propagate_batch_kernel(const __grid_constant__ BatchParams bp) {
     extern __shared__ float4 smem4[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(smem4);
     __shared__ int s_item;
@@ -69,34 +66,52 @@ __global__ void __launch_bounds__(kBatchThreads, 1) propagate_batch_kernel(const
             const long long k = (long long)w.y + slot_local;
             if (k < w.z) {
                 if (lay.chain)
-                    advance_any<true>(lay.per_lane, p, sm, prm, masks, pos, frc, k, L, g, base, gmask);
+                    advance_replica<B, true>(p, sm, prm, masks, pos, frc, k, L, g, base, gmask);
                 else
-                    advance_any<false>(lay.per_lane, p, sm, prm, masks, pos, frc, k, L, g, base, gmask);
+                    advance_replica<B, false>(p, sm, prm, masks, pos, frc, k, L, g, base, gmask);
             }
         }
     }
 }
 
-}  // namespace
-
-cudaError_t launch_propagate_batch(const BatchParams& bp, int grid, size_t smem, cudaStream_t s) {
+template <int B>
+cudaError_t launch_b(const BatchParams& bp, int grid, size_t smem, cudaStream_t s, int* blocks_per_sm) {
     static size_t configured = 0;
     if (smem > configured) {
-        const cudaError_t e = cudaFuncSetAttribute(
-            propagate_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const cudaError_t e = cudaFuncSetAttribute(propagate_batch_kernel<B>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = smem;
     }
-    propagate_batch_kernel<<<grid, kBatchThreads, smem, s>>>(bp);
+    if (blocks_per_sm)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, propagate_batch_kernel<B>,
+                                                             kBatchThreads, smem);
+    propagate_batch_kernel<B><<<grid, kBatchThreads, smem, s>>>(bp);
     return cudaGetLastError();
 }
 
-cudaError_t propagate_batch_occupancy(size_t smem, int* blocks_per_sm) {
-    const cudaError_t e = cudaFuncSetAttribute(
-        propagate_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, propagate_batch_kernel,
-                                                         kBatchThreads, smem);
+cudaError_t dispatch_b(int B, const BatchParams* bp, int grid, size_t smem, cudaStream_t s,
+                       int* blocks_per_sm) {
+    static const BatchParams empty{};
+    const BatchParams& q = bp ? *bp : empty;
+    switch (B) {
+        case 3: return launch_b<3>(q, grid, smem, s, blocks_per_sm);
+        case 4: return launch_b<4>(q, grid, smem, s, blocks_per_sm);
+        case 5: return launch_b<5>(q, grid, smem, s, blocks_per_sm);
+        case 6: return launch_b<6>(q, grid, smem, s, blocks_per_sm);
+        case 7: return launch_b<7>(q, grid, smem, s, blocks_per_sm);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_propagate_batch(const BatchParams& bp, int B, int grid, size_t smem, cudaStream_t s) {
+    return dispatch_b(B, &bp, grid, smem, s, nullptr);
+}
+
+cudaError_t propagate_batch_occupancy(int B, size_t smem, int* blocks_per_sm) {
+    return dispatch_b(B, nullptr, 0, smem, nullptr, blocks_per_sm);
 }
 
 }  // namespace pamd
