@@ -313,6 +313,22 @@ int pamd_resample_counts_noalloc(const double* E_dev, int64_t R, double T_prev, 
                                  uint64_t seed, uint32_t resample_index, int32_t mol_id,
                                  int32_t* counts_dev, double* lnQ_dev, void* stream);
 
+/*
+ * Checkpoint files.  pamd_checkpoint writes the current population (state,
+ * energies, family ids), the random-counter state (seed, MD step, resampling
+ * index) and the running sum of ln Q to `path` (written to path.tmp, then
+ * renamed), with a checksum.  pamd_restore reads such a file into a context
+ * made for the same topology, population size and precision; afterwards the
+ * run continues bit-identically to the one that wrote it.  The file is in
+ * the machine's byte order.  A batch context is checkpointed molecule by
+ * molecule (pamd_batch_sub).  Synchronous.  Errors: PAMD_EINVAL (null path,
+ * unreadable or unwritable file, wrong magic, another population, checksum
+ * mismatch; the context is unchanged), PAMD_EUNSUPPORTED (batch context),
+ * PAMD_ECUDA.
+ */
+int pamd_checkpoint(pamd_ctx* ctx, const char* path);
+int pamd_restore(pamd_ctx* ctx, const char* path);
+
 /* Random-counter state: global MD step and resampling index.  A restarted
  * run that restores both (with the same seed and population) continues
  * bit-identically. */

@@ -161,6 +161,17 @@ int pamd_mlp_adam_step(pamd_mlp* mlp, double lr, double beta1, double beta2, dou
  */
 int pamd_set_force_model(pamd_ctx* ctx, pamd_mlp* mlp);
 
+/*
+ * Model files: pamd_mlp_save writes the shape and every parameter (FP32, the
+ * normalisation included) with a checksum, in the machine's byte order, to
+ * `path` (via path.tmp and a rename); pamd_mlp_load creates a model from such
+ * a file (stream as in pamd_mlp_create).  Synchronous.  Errors: PAMD_EINVAL
+ * (null argument, unreadable or unwritable file, not a model file, checksum
+ * mismatch), PAMD_ENOMEM, PAMD_ECUDA.
+ */
+int pamd_mlp_save(pamd_mlp* mlp, const char* path);
+int pamd_mlp_load(pamd_mlp** out, const char* path, void* stream);
+
 /* Wait for the model's queued work; PAMD_ETIMEOUT if a tensor-core
  * pipeline wait ran out, PAMD_ECUDA on an asynchronous CUDA error. */
 int pamd_mlp_sync(pamd_mlp* mlp);

@@ -10,5 +10,5 @@ from .pamd import (  # noqa: F401
     pamd_batch_size, pamd_batch_sub, pamd_get_counters, pamd_get_state, pamd_info, pamd_init,
     pamd_init_batch, pamd_last_error, pamd_launch_count,
     pamd_observables, pamd_options_default, pamd_propagate, pamd_reset, pamd_resample, pamd_set_counters,
-    pamd_set_state, pamd_sync, torch_options,
+    pamd_set_state, pamd_sync, torch_options, pamd_checkpoint, pamd_restore,
 )

@@ -1571,6 +1571,151 @@ int pamd_sync(pamd_ctx* c) {
     return PAMD_OK;
 }
 
+}  // extern "C"
+
+// ---- checkpoint files ------------------------------------------------------
+//
+// Layout (native byte order): 8-byte magic, then a header of fixed-size
+// fields, then the payload, then an FNV-1a 64 checksum of header and payload.
+
+namespace {
+
+constexpr char kCkptMagic[8] = {'P', 'A', 'M', 'D', 'C', 'K', 'P', '1'};
+
+struct CkptHeader {
+    uint32_t version;
+    int32_t precision;
+    int64_t R;
+    int32_t N, Np;
+    uint64_t seed;
+    uint32_t step, resample_index;
+    double sum_lnQ;
+    int32_t mol, pad_;
+    uint64_t topology_hash;
+};
+
+uint64_t fnv1a(const void* data, size_t n, uint64_t h = 1469598103934665603ull) {
+    const unsigned char* b = static_cast<const unsigned char*>(data);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+uint64_t topology_hash(const HostTopology& t) {
+    uint64_t h = fnv1a(&t.n_atoms, sizeof(t.n_atoms));
+    auto mix = [&](const auto& v) {
+        if (!v.empty()) h = fnv1a(v.data(), v.size() * sizeof(v[0]), h);
+        const uint64_t n = v.size();
+        h = fnv1a(&n, sizeof(n), h);
+    };
+    mix(t.mass); mix(t.charge); mix(t.sigma); mix(t.epsilon);
+    mix(t.bond); mix(t.bond_r0); mix(t.bond_k); mix(t.angle); mix(t.angle_t0); mix(t.angle_k);
+    mix(t.dihedral); mix(t.dih_n); mix(t.dih_k); mix(t.dih_phase); mix(t.excl); mix(t.pair14);
+    h = fnv1a(&t.scale14_lj, sizeof(double), h);
+    h = fnv1a(&t.scale14_coul, sizeof(double), h);
+    return h;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pamd_checkpoint(pamd_ctx* c, const char* path) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (is_batch(c)) return fail(PAMD_EUNSUPPORTED, "checkpoint a batch molecule by molecule (pamd_batch_sub)");
+    if (!path) return fail(PAMD_EINVAL, "null path");
+    CkptHeader h{};
+    h.version = 1;
+    h.precision = c->precision;
+    h.R = c->R;
+    h.N = c->N;
+    h.Np = c->Np;
+    h.seed = c->seed;
+    h.step = c->step;
+    h.resample_index = c->resample_index;
+    h.mol = c->mol;
+    h.topology_hash = topology_hash(c->host_top);
+    std::vector<unsigned char> st(state_bytes(c));
+    std::vector<double> E((size_t)c->R);
+    std::vector<int32_t> fam((size_t)c->R);
+    PAMD_CU(c, cudaMemcpyAsync(&h.sum_lnQ, &c->b.scal->sum_lnQ, 8, cudaMemcpyDeviceToHost, c->stream));
+    PAMD_CU(c, cudaMemcpyAsync(st.data(), cur_state(c), st.size(), cudaMemcpyDeviceToHost, c->stream));
+    PAMD_CU(c, cudaMemcpyAsync(E.data(), cur_E(c), 8 * E.size(), cudaMemcpyDeviceToHost, c->stream));
+    PAMD_CU(c, cudaMemcpyAsync(fam.data(), cur_fam(c), 4 * fam.size(), cudaMemcpyDeviceToHost, c->stream));
+    PAMD_CU(c, cudaStreamSynchronize(c->stream));
+    uint64_t sum = fnv1a(&h, sizeof(h));
+    sum = fnv1a(st.data(), st.size(), sum);
+    sum = fnv1a(E.data(), 8 * E.size(), sum);
+    sum = fnv1a(fam.data(), 4 * fam.size(), sum);
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = std::fopen(tmp.c_str(), "wb");
+    if (!f) return fail(PAMD_EINVAL, std::string("cannot write ") + tmp);
+    bool ok = std::fwrite(kCkptMagic, 1, 8, f) == 8 && std::fwrite(&h, sizeof(h), 1, f) == 1 &&
+              std::fwrite(st.data(), 1, st.size(), f) == st.size() &&
+              std::fwrite(E.data(), 8, E.size(), f) == E.size() &&
+              std::fwrite(fam.data(), 4, fam.size(), f) == fam.size() &&
+              std::fwrite(&sum, sizeof(sum), 1, f) == 1;
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok || std::rename(tmp.c_str(), path) != 0) {
+        std::remove(tmp.c_str());
+        return fail(PAMD_EINVAL, std::string("cannot write ") + path);
+    }
+    return PAMD_OK;
+}
+
+int pamd_restore(pamd_ctx* c, const char* path) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (is_batch(c)) return fail(PAMD_EUNSUPPORTED, "restore a batch molecule by molecule (pamd_batch_sub)");
+    if (!path) return fail(PAMD_EINVAL, "null path");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(PAMD_EINVAL, std::string("cannot read ") + path);
+    char magic[8];
+    CkptHeader h{};
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kCkptMagic, 8) == 0 &&
+              std::fread(&h, sizeof(h), 1, f) == 1;
+    if (!ok || h.version != 1) {
+        std::fclose(f);
+        return fail(PAMD_EINVAL, std::string(path) + ": not a checkpoint of this library");
+    }
+    if (h.precision != c->precision || h.R != c->R || h.N != c->N || h.Np != c->Np ||
+        h.topology_hash != topology_hash(c->host_top)) {
+        std::fclose(f);
+        return fail(PAMD_EINVAL, std::string(path) + ": checkpoint of another population "
+                                 "(precision, R, atoms or topology differ)");
+    }
+    std::vector<unsigned char> st(state_bytes(c));
+    std::vector<double> E((size_t)c->R);
+    std::vector<int32_t> fam((size_t)c->R);
+    uint64_t sum_file = 0;
+    ok = std::fread(st.data(), 1, st.size(), f) == st.size() &&
+         std::fread(E.data(), 8, E.size(), f) == E.size() &&
+         std::fread(fam.data(), 4, fam.size(), f) == fam.size() &&
+         std::fread(&sum_file, sizeof(sum_file), 1, f) == 1;
+    std::fclose(f);
+    uint64_t sum = fnv1a(&h, sizeof(h));
+    sum = fnv1a(st.data(), st.size(), sum);
+    sum = fnv1a(E.data(), 8 * E.size(), sum);
+    sum = fnv1a(fam.data(), 4 * fam.size(), sum);
+    if (!ok || sum != sum_file) return fail(PAMD_EINVAL, std::string(path) + ": truncated or corrupt checkpoint");
+    for (int32_t v : fam)
+        if (v < 0 || v >= c->R) return fail(PAMD_EINVAL, std::string(path) + ": family ids out of range");
+    // the restored population goes to the main buffers
+    c->cur_is_alt = false;
+    PAMD_CU(c, cudaMemcpyAsync(c->b.state, st.data(), st.size(), cudaMemcpyHostToDevice, c->stream));
+    PAMD_CU(c, cudaMemcpyAsync(c->b.E, E.data(), 8 * E.size(), cudaMemcpyHostToDevice, c->stream));
+    PAMD_CU(c, cudaMemcpyAsync(c->b.fam, fam.data(), 4 * fam.size(), cudaMemcpyHostToDevice, c->stream));
+    PAMD_CU(c, cudaMemcpyAsync(&c->b.scal->sum_lnQ, &h.sum_lnQ, 8, cudaMemcpyHostToDevice, c->stream));
+    PAMD_CU(c, cudaStreamSynchronize(c->stream));
+    c->seed = h.seed;
+    c->step = h.step;
+    c->resample_index = h.resample_index;
+    return PAMD_OK;
+}
+
 int pamd_set_force_model(pamd_ctx* c, pamd_mlp* m) {
     int rc = check_ctx(c);
     if (rc) return rc;

@@ -8,6 +8,7 @@
 // transpose, second-derivative terms, column sums) is FP32 here; energies and
 // loss sums are FP64.
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -867,6 +868,110 @@ int pamd_mlp_adam_step(pamd_mlp* m, double lr, double beta1, double beta2, doubl
                                                              (float)eps, bc1, bc2);
     if ((rc = launch_check(m, "Adam"))) return rc;
     return pack(m);
+}
+
+// Model file: magic, {N, H}, the FP32 parameter block (W1 padded to Pp
+// columns), mu and sd [Pp], mu_E, sigma_E, FNV-1a 64 checksum of all before.
+static const char kMlpMagic[8] = {'P', 'A', 'M', 'D', 'M', 'L', 'P', '1'};
+
+static uint64_t mlp_fnv(const void* d, size_t n, uint64_t h) {
+    const unsigned char* b = static_cast<const unsigned char*>(d);
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+int pamd_mlp_save(pamd_mlp* m, const char* path) {
+    int rc = check_model(m);
+    if (rc) return rc;
+    if (!path) return mfail(PAMD_EINVAL, "pamd_mlp_save: null path");
+    std::vector<float> prm(m->n_params), mu(m->Pp), sd(m->Pp);
+    MLP_CU(m, cudaStreamSynchronize(m->stream));
+    MLP_CU(m, cudaMemcpy(prm.data(), m->params, 4 * prm.size(), cudaMemcpyDeviceToHost));
+    MLP_CU(m, cudaMemcpy(mu.data(), m->mu, 4 * mu.size(), cudaMemcpyDeviceToHost));
+    MLP_CU(m, cudaMemcpy(sd.data(), m->sd, 4 * sd.size(), cudaMemcpyDeviceToHost));
+    const int32_t shape[2] = {m->N, m->H};
+    const double norm[2] = {m->mu_E, m->sigma_E};
+    uint64_t h = mlp_fnv(kMlpMagic, 8, 1469598103934665603ull);
+    h = mlp_fnv(shape, sizeof(shape), h);
+    h = mlp_fnv(prm.data(), 4 * prm.size(), h);
+    h = mlp_fnv(mu.data(), 4 * mu.size(), h);
+    h = mlp_fnv(sd.data(), 4 * sd.size(), h);
+    h = mlp_fnv(norm, sizeof(norm), h);
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = std::fopen(tmp.c_str(), "wb");
+    if (!f) return mfail(PAMD_EINVAL, std::string("pamd_mlp_save: cannot write ") + tmp);
+    bool ok = std::fwrite(kMlpMagic, 1, 8, f) == 8 && std::fwrite(shape, sizeof(shape), 1, f) == 1 &&
+              std::fwrite(prm.data(), 4, prm.size(), f) == prm.size() &&
+              std::fwrite(mu.data(), 4, mu.size(), f) == mu.size() &&
+              std::fwrite(sd.data(), 4, sd.size(), f) == sd.size() &&
+              std::fwrite(norm, sizeof(norm), 1, f) == 1 && std::fwrite(&h, sizeof(h), 1, f) == 1;
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok || std::rename(tmp.c_str(), path) != 0) {
+        std::remove(tmp.c_str());
+        return mfail(PAMD_EINVAL, std::string("pamd_mlp_save: cannot write ") + path);
+    }
+    return PAMD_OK;
+}
+
+int pamd_mlp_load(pamd_mlp** out, const char* path, void* stream) {
+    if (!out || !path) return mfail(PAMD_EINVAL, "pamd_mlp_load: null output or path");
+    *out = nullptr;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return mfail(PAMD_EINVAL, std::string("pamd_mlp_load: cannot read ") + path);
+    char magic[8];
+    int32_t shape[2] = {0, 0};
+    if (std::fread(magic, 1, 8, f) != 8 || std::memcmp(magic, kMlpMagic, 8) != 0 ||
+        std::fread(shape, sizeof(shape), 1, f) != 1) {
+        std::fclose(f);
+        return mfail(PAMD_EINVAL, std::string("pamd_mlp_load: ") + path + " is not a model file");
+    }
+    pamd_mlp* m = nullptr;
+    int rc = pamd_mlp_create(&m, shape[0], shape[1], 0, stream);
+    if (rc) {
+        std::fclose(f);
+        return rc;
+    }
+    std::vector<float> prm(m->n_params), mu(m->Pp), sd(m->Pp);
+    double norm[2] = {0.0, 1.0};
+    uint64_t h_file = 0;
+    bool ok = std::fread(prm.data(), 4, prm.size(), f) == prm.size() &&
+              std::fread(mu.data(), 4, mu.size(), f) == mu.size() &&
+              std::fread(sd.data(), 4, sd.size(), f) == sd.size() &&
+              std::fread(norm, sizeof(norm), 1, f) == 1 && std::fread(&h_file, sizeof(h_file), 1, f) == 1;
+    std::fclose(f);
+    uint64_t h = mlp_fnv(kMlpMagic, 8, 1469598103934665603ull);
+    h = mlp_fnv(shape, sizeof(shape), h);
+    h = mlp_fnv(prm.data(), 4 * prm.size(), h);
+    h = mlp_fnv(mu.data(), 4 * mu.size(), h);
+    h = mlp_fnv(sd.data(), 4 * sd.size(), h);
+    h = mlp_fnv(norm, sizeof(norm), h);
+    bool sane = ok && h == h_file && norm[1] > 0.0 && std::isfinite(norm[0]) && std::isfinite(norm[1]);
+    for (size_t p = 0; sane && p < sd.size(); ++p) sane = sd[p] > 0.0f && std::isfinite(sd[p]);
+    if (!sane) {
+        pamd_mlp_destroy(m);
+        return mfail(PAMD_EINVAL, std::string("pamd_mlp_load: ") + path + " is truncated or corrupt");
+    }
+    std::vector<float> isd(m->Pp);
+    for (int p = 0; p < m->Pp; ++p) isd[p] = (float)(1.0 / (double)sd[p]);
+    m->mu_E = norm[0];
+    m->sigma_E = norm[1];
+    cudaError_t e = cudaMemcpy(m->params, prm.data(), 4 * prm.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->mu, mu.data(), 4 * mu.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->sd, sd.data(), 4 * sd.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->inv_sd, isd.data(), 4 * isd.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        pamd_mlp_destroy(m);
+        return mfail(PAMD_ECUDA, std::string("pamd_mlp_load: ") + cudaGetErrorString(e));
+    }
+    if ((rc = pack(m)) || (rc = read_model_status(m))) {
+        pamd_mlp_destroy(m);
+        return rc;
+    }
+    *out = m;
+    return PAMD_OK;
 }
 
 int pamd_mlp_sync(pamd_mlp* m) {

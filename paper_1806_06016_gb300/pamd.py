@@ -95,7 +95,8 @@ EXPORTS = [
     "pamd_gemm_bf16", "pamd_gemm_bf16_time", "pamd_mlp_create", "pamd_mlp_info", "pamd_mlp_set_params",
     "pamd_mlp_get_params", "pamd_mlp_fit_normalization", "pamd_mlp_energy_forces",
     "pamd_mlp_loss_grads", "pamd_mlp_get_grads", "pamd_mlp_adam_step", "pamd_set_force_model",
-    "pamd_mlp_sync", "pamd_mlp_launch_count", "pamd_mlp_destroy",
+    "pamd_mlp_sync", "pamd_mlp_launch_count", "pamd_mlp_destroy", "pamd_mlp_save", "pamd_mlp_load",
+    "pamd_checkpoint", "pamd_restore",
 ]
 
 _lib = None
@@ -156,6 +157,10 @@ def load(path: str | None = None):
             "pamd_mlp_sync": (C.c_int, [P]),
             "pamd_mlp_launch_count": (I64, [P]),
             "pamd_mlp_destroy": (None, [P]),
+            "pamd_mlp_save": (C.c_int, [P, C.c_char_p]),
+            "pamd_mlp_load": (C.c_int, [C.POINTER(P), C.c_char_p, P]),
+            "pamd_checkpoint": (C.c_int, [P, C.c_char_p]),
+            "pamd_restore": (C.c_int, [P, C.c_char_p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -385,6 +390,14 @@ def pamd_resample_counts_noalloc(E_dev: int, R: int, T_prev: float, T_next: floa
         int(mol_id), C.c_void_p(counts_dev), C.c_void_p(lnQ_dev or None), C.c_void_p(stream or None)))
 
 
+def pamd_checkpoint(ctx, path: str) -> None:
+    _check(load().pamd_checkpoint(ctx, os.fsencode(path)))
+
+
+def pamd_restore(ctx, path: str) -> None:
+    _check(load().pamd_restore(ctx, os.fsencode(path)))
+
+
 def pamd_launch_count(ctx) -> int:
     return int(load().pamd_launch_count(ctx))
 
@@ -438,6 +451,12 @@ class Population:
 
     def info(self):
         return pamd_info(self.ctx)
+
+    def checkpoint(self, path):
+        pamd_checkpoint(self.ctx, path)
+
+    def restore(self, path):
+        pamd_restore(self.ctx, path)
 
     def autotune(self, theta_probe=20):
         return pamd_autotune(self.ctx, theta_probe)

@@ -8,6 +8,7 @@ torch.autograd.Function whose backward is the library's force kernel.
 from __future__ import annotations
 
 import ctypes as C
+import os
 
 import numpy as np
 
@@ -197,6 +198,25 @@ class MLP:
                 step += 1
         self.sync()
         return hist
+
+    def save(self, path: str) -> None:
+        self._call(self._lib.pamd_mlp_save, os.fsencode(path))
+
+    @classmethod
+    def load(cls, path: str) -> "MLP":
+        """A model read from a file written by ``save``."""
+        self = cls.__new__(cls)
+        torch = _torch()
+        self._torch = torch
+        self._lib = _p.load()
+        self._stream = torch.cuda.Stream()
+        h = C.c_void_p()
+        _p._check(self._lib.pamd_mlp_load(C.byref(h), os.fsencode(path), C.c_void_p(self._stream.cuda_stream)))
+        self._h = h
+        n = C.c_int32(); npairs = C.c_int32(); hid = C.c_int32()
+        _p._check(self._lib.pamd_mlp_info(h, C.byref(n), C.byref(npairs), C.byref(hid)))
+        self.n_atoms, self.hidden, self.n_pairs = n.value, hid.value, npairs.value
+        return self
 
     def close(self):
         if getattr(self, "_h", None):

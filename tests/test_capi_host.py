@@ -117,3 +117,19 @@ def test_surrogate_argument_validation(lib):
     assert lib.pamd_mlp_loss_grads(None, None, None, None, None, 4, 1.0, None) == pamd.PAMD_EINVAL
     assert lib.pamd_mlp_launch_count(None) == 0
     lib.pamd_mlp_destroy(None)
+
+
+def test_checkpoint_and_model_files_validation(lib, tmp_path):
+    """File entry points reject null handles, missing and foreign files
+    before any device work."""
+    from paper_1806_06016_gb300 import pamd
+    assert lib.pamd_checkpoint(None, b"x") == pamd.PAMD_EINVAL
+    assert lib.pamd_restore(None, b"x") == pamd.PAMD_EINVAL
+    assert lib.pamd_mlp_save(None, b"x") == pamd.PAMD_EINVAL
+    h = C.c_void_p()
+    assert lib.pamd_mlp_load(C.byref(h), str(tmp_path / "missing").encode(), None) == pamd.PAMD_EINVAL
+    junk = tmp_path / "junk.bin"
+    junk.write_bytes(b"not a model file at all")
+    assert lib.pamd_mlp_load(C.byref(h), str(junk).encode(), None) == pamd.PAMD_EINVAL
+    assert "not a model file" in pamd.pamd_last_error()
+    assert not h.value

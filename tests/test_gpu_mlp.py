@@ -265,3 +265,32 @@ def test_training_gain_over_untrained_network(env):
     finally:
         trained.close()
         untrained.close()
+
+
+def test_model_file_roundtrip(env, tmp_path):
+    torch, _, S = env
+    n = 22
+    x = pi.perturbed_positions(pi.make_chain(n, 3), 32, 0.03, 7)
+    model, _ = _model_and_params(env, n, 128, 5, x)
+    path = str(tmp_path / "m.mlp")
+    try:
+        model.save(path)
+        loaded = S.MLP.load(path)
+        try:
+            pa, pb = model.get_params(), loaded.get_params()
+            for k in pa:
+                np.testing.assert_array_equal(np.asarray(pa[k]), np.asarray(pb[k]))
+            xt = torch.from_numpy(x.astype(np.float32)).cuda()
+            Ea, Fa = model.energy_forces(xt)
+            Eb, Fb = loaded.energy_forces(xt)
+            np.testing.assert_array_equal(Ea.cpu().numpy(), Eb.cpu().numpy())
+            np.testing.assert_array_equal(Fa.cpu().numpy(), Fb.cpu().numpy())
+        finally:
+            loaded.close()
+        raw = bytearray(open(path, "rb").read())
+        raw[-20] ^= 1
+        open(path, "wb").write(bytes(raw))
+        with pytest.raises(Exception):
+            S.MLP.load(path)
+    finally:
+        model.close()

@@ -503,3 +503,46 @@ def test_autotune_keeps_state_and_parity(lib, orc):
         assert lib.pamd_autotune(ctx, 5)["from_cache"] == 1
     finally:
         lib.pamd_destroy(ctx)
+
+
+def test_checkpoint_file_roundtrip(lib, tmp_path):
+    """A run restored from a checkpoint file continues bit-identically;
+    corrupt or foreign files are refused and leave the population unchanged."""
+    top = pi.make_chain(22, 5)
+    temps = pi.geometric_schedule(900.0, 700.0, 2)
+    path = str(tmp_path / "run.ckpt")
+    pop = lib.Population(top, 300, temps[0], 21)
+    other = lib.Population(top, 301, temps[0], 21)
+    try:
+        pop.propagate(15, 0.001, temps[0])
+        pop.resample(temps[0], temps[1], want_copies=False)
+        pop.checkpoint(path)
+        pop.propagate(15, 0.001, temps[1])
+        pop.resample(temps[1], temps[2], want_copies=False)
+        a = pop.state()
+        ca = lib.pamd_get_counters(pop.ctx)
+        pop.reset(temps[0], 99)            # scramble, then come back
+        pop.propagate(3, 0.001, temps[0])
+        pop.restore(path)
+        pop.propagate(15, 0.001, temps[1])
+        pop.resample(temps[1], temps[2], want_copies=False)
+        b = pop.state()
+        for u, w in zip(a, b):
+            np.testing.assert_array_equal(u, w)
+        assert lib.pamd_get_counters(pop.ctx) == ca
+        # corrupt: flip one payload byte
+        raw = bytearray(open(path, "rb").read())
+        raw[200] ^= 0x40
+        bad = str(tmp_path / "bad.ckpt")
+        open(bad, "wb").write(bytes(raw))
+        before = pop.state()
+        with pytest.raises(lib.PamdError) as e:
+            pop.restore(bad)
+        assert e.value.code == lib.PAMD_EINVAL
+        for u, w in zip(before, pop.state()):
+            np.testing.assert_array_equal(u, w)
+        with pytest.raises(lib.PamdError):
+            other.restore(path)            # another population size
+    finally:
+        pop.close()
+        other.close()
