@@ -756,15 +756,12 @@ def run_surrogate(args, w):
             (xr[-8192:] - xr[-8192:].mean(1, keepdims=True)) ** 2, axis=2), axis=1))))
         # configurations the surrogate reaches far outside the physical range
         # (overlapping atoms: exact energies up to 1e11 kJ/mol) would swamp the
-        # loss; their labels are clipped to 6 SD above the training energies
-        # and to 5x the training force RMS (directions kept), which still
-        # teaches the network a repulsive wall there
+        # loss; keep those within 6 SD of the training energies and 5x the
+        # training force RMS.  (Clipping their labels instead, which breaks the
+        # energy-force consistency of the data, made the network diverge.)
         f_rms = np.sqrt(np.mean(Fr.astype(np.float64) ** 2, axis=(1, 2)))
-        e_hi = E_tr.mean() + 6.0 * E_tr.std()
-        f_hi = 5.0 * np.sqrt(np.mean(F_tr.astype(np.float64) ** 2))
-        keep = (Er <= e_hi) & (f_rms <= f_hi)
-        Er = np.minimum(Er, e_hi)
-        Fr = (Fr * np.minimum(1.0, f_hi / np.maximum(f_rms, 1e-30))[:, None, None]).astype(np.float32)
+        keep = (Er <= E_tr.mean() + 6.0 * E_tr.std()) & (f_rms <= 5.0 * np.sqrt(np.mean(F_tr.astype(np.float64) ** 2)))
+        xr, Er, Fr = xr[keep], Er[keep], Fr[keep]
         xt = torch.cat([xt, dev(xr)])
         Et = torch.cat([Et, dev(Er)])
         Ft = torch.cat([Ft, dev(Fr)])
@@ -773,7 +770,7 @@ def run_surrogate(args, w):
                              lr=3e-4, lr_final=1e-5, seed=r + 1, report_every=2000)
         torch.cuda.synchronize()
         out["refinement"].append({"round": r + 1, "added_samples": int(len(xr)),
-                                  "clipped_samples": int((~keep).sum()),
+                                  "discarded_samples": int((~keep).sum()),
                                   "surrogate_rg_at_250K_before": rg_end,
                                   "exact_E_mean_of_added": float(Er.mean()),
                                   "harvest_s": harvest_r, "train_s": time.perf_counter() - t0,
@@ -933,9 +930,9 @@ def main():
     ap.add_argument("--train-samples", type=int, default=1 << 21, help="surrogate mode")
     ap.add_argument("--epochs", type=int, default=40, help="surrogate mode: training epochs")
     ap.add_argument("--batch", type=int, default=2048, help="surrogate mode: minibatch")
-    ap.add_argument("--refine-rounds", type=int, default=3,
+    ap.add_argument("--refine-rounds", type=int, default=2,
                     help="surrogate mode: rounds of exact labels for surrogate-visited states")
-    ap.add_argument("--refine-epochs", type=int, default=6, help="surrogate mode: epochs per round")
+    ap.add_argument("--refine-epochs", type=int, default=8, help="surrogate mode: epochs per round")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.mode == "kernel":
