@@ -69,7 +69,12 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # dram bytes (read + write) of one propagate launch from the ncu capture in
 # profiles/, keyed by the hash of the kernel source it was taken on; the value
 # is dropped automatically when the kernel source changes.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/propagate_kernel_75atom_R8192_theta100.md: dram__bytes_read.sum
+    # 15.05 MB + dram__bytes_write.sum 0 (the written state stays in L2 until
+    # after the kernel); the state moves once per launch whatever theta is
+    "82c42a4517bd10bf": 15045632,
+}
 
 
 def flop_per_replica_step(n):
@@ -201,7 +206,7 @@ def run_reference(args, w):
 
 def config_of(w, args):
     return {"workload": w["workload"], "n_atoms": w["n_atoms"],
-            "replicas_per_gpu": w["R"] * w.get("batch", 1),
+            "replicas_per_gpu": (getattr(args, "replicas", 0) or w["R"]) * w.get("batch", 1),
             "theta": w["theta"], "temperature_steps": w["K"], "T_first_K": w["T0"],
             "T_last_K": w["TK"], "dt_fs": w["dt"] * 1e3, "gamma_per_ps": w["gamma"],
             "precision": "FP32 forces/integration, FP64 energies/weights/lnQ",
@@ -237,7 +242,7 @@ def run_gpu(args, w):
     pamd.load()
 
     temps = pi.geometric_schedule(w["T0"], w["TK"], w["K"])
-    R, theta, dt = w["R"], w["theta"], w["dt"]
+    R, theta, dt = args.replicas or w["R"], w["theta"], w["dt"]
     seed = w["seed"] + 7919 * rank
     # the library launches on this stream; the timing events are recorded on it
     stream = torch.cuda.Stream()
@@ -918,7 +923,8 @@ def main():
                                        "surrogate_kernel"],
                     default="anneal")
     ap.add_argument("--theta", type=int, default=0, help="kernel mode: steps per launch")
-    ap.add_argument("--replicas", type=int, default=0, help="kernel mode: population size")
+    ap.add_argument("--replicas", type=int, default=0,
+                    help="population size (per molecule for the batched workload); default: the workload's")
     ap.add_argument("--lanes", type=int, default=0, help="kernel mode: lanes per replica")
     ap.add_argument("--warps", type=int, default=0, help="kernel mode: warps per block")
     ap.add_argument("--autotune", action="store_true", help="kernel mode: tune the launch shape")

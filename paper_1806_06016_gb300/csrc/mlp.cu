@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -374,12 +375,23 @@ int pack(pamd_mlp* m) {
 size_t forces_smem(const pamd_mlp* m) { return sizeof(float) * (3 * kXs + (size_t)gamma_floats(m->N, m->Pp)); }
 size_t loss_smem(const pamd_mlp* m) { return sizeof(float) * (6 * kXs + (size_t)gamma_floats(m->N, m->Pp)); }
 
+// The dynamic shared-memory limit of a kernel is process-wide: raise it to the
+// largest model created so far, never lower it.
 int set_smem_attrs(const pamd_mlp* m) {
-    cudaError_t e = cudaFuncSetAttribute(mlp_forces_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)forces_smem(m));
-    if (e == cudaSuccess)
+    static std::mutex mu;
+    static size_t forces_max = 0, loss_max = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    cudaError_t e = cudaSuccess;
+    if (forces_smem(m) > forces_max) {
+        e = cudaFuncSetAttribute(mlp_forces_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)forces_smem(m));
+        if (e == cudaSuccess) forces_max = forces_smem(m);
+    }
+    if (e == cudaSuccess && loss_smem(m) > loss_max) {
         e = cudaFuncSetAttribute(mlp_loss_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)loss_smem(m));
+        if (e == cudaSuccess) loss_max = loss_smem(m);
+    }
     return e == cudaSuccess ? PAMD_OK : mfail(PAMD_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
 }
 
@@ -413,7 +425,7 @@ int mlp_ensure_work(pamd_mlp* m, long long M, bool train) {
     const size_t H = (size_t)m->H, Pp = (size_t)m->Pp, C = (size_t)cap;
     std::vector<size_t> sizes;
     // order: a h1 d2 d1 s1 ga part | z1 z2 s2 w2d2 zd1 zd2 h1b t0 t1 t2 nu_a hd1 z2b A1T B1T A2T B2T ebar loss
-    sizes = {2 * C * Pp, 2 * C * H, 2 * C * H, 2 * C * H, 4 * C * H, 4 * C * Pp, 4 * C * (size_t)m->nparts};
+    sizes = {2 * C * Pp, 2 * C * H, 2 * C * H, 2 * C * H, 4 * C * H, 2 * C * Pp, 4 * C * (size_t)m->nparts};
     if (tr) {
         for (int i = 0; i < 10; ++i) sizes.push_back(4 * C * H);
         sizes.push_back(2 * C * Pp);
@@ -453,7 +465,7 @@ int mlp_ensure_work(pamd_mlp* m, long long M, bool train) {
     nw.d2 = reinterpret_cast<__nv_bfloat16*>(take());
     nw.d1 = reinterpret_cast<__nv_bfloat16*>(take());
     nw.s1 = reinterpret_cast<float*>(take());
-    nw.ga = reinterpret_cast<float*>(take());
+    nw.ga = reinterpret_cast<__nv_bfloat16*>(take());
     nw.part = reinterpret_cast<float*>(take());
     if (tr) {
         float** f32[10] = {&nw.z1, &nw.z2, &nw.s2, &nw.w2d2, &nw.zd1, &nw.zd2, &nw.h1b, &nw.t0, &nw.t1, &nw.t2};
@@ -501,7 +513,7 @@ int mlp_gemms(pamd_mlp* m, int M, bool forces, cudaStream_t s, int* status) {
     // de/da = d1 W1
     g = GemmArgs{};
     g.A = w.d1; g.B = m->W1Tb; g.M = M; g.N = Pp; g.K = H; g.lda = H; g.ldb = H;
-    g.epi = kEpiStore; g.C = w.ga; g.ldc = Pp;
+    g.epi = kEpiStore; g.Cb = w.ga; g.ldcb = Pp; g.ldc = Pp;
     return gemm(m, g, s, status);
 }
 
@@ -777,7 +789,7 @@ int pamd_mlp_loss_grads(pamd_mlp* m, const float* x_dev, const double* E_dev, co
     if ((rc = gemm(m, g, s))) return rc;
     g = GemmArgs{};
     g.A = w.d1; g.B = m->W1Tb; g.M = Mi; g.N = Pp; g.K = H; g.lda = H; g.ldb = H;
-    g.epi = kEpiStore; g.C = w.ga; g.ldc = Pp;
+    g.epi = kEpiStore; g.Cb = w.ga; g.ldcb = Pp; g.ldc = Pp;
     if ((rc = gemm(m, g, s))) return rc;
     // loss, energy cotangent and the tangent direction nu_a
     LossArgs L{};

@@ -102,7 +102,7 @@ __device__ __forceinline__ void init_gamma(int N, float* gam) {
 }
 
 // fill the table from de/da of one configuration (whole block)
-__device__ __forceinline__ void load_gamma(const float* xs, const float* __restrict__ ga_row,
+__device__ __forceinline__ void load_gamma(const float* xs, const __nv_bfloat16* __restrict__ ga_row,
                                            const float* __restrict__ inv_sd,
                                            const ushort2* __restrict__ pairs, int P, int N, float* gam) {
     if (gamma_matrix(N)) {
@@ -114,12 +114,12 @@ __device__ __forceinline__ void load_gamma(const float* xs, const float* __restr
             const float dy = xs[kXs + ij.x] - xs[kXs + ij.y];
             const float dz = xs[2 * kXs + ij.x] - xs[2 * kXs + ij.y];
             const float ir = rsqrtf(dx * dx + dy * dy + dz * dz);
-            const float c = __ldcs(ga_row + p) * inv_sd[p] * ir * ir * ir;
+            const float c = __bfloat162float(ga_row[p]) * inv_sd[p] * ir * ir * ir;
             gam[ij.x * S + ij.y] = c;
             gam[ij.y * S + ij.x] = c;
         }
     } else {
-        for (int p = threadIdx.x; p < P; p += blockDim.x) gam[p] = ga_row[p] * inv_sd[p];
+        for (int p = threadIdx.x; p < P; p += blockDim.x) gam[p] = __bfloat162float(ga_row[p]) * inv_sd[p];
     }
 }
 

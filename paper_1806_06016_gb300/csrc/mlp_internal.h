@@ -21,7 +21,7 @@ struct MlpWork {
     __nv_bfloat16* d2 = nullptr; // [cap][H] w3 * silu'(z2)
     __nv_bfloat16* d1 = nullptr; // [cap][H] (W2^T d2) * silu'(z1)
     float* s1 = nullptr;         // [cap][H] silu'(z1)
-    float* ga = nullptr;         // [cap][Pp] de/da
+    __nv_bfloat16* ga = nullptr; // [cap][Pp] de/da (BF16: it feeds an FP32 sum of per-pair terms)
     float* part = nullptr;       // [cap][nparts] partial sums of w3 . h2
     // training only
     float* z1 = nullptr;         // [cap][H]
@@ -69,7 +69,7 @@ struct ForceArgs {
     ConfigView cv;
     int M, N, P, Pp, nparts;
     const ushort2* pairs;    // [Pp] (i, j)
-    const float* ga;         // [M][Pp]
+    const __nv_bfloat16* ga; // [M][Pp]
     const float* part;       // [M][nparts]
     const float* inv_sd;
     const float* b3;         // device scalar
@@ -84,7 +84,7 @@ struct LossArgs {
     const float* F_ref;      // [n][N][3]
     int M, N, P, Pp, nparts;
     const ushort2* pairs;    // [Pp] (i, j)
-    const float* ga;
+    const __nv_bfloat16* ga;
     const float* part;
     const float* inv_sd;
     const float* b3;         // device scalar
@@ -112,7 +112,7 @@ struct MlpStepParams {
     long long R;
     int N, Np, P, Pp, nparts;
     int mode, step_index, theta;
-    const float* ga;
+    const __nv_bfloat16* ga;
     const float* part;
     const float* mu;
     const float* inv_sd;

@@ -8,6 +8,7 @@ torch.autograd.Function whose backward is the library's force kernel.
 from __future__ import annotations
 
 import ctypes as C
+import functools
 import os
 
 import numpy as np
@@ -235,6 +236,7 @@ def attach(ctx, model: MLP | None) -> None:
     _p._check(_p.load().pamd_set_force_model(ctx, None if model is None else model._h))
 
 
+@functools.lru_cache(maxsize=None)
 def _autograd_function():
     torch = _torch()
 
