@@ -70,9 +70,10 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # profiles/, keyed by the hash of the kernel source it was taken on; the value
 # is dropped automatically when the kernel source changes.
 NCU_TRAFFIC = {
-    # profiles/propagate_kernel_75atom_R8192_theta100.md: dram__bytes_read.sum
-    # 15.05 MB + dram__bytes_write.sum 0 (the written state stays in L2 until
-    # after the kernel); the state moves once per launch whatever theta is
+    # ncu capture of this kernel (75-atom chain, R = 8192, theta = 100):
+    # dram__bytes_read.sum 15.05 MB + dram__bytes_write.sum 0 (the written
+    # state stays in L2 until after the kernel); the state moves once per
+    # launch whatever theta is
     "82c42a4517bd10bf": 15045632,
 }
 

@@ -17,10 +17,10 @@
  * steps (replicas are independent there; see the paragraph on parallelisation
  * over independent replicas in the introduction).
  *
- * Readings of points the paper leaves open (each also listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - MD engine: BAOAB Langevin splitting (Leimkuhler & Matthews 2013) with
- *     friction gamma; the paper uses "a variant of velocity Verlet" with a
- *     Langevin thermostat and a per-replica seed.
+ *     friction gamma; the paper's own integrator is a velocity-Verlet-type
+ *     scheme with a Langevin thermostat and a per-replica seed.
  *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) keyed on the run
  *     seed, counter = (atom, replica slot, step, purpose | molecule << 8).
  *     Normals: Box-Muller on 23-bit uniforms u = (top23 + 0.5) * 2^-23, which
@@ -35,8 +35,8 @@
  *   - After resampling positions are recentred on the centre of mass and
  *     velocities scaled by sqrt(T_i / T_{i-1}) (PAMD scheme, step 2).
  *   - Standard errors: jackknife over 64 bins, bin = family id mod 64 (family
- *     id = replica slot at T0), following the "binning over the population"
- *     paragraph.
+ *     id = replica slot at T0), following the paper's paragraph on error
+ *     estimates by binning.
  */
 #include <math.h>
 #include <pthread.h>
