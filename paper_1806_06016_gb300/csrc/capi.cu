@@ -335,6 +335,13 @@ int build_topology(const pamd_topology* t, int lanes_req, TopoLayout* lay_out,
     lay.off_cbond = off; off += round_up(std::max(N - 1, 0) * 8, 16);
     lay.off_cangle = off; off += round_up(std::max(N - 2, 0) * 8, 16);
     lay.off_cdih = off; off += round_up(std::max(N - 3, 0) * 16, 16);
+    // pair-parameter table of the half-ring tiles (chain layouts, when small)
+    const size_t tab_bytes = (size_t)TH * B * B * L * 16;
+    if (chain && TH > 0 && tab_bytes <= kPairTableMaxBytes) {
+        lay.ptab = 1;
+        lay.off_ptab = off;
+        off += (int)tab_bytes;
+    }
     lay.bytes = off;
     blob.assign(off, 0);
     float* prm = reinterpret_cast<float*>(blob.data() + lay.off_params);
@@ -347,6 +354,25 @@ int build_topology(const pamd_topology* t, int lanes_req, TopoLayout* lay_out,
         q[3] = (float)(1.0 / t->mass[i]);
     }
     std::memcpy(blob.data() + lay.off_masks, masks.data(), masks.size() * 8);
+    if (lay.ptab) {
+        // the FP32 products the kernel's mixing would form, so both paths agree bitwise
+        float* tb = reinterpret_cast<float*>(blob.data() + lay.off_ptab);
+        for (int t = 1; t <= TH; ++t)
+            for (int g = 0; g < L; ++g) {
+                const int J = (g + t) % L;
+                for (int b = 0; b < B; ++b)
+                    for (int a = 0; a < B; ++a) {
+                        const float* pi = prm + 4 * (g * lay.block_stride + a);
+                        const float* pj = prm + 4 * (J * lay.block_stride + b);
+                        const float sg = pi[0] + pj[0];
+                        float* e = tb + 4 * ((((size_t)(t - 1) * B * B + (size_t)b * B + a) * L) + g);
+                        e[0] = sg * sg;
+                        e[1] = pi[1] * pj[1];
+                        e[2] = pi[2] * pj[2];
+                        e[3] = 0.0f;
+                    }
+            }
+    }
     if (!bonds.empty()) std::memcpy(blob.data() + lay.off_bonds, bonds.data(), bonds.size() * 16);
     if (!angles.empty()) std::memcpy(blob.data() + lay.off_angles, angles.data(), angles.size() * 32);
     if (!dihs.empty()) std::memcpy(blob.data() + lay.off_dihs, dihs.data(), dihs.size() * 32);
@@ -383,6 +409,7 @@ int build_topology(const pamd_topology* t, int lanes_req, TopoLayout* lay_out,
 cudaError_t propagate_dispatch_any(const TopoLayout& lay, const PropParams* p, int warps, int grid,
                                    size_t smem, cudaStream_t s, int* occ) {
     const bool chain = lay.chain != 0;
+    const bool table = lay.ptab != 0;
     if (lay.paired) {
         switch (lay.per_lane) {
             case 2: return propagate2_b2(p, chain, warps, grid, smem, s, occ);
@@ -392,14 +419,14 @@ cudaError_t propagate_dispatch_any(const TopoLayout& lay, const PropParams* p, i
         }
     }
     switch (lay.per_lane) {
-        case 1: return propagate_b1(p, chain, warps, grid, smem, s, occ);
-        case 2: return propagate_b2(p, chain, warps, grid, smem, s, occ);
-        case 3: return propagate_b3(p, chain, warps, grid, smem, s, occ);
-        case 4: return propagate_b4(p, chain, warps, grid, smem, s, occ);
-        case 5: return propagate_b5(p, chain, warps, grid, smem, s, occ);
-        case 6: return propagate_b6(p, chain, warps, grid, smem, s, occ);
-        case 7: return propagate_b7(p, chain, warps, grid, smem, s, occ);
-        case 8: return propagate_b8(p, chain, warps, grid, smem, s, occ);
+        case 1: return propagate_b1(p, chain, table, warps, grid, smem, s, occ);
+        case 2: return propagate_b2(p, chain, table, warps, grid, smem, s, occ);
+        case 3: return propagate_b3(p, chain, table, warps, grid, smem, s, occ);
+        case 4: return propagate_b4(p, chain, table, warps, grid, smem, s, occ);
+        case 5: return propagate_b5(p, chain, table, warps, grid, smem, s, occ);
+        case 6: return propagate_b6(p, chain, table, warps, grid, smem, s, occ);
+        case 7: return propagate_b7(p, chain, table, warps, grid, smem, s, occ);
+        case 8: return propagate_b8(p, chain, table, warps, grid, smem, s, occ);
         default: return cudaErrorInvalidValue;
     }
 }

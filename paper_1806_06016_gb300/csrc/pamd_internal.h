@@ -17,6 +17,7 @@ constexpr double kCoulomb = 138.935458;        // kJ mol^-1 nm e^-2
 constexpr int kNumBins = 64;                   // family bins for jackknife errors
 constexpr uint32_t kPurposeNoise = 0u, kPurposeInit = 1u, kPurposeResample = 2u;
 constexpr int kMaxColors = 64;                 // colour classes per bonded term type
+constexpr size_t kPairTableMaxBytes = 48 * 1024;  // largest pair-parameter table kept in shared memory
 
 // Bonded terms as laid out in the topology blob (16-byte aligned records).
 struct BondRec { int32_t i, j; float r0, k; };
@@ -45,6 +46,8 @@ struct TopoLayout {
     int off_cdih;              // chain: float4 [N-3] {k, n, cos phase, sin phase} of (d..d+3)
     float s14_lj, s14_c;       // chain: 1-4 scale factors
     int paired;                // launch: 1 = two replicas per lane group (packed FP32x2)
+    int ptab, off_ptab;        // chain: 1 if float4 [L/2][B][B][L] {sigma_ij^2, eps_ij, qq_ij, 0}
+                               //   of the half-ring tiles follows (entry ((t-1) B^2 + b B + a) L + g)
     int bytes;                 // total, multiple of 16
 };
 
@@ -270,8 +273,8 @@ namespace pamd {
 // translation unit).  With p == null they only report how many blocks of that
 // shape fit on one SM.
 #define PAMD_DECLARE_PROPAGATE(B)                                                            \
-    cudaError_t propagate_b##B(const PropParams* p, bool chain, int warps, int grid, size_t smem, \
-                               cudaStream_t s, int* blocks_per_sm);
+    cudaError_t propagate_b##B(const PropParams* p, bool chain, bool table, int warps, int grid, \
+                               size_t smem, cudaStream_t s, int* blocks_per_sm);
 PAMD_DECLARE_PROPAGATE(1)
 PAMD_DECLARE_PROPAGATE(2)
 PAMD_DECLARE_PROPAGATE(3)

@@ -375,9 +375,10 @@ __device__ __noinline__ double energy_pass2(const unsigned char* sm, const TopoL
 #pragma unroll
             for (int b = a + 1; b < B; ++b) {
                 if ((m >> (a * B + b)) & 1ull) continue;
+                const float sg = hsi[a] + hsi[b];
                 float fs, e;
                 pair_lj_coul<true>(pi_[b].x - pi_[a].x, pi_[b].y - pi_[a].y, pi_[b].z - pi_[a].z,
-                                   hsi[a] + hsi[b], sei[a] * sei[b], qi[a] * qi[b], fs, e);
+                                   sg * sg, sei[a] * sei[b], qi[a] * qi[b], fs, e);
                 e_acc += (double)e;
             }
     }
@@ -394,9 +395,10 @@ __device__ __noinline__ double energy_pass2(const unsigned char* sm, const TopoL
 #pragma unroll
             for (int a = 0; a < B; ++a) {
                 if ((m >> (a * B + b)) & 1ull) continue;
+                const float sg = hsi[a] + cj.x;
                 float fs, e;
                 pair_lj_coul<true>(pj.x - pi_[a].x, pj.y - pi_[a].y, pj.z - pi_[a].z,
-                                   hsi[a] + cj.x, sei[a] * cj.y, qi[a] * cj.z, fs, e);
+                                   sg * sg, sei[a] * cj.y, qi[a] * cj.z, fs, e);
                 e_acc += (double)e;
             }
         }

@@ -2,12 +2,12 @@
 #include "propagate_impl.cuh"
 
 namespace pamd {
-cudaError_t propagate_b7(const PropParams* p, bool chain, int warps, int grid, size_t smem,
-                         cudaStream_t s, int* blocks_per_sm) {
-    return propagate_dispatch_b<7>(p, chain, warps, grid, smem, s, blocks_per_sm);
+cudaError_t propagate_b7(const PropParams* p, bool chain, bool table, int warps, int grid,
+                         size_t smem, cudaStream_t s, int* blocks_per_sm) {
+    return propagate_dispatch_b<7>(p, chain, table, warps, grid, smem, s, blocks_per_sm);
 }
-cudaError_t propagate_b8(const PropParams* p, bool chain, int warps, int grid, size_t smem,
-                         cudaStream_t s, int* blocks_per_sm) {
-    return propagate_dispatch_b<8>(p, chain, warps, grid, smem, s, blocks_per_sm);
+cudaError_t propagate_b8(const PropParams* p, bool chain, bool table, int warps, int grid,
+                         size_t smem, cudaStream_t s, int* blocks_per_sm) {
+    return propagate_dispatch_b<8>(p, chain, table, warps, grid, smem, s, blocks_per_sm);
 }
 }  // namespace pamd

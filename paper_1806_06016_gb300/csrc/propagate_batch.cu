@@ -65,10 +65,12 @@ __global__ void __launch_bounds__(kBatchThreads, BatchCfg<B>::MIN_BLOCKS)
             float4* frc = pos + lay.nk;
             const long long k = (long long)w.y + slot_local;
             if (k < w.z) {
-                if (lay.chain)
-                    advance_replica<B, true>(p, sm, prm, masks, pos, frc, k, L, g, base, gmask);
+                if (lay.chain && lay.ptab)
+                    advance_replica<B, true, true>(p, sm, prm, masks, pos, frc, k, L, g, base, gmask);
+                else if (lay.chain)
+                    advance_replica<B, true, false>(p, sm, prm, masks, pos, frc, k, L, g, base, gmask);
                 else
-                    advance_replica<B, false>(p, sm, prm, masks, pos, frc, k, L, g, base, gmask);
+                    advance_replica<B, false, false>(p, sm, prm, masks, pos, frc, k, L, g, base, gmask);
             }
         }
     }

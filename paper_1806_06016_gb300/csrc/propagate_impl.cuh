@@ -51,15 +51,16 @@ struct PropCfg {
 };
 
 // Lennard-Jones + Coulomb for one pair.  d = x_j - x_i.  With
-// eps = 24 sqrt(eps_i eps_j) and qq = k_e q_i q_j the force on i is -fs * d
-// and on j +fs * d; e is 4 eps_ij [(s/r)^12 - (s/r)^6] + k_e q_i q_j / r.
+// sig2 = sigma_ij^2, eps = 24 sqrt(eps_i eps_j) and qq = k_e q_i q_j the force
+// on i is -fs * d and on j +fs * d; e is 4 eps_ij [(s/r)^12 - (s/r)^6] +
+// k_e q_i q_j / r.
 template <bool ENERGY>
-__device__ __forceinline__ void pair_lj_coul(float dx, float dy, float dz, float sig, float eps,
+__device__ __forceinline__ void pair_lj_coul(float dx, float dy, float dz, float sig2, float eps,
                                              float qq, float& fs, float& e) {
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     const float rinv = rsqrtf(r2);
     const float rinv2 = rinv * rinv;
-    const float s2 = sig * sig * rinv2;
+    const float s2 = sig2 * rinv2;
     const float s6 = s2 * s2 * s2;
     const float lj = eps * s6 * fmaf(2.0f, s6, -1.0f);
     fs = fmaf(qq, rinv, lj) * rinv2;
@@ -73,25 +74,45 @@ __device__ __forceinline__ void pair_lj_coul(float dx, float dy, float dz, float
 // memory before the next is loaded.  Per accumulator the summation order is
 // that of a full B x B sweep (a inner for the partner, b increasing for the
 // lane's own atoms).
-template <int B, bool MASKED, bool ENERGY>
+//
+// With TABLE the pair parameters {sigma_ij^2, eps_ij, qq_ij} come from a
+// per-tile table in shared memory (entry (b, a) at tab[(b B + a) L]; the L
+// lanes of a group read consecutive float4s) instead of being mixed from the
+// per-atom parameters: the same values (the table holds exactly the FP32
+// products the mixing computes), four fewer FMA-pipe instructions per pair.
+template <int B, bool MASKED, bool ENERGY, bool TABLE>
 __device__ __forceinline__ void pair_tile(const float (&xi)[B], const float (&yi)[B],
                                           const float (&zi)[B], const float (&hsi)[B],
                                           const float (&sei)[B], const float (&qi)[B],
                                           float (&fxi)[B], float (&fyi)[B], float (&fzi)[B],
                                           const float4* pj_s, const float4* cj_s, float4* fj_s,
-                                          unsigned long long mask, double& e_acc) {
+                                          const float4* tab, int L, unsigned long long mask,
+                                          double& e_acc) {
 #pragma unroll
     for (int b = 0; b < B; ++b) {
         const float4 pj = pj_s[b];
-        const float4 cj = cj_s[b];
+        float4 cj = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (!TABLE) cj = cj_s[b];
         float fxj = 0.0f, fyj = 0.0f, fzj = 0.0f;
 #pragma unroll
         for (int a = 0; a < B; ++a) {
             const float dx = pj.x - xi[a];
             const float dy = pj.y - yi[a];
             const float dz = pj.z - zi[a];
+            float sig2, eps, qq;
+            if (TABLE) {
+                const float4 t = tab[(b * B + a) * L];
+                sig2 = t.x;
+                eps = t.y;
+                qq = t.z;
+            } else {
+                const float sg = hsi[a] + cj.x;
+                sig2 = sg * sg;
+                eps = sei[a] * cj.y;
+                qq = qi[a] * cj.z;
+            }
             float fs, e;
-            pair_lj_coul<ENERGY>(dx, dy, dz, hsi[a] + cj.x, sei[a] * cj.y, qi[a] * cj.z, fs, e);
+            pair_lj_coul<ENERGY>(dx, dy, dz, sig2, eps, qq, fs, e);
             if (MASKED) {
                 const bool skip = (mask >> (a * B + b)) & 1ull;
                 fs = skip ? 0.0f : fs;
@@ -438,7 +459,7 @@ __device__ __forceinline__ void bonded_colored_energy(const unsigned char* sm, c
 // Forces on the lane's B atoms (registers fx, fy, fz); positions must already
 // be in shared memory and the lane's force slots zeroed, with a __syncwarp
 // after both.
-template <int B, bool CHAIN, bool ENERGY>
+template <int B, bool CHAIN, bool ENERGY, bool TABLE = false>
 __device__ __forceinline__ void compute_forces(const unsigned char* sm, const TopoLayout& lay,
                                                const float4* prm, const float4* pos, float4* frc,
                                                const unsigned long long* masks, int L, int g,
@@ -458,9 +479,9 @@ __device__ __forceinline__ void compute_forces(const unsigned char* sm, const To
 #pragma unroll
             for (int b = a + 1; b < B; ++b) {
                 const float dx = xi[b] - xi[a], dy = yi[b] - yi[a], dz = zi[b] - zi[a];
+                const float sg = hsi[a] + hsi[b];
                 float fs, e;
-                pair_lj_coul<ENERGY>(dx, dy, dz, hsi[a] + hsi[b], sei[a] * sei[b], qi[a] * qi[b],
-                                     fs, e);
+                pair_lj_coul<ENERGY>(dx, dy, dz, sg * sg, sei[a] * sei[b], qi[a] * qi[b], fs, e);
                 const bool skip = (m >> (a * B + b)) & 1ull;
                 fs = skip ? 0.0f : fs;
                 fx[a] = fmaf(-fs, dx, fx[a]);
@@ -482,13 +503,16 @@ __device__ __forceinline__ void compute_forces(const unsigned char* sm, const To
             int J = g + t;
             J = (J >= L) ? J - L : J;
             const int sJ = J * C::BS;
+            const float4* tab = nullptr;
+            if (TABLE)
+                tab = reinterpret_cast<const float4*>(sm + lay.off_ptab) + (size_t)(t - 1) * B * B * L + g;
             const unsigned long long m = masks[t * L + g];
             if (m == 0ull)
-                pair_tile<B, false, ENERGY>(xi, yi, zi, hsi, sei, qi, fx, fy, fz, pos + sJ, prm + sJ,
-                                            frc + sJ, m, e_acc);
+                pair_tile<B, false, ENERGY, TABLE>(xi, yi, zi, hsi, sei, qi, fx, fy, fz, pos + sJ,
+                                                   prm + sJ, frc + sJ, tab, L, m, e_acc);
             else
-                pair_tile<B, true, ENERGY>(xi, yi, zi, hsi, sei, qi, fx, fy, fz, pos + sJ, prm + sJ,
-                                           frc + sJ, m, e_acc);
+                pair_tile<B, true, ENERGY, TABLE>(xi, yi, zi, hsi, sei, qi, fx, fy, fz, pos + sJ,
+                                                  prm + sJ, frc + sJ, tab, L, m, e_acc);
         }
         __syncwarp(gmask);
     }
@@ -531,8 +555,9 @@ __device__ __noinline__ double energy_pass(const unsigned char* sm, const TopoLa
 #pragma unroll
             for (int b = a + 1; b < B; ++b) {
                 if ((m >> (a * B + b)) & 1ull) continue;
+                const float sg = hsi[a] + hsi[b];
                 float fs, e;
-                pair_lj_coul<true>(xi[b] - xi[a], yi[b] - yi[a], zi[b] - zi[a], hsi[a] + hsi[b],
+                pair_lj_coul<true>(xi[b] - xi[a], yi[b] - yi[a], zi[b] - zi[a], sg * sg,
                                    sei[a] * sei[b], qi[a] * qi[b], fs, e);
                 e_acc += (double)e;
             }
@@ -551,8 +576,9 @@ __device__ __noinline__ double energy_pass(const unsigned char* sm, const TopoLa
 #pragma unroll
             for (int a = 0; a < B; ++a) {
                 if ((m >> (a * B + b)) & 1ull) continue;
+                const float sg = hsi[a] + cj.x;
                 float fs, e;
-                pair_lj_coul<true>(pj.x - xi[a], pj.y - yi[a], pj.z - zi[a], hsi[a] + cj.x,
+                pair_lj_coul<true>(pj.x - xi[a], pj.y - yi[a], pj.z - zi[a], sg * sg,
                                    sei[a] * cj.y, qi[a] * cj.z, fs, e);
                 e_acc += (double)e;
             }
@@ -580,7 +606,7 @@ __device__ __forceinline__ double group_sum(double v, unsigned gmask, int base, 
 // group, lanes base .. base+L-1 of the warp, mask gmask); pos / frc are the
 // group's shared-memory slots.  Used by the single-molecule kernel and by the
 // batched kernel.
-template <int B, bool CHAIN>
+template <int B, bool CHAIN, bool TABLE = false>
 __device__ __forceinline__ void advance_replica(const PropParams& p, const unsigned char* sm,
                                                 const float4* prm,
                                                 const unsigned long long* masks, float4* pos,
@@ -649,8 +675,8 @@ __device__ __forceinline__ void advance_replica(const PropParams& p, const unsig
             }
             __syncwarp(gmask);
         }
-        compute_forces<B, CHAIN, false>(sm, lay, prm, pos, frc, masks, L, g, gmask, xi, yi, zi,
-                                        hsi, sei, qi, fx, fy, fz, e_acc);
+        compute_forces<B, CHAIN, false, TABLE>(sm, lay, prm, pos, frc, masks, L, g, gmask, xi, yi,
+                                               zi, hsi, sei, qi, fx, fy, fz, e_acc);
         if (s >= 0) {
 #pragma unroll
             for (int a = 0; a < B; ++a) {                   // B
@@ -716,7 +742,7 @@ __device__ __forceinline__ void advance_replica(const PropParams& p, const unsig
     __syncwarp(gmask);
 }
 
-template <int B, bool CHAIN>
+template <int B, bool CHAIN, bool TABLE>
 __global__ void __launch_bounds__(256, PropCfg<B>::MIN_BLOCKS) propagate_kernel(const PropParams p) {
     using C = PropCfg<B>;
     extern __shared__ float4 smem4[];
@@ -747,13 +773,13 @@ __global__ void __launch_bounds__(256, PropCfg<B>::MIN_BLOCKS) propagate_kernel(
 
     for (long long k = (long long)blockIdx.x * rpb + slot_local; k < p.R;
          k += (long long)gridDim.x * rpb)
-        advance_replica<B, CHAIN>(p, sm, prm, masks, pos, frc, k, L, g, base, gmask);
+        advance_replica<B, CHAIN, TABLE>(p, sm, prm, masks, pos, frc, k, L, g, base, gmask);
 }
 
-template <int B, bool CHAIN>
+template <int B, bool CHAIN, bool TABLE>
 cudaError_t propagate_launch_one(const PropParams* p, int warps, int grid, size_t smem,
                                  cudaStream_t s, int* blocks_per_sm) {
-    auto kern = propagate_kernel<B, CHAIN>;
+    auto kern = propagate_kernel<B, CHAIN, TABLE>;
     static size_t configured = 0;
     if (smem > configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -766,13 +792,16 @@ cudaError_t propagate_launch_one(const PropParams* p, int warps, int grid, size_
     return cudaGetLastError();
 }
 
+// chain: the linear-chain bonded layout; table: the layout carries the
+// pair-parameter table (chain layouts only)
 template <int B>
-cudaError_t propagate_dispatch_b(const PropParams* p, bool chain, int warps, int grid, size_t smem,
-                                 cudaStream_t s, int* blocks_per_sm) {
+cudaError_t propagate_dispatch_b(const PropParams* p, bool chain, bool table, int warps, int grid,
+                                 size_t smem, cudaStream_t s, int* blocks_per_sm) {
     if constexpr (B >= 3) {
-        if (chain) return propagate_launch_one<B, true>(p, warps, grid, smem, s, blocks_per_sm);
+        if (chain && table) return propagate_launch_one<B, true, true>(p, warps, grid, smem, s, blocks_per_sm);
+        if (chain) return propagate_launch_one<B, true, false>(p, warps, grid, smem, s, blocks_per_sm);
     }
-    return propagate_launch_one<B, false>(p, warps, grid, smem, s, blocks_per_sm);
+    return propagate_launch_one<B, false, false>(p, warps, grid, smem, s, blocks_per_sm);
 }
 
 }  // namespace pamd
