@@ -254,8 +254,9 @@ def run_gpu(args, w):
         sizes = batch_sizes(w)
         tops = [pi.make_chain(n, m + 1) for m, n in enumerate(sizes)]
         top = tops[int(np.argmax(sizes))]
+        # per-molecule launch shapes by measurement among the batched kernel's shapes (untimed)
         ctx = pamd.pamd_init_batch(tops, [R] * len(tops), [temps[0]] * len(tops), seed,
-                                   pamd.torch_options(gamma_per_ps=w["gamma"]))
+                                   pamd.torch_options(gamma_per_ps=w["gamma"], autotune=1))
         pop = pamd.Population.__new__(pamd.Population)
         pop.ctx, pop.top, pop.R = ctx, top, R * len(tops)
         tune = {"per_molecule": [pamd.pamd_info(pamd.pamd_batch_sub(ctx, m)) for m in range(len(tops))]}

@@ -589,6 +589,16 @@ struct TuneKey {
 struct TuneShape {
     int L, W, paired;
 };
+// Shapes a tuning run may choose: atoms per lane bmin..bmax, the given warp
+// counts, packed two-replica kernels or not.  The batched kernel needs
+// B = 3..7, kBatchThreads / 32 warps and single replicas.
+struct TuneLimits {
+    int bmin, bmax;
+    bool paired_ok;
+    std::vector<int> warps;
+    int key_tag;  // separates the cache entries of restricted searches
+};
+int autotune_with(pamd_ctx* c, int32_t theta_probe, const TuneLimits& lim, pamd_tune* out);
 std::mutex g_tune_mu;
 std::vector<std::pair<TuneKey, TuneShape>> g_tune;
 
@@ -1075,6 +1085,14 @@ int pamd_init_batch(pamd_ctx** out, int32_t n_mol, const pamd_topology* tops, co
             return bail(rc, msg);
         }
         c->subs.push_back(sub);
+        if (o.autotune && sub->N >= 3) {
+            // measured choice among the batched kernel's shapes
+            const int trc = autotune_with(sub, 20, TuneLimits{3, 7, false, {kBatchThreads / 32}, -2}, nullptr);
+            if (trc && trc != PAMD_EUNSUPPORTED) {
+                const std::string msg = "molecule " + std::to_string(m) + ": " + g_err;
+                return bail(trc, msg);
+            }
+        }
         if (sub->warps_per_block != kBatchThreads / 32 || sub->lay.per_lane < 3 || sub->lay.per_lane > 7)
             return bail(PAMD_EUNSUPPORTED, "molecule " + std::to_string(m) + " does not fit the batched kernel");
         c->R += R[m];
@@ -1431,6 +1449,15 @@ int pamd_autotune(pamd_ctx* c, int32_t theta_probe, pamd_tune* out) {
     if (rc) return rc;
     if (is_batch(c)) return fail(PAMD_EINVAL, "batch context: call this on pamd_batch_sub(ctx, m)");
     if (theta_probe < 1 || theta_probe > 1000) return fail(PAMD_EINVAL, "theta_probe must be 1..1000");
+    return autotune_with(c, theta_probe, TuneLimits{1, 8, true, {2, 4, 8}, 0}, out);
+}
+
+}  // extern "C"
+
+namespace {
+
+int autotune_with(pamd_ctx* c, int32_t theta_probe, const TuneLimits& lim, pamd_tune* out) {
+    int rc = PAMD_OK;
     // the shapes tuned are those of the exact-force kernel
     struct ModelDetach {
         pamd_ctx* c;
@@ -1444,7 +1471,7 @@ int pamd_autotune(pamd_ctx* c, int32_t theta_probe, pamd_tune* out) {
     }
     const pamd_topology t = c->host_top.view();
     const int chain = (int)is_linear_chain(&t);
-    const TuneKey key{c->N, c->R, chain, c->lanes_req};
+    const TuneKey key{c->N, c->R, chain, lim.key_tag ? lim.key_tag : c->lanes_req};
     TuneShape best_shape{0, 0, 0};
     double best_ms = 0.0;
     bool cached = tune_cache_lookup(key, &best_shape);
@@ -1475,15 +1502,15 @@ int pamd_autotune(pamd_ctx* c, int32_t theta_probe, pamd_tune* out) {
         PAMD_CU(c, cudaEventCreate(&e1));
         double best = 1e300;
         std::vector<TuneShape> shapes;
-        for (int b = 1; b <= 8; ++b) {
+        for (int b = lim.bmin; b <= lim.bmax; ++b) {
             int l = c->lanes_req ? c->lanes_req : (c->N + b - 1) / b;
             if (l > 32) continue;
             const int bb = (c->N + l - 1) / l;
-            if (bb > 8) continue;
+            if (bb < lim.bmin || bb > lim.bmax) continue;
             l = (c->N + bb - 1) / bb;
-            for (int paired = 0; paired <= 1; ++paired) {
+            for (int paired = 0; paired <= (lim.paired_ok ? 1 : 0); ++paired) {
                 if (paired && (bb < 2 || bb > 4)) continue;
-                for (int w : {2, 4, 8}) {
+                for (int w : lim.warps) {
                     bool dup = false;
                     for (auto& s2 : shapes) dup = dup || (s2.L == l && s2.W == w && s2.paired == paired);
                     if (!dup) shapes.push_back({l, w, paired});
@@ -1540,6 +1567,10 @@ int pamd_autotune(pamd_ctx* c, int32_t theta_probe, pamd_tune* out) {
     }
     return PAMD_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 int pamd_get_counters(pamd_ctx* c, uint32_t* step, uint32_t* ridx, double* sum_lnQ) {
     int rc = check_ctx(c);

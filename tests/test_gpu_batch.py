@@ -147,3 +147,28 @@ def test_sixteen_uneven_molecules(lib, orc):
             assert np.abs(E[sample] - eo).max() < 1e-4 * np.abs(eo).max()
     finally:
         lib.pamd_destroy(batch)
+
+
+def test_batch_autotuned_shapes(lib, orc):
+    """With autotuning each molecule gets a measured shape among the batched
+    kernel's (3..7 atoms per lane), and the batch still matches the oracle."""
+    sizes, R = [22, 75, 130], 256
+    tops = [pi.make_chain(n, 30 + n) for n in sizes]
+    T, dt, seed = 700.0, 0.001, 5
+    o = lib.pamd_options_default()
+    o.autotune = 1
+    batch = lib.pamd_init_batch(tops, [R] * 3, [T] * 3, seed, o)
+    try:
+        subs = [lib.pamd_batch_sub(batch, m) for m in range(3)]
+        for s_ in subs:
+            assert 3 <= lib.pamd_info(s_)["atoms_per_lane"] <= 7
+        starts = [lib.pamd_get_state(s_) for s_ in subs]
+        lib.pamd_propagate(batch, 6, dt, T)
+        for m in range(3):
+            x, _, _, _ = lib.pamd_get_state(subs[m])
+            sample = np.array([0, R - 1])
+            xo, _, _ = orc.propagate(tops[m], starts[m][0][sample], starts[m][1][sample], 6, dt, T,
+                                     1.0, seed, 0, mol=m, slots=sample)
+            assert np.abs(x[sample] - xo).max() < 1e-4
+    finally:
+        lib.pamd_destroy(batch)
