@@ -213,9 +213,21 @@ __global__ void weights_top_kernel(unsigned long long* blk_w, const double* blk_
         if (threadIdx.x == 0) carry = c + tot;
         __syncthreads();
     }
+    // S = sum of the block sums in a fixed order: each thread a contiguous
+    // chunk, then a fixed shuffle tree per warp, then the warps in order
+    __shared__ double wsum[32];
+    double part = 0.0;
+    {
+        const int per = (nblk + blockDim.x - 1) / blockDim.x;
+        const int lo = threadIdx.x * per, hi = min(lo + per, nblk);
+        for (int b = lo; b < hi; ++b) part += blk_e[b];
+    }
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = part;
+    __syncthreads();
     if (threadIdx.x == 0) {
         double S = 0.0;
-        for (int b = 0; b < nblk; ++b) S += blk_e[b];
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) S += wsum[w];
         s->S = S;
         s->C_total = carry;
         const double lnq = s->m + (log(S) - log((double)R));
@@ -323,9 +335,16 @@ __global__ void cnt_top_kernel(int32_t* blk_sum, const int32_t* blk_max, int nbl
         if (threadIdx.x == 0) carry = c + tot;
         __syncthreads();
     }
+    // largest count: an integer max, the same in any order
+    __shared__ int32_t wmax[32];
+    int32_t mloc = 0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) mloc = max(mloc, blk_max[b]);
+    for (int o = 16; o > 0; o >>= 1) mloc = max(mloc, __shfl_down_sync(0xffffffffu, mloc, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = mloc;
+    __syncthreads();
     if (threadIdx.x == 0) {
         int32_t m = 0;
-        for (int b = 0; b < nblk; ++b) m = max(m, blk_max[b]);
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, wmax[w]);
         s->max_copies = m;
     }
 }
