@@ -217,6 +217,28 @@ def config_of(w, args):
             "l2": "flushed (512 MB write) between timed steps"}
 
 
+# ------------------------------------------------------- multi-rank logic
+
+def rank_seed(seed: int, rank: int) -> int:
+    """Run seed of rank `rank`: every GPU anneals an independent population."""
+    return seed + 7919 * rank
+
+
+def max_over_ranks(x: float, dist=None, device: str = "cpu") -> float:
+    """The largest of the ranks' values (the job is as slow as its slowest rank)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world: int, max_seconds: float) -> float:
+    """Whole-job units per second: all ranks' units over the slowest rank's time."""
+    return units_per_rank * world / max_seconds
+
+
 # ----------------------------------------------------------------- GPU leg
 
 def run_gpu(args, w):
@@ -246,7 +268,7 @@ def run_gpu(args, w):
 
     temps = pi.geometric_schedule(w["T0"], w["TK"], w["K"])
     R, theta, dt = args.replicas or w["R"], w["theta"], w["dt"]
-    seed = w["seed"] + 7919 * rank
+    seed = rank_seed(w["seed"], rank)
     # the library launches on this stream; the timing events are recorded on it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
@@ -295,15 +317,12 @@ def run_gpu(args, w):
     if dist:
         dist.barrier()
     clocks = sampler.stop()
-    t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    max_ms = float(t.item())
+    max_ms = max_over_ranks(elapsed_ms, dist, "cuda")
     total_units = atom_steps(w, R) * args.steps * world
     if w.get("batch"):
         # one batched launch advances all molecules; no single-kernel roofline
         pop.close()
-        line = {"metric": METRIC, "value": total_units / (max_ms / 1e3), "unit": UNIT,
+        line = {"metric": METRIC, "value": job_throughput(total_units / world, world, max_ms / 1e3), "unit": UNIT,
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -314,7 +333,7 @@ def run_gpu(args, w):
         if dist:
             dist.destroy_process_group()
         return
-    value = total_units / (max_ms / 1e3)
+    value = job_throughput(total_units / world, world, max_ms / 1e3)
 
     # dominant kernel: the persistent propagate launch, timed alone in the
     # same shape (theta steps over all R replicas) with events on its stream
@@ -356,10 +375,8 @@ def run_gpu(args, w):
     np_ = (w["n_atoms"] + 3) // 4 * 4
     h2d = R * 6 * np_ * 4 + R * 4 + 8
     d2h = (w["K"] + 1) * ctypes.sizeof(pamd.PamdObs) + 48
-    e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e = {"value": atom_steps(w, R) * e2e_steps * world / float(e2e_t.item()), "unit": UNIT,
+    e2e_max = max_over_ranks(e2e_s, dist, "cuda")
+    e2e = {"value": job_throughput(atom_steps(w, R) * e2e_steps, world, e2e_max), "unit": UNIT,
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "final_e_pot_kJmol": obs[-1]["e_pot"], "final_sum_lnQ": obs[-1]["sum_lnQ"]}
     pop.close()
