@@ -2,17 +2,20 @@
 // for the dense layers of the MLP energy surrogate.
 //
 // C[M x N] (FP32) = A[M x K] . B[N x K]^T, A and B row-major BF16 (both
-// "K-major").  Persistent kernel, one CTA per SM, 128 x 256 output tiles
-// taken in row-major tile order (tiles of one row block share A in L2), six
-// warps with fixed roles:
-//   * one thread of warp 0 streams 128 x 64 tiles of A and 256 x 64 tiles of
-//     B with TMA (cp.async.bulk.tensor, 128-byte swizzle, out-of-range rows
-//     and columns zero-filled) into a ring of kStages shared-memory stages,
-//     each completing a transaction-count mbarrier;
+// "K-major").  Persistent kernel, one CTA per SM, in clusters of two CTAs
+// that compute the 128 x 256 output tiles of two adjacent row blocks in the
+// same column block, so that the 256 x 64 B tile of each k-step is read from
+// L2 once per cluster instead of once per CTA.  Six warps with fixed roles:
+//   * one thread of warp 0 streams the CTA's 128 x 64 tile of A and its half
+//     (128 x 64) of the shared B tile with TMA (cp.async.bulk.tensor, 128-byte
+//     swizzle, out-of-range rows and columns zero-filled), the B half
+//     multicast into both CTAs' stage, into a ring of kStages shared-memory
+//     stages, each completing a transaction-count mbarrier; a stage is
+//     refilled once the products of both CTAs have read it;
 //   * one thread of warp 1 issues four tcgen05.mma (M 128, N 256, K 16) per
 //     stage into one of two FP32 accumulators of 256 tensor-memory columns,
-//     frees each stage with tcgen05.commit, and commits the accumulator when
-//     a tile's last product is issued;
+//     frees each stage in both CTAs with a multicast tcgen05.commit, and
+//     commits the accumulator when a tile's last product is issued;
 //   * warps 2..5 drain a finished accumulator with tcgen05.ld (warp w reads
 //     tensor-memory lanes 32 (w mod 4) ..), apply the bias and the layer's
 //     output transform, store with 16-byte vector stores, and hand the
@@ -22,7 +25,10 @@
 // Every wait on an mbarrier is bounded: after kWaitLimit polls the waiting
 // role records PAMD_ETIMEOUT and raises a shared abort flag, the others stop
 // at their next wait, the CTA waits (bounded) for its own copies and products
-// in flight, frees its tensor memory and returns.
+// in flight, meets its partner at a cluster barrier (so that neither leaves
+// while the other may still write to it), frees its tensor memory and returns.
+// A partner that timed out stops feeding the other, whose own bounded waits
+// then run out as well.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -119,6 +125,39 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t adesc, uint64_t
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
         ::"r"(tmem), "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+// TMA load multicast to the CTAs of the cluster in `mask`: the tile lands at
+// the same shared-memory offset in each and completes each one's mbarrier at
+// the same offset
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                               uint32_t bar, uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        ".multicast::cluster [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar), "h"(mask)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                     : "memory");
+}
+
+// arrive on the mbarrier at this offset in every CTA of `mask` once the
+// products issued so far are done
+__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            bar),
+        "h"(mask)
         : "memory");
 }
 
@@ -252,7 +291,8 @@ __device__ __forceinline__ void epilogue_tile(const GemmArgs& g, uint32_t taddr,
     if (g.epi == kEpiHead && row_ok) g.part[(size_t)row * ntiles + ntile] = head;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA,
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
+    gemm_bf16_kernel(const __grid_constant__ CUtensorMap tmA,
                                                                 const __grid_constant__ CUtensorMap tmB,
                                                                 const __grid_constant__ GemmArgs g) {
     extern __shared__ unsigned char smem_raw[];
@@ -263,9 +303,14 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_bf16_kernel(const __grid_con
     // 1024-byte aligned stages: [A0 | B0 | A1 | B1 | ...]
     const uint32_t base = (smem_u32(smem_raw) + 1023u) & ~1023u;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // The two CTAs of a cluster take row blocks 2p and 2p + 1 of the same
+    // column block: each loads its A tile and half of the shared B tile,
+    // multicast to both.
     const int MT = (g.M + kBM - 1) / kBM, NT = (g.N + kBN - 1) / kBN;
-    const int tiles = MT * NT;
+    const int tiles = ((MT + 1) / 2) * NT;  // tile pairs
     const int KB = (g.K + kBK - 1) / kBK;
+    const int crank = (int)cluster_rank();
+    const int cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
 
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -277,7 +322,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_bf16_kernel(const __grid_con
     if (tid == 0) {
         for (int st = 0; st < kStages; ++st) {
             mbar_init(smem_u32(&full_bar[st]), 1);
-            mbar_init(smem_u32(&empty_bar[st]), 1);
+            mbar_init(smem_u32(&empty_bar[st]), 2);  // both CTAs' products have read it
         }
         for (int q = 0; q < 2; ++q) {
             mbar_init(smem_u32(&accf_bar[q]), 1);
@@ -292,6 +337,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_bf16_kernel(const __grid_con
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    cluster_sync();  // the peer's barriers exist before any multicast reaches them
     const uint32_t tmem = tmem_slot;
     volatile int* abort_flag = &s_abort;
 
@@ -299,8 +345,14 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_bf16_kernel(const __grid_con
         if (lane == 0) {  // TMA producer
             long long gk = 0;
             bool stop = false;
-            for (int t = blockIdx.x; t < tiles && !stop; t += gridDim.x) {
-                const int m0 = (t / NT) * kBM, n0 = (t % NT) * kBN;
+            for (int t = cid; t < tiles && !stop; t += ncl) {
+                // A box of an odd last row block's missing partner, or a B half
+                // past column N, would lie wholly outside its matrix: read a
+                // valid box instead (its products land in rows / columns the
+                // epilogue drops)
+                const int n0 = (t % NT) * kBN;
+                const int ya = min((2 * (t / NT) + crank) * kBM, (MT - 1) * kBM);
+                const int yb = (n0 + crank * (kBN / 2) < g.N) ? n0 + crank * (kBN / 2) : n0;
                 for (int kb = 0; kb < KB; ++kb, ++gk) {
                     const int st = (int)(gk % kStages);
                     if (gk >= kStages &&
@@ -314,18 +366,23 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_bf16_kernel(const __grid_con
                     const uint32_t fb = smem_u32(&full_bar[st]);
                     const uint32_t ta = base + (uint32_t)(st * kStageBytes);
                     mbar_expect_tx(fb, (uint32_t)kStageBytes);
-                    tma_load_2d(ta, &tmA, kb * kBK, m0, fb);
-                    tma_load_2d(ta + kTileA, &tmB, kb * kBK, n0, fb);
+                    tma_load_2d(ta, &tmA, kb * kBK, ya, fb);
+                    tma_load_2d_mc(ta + kTileA + crank * (kTileB / 2), &tmB, kb * kBK, yb, fb,
+                                   (uint16_t)0x3);
                 }
             }
             s_issued = (int)gk;
+            // the peer's last releases of this CTA's stages land before it exits
+            for (long long u = gk > kStages ? gk - kStages : 0; u < gk && !*abort_flag; ++u)
+                if (!mbar_wait(smem_u32(&empty_bar[u % kStages]), (uint32_t)((u / kStages) & 1)))
+                    *abort_flag = 1;
         }
     } else if (warp == 1) {
         if (lane == 0) {  // MMA issuer
             long long gk = 0;
             int i = 0;
             bool stop = false;
-            for (int t = blockIdx.x; t < tiles && !stop; t += gridDim.x, ++i) {
+            for (int t = cid; t < tiles && !stop; t += ncl, ++i) {
                 const int acc = i & 1;
                 if (i >= 2 && !mbar_wait(smem_u32(&acce_bar[acc]), (uint32_t)((i / 2 - 1) & 1))) {
                     *abort_flag = 1;
@@ -346,7 +403,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_bf16_kernel(const __grid_con
                     for (int k = 0; k < kBK / 16; ++k)
                         mma_bf16(td, sw128_desc(ta + k * 32), sw128_desc(ta + kTileA + k * 32),
                                  (kb > 0 || k > 0) ? 1u : 0u);
-                    mma_commit(smem_u32(&empty_bar[st]));
+                    mma_commit_mc(smem_u32(&empty_bar[st]), (uint16_t)0x3);
                 }
                 if (!stop) mma_commit(smem_u32(&accf_bar[acc]));
             }
@@ -357,13 +414,13 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_bf16_kernel(const __grid_con
     } else {  // epilogue warps 2..5
         const int q = warp & 3;  // tensor-memory lane quarter this warp may access
         int i = 0;
-        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
+        for (int t = cid; t < tiles; t += ncl, ++i) {
             const int acc = i & 1;
             if (!mbar_wait(smem_u32(&accf_bar[acc]), (uint32_t)((i / 2) & 1))) *abort_flag = 1;
             __syncwarp();
             if (*abort_flag) break;
             tc_fence_after();
-            const int m0 = (t / NT) * kBM, nt = t % NT;
+            const int m0 = (2 * (t / NT) + crank) * kBM, nt = t % NT;
             const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kBN);
             epilogue_tile(g, taddr, m0 + q * 32 + lane, nt * kBN, nt, NT);
             tc_fence_before();
@@ -383,6 +440,9 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_bf16_kernel(const __grid_con
     }
     tc_fence_before();
     __syncthreads();
+    // neither CTA leaves while the other may still write its shared memory or
+    // arrive on its barriers
+    cluster_sync();
     if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"((uint32_t)kTmemCols)
@@ -425,7 +485,7 @@ cudaError_t launch_gemm_bf16(const GemmArgs& ga, cudaStream_t s) {
         return cudaErrorInvalidValue;
     CUtensorMap tmA, tmB;
     if (!encode_operand(&tmA, ga.A, ga.M, ga.K, ga.lda, kBM) ||
-        !encode_operand(&tmB, ga.B, ga.N, ga.K, ga.ldb, kBN))
+        !encode_operand(&tmB, ga.B, ga.N, ga.K, ga.ldb, kBN / 2))
         return cudaErrorInvalidValue;
     GemmArgs g = ga;
     auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
@@ -435,16 +495,22 @@ cudaError_t launch_gemm_bf16(const GemmArgs& ga, cudaStream_t s) {
     const size_t smem = (size_t)kStages * kStageBytes + 1024;
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
-    static int num_sms = 0;
+    static int max_clusters = 0;
     std::call_once(once, [&] {
         attr = cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int dev = 0;
-        if (attr == cudaSuccess) attr = cudaGetDevice(&dev);
-        if (attr == cudaSuccess) attr = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+        // persistent grid: as many two-CTA clusters as can be resident at once
+        // (an SM left without a partner in its GPC hosts none)
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(2, 1, 1);
+        cfg.blockDim = dim3(kThreads, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        if (attr == cudaSuccess) attr = cudaOccupancyMaxActiveClusters(&max_clusters, gemm_bf16_kernel, &cfg);
+        if (attr == cudaSuccess && max_clusters < 1) attr = cudaErrorInvalidConfiguration;
     });
     if (attr != cudaSuccess) return attr;
-    const long long tiles = (long long)((g.M + kBM - 1) / kBM) * ((g.N + kBN - 1) / kBN);
-    const int grid = (int)(tiles < num_sms ? tiles : num_sms);
+    // one cluster per pair of row blocks and column block, at most max_clusters
+    const long long pairs = (long long)((g.M + 2 * kBM - 1) / (2 * kBM)) * ((g.N + kBN - 1) / kBN);
+    const int grid = 2 * (int)(pairs < max_clusters ? pairs : max_clusters);
     gemm_bf16_kernel<<<grid, kThreads, smem, s>>>(tmA, tmB, g);
     return cudaGetLastError();
 }
