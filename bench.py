@@ -446,22 +446,82 @@ def run_kernel(args, w):
                       "achieved_tflops": achieved, "frac": achieved / FP32_PEAK_TFLOPS}), flush=True)
 
 
-def run_precision(args):
-    """Large-population precision study (75-atom chain, 60 geometric steps
-    1000 -> 250 K, theta = 200): the mixed FP32/FP64 path against the all-FP64
-    GPU path at the same seeds, force errors against the FP64 oracle, and the
-    resampling throughput at R = 2^20.  Prints one JSON line."""
+def run_control(args):
+    """Resampling on and off (the measured-temperature and lowest-temperature
+    energy comparison of the paper's Figs. 2 and 4) on the 75-atom chain: the
+    paper's eight temperatures 700 ... 200 K and R = 10000 replicas, PA with
+    theta = 1000 and 4375 and the resampling-off anneal with theta = 4375, each
+    started from the same population equilibrated at 700 K.  Prints one JSON
+    line."""
     import numpy as np
     import torch
 
-    import oracle
     import pamd_inputs as pi
     from paper_1806_06016_gb300 import build as pbuild
     from paper_1806_06016_gb300 import pamd
 
     torch.cuda.set_device(0)
     pbuild.build()
-    oracle.build()
+    N, dt, seed = 75, 0.001, 12345
+    R = args.replicas or 10000
+    theta_eq = args.theta or 20000
+    temps = np.array([700.0, 585.0, 489.0, 409.0, 342.0, 286.0, 239.0, 200.0])
+    top = pi.make_chain(N, 1)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    # one equilibrated population at T0, copied into every run
+    with pamd.Population(top, R, temps[0], seed, pamd.torch_options()) as pop:
+        pop.propagate(theta_eq, dt, temps[0])
+        x0, v0, _, _ = pop.state()
+    runs = {}
+    for name, theta, resample in (("pa_theta1000", 1000, True), ("pa_theta4375", 4375, True),
+                                  ("anneal_theta4375", 4375, False)):
+        with pamd.Population(top, R, temps[0], seed + 1, pamd.torch_options()) as pop:
+            pop.set_state(x0, v0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            obs = pop.anneal(temps, theta, dt, resample=resample)
+            wall = time.perf_counter() - t0
+            _, _, E, fam = pop.state()
+        runs[name] = {
+            "theta": theta, "resample": resample, "wall_s": wall,
+            "atom_steps_per_s": N * R * theta * len(temps) / wall,
+            "T_m": [o["t_meas"] for o in obs],
+            "e_pot": [o["e_pot"] for o in obs], "e_pot_se": [o["e_pot_se"] for o in obs],
+            "rg": [o["rg"] for o in obs], "n_families": [o["n_families"] for o in obs],
+            "sum_lnQ": [o["sum_lnQ"] for o in obs],
+            "E_final": E,
+        }
+    out = {"mode": "control", "n_atoms": N, "replicas": R, "dt_ps": dt, "theta_equilibration": theta_eq,
+           "T_K": temps.tolist()}
+    for name, r in runs.items():
+        E = r.pop("E_final")
+        q = np.quantile(E, [0.05, 0.25, 0.5, 0.75, 0.95])
+        r["E_final_quantiles_5_25_50_75_95"] = [float(v) for v in q]
+        r["T_m_minus_T_max_K"] = float(np.max(np.abs(np.array(r["T_m"]) - temps)))
+        out[name] = r
+    # lowest temperature: PA vs anneal, mean difference in combined family-binned errors
+    a, b = out["pa_theta4375"], out["anneal_theta4375"]
+    d = b["e_pot"][-1] - a["e_pot"][-1]
+    out["anneal_minus_pa_e_pot_200K"] = {"kJmol": d, "combined_se": float(np.hypot(a["e_pot_se"][-1], b["e_pot_se"][-1]))}
+    print(json.dumps(out), flush=True)
+
+
+def run_precision(args):
+    """Large-population precision study (75-atom chain, 60 geometric steps
+    1000 -> 250 K, theta = 200): the mixed FP32/FP64 path against the all-FP64
+    GPU path at the same seeds, the mixed path's force error against the FP64
+    path on the same configurations, and the
+    resampling throughput at R = 2^20.  Prints one JSON line."""
+    import numpy as np
+    import torch
+
+    import pamd_inputs as pi
+    from paper_1806_06016_gb300 import build as pbuild
+    from paper_1806_06016_gb300 import pamd
+
+    torch.cuda.set_device(0)
+    pbuild.build()
     N, theta, K, dt, seed = 75, 200, 60, 0.001, 12345
     R = args.replicas or 2048
     top = pi.make_chain(N, 1)
@@ -517,15 +577,15 @@ def run_precision(args):
     out["anneal_ms"] = {"mixed": ms32, "fp64": ms64}
     out["families_final"] = {"mixed": [r[0][-1]["n_families"] for r in runs[0]],
                              "fp64": [r[0][-1]["n_families"] for r in runs[1]]}
-    # force errors on the final configurations (64 replicas) against the oracle
-    t = oracle.Topo(top)
-    num32 = num64 = den = 0.0
-    for k in range(0, R, max(1, R // 64)):
-        _, fo, _ = oracle.energy_forces(t, x32[k])
-        num32 += float(np.sum((f32[k] - fo) ** 2)); den += float(np.sum(fo ** 2))
-        _, fo64, _ = oracle.energy_forces(t, x64[k])
-        num64 += float(np.sum((f64[k] - fo64) ** 2))
-    out["force_rel_rmse"] = {"mixed": math.sqrt(num32 / den), "fp64": math.sqrt(num64 / den)}
+    # force error of the mixed path on its final configurations, against the
+    # all-FP64 GPU path evaluated on the same configurations (that path is held
+    # to the FP64 oracle at 1e-10 by the parity tests)
+    ref = pamd.Population(top, R, temps[0], seed, pamd.torch_options(precision=1))
+    ref.set_state(x32, np.zeros_like(x32))
+    f_ref, _ = ref.forces()
+    ref.close()
+    out["force_rel_rmse_vs_fp64_gpu"] = {
+        "mixed": math.sqrt(float(np.sum((f32 - f_ref) ** 2)) / float(np.sum(f_ref ** 2)))}
     # resampling at R = 2^20: whole chain (weights, scans, counts, gather)
     big = 1 << 20
     pop = pamd.Population(top, big, 1000.0, seed, pamd.torch_options())
@@ -941,9 +1001,10 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", choices=["anneal", "kernel", "precision", "resample", "gemm", "surrogate",
-                                       "surrogate_kernel"],
+                                       "surrogate_kernel", "control"],
                     default="anneal")
-    ap.add_argument("--theta", type=int, default=0, help="kernel mode: steps per launch")
+    ap.add_argument("--theta", type=int, default=0,
+                    help="kernel mode: steps per launch; control mode: equilibration steps at 700 K")
     ap.add_argument("--replicas", type=int, default=0,
                     help="population size (per molecule for the batched workload); default: the workload's")
     ap.add_argument("--lanes", type=int, default=0, help="kernel mode: lanes per replica")
@@ -966,6 +1027,8 @@ def main():
         run_kernel(args, w)
     elif args.mode == "precision":
         run_precision(args)
+    elif args.mode == "control":
+        run_control(args)
     elif args.mode == "resample":
         run_resample(args)
     elif args.mode == "gemm":

@@ -360,6 +360,33 @@ def test_c1_anneal_statistical_parity(lib, orc):
     assert np.all(np.abs(g - o) <= 3 * s), (g - o) / s
 
 
+def test_c1_anneal_control_statistical_parity(lib, orc):
+    """The resampling-off anneal (every copy kept once, velocities rescaled):
+    same statistics as the oracle's, and no family is ever pruned."""
+    top = pi.make_chain(22, 1)
+    temps = pi.geometric_schedule(1000.0, 300.0, 20)
+    R, theta, dt, gamma, seed = 256, 100, 0.001, 1.0, 4321
+    ctx = lib.pamd_init(top, R, temps[0], seed, _opts(lib, gamma_per_ps=gamma))
+    try:
+        og = lib.pamd_anneal(ctx, temps, theta, dt, resample=False)
+        _, _, _, fam = lib.pamd_get_state(ctx)
+    finally:
+        lib.pamd_destroy(ctx)
+    oo, _, _, ofam, _ = orc.anneal(top, R, temps, theta, dt, gamma, seed, resample=False)
+    np.testing.assert_array_equal(fam, np.arange(R))
+    np.testing.assert_array_equal(ofam, np.arange(R))
+    assert all(o["n_families"] == R for o in og)
+    for key, se in (("e_pot", "e_pot_se"), ("e_kin", "e_kin_se"), ("rg", "rg_se")):
+        g = np.array([o[key] for o in og])
+        o = np.array([o[key] for o in oo])
+        s = np.sqrt(np.array([x[se] for x in og]) ** 2 + np.array([x[se] for x in oo]) ** 2)
+        assert np.all(np.abs(g - o) <= 3 * s), (key, (g - o) / s)
+    # ln Q is still recorded (it estimates the free-energy steps from the
+    # unresampled population); the two sides agree statistically
+    lg = np.array([o["sum_lnQ"] for o in og]); lo = np.array([o["sum_lnQ"] for o in oo])
+    assert np.all(np.abs(lg - lo) <= 0.05 * np.abs(lo) + 1.0), lg - lo
+
+
 def test_harmonic_chain_closed_forms_on_gpu(lib):
     n, kb = 6, 400.0
     top = pi.make_harmonic_chain(n, kb, 0.0)
