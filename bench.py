@@ -507,6 +507,76 @@ def run_control(args):
     print(json.dumps(out), flush=True)
 
 
+def run_wham(args):
+    """WHAM refinement of the free energies (free-energy paragraph).  (1) The
+    75-atom R = 8192 anneal (theta = 1000, 100 steps 1000 -> 250 K) records its
+    energies at all 101 temperatures; WHAM seeded with the running sum of ln Q
+    refines ln Z(T_i) and reweights <E> to the midpoints of the schedule.  (2)
+    Synthetic energies shaped like the R = 2^20 anneal (61 temperatures x 2^20
+    samples, 512 MB): the histogram pass alone (no sweeps) and with 100 sweeps,
+    each call timed on the host (it synchronises).  Prints one JSON line."""
+    import numpy as np
+    import torch
+
+    import pamd_inputs as pi
+    from paper_1806_06016_gb300 import build as pbuild
+    from paper_1806_06016_gb300 import pamd
+
+    torch.cuda.set_device(0)
+    pbuild.build()
+    w = WORKLOADS["c2"]
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    sh = stream.cuda_stream
+    out = {"mode": "wham"}
+    R = args.replicas or w["R"]
+    temps = pi.geometric_schedule(w["T0"], w["TK"], w["K"])
+    top = pi.make_chain(w["n_atoms"], w["gen_seed"])
+    rec = torch.empty((len(temps), R), dtype=torch.float64, device="cuda")
+    with pamd.Population(top, R, temps[0], w["seed"], pamd.torch_options()) as pop:
+        pamd.pamd_record_energies(pop.ctx, rec.data_ptr(), len(temps))
+        obs = pop.anneal(temps, w["theta"], w["dt"])
+    z = np.array([o["sum_lnQ"] for o in obs])
+    mids = np.sqrt(temps[1:] * temps[:-1])
+    t0 = time.perf_counter()
+    g = pamd.pamd_wham(rec.data_ptr(), len(temps), R, temps, 2000, lnZ_init=z, max_iter=2000, tol=1e-10,
+                       T_eval=mids, stream=sh)
+    dt_call = time.perf_counter() - t0
+    e_pa = np.array([o["e_pot"] for o in obs])
+    # the PA means at neighbouring temperatures bracket the reweighted midpoint values
+    between = np.mean((g["e_mean_eval"] - e_pa[1:]) * (g["e_mean_eval"] - e_pa[:-1]) <= 0)
+    out["anneal"] = {
+        "workload": w["workload"], "n_bins": 2000, "sweeps": g["iterations"], "last_change": g["max_delta"],
+        "call_s": dt_call,
+        "lnZ_wham_minus_sum_lnQ_max_abs": float(np.max(np.abs(g["lnZ"] - (z - z[0])))),
+        "lnZ_final": {"wham": float(g["lnZ"][-1]), "sum_lnQ": float(z[-1] - z[0])},
+        "midpoint_e_mean_between_neighbours_fraction": float(between),
+    }
+    # synthetic large set: Gaussian energies whose mean and width follow the
+    # 75-atom chain's (mean from the PA run, width sqrt(k_B T^2 C_v) ~ 10 kJ/mol)
+    K4, R4 = 60, 1 << 20
+    t4 = pi.geometric_schedule(1000.0, 250.0, K4)
+    mean4 = np.ascontiguousarray(np.interp(t4[::-1], temps[::-1], e_pa[::-1])[::-1])
+    gen = torch.Generator(device="cuda").manual_seed(1)
+    E4 = torch.randn((K4 + 1, R4), dtype=torch.float64, device="cuda", generator=gen)
+    E4.mul_(torch.from_numpy(0.04 * t4).cuda()[:, None]).add_(torch.from_numpy(mean4).cuda()[:, None])
+    torch.cuda.synchronize()
+    times = {}
+    for name, iters in (("histograms_only", 0), ("sweeps_100", 100)):
+        ts = []
+        for _ in range(max(3, args.steps)):
+            t0 = time.perf_counter()
+            pamd.pamd_wham(E4.data_ptr(), K4 + 1, R4, t4, 4096, max_iter=iters, tol=0.0, stream=sh)
+            ts.append(time.perf_counter() - t0)
+        times[name] = statistics.median(ts)
+    nbytes = 8 * (K4 + 1) * R4
+    out["large"] = {"temperatures": K4 + 1, "samples_per_temperature": R4, "bytes": nbytes, "n_bins": 4096,
+                    "call_s": times,
+                    "histogram_call_GBps": nbytes / times["histograms_only"] / 1e9,
+                    "sweep_ms": 1e3 * (times["sweeps_100"] - times["histograms_only"]) / 100}
+    print(json.dumps(out), flush=True)
+
+
 def run_precision(args):
     """Large-population precision study (75-atom chain, 60 geometric steps
     1000 -> 250 K, theta = 200): the mixed FP32/FP64 path against the all-FP64
@@ -1001,7 +1071,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", choices=["anneal", "kernel", "precision", "resample", "gemm", "surrogate",
-                                       "surrogate_kernel", "control"],
+                                       "surrogate_kernel", "control", "wham"],
                     default="anneal")
     ap.add_argument("--theta", type=int, default=0,
                     help="kernel mode: steps per launch; control mode: equilibration steps at 700 K")
@@ -1029,6 +1099,8 @@ def main():
         run_precision(args)
     elif args.mode == "control":
         run_control(args)
+    elif args.mode == "wham":
+        run_wham(args)
     elif args.mode == "resample":
         run_resample(args)
     elif args.mode == "gemm":

@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "../../include/pamd_wham.h"
 #include "mlp_internal.h"
 #include "pamd_internal.h"
 
@@ -1234,6 +1235,25 @@ int pamd_observables(pamd_ctx* c, double T, pamd_obs* out) {
     return rc;
 }
 
+namespace {
+// Row i of the energy record (pamd_record_energies) <- the current energies.
+cudaError_t record_energies(pamd_ctx* c, int i) {
+    if (!c->rec_E || i >= c->rec_rows) return cudaSuccess;
+    return cudaMemcpyAsync(c->rec_E + (size_t)i * (size_t)c->R, cur_E(c), sizeof(double) * (size_t)c->R,
+                           cudaMemcpyDeviceToDevice, c->stream);
+}
+}  // namespace
+
+int pamd_record_energies(pamd_ctx* c, double* E_dev, int32_t rows) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (is_batch(c)) return fail(PAMD_EINVAL, "energy recording: single-molecule contexts only");
+    if (rows < 0 || (rows > 0 && !E_dev)) return fail(PAMD_EINVAL, "energy recording: rows >= 0, E_dev for rows > 0");
+    c->rec_E = rows > 0 ? E_dev : nullptr;
+    c->rec_rows = rows > 0 ? rows : 0;
+    return PAMD_OK;
+}
+
 int pamd_anneal(pamd_ctx* c, int32_t K, const double* T, int32_t theta, double dt_ps,
                 int32_t resample, pamd_obs* per_step_out) {
     int rc = check_ctx(c);
@@ -1250,6 +1270,8 @@ int pamd_anneal(pamd_ctx* c, int32_t K, const double* T, int32_t theta, double d
     key.resample = resample ? 1 : 0;
     key.dt = dt_ps;
     key.T.assign(T, T + K + 1);
+    key.rec = c->rec_E;
+    key.rec_rows = c->rec_rows;
     // the captured graph starts from the main buffers
     if (c->cur_is_alt) {
         const size_t st_bytes = state_bytes(c);
@@ -1264,6 +1286,7 @@ int pamd_anneal(pamd_ctx* c, int32_t K, const double* T, int32_t theta, double d
         PAMD_CU(c, launch_set_counters(c, c->step, c->resample_index));
         int err = launch_prop(c, theta, dt_ps, T[0], c->b.counters, 0u, nullptr);
         if (!err && launch_observe(c, T[0], c->b.obs) != cudaSuccess) err = PAMD_ECUDA;
+        if (!err && record_energies(c, 0) != cudaSuccess) err = PAMD_ECUDA;
         for (int i = 1; i <= K && !err; ++i) {
             if (launch_resample(c, T[i - 1], T[i], resample ? 1 : 0, c->b.counters, (uint32_t)i) != cudaSuccess) {
                 err = PAMD_ECUDA;
@@ -1272,6 +1295,7 @@ int pamd_anneal(pamd_ctx* c, int32_t K, const double* T, int32_t theta, double d
             c->cur_is_alt = !c->cur_is_alt;
             err = launch_prop(c, theta, dt_ps, T[i], c->b.counters, (uint32_t)i * (uint32_t)theta, nullptr);
             if (!err && launch_observe(c, T[i], c->b.obs + i) != cudaSuccess) err = PAMD_ECUDA;
+            if (!err && record_energies(c, i) != cudaSuccess) err = PAMD_ECUDA;
         }
         if (err) {
             c->broken = true;
@@ -1294,6 +1318,7 @@ int pamd_anneal(pamd_ctx* c, int32_t K, const double* T, int32_t theta, double d
         const long long before = c->launches;
         int err = launch_prop(c, theta, dt_ps, T[0], c->b.counters, 0u, nullptr);
         if (!err && launch_observe(c, T[0], c->b.obs) != cudaSuccess) err = PAMD_ECUDA;
+        if (!err && record_energies(c, 0) != cudaSuccess) err = PAMD_ECUDA;
         for (int i = 1; i <= K && !err; ++i) {
             if (launch_resample(c, T[i - 1], T[i], resample ? 1 : 0, c->b.counters, (uint32_t)i) != cudaSuccess) {
                 err = PAMD_ECUDA;
@@ -1302,6 +1327,7 @@ int pamd_anneal(pamd_ctx* c, int32_t K, const double* T, int32_t theta, double d
             c->cur_is_alt = !c->cur_is_alt;
             err = launch_prop(c, theta, dt_ps, T[i], c->b.counters, (uint32_t)i * (uint32_t)theta, nullptr);
             if (!err && launch_observe(c, T[i], c->b.obs + i) != cudaSuccess) err = PAMD_ECUDA;
+            if (!err && record_energies(c, i) != cudaSuccess) err = PAMD_ECUDA;
         }
         if (!err && c->cur_is_alt) {
             const size_t st_bytes = state_bytes(c);

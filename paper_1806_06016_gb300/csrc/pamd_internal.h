@@ -165,8 +165,11 @@ struct GraphKey {
     int K = -1, theta = -1, resample = -1;
     double dt = 0;
     std::vector<double> T;
+    const double* rec = nullptr;  // energy recording target (pamd_record_energies)
+    int rec_rows = 0;
     bool operator==(const GraphKey& o) const {
-        return K == o.K && theta == o.theta && resample == o.resample && dt == o.dt && T == o.T;
+        return K == o.K && theta == o.theta && resample == o.resample && dt == o.dt && T == o.T &&
+               rec == o.rec && rec_rows == o.rec_rows;
     }
 };
 
@@ -265,6 +268,8 @@ struct pamd_ctx {
     std::vector<BatchGroup> groups;
     unsigned char* top64_blob = nullptr;
     pamd_mlp* mlp = nullptr;      // force model replacing the exact forces (pamd_set_force_model)
+    double* rec_E = nullptr;      // caller's [rec_rows][R] energy record of pamd_anneal, or null
+    int rec_rows = 0;
 };
 
 namespace pamd {

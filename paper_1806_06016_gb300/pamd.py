@@ -97,7 +97,23 @@ EXPORTS = [
     "pamd_mlp_loss_grads", "pamd_mlp_get_grads", "pamd_mlp_adam_step", "pamd_set_force_model",
     "pamd_mlp_sync", "pamd_mlp_launch_count", "pamd_mlp_destroy", "pamd_mlp_save", "pamd_mlp_load",
     "pamd_checkpoint", "pamd_restore",
+    # multiple-histogram reweighting (include/pamd_wham.h)
+    "pamd_record_energies", "pamd_wham",
 ]
+
+class PamdWhamArgs(C.Structure):
+    _fields_ = [("E", C.c_void_p), ("n_temps", C.c_int32), ("R", C.c_int64), ("T", C.c_void_p),
+                ("n_bins", C.c_int32), ("e_min", C.c_double), ("e_max", C.c_double),
+                ("lnZ_init", C.c_void_p), ("max_iter", C.c_int32), ("tol", C.c_double),
+                ("n_eval", C.c_int32), ("T_eval", C.c_void_p), ("stream", C.c_void_p)]
+
+
+class PamdWhamResult(C.Structure):
+    _fields_ = [("lnZ", C.c_void_p), ("ln_g", C.c_void_p), ("hist", C.c_void_p),
+                ("lnZ_eval", C.c_void_p), ("e_mean_eval", C.c_void_p), ("e_var_eval", C.c_void_p),
+                ("e_min", C.c_double), ("bin_width", C.c_double), ("iterations", C.c_int32),
+                ("max_delta", C.c_double)]
+
 
 _lib = None
 _lock = threading.Lock()
@@ -161,6 +177,8 @@ def load(path: str | None = None):
             "pamd_mlp_load": (C.c_int, [C.POINTER(P), C.c_char_p, P]),
             "pamd_checkpoint": (C.c_int, [P, C.c_char_p]),
             "pamd_restore": (C.c_int, [P, C.c_char_p]),
+            "pamd_record_energies": (C.c_int, [P, P, I32]),
+            "pamd_wham": (C.c_int, [C.POINTER(PamdWhamArgs), C.POINTER(PamdWhamResult)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -388,6 +406,40 @@ def pamd_resample_counts_noalloc(E_dev: int, R: int, T_prev: float, T_next: floa
     _check(load().pamd_resample_counts_noalloc(
         C.c_void_p(E_dev), int(R), float(T_prev), float(T_next), int(seed), int(resample_index),
         int(mol_id), C.c_void_p(counts_dev), C.c_void_p(lnQ_dev or None), C.c_void_p(stream or None)))
+
+
+def pamd_record_energies(ctx, E_dev: int, rows: int) -> None:
+    """Record the energies pamd_anneal measures into device memory [rows][R]
+    float64 at address E_dev (e.g. ``tensor.data_ptr()``); rows = 0 stops."""
+    _check(load().pamd_record_energies(ctx, C.c_void_p(E_dev or None), int(rows)))
+
+
+def pamd_wham(E_dev: int, n_temps: int, R: int, T, n_bins: int, e_range=None, lnZ_init=None,
+              max_iter: int = 100, tol: float = 1e-10, T_eval=None, stream: int = 0,
+              want_hist: bool = False) -> dict:
+    """Histograms and self-consistency sweeps of the device energies E_dev
+    ([n_temps][R] float64, row i sampled at T[i]); results as numpy arrays."""
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    Te = None if T_eval is None else np.ascontiguousarray(np.atleast_1d(T_eval), dtype=np.float64)
+    z0 = None if lnZ_init is None else np.ascontiguousarray(lnZ_init, dtype=np.float64)
+    ne = 0 if Te is None else len(Te)
+    lo, hi = (0.0, 0.0) if e_range is None else (float(e_range[0]), float(e_range[1]))
+    a = PamdWhamArgs(C.c_void_p(E_dev), int(n_temps), int(R), _ptr(T), int(n_bins), lo, hi, _ptr(z0),
+                     int(max_iter), float(tol), ne, _ptr(Te), C.c_void_p(stream or None))
+    lnZ = np.zeros(n_temps)
+    ln_g = np.zeros(n_bins)
+    hist = np.zeros((n_temps, n_bins), np.uint32) if want_hist else None
+    ev = np.zeros((3, max(ne, 1)))
+    r = PamdWhamResult(_ptr(lnZ), _ptr(ln_g), _ptr(hist), _ptr(ev[0]) if ne else None,
+                       _ptr(ev[1]) if ne else None, _ptr(ev[2]) if ne else None)
+    _check(load().pamd_wham(C.byref(a), C.byref(r)))
+    out = {"lnZ": lnZ, "ln_g": ln_g, "e_min": r.e_min, "bin_width": r.bin_width,
+           "iterations": r.iterations, "max_delta": r.max_delta}
+    if want_hist:
+        out["hist"] = hist
+    if ne:
+        out["lnZ_eval"], out["e_mean_eval"], out["e_var_eval"] = ev[0].copy(), ev[1].copy(), ev[2].copy()
+    return out
 
 
 def pamd_checkpoint(ctx, path: str) -> None:

@@ -1,5 +1,5 @@
 """CPU-only checks of the C-ABI library: it builds, loads, exports every
-function include/pamd.h and include/pamd_mlp.h declare, and rejects bad
+function the headers under include/ declare, and rejects bad
 arguments before touching the GPU."""
 import ctypes as C
 import os
@@ -15,7 +15,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _header_functions():
     names = set()
-    for h in ("pamd.h", "pamd_mlp.h"):
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
         txt = open(os.path.join(ROOT, "include", h)).read()
         txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
         names |= set(re.findall(r"\b(pamd_[a-z0-9_]+)\s*\(", txt))
@@ -133,3 +135,31 @@ def test_checkpoint_and_model_files_validation(lib, tmp_path):
     assert lib.pamd_mlp_load(C.byref(h), str(junk).encode(), None) == pamd.PAMD_EINVAL
     assert "not a model file" in pamd.pamd_last_error()
     assert not h.value
+
+
+def test_wham_rejects_bad_arguments_before_touching_the_gpu(lib):
+    from paper_1806_06016_gb300 import pamd
+    T = np.array([300.0, 250.0])
+    fake = 256  # never dereferenced: every case fails validation first
+
+    def rc(**kw):
+        args = dict(n_temps=2, R=10, T=T, n_bins=16, e_range=None, max_iter=5, tol=0.0, T_eval=None)
+        args.update(kw)
+        try:
+            pamd.pamd_wham(fake, args.pop("n_temps"), args.pop("R"), args.pop("T"), args.pop("n_bins"), **args)
+        except pamd.PamdError as e:
+            return e.code
+        return 0
+
+    assert rc(n_bins=0) == pamd.PAMD_EINVAL
+    assert rc(n_bins=65537) == pamd.PAMD_EINVAL
+    assert rc(n_temps=0, T=np.zeros(0)) == pamd.PAMD_EINVAL
+    assert rc(R=0) == pamd.PAMD_EINVAL
+    assert rc(T=np.array([300.0, -1.0])) == pamd.PAMD_EINVAL
+    assert rc(max_iter=-1) == pamd.PAMD_EINVAL
+    assert rc(tol=-1.0) == pamd.PAMD_EINVAL
+    assert rc(T_eval=[0.0]) == pamd.PAMD_EINVAL
+    assert rc(e_range=(0.0, np.inf)) == pamd.PAMD_EINVAL
+    assert rc(lnZ_init=[0.0, np.nan]) == pamd.PAMD_EINVAL
+    with pytest.raises(pamd.PamdError):
+        pamd.pamd_record_energies(None, 0, 0)
