@@ -577,6 +577,66 @@ def run_wham(args):
     print(json.dumps(out), flush=True)
 
 
+def run_adaptive(args):
+    """Temperature schedules from the overlap condition and systematic
+    resampling on the 75-atom R = 8192 workload (theta = 1000, 1000 -> 250 K):
+    the geometric 100-step schedule with multinomial and with systematic
+    resampling, and adaptive schedules for two overlap targets; plus the cost
+    of one overlap step at R = 8192 and R = 2^20.  Prints one JSON line."""
+    import numpy as np
+    import torch
+
+    import pamd_inputs as pi
+    from paper_1806_06016_gb300 import build as pbuild
+    from paper_1806_06016_gb300 import pamd
+
+    torch.cuda.set_device(0)
+    pbuild.build()
+    w = WORKLOADS["c2"]
+    R = args.replicas or w["R"]
+    top = pi.make_chain(w["n_atoms"], w["gen_seed"])
+    temps = pi.geometric_schedule(w["T0"], w["TK"], w["K"])
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    out = {"mode": "adaptive", "workload": w["workload"], "replicas": R}
+
+    def summary(obs, wall, temps_used):
+        return {"temperatures": len(temps_used), "wall_s": wall,
+                "atom_steps_per_s": w["n_atoms"] * R * w["theta"] * len(temps_used) / wall,
+                "e_pot_final": obs[-1]["e_pot"], "e_pot_se_final": obs[-1]["e_pot_se"],
+                "rg_final": obs[-1]["rg"], "sum_lnQ_final": obs[-1]["sum_lnQ"],
+                "families_final": obs[-1]["n_families"],
+                "T_first_steps": [float(t) for t in temps_used[:6]]}
+
+    for rule, name in ((pamd.PAMD_RESAMPLE_MULTINOMIAL, "geometric_multinomial"),
+                       (pamd.PAMD_RESAMPLE_SYSTEMATIC, "geometric_systematic")):
+        with pamd.Population(top, R, temps[0], w["seed"], pamd.torch_options(resample_rule=rule)) as pop:
+            pop.anneal(temps, w["theta"], w["dt"])  # graph capture and warm-up
+            pop.reset(temps[0], w["seed"])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            obs = pop.anneal(temps, w["theta"], w["dt"])
+            out[name] = summary(obs, time.perf_counter() - t0, temps)
+    for alpha in (0.5, 0.8):
+        with pamd.Population(top, R, temps[0], w["seed"], pamd.torch_options()) as pop:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            obs, used = pamd.pamd_anneal_adaptive(pop.ctx, w["T0"], w["TK"], alpha, w["theta"], w["dt"], 400)
+            out[f"adaptive_alpha{alpha}"] = summary(obs, time.perf_counter() - t0, used)
+    # one overlap step (the search alone: 2 + 2 x 4 launches and one synchronisation)
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    for n in (R, 1 << 20):
+        E = torch.randn(n, dtype=torch.float64, device="cuda", generator=gen).mul_(40.0).sub_(2000.0)
+        pamd.pamd_overlap_temperature(E.data_ptr(), n, 1000.0, 250.0, 0.5, stream.cuda_stream)
+        ts = []
+        for _ in range(20):
+            t0 = time.perf_counter()
+            pamd.pamd_overlap_temperature(E.data_ptr(), n, 1000.0, 250.0, 0.5, stream.cuda_stream)
+            ts.append(time.perf_counter() - t0)
+        out[f"overlap_step_ms_R{n}"] = 1e3 * statistics.median(ts)
+    print(json.dumps(out), flush=True)
+
+
 def run_precision(args):
     """Large-population precision study (75-atom chain, 60 geometric steps
     1000 -> 250 K, theta = 200): the mixed FP32/FP64 path against the all-FP64
@@ -1071,7 +1131,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", choices=["anneal", "kernel", "precision", "resample", "gemm", "surrogate",
-                                       "surrogate_kernel", "control", "wham"],
+                                       "surrogate_kernel", "control", "wham", "adaptive"],
                     default="anneal")
     ap.add_argument("--theta", type=int, default=0,
                     help="kernel mode: steps per launch; control mode: equilibration steps at 700 K")
@@ -1101,6 +1161,8 @@ def main():
         run_control(args)
     elif args.mode == "wham":
         run_wham(args)
+    elif args.mode == "adaptive":
+        run_adaptive(args)
     elif args.mode == "resample":
         run_resample(args)
     elif args.mode == "gemm":

@@ -57,6 +57,21 @@ extern "C" {
 #define PAMD_PREC_MIXED 0 /* FP32 forces/integration, FP64 energies and weights */
 #define PAMD_PREC_FP64 1  /* everything in FP64 on the GPU */
 
+/*
+ * Resampling rules (the resampling paragraph: the paper draws R multinomial
+ * samples and notes that other implementations exist).  Both keep the
+ * population size R and use the same integer weights W_j and inclusive sums
+ * C_j (C = C_{R-1}); they differ in the targets t_k whose ancestor is the
+ * first j with C_j > t_k:
+ *   MULTINOMIAL  t_k = floor(u_k C / 2^64), u_k an independent 64-bit Philox
+ *                uniform per new slot k;
+ *   SYSTEMATIC   t_k = floor((k C + V) / R), V = floor(u_0 C / 2^64): one
+ *                uniform per resampling, each n_j = floor(R W_j / C) or one
+ *                more (lower variance of the copy numbers).
+ */
+#define PAMD_RESAMPLE_MULTINOMIAL 0
+#define PAMD_RESAMPLE_SYSTEMATIC 1
+
 typedef struct pamd_ctx pamd_ctx; /* opaque, owned by the library */
 
 /*
@@ -111,6 +126,8 @@ typedef struct pamd_options {
     void (*dev_free)(void* ptr, void* user);      /* NULL = cudaFree */
     void* alloc_user;
     void* stream;               /* cudaStream_t; NULL = a non-blocking stream the context creates */
+    int32_t resample_rule;      /* PAMD_RESAMPLE_MULTINOMIAL (the paper's choice) or
+                                   PAMD_RESAMPLE_SYSTEMATIC */
 } pamd_options;
 
 /* Per-temperature population averages (PAMD scheme, step 4) with jackknife

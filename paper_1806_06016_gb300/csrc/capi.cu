@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "../../include/pamd_adaptive.h"
 #include "../../include/pamd_wham.h"
 #include "mlp_internal.h"
 #include "pamd_internal.h"
@@ -907,10 +908,13 @@ int pamd_init(pamd_ctx** out, const pamd_topology* top, int64_t R, double T0, ui
         return fail(PAMD_EINVAL, "replicas_per_lane must be 0, 1 or 2");
     if ((o.dev_alloc == nullptr) != (o.dev_free == nullptr))
         return fail(PAMD_EINVAL, "dev_alloc and dev_free must both be set or both be NULL");
+    if (o.resample_rule != PAMD_RESAMPLE_MULTINOMIAL && o.resample_rule != PAMD_RESAMPLE_SYSTEMATIC)
+        return fail(PAMD_EINVAL, "resample_rule must be PAMD_RESAMPLE_MULTINOMIAL or PAMD_RESAMPLE_SYSTEMATIC");
 
     pamd_ctx* c = new (std::nothrow) pamd_ctx();
     if (!c) return fail(PAMD_ENOMEM, "host allocation");
     c->R = R;
+    c->resample_rule = o.resample_rule;
     c->precision = o.precision;
     c->gamma = o.gamma_per_ps;
     c->seed = seed;
@@ -1252,6 +1256,63 @@ int pamd_record_energies(pamd_ctx* c, double* E_dev, int32_t rows) {
     c->rec_E = rows > 0 ? E_dev : nullptr;
     c->rec_rows = rows > 0 ? rows : 0;
     return PAMD_OK;
+}
+
+int pamd_next_temperature(pamd_ctx* c, double T_prev, double T_final, double alpha_target,
+                          double* T_next_out, double* alpha_out) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (is_batch(c)) return fail(PAMD_EINVAL, "overlap step: single-molecule contexts only");
+    if (!T_next_out) return fail(PAMD_EINVAL, "overlap step: T_next_out is required");
+    if ((rc = overlap_check_args(c->R, T_prev, T_final, alpha_target))) return rc;
+    if (!c->ov_work) {
+        c->ov_work = dalloc(c, overlap_work_bytes(c->R));
+        if (!c->ov_work) return fail(PAMD_ENOMEM, "overlap step scratch");
+    }
+    rc = overlap_step(c->stream, cur_E(c), c->R, T_prev, T_final, alpha_target, c->ov_work, c->num_sms,
+                      T_next_out, alpha_out, &c->launches);
+    if (rc == PAMD_ECUDA) c->broken = true;
+    return rc;
+}
+
+int pamd_anneal_adaptive(pamd_ctx* c, double T0, double T_final, double alpha_target, int32_t theta,
+                         double dt_ps, int32_t max_steps, int32_t resample, pamd_obs* obs_out,
+                         double* T_out, int32_t* n_temps_out) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (is_batch(c)) return fail(PAMD_EINVAL, "adaptive anneal: single-molecule contexts only");
+    if (!(T0 > 0) || !std::isfinite(T0) || !(T_final > 0) || !(T_final < T0))
+        return fail(PAMD_EINVAL, "adaptive anneal: 0 < T_final < T0 required");
+    if (!(alpha_target > 0) || !(alpha_target < 1))
+        return fail(PAMD_EINVAL, "adaptive anneal: alpha_target must be in (0, 1)");
+    if (max_steps < 0 || theta < 0 || !(dt_ps > 0) || !std::isfinite(dt_ps))
+        return fail(PAMD_EINVAL, "adaptive anneal: max_steps >= 0, theta >= 0, dt > 0");
+    pamd_obs o;
+    if ((rc = pamd_propagate(c, theta, dt_ps, T0)) || (rc = pamd_observables(c, T0, &o))) return rc;
+    PAMD_CU(c, record_energies(c, 0));
+    if (obs_out) obs_out[0] = o;
+    if (T_out) T_out[0] = T0;
+    int n = 1;
+    double T = T0;
+    for (int i = 1; i <= max_steps && T > T_final; ++i) {
+        double Tn = T;
+        if ((rc = pamd_next_temperature(c, T, T_final, alpha_target, &Tn, nullptr))) return rc;
+        if (!(Tn < T))
+            return fail(PAMD_EINVAL, "adaptive anneal: no lower temperature meets the overlap target "
+                                     "(alpha_target too close to 1 for this population)");
+        c->resample_index += 1;
+        cudaError_t e = launch_resample(c, T, Tn, resample ? 1 : 0, nullptr, c->resample_index);
+        if (e != cudaSuccess) return cuda_fail(c, e, "resample launch");
+        c->cur_is_alt = !c->cur_is_alt;
+        if ((rc = pamd_propagate(c, theta, dt_ps, Tn)) || (rc = pamd_observables(c, Tn, &o))) return rc;
+        PAMD_CU(c, record_energies(c, i));
+        if (obs_out) obs_out[i] = o;
+        if (T_out) T_out[i] = Tn;
+        T = Tn;
+        ++n;
+    }
+    if (n_temps_out) *n_temps_out = n;
+    return read_status(c);
 }
 
 int pamd_anneal(pamd_ctx* c, int32_t K, const double* T, int32_t theta, double dt_ps,

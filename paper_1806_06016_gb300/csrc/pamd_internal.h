@@ -270,6 +270,8 @@ struct pamd_ctx {
     pamd_mlp* mlp = nullptr;      // force model replacing the exact forces (pamd_set_force_model)
     double* rec_E = nullptr;      // caller's [rec_rows][R] energy record of pamd_anneal, or null
     int rec_rows = 0;
+    void* ov_work = nullptr;      // scratch of the adaptive temperature step (allocated on first use)
+    int resample_rule = PAMD_RESAMPLE_MULTINOMIAL;
 };
 
 namespace pamd {
@@ -327,6 +329,13 @@ cudaError_t launch_gemm_bf16(const GemmArgs& g, cudaStream_t s);
 
 // message returned by pamd_last_error() on this thread (capi.cu)
 void set_last_error(const std::string& msg);
+// Adaptive temperature step (adaptive.cu): scratch size, argument check and
+// the search on device energies E [R]; synchronises s.
+size_t overlap_work_bytes(long long R);
+int overlap_check_args(long long R, double T_prev, double T_final, double alpha_target);
+int overlap_step(cudaStream_t s, const double* E, long long R, double T_prev, double T_final,
+                 double alpha_target, void* work, int num_sms, double* T_next, double* alpha_out,
+                 long long* launches);
 
 // resampling kernels defined in resample.cu, also launched by noalloc.cu
 __global__ void reset_scalars_kernel(DevScalars* s);

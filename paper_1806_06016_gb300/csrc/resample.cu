@@ -272,9 +272,31 @@ __global__ void counts_kernel(const unsigned long long* C, long long R, const De
             cnt[k] = 1;
             continue;
         }
-        const uint4 o = philox4x32_10(make_uint4((uint32_t)k, ridx, 0u, purpose), seed_key(seed));
-        const unsigned long long u = (unsigned long long)o.x | ((unsigned long long)o.y << 32);
-        const unsigned long long t = __umul64hi(u, total);
+        unsigned long long t;
+        if (do_resample == 2) {
+            // systematic: t_k = floor((k C + V) / R), V = floor(u_0 C / 2^64), by
+            // long division in 32-bit digits (the numerator is below 2^84 and
+            // the quotient below C)
+            const uint4 o = philox4x32_10(make_uint4(0u, ridx, 0u, purpose), seed_key(seed));
+            const unsigned long long u0 = (unsigned long long)o.x | ((unsigned long long)o.y << 32);
+            const unsigned long long V = __umul64hi(u0, total);
+            const unsigned long long plo = (unsigned long long)k * total;  // low 64 bits of k C
+            unsigned long long phi = __umul64hi((unsigned long long)k, total);
+            const unsigned long long lo64 = plo + V;
+            phi += (lo64 < plo) ? 1ull : 0ull;
+            const unsigned long long r64 = (unsigned long long)R;
+            unsigned long long rem = phi % r64;  // phi < R: the quotient's high word is zero
+            unsigned long long cur = (rem << 32) | (lo64 >> 32);
+            const unsigned long long q1 = cur / r64;
+            rem = cur % r64;
+            cur = (rem << 32) | (lo64 & 0xffffffffull);
+            const unsigned long long q0 = cur / r64;
+            t = (q1 << 32) | q0;
+        } else {
+            const uint4 o = philox4x32_10(make_uint4((uint32_t)k, ridx, 0u, purpose), seed_key(seed));
+            const unsigned long long u = (unsigned long long)o.x | ((unsigned long long)o.y << 32);
+            t = __umul64hi(u, total);
+        }
         long long lo = 0, hi = R;
         while (lo < hi) {
             const long long mid = lo + ((hi - lo) >> 1);
@@ -668,9 +690,10 @@ cudaError_t launch_resample(pamd_ctx* c, double T_prev, double T_next, int do_re
     scan_local_u64_kernel<<<nblk, kScanThreads, 0, s>>>(c->b.W, R, c->b.blk_u64, c->b.C);
     cudaError_t e = cudaMemsetAsync(c->b.cnt, 0, sizeof(int32_t) * (size_t)R, s);
     if (e != cudaSuccess) return e;
+    const int rule = !do_resample ? 0 : (c->resample_rule == PAMD_RESAMPLE_SYSTEMATIC ? 2 : 1);
     counts_kernel<<<grid_for(R, 256, c->num_sms * 16), 256, 0, s>>>(
         c->b.C, R, c->b.scal, c->seed, dev_counters, resample_offset,
-        kPurposeResample | ((uint32_t)c->mol << 8), do_resample, c->b.cnt);
+        kPurposeResample | ((uint32_t)c->mol << 8), rule, c->b.cnt);
     cnt_block_kernel<<<nblk, kScanThreads, 0, s>>>(c->b.cnt, R, c->b.blk_i32, c->b.blk_i32 + nblk);
     cnt_top_kernel<<<1, kScanThreads, 0, s>>>(c->b.blk_i32, c->b.blk_i32 + nblk, nblk, c->b.scal);
     cnt_local_kernel<<<nblk, kScanThreads, 0, s>>>(c->b.cnt, R, c->b.blk_i32, c->b.cnt_incl);

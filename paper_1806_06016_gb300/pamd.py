@@ -20,6 +20,7 @@ PAMD_OK = 0
 PAMD_EINVAL, PAMD_ENOMEM, PAMD_ECUDA, PAMD_ETIMEOUT = -1, -2, -3, -4
 PAMD_ENONFINITE, PAMD_ESTATE, PAMD_EUNSUPPORTED = -5, -6, -7
 PAMD_PREC_MIXED, PAMD_PREC_FP64 = 0, 1
+PAMD_RESAMPLE_MULTINOMIAL, PAMD_RESAMPLE_SYSTEMATIC = 0, 1
 PAMD_MAX_ATOMS = 256
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -60,6 +61,7 @@ class PamdOptions(C.Structure):
         ("dev_free", FREE_FN),
         ("alloc_user", C.c_void_p),
         ("stream", C.c_void_p),
+        ("resample_rule", C.c_int32),
     ]
 
 
@@ -99,6 +101,8 @@ EXPORTS = [
     "pamd_checkpoint", "pamd_restore",
     # multiple-histogram reweighting (include/pamd_wham.h)
     "pamd_record_energies", "pamd_wham",
+    # temperature schedules from the overlap condition (include/pamd_adaptive.h)
+    "pamd_overlap_temperature", "pamd_next_temperature", "pamd_anneal_adaptive",
 ]
 
 class PamdWhamArgs(C.Structure):
@@ -179,6 +183,10 @@ def load(path: str | None = None):
             "pamd_restore": (C.c_int, [P, C.c_char_p]),
             "pamd_record_energies": (C.c_int, [P, P, I32]),
             "pamd_wham": (C.c_int, [C.POINTER(PamdWhamArgs), C.POINTER(PamdWhamResult)]),
+            "pamd_overlap_temperature": (C.c_int, [P, I64, D, D, D, C.POINTER(D), C.POINTER(D), P]),
+            "pamd_next_temperature": (C.c_int, [P, D, D, D, C.POINTER(D), C.POINTER(D)]),
+            "pamd_anneal_adaptive": (C.c_int, [P, D, D, D, I32, D, I32, I32, C.POINTER(PamdObs), P,
+                                               C.POINTER(I32)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -440,6 +448,37 @@ def pamd_wham(E_dev: int, n_temps: int, R: int, T, n_bins: int, e_range=None, ln
     if ne:
         out["lnZ_eval"], out["e_mean_eval"], out["e_var_eval"] = ev[0].copy(), ev[1].copy(), ev[2].copy()
     return out
+
+
+def pamd_overlap_temperature(E_dev: int, R: int, T_prev: float, T_final: float, alpha_target: float,
+                             stream: int = 0):
+    """(T_next, overlap at T_next) from R device energies (address E_dev)."""
+    t, a = C.c_double(), C.c_double()
+    _check(load().pamd_overlap_temperature(C.c_void_p(E_dev), int(R), float(T_prev), float(T_final),
+                                           float(alpha_target), C.byref(t), C.byref(a),
+                                           C.c_void_p(stream or None)))
+    return t.value, a.value
+
+
+def pamd_next_temperature(ctx, T_prev: float, T_final: float, alpha_target: float):
+    """(T_next, overlap at T_next) for the context's current population."""
+    t, a = C.c_double(), C.c_double()
+    _check(load().pamd_next_temperature(ctx, float(T_prev), float(T_final), float(alpha_target),
+                                        C.byref(t), C.byref(a)))
+    return t.value, a.value
+
+
+def pamd_anneal_adaptive(ctx, T0: float, T_final: float, alpha_target: float, theta: int, dt_ps: float,
+                         max_steps: int, resample: bool = True):
+    """(per-temperature observable dicts, temperatures) of an anneal whose
+    temperatures follow the overlap condition."""
+    obs = (PamdObs * (max_steps + 1))()
+    temps = np.zeros(max_steps + 1)
+    n = C.c_int32()
+    _check(load().pamd_anneal_adaptive(ctx, float(T0), float(T_final), float(alpha_target), int(theta),
+                                       float(dt_ps), int(max_steps), int(bool(resample)), obs, _ptr(temps),
+                                       C.byref(n)))
+    return [obs[i].as_dict() for i in range(n.value)], temps[: n.value].copy()
 
 
 def pamd_checkpoint(ctx, path: str) -> None:

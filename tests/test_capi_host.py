@@ -163,3 +163,19 @@ def test_wham_rejects_bad_arguments_before_touching_the_gpu(lib):
     assert rc(lnZ_init=[0.0, np.nan]) == pamd.PAMD_EINVAL
     with pytest.raises(pamd.PamdError):
         pamd.pamd_record_energies(None, 0, 0)
+
+
+def test_adaptive_and_rule_arguments_rejected_before_touching_the_gpu(lib):
+    from paper_1806_06016_gb300 import pamd
+    fake = 256
+    bad = [(10, 300.0, 300.0, 0.5), (10, 300.0, 400.0, 0.5), (0, 300.0, 200.0, 0.5),
+           (10, 300.0, 200.0, 0.0), (10, 300.0, 200.0, 1.0), (10, -1.0, -2.0, 0.5)]
+    for R, Tp, Tf, a in bad:
+        with pytest.raises(pamd.PamdError) as ei:
+            pamd.pamd_overlap_temperature(fake, R, Tp, Tf, a)
+        assert ei.value.code == pamd.PAMD_EINVAL
+    with pytest.raises(pamd.PamdError):
+        pamd.pamd_next_temperature(None, 300.0, 200.0, 0.5)
+    with pytest.raises(pamd.PamdError):
+        pamd.pamd_anneal_adaptive(None, 300.0, 200.0, 0.5, 10, 0.001, 5)
+    assert _init_rc(pi.make_chain(5, 1), resample_rule=2)[0] == pamd.PAMD_EINVAL
