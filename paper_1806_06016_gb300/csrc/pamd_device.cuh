@@ -43,6 +43,24 @@ __device__ __forceinline__ float3 normal3(unsigned long long seed, uint32_t atom
     return make_float3(r0 * c0, r0 * s0, r1 * c1);
 }
 
+// The same three normals with the hardware sine and cosine (absolute error
+// below 2^-21 on [-pi, pi)) in place of sincospi / cospi: the O-step noise of
+// the FP32 dynamics kernels, where that error is far below the FP32 rounding
+// of the velocities.  cos(2 pi u) = -cos(2 pi (u - 1/2)) keeps the argument in
+// [-pi, pi); the logarithm stays the accurate one (near u = 1 the fast one
+// could change sign).
+__device__ __forceinline__ float3 normal3_fast(unsigned long long seed, uint32_t atom, uint32_t slot,
+                                               uint32_t step, uint32_t purpose) {
+    const uint4 o = philox4x32_10(make_uint4(atom, slot, step, purpose), seed_key(seed));
+    const float r0 = sqrtf(-2.0f * logf(uniform23(o.x)));
+    const float r1 = sqrtf(-2.0f * logf(uniform23(o.z)));
+    const float two_pi = 6.2831853071795864769f;
+    float s0, c0;
+    __sincosf(two_pi * (uniform23(o.y) - 0.5f), &s0, &c0);
+    const float c1 = __cosf(two_pi * (uniform23(o.w) - 0.5f));
+    return make_float3(-r0 * c0, -r0 * s0, -r1 * c1);
+}
+
 // Taylor coefficients 1/n!, n = 0..13, filled on the host (correctly rounded
 // binary64 divisions of exact factorials) and passed as a kernel argument.
 struct ExpCoef {

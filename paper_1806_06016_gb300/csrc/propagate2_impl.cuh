@@ -534,8 +534,8 @@ __global__ void __launch_bounds__(256, PropCfg2<B>::MIN_BLOCKS) propagate2_kerne
                     yn[a] = fma2(nhdt, vy[a], yn[a]);
                     zn[a] = fma2(nhdt, vz[a], zn[a]);
                     if (i < N) {                                     // O
-                        const float3 za = normal3(p.seed, (uint32_t)i, (uint32_t)kA, step, p.purpose_mol);
-                        const float3 zb = normal3(p.seed, (uint32_t)i, (uint32_t)kB, step, p.purpose_mol);
+                        const float3 za = normal3_fast(p.seed, (uint32_t)i, (uint32_t)kA, step, p.purpose_mol);
+                        const float3 zb = normal3_fast(p.seed, (uint32_t)i, (uint32_t)kB, step, p.purpose_mol);
                         const float2 sdv = bc2(sd[a]);
                         vx[a] = fma2(c1, vx[a], mul2(sdv, make_float2(za.x, zb.x)));
                         vy[a] = fma2(c1, vy[a], mul2(sdv, make_float2(za.y, zb.y)));

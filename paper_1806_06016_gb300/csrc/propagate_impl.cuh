@@ -161,13 +161,19 @@ __device__ __forceinline__ float3 f3axpby(float a, float3 x, float b, float3 y) 
 
 // ---- bonded term kernels on positions; return forces on each atom ----------
 
+// The bonded terms take every length and inverse length from one reciprocal
+// square root (MUFU) per squared length, r = r^2 * (1/r), instead of square
+// roots and divisions.
+
 // 1/2 k (r - r0)^2 ; force on atom i (atom j gets the opposite)
 template <bool ENERGY>
 __device__ __forceinline__ float3 bond_force(float3 pi_, float3 pj_, float r0, float k,
                                              double& e_acc) {
     const float3 d = f3sub(pi_, pj_);
-    const float r = sqrtf(dot3(d, d));
-    const float gk = (r0 == 0.0f) ? k : k * (r - r0) / r;
+    const float r2 = dot3(d, d);
+    const float ri = rsqrtf(r2);
+    const float r = r2 * ri;
+    const float gk = (r0 == 0.0f) ? k : k * (r - r0) * ri;
     if (ENERGY) e_acc += (double)(0.5f * k * (r - r0) * (r - r0));
     return f3scale(-gk, d);
 }
@@ -179,12 +185,15 @@ __device__ __forceinline__ void angle_force(float3 pi_, float3 pj_, float3 pk_, 
     const float3 u = f3sub(pi_, pj_);
     const float3 w = f3sub(pk_, pj_);
     const float3 uxw = cross3(u, w);
-    const float s = sqrtf(dot3(uxw, uxw));
+    const float s2 = dot3(uxw, uxw);
+    const float rs = rsqrtf(s2);
+    const float s = s2 * rs;
     const float cw = dot3(u, w);
     const float dth = atan2f(s, cw) - t0;
     const float gk = kk * dth;
-    const float is = gk / s;
-    const float cu = cw / dot3(u, u), cv = cw / dot3(w, w);
+    const float is = gk * rs;
+    const float ru = rsqrtf(dot3(u, u)), rw = rsqrtf(dot3(w, w));
+    const float cu = cw * (ru * ru), cv = cw * (rw * rw);
     // F_i = -gk dtheta/du = gk (w - cu u)/s ; F_k = gk (u - cv w)/s
     fi = make_float3(is * (w.x - cu * u.x), is * (w.y - cu * u.y), is * (w.z - cu * u.z));
     fk = make_float3(is * (u.x - cv * w.x), is * (u.y - cv * w.y), is * (u.z - cv * w.z));
@@ -204,10 +213,16 @@ __device__ __forceinline__ void dihedral_force(float3 pi_, float3 pj_, float3 pk
     const float3 A = cross3(F, G);
     const float3 Bv = cross3(H, G);
     const float AA = dot3(A, A), BB = dot3(Bv, Bv);
-    const float lg = sqrtf(dot3(G, G));
-    const float rab = rsqrtf(AA * BB);
+    const float GG = dot3(G, G);
+    const float rlg = rsqrtf(GG);
+    const float lg = GG * rlg;
+    const float rA = rsqrtf(AA), rB = rsqrtf(BB);
+    const float rA2 = rA * rA, rB2 = rB * rB;
+    const float rab = rA * rB;
     const float cphi = dot3(A, Bv) * rab;
-    const float sphi = dot3(cross3(Bv, A), G) * rab / lg;
+    // sin phi = ((B x A) . G) / (|A| |B| |G|), and (B x A) . G = -(F . B) |G|^2
+    // because B . G = 0, so sin phi = -(F . B) |G| / (|A| |B|)
+    const float sphi = -dot3(F, Bv) * lg * rab;
     float cn = cphi, sn = sphi;
     const int n = (int)nn;
     for (int q = 1; q < n; ++q) {
@@ -216,8 +231,8 @@ __device__ __forceinline__ void dihedral_force(float3 pi_, float3 pj_, float3 pk
         cn = c2;
     }
     const float dEdphi = -kd * nn * (sn * cph - cn * sph);
-    const float ia = lg / AA, ib = lg / BB;
-    const float pa = dot3(F, G) / (AA * lg), pb = dot3(H, G) / (BB * lg);
+    const float ia = lg * rA2, ib = lg * rB2;
+    const float pa = dot3(F, G) * rA2 * rlg, pb = dot3(H, G) * rB2 * rlg;
     fi = f3scale(dEdphi * ia, A);
     fl = f3scale(-dEdphi * ib, Bv);
     fj = f3axpby(-dEdphi * (ia + pa), A, dEdphi * pb, Bv);
@@ -661,7 +676,7 @@ __device__ __forceinline__ void advance_replica(const PropParams& p, const unsig
                 yi[a] = fmaf(p.hdt, vy[a], yi[a]);
                 zi[a] = fmaf(p.hdt, vz[a], zi[a]);
                 if (i < N) {                                // O
-                    const float3 z = normal3(p.seed, (uint32_t)i, (uint32_t)k, step, p.purpose_mol);
+                    const float3 z = normal3_fast(p.seed, (uint32_t)i, (uint32_t)k, step, p.purpose_mol);
                     vx[a] = fmaf(p.c1, vx[a], sd[a] * z.x);
                     vy[a] = fmaf(p.c1, vy[a], sd[a] * z.y);
                     vz[a] = fmaf(p.c1, vz[a], sd[a] * z.z);

@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kMlpThreads) mlp_step_kernel(const MlpStepPara
                 y = fmaf(p.hdt, vy, y);
                 z = fmaf(p.hdt, vz, z);
                 const float sd = p.c2kT * sqrtf(im);  // O
-                const float3 n = normal3(p.seed, (uint32_t)i, (uint32_t)k, step, p.purpose_mol);
+                const float3 n = normal3_fast(p.seed, (uint32_t)i, (uint32_t)k, step, p.purpose_mol);
                 vx = fmaf(p.c1, vx, sd * n.x);
                 vy = fmaf(p.c1, vy, sd * n.y);
                 vz = fmaf(p.c1, vz, sd * n.z);

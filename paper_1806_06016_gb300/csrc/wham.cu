@@ -66,15 +66,29 @@ __device__ double block_sum(double v, double* sh) {
     return r;
 }
 
+// Samples are read kUnroll per thread per step (coalesced across the block,
+// independent loads in flight) so that the HBM-bound passes keep enough
+// bytes in flight.
+constexpr int kUnroll = 8;
+
 __global__ void __launch_bounds__(kT) range_kernel(const double* E, long long n, double* bmin,
                                                    double* bmax) {
     __shared__ double sh[kT];
     double lo = INFINITY, hi = -INFINITY;
-    for (long long i = (long long)blockIdx.x * kT + threadIdx.x; i < n; i += (long long)gridDim.x * kT) {
-        const double e = E[i];
-        if (isfinite(e)) {
-            lo = fmin(lo, e);
-            hi = fmax(hi, e);
+    const long long stride = (long long)gridDim.x * kT;
+    for (long long i0 = (long long)blockIdx.x * kT + threadIdx.x; i0 < n; i0 += stride * kUnroll) {
+        double v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const long long i = i0 + u * stride;
+            v[u] = i < n ? E[i] : NAN;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            if (isfinite(v[u])) {
+                lo = fmin(lo, v[u]);
+                hi = fmax(hi, v[u]);
+            }
         }
     }
     hi = block_max(hi, sh);
@@ -111,15 +125,25 @@ __global__ void __launch_bounds__(kT) hist_kernel(const double* E, long long R, 
         for (int b = threadIdx.x; b < nbins; b += kT) sh_hist[b] = 0u;
         __syncthreads();
     }
-    for (long long k = (long long)blockIdx.x * kT + threadIdx.x; k < R; k += (long long)gridDim.x * kT) {
-        const double e = row[k];
-        if (!(e >= e_min && e <= e_max)) continue;  // NaN and out-of-range samples are dropped
-        long long b = (long long)floor(__dmul_rn(__dsub_rn(e, e_min), inv));
-        b = b < 0 ? 0 : (b > nbins - 1 ? nbins - 1 : b);
-        if (smem_bins)
-            atomicAdd(&sh_hist[b], 1u);
-        else
-            atomicAdd(&gh[b], 1u);
+    const long long stride = (long long)gridDim.x * kT;
+    for (long long k0 = (long long)blockIdx.x * kT + threadIdx.x; k0 < R; k0 += stride * kUnroll) {
+        double v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const long long k = k0 + u * stride;
+            v[u] = k < R ? row[k] : NAN;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const double e = v[u];
+            if (!(e >= e_min && e <= e_max)) continue;  // NaN and out-of-range samples are dropped
+            long long b = (long long)floor(__dmul_rn(__dsub_rn(e, e_min), inv));
+            b = b < 0 ? 0 : (b > nbins - 1 ? nbins - 1 : b);
+            if (smem_bins)
+                atomicAdd(&sh_hist[b], 1u);
+            else
+                atomicAdd(&gh[b], 1u);
+        }
     }
     if (smem_bins) {
         __syncthreads();
@@ -339,7 +363,7 @@ extern "C" int pamd_wham(const pamd_wham_args* a, pamd_wham_result* r) {
     if (e != cudaSuccess) return cuda_err(e, "device query");
 
     const long long n_all = (long long)nT * R;
-    const int range_blocks = (int)std::min<long long>((n_all + kT - 1) / kT, 4LL * sms);
+    const int range_blocks = (int)std::min<long long>((n_all + kT * kUnroll - 1) / (kT * kUnroll), 16LL * sms);
     // workspace layout
     Work wk;
     size_t off = 0;
@@ -403,8 +427,8 @@ extern "C" int pamd_wham(const pamd_wham_args* a, pamd_wham_result* r) {
     if ((e = cudaMemsetAsync(wk.hist, 0, sizeof(unsigned) * (size_t)nT * nb, s)) != cudaSuccess)
         return cuda_err(e, "clear histograms");
     const int smem_bins = nb <= kSmemBins ? 1 : 0;
-    long long bx = (R + 16LL * kT - 1) / (16LL * kT);
-    const long long want = (4LL * sms + nT - 1) / nT;
+    long long bx = (R + (long long)kT * kUnroll - 1) / ((long long)kT * kUnroll);
+    const long long want = (16LL * sms + nT - 1) / nT;
     if (bx > want) bx = want;
     if (bx < 1) bx = 1;
     hist_kernel<<<dim3((unsigned)bx, (unsigned)nT), kT, smem_bins ? sizeof(unsigned) * nb : 0, s>>>(
