@@ -77,6 +77,9 @@ NCU_TRAFFIC = {
     "82c42a4517bd10bf": 15045632,
     # the same capture after the pair-parameter table: 15.30 MB read, 0 written
     "c465a4813deb4e22": 15304704,
+    # after the bonded terms moved to reciprocal square roots and the O-step
+    # noise to the hardware sine/cosine: 15.09 MB read, 0 written
+    "226d5425bfeba8c3": 15087360,
 }
 
 
