@@ -738,6 +738,31 @@ def run_precision(args):
     chain_ms = statistics.mean(ms[1:])
     out["resample_R2p20"] = {"chain_ms": chain_ms, "gather_bytes": gather_bytes,
                              "gather_GBps_lower_bound": gather_bytes / (chain_ms / 1e3) / 1e9}
+    if args.replicas == 0:
+        # the whole schedule in mixed precision at the full population R = 2^20
+        # (the all-FP64 path would take hours there); its <E>(T) against the
+        # FP64 runs above, in combined standard errors
+        with pamd.Population(top, big, temps[0], seed, pamd.torch_options()) as pop:
+            pop.autotune(20)
+            pop.anneal(temps[:2], theta, dt)  # graph of a short schedule: warms up the kernels
+            pop.reset(temps[0], seed)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            obs = pop.anneal(temps, theta, dt)
+            ev1.record(stream)
+            ev1.synchronize()
+            t_ms = ev0.elapsed_time(ev1)
+        e_big = np.array([o["e_pot"] for o in obs]); s_big = np.array([o["e_pot_se"] for o in obs])
+        comb_big = np.sqrt(s_big ** 2 + s64 ** 2)
+        out["mixed_R2p20"] = {
+            "anneal_s": t_ms / 1e3, "atom_steps_per_s": N * big * theta * (K + 1) / (t_ms / 1e3),
+            "e_pot_kJmol": [float(v) for v in e_big[::10]], "e_pot_se_kJmol": [float(v) for v in s_big[::10]],
+            "e_minus_fp64_R2048_in_se_max": float(np.max(np.abs(e_big - e64) / comb_big)),
+            "e_minus_mixed_R2048_in_se_max": float(np.max(np.abs(e_big - e32) / np.sqrt(s_big ** 2 + s32 ** 2))),
+            "e_fp64_R2048_kJmol": [float(v) for v in e64[::10]],
+            "e_mixed_R2048_kJmol": [float(v) for v in e32[::10]],
+            "sum_lnQ_final": obs[-1]["sum_lnQ"], "families_final": obs[-1]["n_families"],
+            "rg_final": obs[-1]["rg"]}
     print(json.dumps(out), flush=True)
 
 
