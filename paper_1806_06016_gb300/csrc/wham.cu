@@ -7,10 +7,13 @@
 //
 // Kernels:
 //   range_kernel / range_final_kernel  min and max of the finite samples
-//   hist_kernel     one grid row per temperature; integer counters in shared
-//                   memory (up to kSmemBins bins) merged into global memory
-//                   with integer atomics, so the counts are exact and
-//                   independent of scheduling.  HBM-bound: 8 bytes per sample.
+//   hist_edges_kernel / hist_kernel   one grid row per temperature; integer
+//                   counters in shared memory merged into global memory with
+//                   integer atomics, so the counts are exact and independent
+//                   of scheduling.  Up to kEdgeBins bins the bin comes from
+//                   exact key-space edges (no FP64 work per sample: GB300's
+//                   FP64 rate would bound the pass), above that from the FP64
+//                   definition directly.
 //   rowsum_kernel / colsum_kernel      N_i and ln H(b)
 //   dos_kernel      one thread per bin: ln g_b from the current ln Z_i
 //   lnz_kernel      one block per temperature: ln Z_i = ln sum_b g_b e^(-beta_i E_b)
@@ -21,6 +24,7 @@
 // Sums of exponentials are max + ln sum exp(x - max), each sum taken in a
 // fixed order (thread-strided partial sums, then a fixed tree).
 #include <cmath>
+#include <cstring>
 #include <limits>
 #include <string>
 #include <vector>
@@ -71,31 +75,48 @@ __device__ double block_sum(double v, double* sh) {
 // bytes in flight.
 constexpr int kUnroll = 8;
 
+// Order-preserving map of a double's bits to a signed 64-bit key: for
+// doubles a < b (neither NaN), key(a) < key(b), and -0 and +0 both map to 0,
+// so key comparisons agree with IEEE comparisons.  Range tests and min / max
+// then run on the integer pipes, which GB300 has in far greater number than
+// FP64 units.  NaNs map beyond the keys of +-inf.  The map is its own inverse
+// on every key except 0, which goes back to +0.
+__host__ __device__ __forceinline__ long long order_key(long long bits) {
+    if (bits >= 0) return bits;
+    return bits == (long long)0x8000000000000000ULL ? 0 : (bits ^ 0x7fffffffffffffffLL);
+}
+constexpr long long kKeyPosInf = 0x7ff0000000000000LL;
+constexpr long long kKeyNegInf = -0x7ff0000000000001LL;  // order_key of -inf
+
 __global__ void __launch_bounds__(kT) range_kernel(const double* E, long long n, double* bmin,
                                                    double* bmax) {
     __shared__ double sh[kT];
-    double lo = INFINITY, hi = -INFINITY;
+    const long long* Eb = reinterpret_cast<const long long*>(E);
+    long long klo = kKeyPosInf, khi = kKeyNegInf;  // finite keys lie strictly between
     const long long stride = (long long)gridDim.x * kT;
     for (long long i0 = (long long)blockIdx.x * kT + threadIdx.x; i0 < n; i0 += stride * kUnroll) {
-        double v[kUnroll];
+        long long v[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             const long long i = i0 + u * stride;
-            v[u] = i < n ? E[i] : NAN;
+            v[u] = i < n ? order_key(Eb[i]) : kKeyPosInf;
         }
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-            if (isfinite(v[u])) {
-                lo = fmin(lo, v[u]);
-                hi = fmax(hi, v[u]);
+            if (v[u] > kKeyNegInf && v[u] < kKeyPosInf) {  // finite
+                klo = min(klo, v[u]);
+                khi = max(khi, v[u]);
             }
         }
     }
-    hi = block_max(hi, sh);
-    lo = -block_max(-lo, sh);
+    // back to doubles for the block reduction (exact: min and max pick values)
+    const double lo = klo < kKeyPosInf ? __longlong_as_double(order_key(klo)) : INFINITY;
+    const double hi = khi > kKeyNegInf ? __longlong_as_double(order_key(khi)) : -INFINITY;
+    const double rhi = block_max(hi, sh);
+    const double rlo = -block_max(-lo, sh);
     if (threadIdx.x == 0) {
-        bmin[blockIdx.x] = lo;
-        bmax[blockIdx.x] = hi;
+        bmin[blockIdx.x] = rlo;
+        bmax[blockIdx.x] = rhi;
     }
 }
 
@@ -116,8 +137,12 @@ __global__ void __launch_bounds__(kT) range_final_kernel(const double* bmin, con
 }
 
 // Row blockIdx.y of E (the samples of one temperature) into hist[row][:].
+// The range test runs on the order keys (kmin = key(e_min), kmax =
+// key(e_max)); the bin is floor((e - e_min) * inv) in FP64 as the definition
+// states, taken with one round-down conversion.
 __global__ void __launch_bounds__(kT) hist_kernel(const double* E, long long R, int nbins, double e_min,
-                                                  double e_max, double inv, unsigned* hist, int smem_bins) {
+                                                  long long kmin, long long kmax, double inv, unsigned* hist,
+                                                  int smem_bins) {
     extern __shared__ unsigned sh_hist[];
     const double* row = E + (size_t)blockIdx.y * (size_t)R;
     unsigned* gh = hist + (size_t)blockIdx.y * (size_t)nbins;
@@ -125,19 +150,21 @@ __global__ void __launch_bounds__(kT) hist_kernel(const double* E, long long R, 
         for (int b = threadIdx.x; b < nbins; b += kT) sh_hist[b] = 0u;
         __syncthreads();
     }
+    const long long* rowb = reinterpret_cast<const long long*>(row);
     const long long stride = (long long)gridDim.x * kT;
     for (long long k0 = (long long)blockIdx.x * kT + threadIdx.x; k0 < R; k0 += stride * kUnroll) {
-        double v[kUnroll];
+        long long v[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             const long long k = k0 + u * stride;
-            v[u] = k < R ? row[k] : NAN;
+            v[u] = k < R ? rowb[k] : 0x7fffffffffffffffLL;  // a NaN: dropped below
         }
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-            const double e = v[u];
-            if (!(e >= e_min && e <= e_max)) continue;  // NaN and out-of-range samples are dropped
-            long long b = (long long)floor(__dmul_rn(__dsub_rn(e, e_min), inv));
+            const long long key = order_key(v[u]);
+            if (key < kmin || key > kmax) continue;  // NaN and out-of-range samples are dropped
+            const double e = __longlong_as_double(v[u]);
+            long long b = __double2ll_rd(__dmul_rn(__dsub_rn(e, e_min), inv));
             b = b < 0 ? 0 : (b > nbins - 1 ? nbins - 1 : b);
             if (smem_bins)
                 atomicAdd(&sh_hist[b], 1u);
@@ -150,6 +177,68 @@ __global__ void __launch_bounds__(kT) hist_kernel(const double* E, long long R, 
         for (int b = threadIdx.x; b < nbins; b += kT)
             if (sh_hist[b]) atomicAdd(&gh[b], sh_hist[b]);
     }
+}
+
+// The same histogram without FP64 arithmetic per sample (up to kEdgeBins
+// bins): the host has found, for every bin b >= 1, the smallest order key
+// edges[b - 1] whose value the definition puts in bin b or above (the bin is
+// a non-decreasing function of the key).  A sample's bin is estimated in FP32
+// and then moved to the one with edges[b - 1] <= key < edges[b], so the count
+// is exactly the definition's.  Edges and counters live in shared memory.
+constexpr int kEdgeBins = 4096;
+
+// edges[b - 1] for b = 1 .. nbins - 1: the smallest key in [kmin, kmax] whose
+// value the definition puts in bin b or above (kmax + 1 if none), by
+// bisection over keys, one thread per edge.
+__global__ void edges_kernel(int nbins, double e_min, double inv, long long kmin, long long kmax,
+                             long long* edges) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x + 1;
+    if (b >= nbins) return;
+    long long lo = kmin, hi = kmax + 1;
+    while (lo < hi) {
+        // keys of a range across zero span nearly 2^64: halve the unsigned gap
+        const long long mid = lo + (long long)(((unsigned long long)hi - (unsigned long long)lo) / 2ull);
+        const double e = __longlong_as_double(mid >= 0 ? mid : (mid ^ 0x7fffffffffffffffLL));
+        const long long bin = __double2ll_rd(__dmul_rn(__dsub_rn(e, e_min), inv));
+        if (bin >= b) hi = mid;
+        else lo = mid + 1;
+    }
+    edges[b - 1] = lo;
+}
+
+__global__ void __launch_bounds__(kT) hist_edges_kernel(const double* E, long long R, int nbins,
+                                                        float e_min_f, float inv_f, long long kmin,
+                                                        long long kmax, const long long* edges_g,
+                                                        unsigned* hist) {
+    extern __shared__ long long sh_edges[];                   // [nbins - 1]
+    unsigned* sh_hist = reinterpret_cast<unsigned*>(sh_edges + (nbins - 1));  // [nbins]
+    const long long* rowb = reinterpret_cast<const long long*>(E + (size_t)blockIdx.y * (size_t)R);
+    unsigned* gh = hist + (size_t)blockIdx.y * (size_t)nbins;
+    for (int b = threadIdx.x; b < nbins - 1; b += kT) sh_edges[b] = edges_g[b];
+    for (int b = threadIdx.x; b < nbins; b += kT) sh_hist[b] = 0u;
+    __syncthreads();
+    const long long stride = (long long)gridDim.x * kT;
+    for (long long k0 = (long long)blockIdx.x * kT + threadIdx.x; k0 < R; k0 += stride * kUnroll) {
+        long long v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const long long k = k0 + u * stride;
+            v[u] = k < R ? rowb[k] : 0x7fffffffffffffffLL;  // a NaN: dropped below
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const long long key = order_key(v[u]);
+            if (key < kmin || key > kmax) continue;  // NaN and out-of-range samples are dropped
+            const float t = (__double2float_rn(__longlong_as_double(v[u])) - e_min_f) * inv_f;
+            int b = t > 0.0f ? (t < (float)(nbins - 1) ? (int)t : nbins - 1) : 0;
+            while (b > 0 && key < sh_edges[b - 1]) --b;
+            while (b < nbins - 1 && key >= sh_edges[b]) ++b;
+            atomicAdd(&sh_hist[b], 1u);
+        }
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbins; b += kT)
+        if (sh_hist[b]) atomicAdd(&gh[b], sh_hist[b]);
 }
 
 // N_i = sum_b H_i(b) (exact, 64-bit) and ln N_i (-inf for an empty row).
@@ -296,6 +385,7 @@ struct Work {
     double *ln_g = nullptr, *beta_eval = nullptr, *eval = nullptr, *bmin = nullptr, *bmax = nullptr;
     double* range = nullptr;
     unsigned long long* N = nullptr;
+    long long* edges = nullptr;
     SweepState* st = nullptr;
     ~Work() {
         if (base) cudaFree(base);
@@ -381,6 +471,7 @@ extern "C" int pamd_wham(const pamd_wham_args* a, pamd_wham_result* r) {
     const size_t o_bmax = off; off += align256(sizeof(double) * range_blocks);
     const size_t o_rng = off; off += align256(sizeof(double) * 2);
     const size_t o_st = off; off += align256(sizeof(SweepState));
+    const size_t o_edges = off; off += align256(sizeof(long long) * (size_t)std::min(nb, kEdgeBins));
     e = cudaMalloc(&wk.base, off);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -403,6 +494,7 @@ extern "C" int pamd_wham(const pamd_wham_args* a, pamd_wham_result* r) {
     wk.bmax = reinterpret_cast<double*>(base + o_bmax);
     wk.range = reinterpret_cast<double*>(base + o_rng);
     wk.st = reinterpret_cast<SweepState*>(base + o_st);
+    wk.edges = reinterpret_cast<long long*>(base + o_edges);
 
     // energy range
     double e_min = a->e_min, e_max = a->e_max;
@@ -431,8 +523,19 @@ extern "C" int pamd_wham(const pamd_wham_args* a, pamd_wham_result* r) {
     const long long want = (16LL * sms + nT - 1) / nT;
     if (bx > want) bx = want;
     if (bx < 1) bx = 1;
-    hist_kernel<<<dim3((unsigned)bx, (unsigned)nT), kT, smem_bins ? sizeof(unsigned) * nb : 0, s>>>(
-        a->E, R, nb, e_min, e_max, inv, wk.hist, smem_bins);
+    long long bmin_bits, bmax_bits;
+    std::memcpy(&bmin_bits, &e_min, 8);
+    std::memcpy(&bmax_bits, &e_max, 8);
+    const long long kmin = order_key(bmin_bits), kmax = order_key(bmax_bits);
+    if (nb <= kEdgeBins) {
+        if (nb > 1) edges_kernel<<<(nb - 1 + 63) / 64, 64, 0, s>>>(nb, e_min, inv, kmin, kmax, wk.edges);
+        const size_t smem = sizeof(long long) * (size_t)(nb - 1) + sizeof(unsigned) * (size_t)nb;
+        hist_edges_kernel<<<dim3((unsigned)bx, (unsigned)nT), kT, smem, s>>>(
+            a->E, R, nb, (float)e_min, (float)inv, kmin, kmax, wk.edges, wk.hist);
+    } else {
+        hist_kernel<<<dim3((unsigned)bx, (unsigned)nT), kT, smem_bins ? sizeof(unsigned) * nb : 0, s>>>(
+            a->E, R, nb, e_min, kmin, kmax, inv, wk.hist, smem_bins);
+    }
     rowsum_kernel<<<nT, kT, 0, s>>>(wk.hist, nb, wk.lnN, wk.N);
     colsum_kernel<<<(nb + kT - 1) / kT, kT, 0, s>>>(wk.hist, nT, nb, wk.lnH);
     std::vector<unsigned long long> N(nT);

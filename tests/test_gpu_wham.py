@@ -173,3 +173,17 @@ def test_harmonic_chain_anneal_then_wham_gives_the_closed_forms(env):
     exact = 0.5 * d * np.log(temps / temps[0])
     assert np.max(np.abs(g["lnZ"] - exact)) < 0.05, g["lnZ"] - exact
     np.testing.assert_allclose(g["e_mean_eval"], 0.5 * d * KB * T_eval, rtol=0.02)
+
+
+def test_wham_range_edges_and_signed_zero(env):
+    """Samples at and next to the range ends, signed zeros and denormals are
+    counted exactly as the IEEE comparisons of the definition count them."""
+    T = np.array([300.0, 250.0])
+    edge = [0.0, -0.0, 5e-324, -5e-324, 10.0, np.nextafter(10.0, 20.0), np.nextafter(10.0, 0.0),
+            np.nextafter(0.0, -1.0), 2.5, 7.5, np.nan, -np.inf, np.inf]
+    E = np.array([edge, edge[::-1]])
+    g, o = _run_both(env, E, T, 4, e_range=(0.0, 10.0), max_iter=2, tol=0.0)
+    _compare(g, o)
+    assert g["hist"].sum() == 2 * 7
+    g, o = _run_both(env, E, T, 3, e_range=(-0.0, 10.0), max_iter=2, tol=0.0)
+    _compare(g, o)
