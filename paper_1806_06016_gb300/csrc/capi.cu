@@ -371,7 +371,7 @@ int build_topology(const pamd_topology* t, int lanes_req, TopoLayout* lay_out,
                         e[0] = sg * sg;
                         e[1] = pi[1] * pj[1];
                         e[2] = pi[2] * pj[2];
-                        e[3] = 0.0f;
+                        e[3] = e[1] + e[1];  // 2 eps_ij, exact
                     }
             }
     }

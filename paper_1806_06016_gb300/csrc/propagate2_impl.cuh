@@ -94,7 +94,7 @@ __device__ __forceinline__ void pair2(float2 xj, float2 yj, float2 zj, float2 xn
     const float2 rinv2 = mul2(rinv, rinv);
     const float2 s2 = mul2(bc2(sig * sig), rinv2);
     const float2 s6 = mul2(mul2(s2, s2), s2);
-    const float2 lj = mul2(mul2(bc2(eps), s6), fma2(bc2(2.0f), s6, bc2(-1.0f)));
+    const float2 lj = mul2(s6, fma2(bc2(eps + eps), s6, bc2(-eps)));  // eps (2 s^12 - s^6)
     float2 fs = mul2(fma2(bc2(qq), rinv, lj), rinv2);
     if (MASKED) fs = skip ? make_float2(0.0f, 0.0f) : fs;
     gxi = fma2(fs, dx, gxi);
@@ -376,9 +376,10 @@ __device__ __noinline__ double energy_pass2(const unsigned char* sm, const TopoL
             for (int b = a + 1; b < B; ++b) {
                 if ((m >> (a * B + b)) & 1ull) continue;
                 const float sg = hsi[a] + hsi[b];
+                const float eps = sei[a] * sei[b];
                 float fs, e;
                 pair_lj_coul<true>(pi_[b].x - pi_[a].x, pi_[b].y - pi_[a].y, pi_[b].z - pi_[a].z,
-                                   sg * sg, sei[a] * sei[b], qi[a] * qi[b], fs, e);
+                                   sg * sg, eps, eps + eps, qi[a] * qi[b], fs, e);
                 e_acc += (double)e;
             }
     }
@@ -396,9 +397,10 @@ __device__ __noinline__ double energy_pass2(const unsigned char* sm, const TopoL
             for (int a = 0; a < B; ++a) {
                 if ((m >> (a * B + b)) & 1ull) continue;
                 const float sg = hsi[a] + cj.x;
+                const float eps = sei[a] * cj.y;
                 float fs, e;
                 pair_lj_coul<true>(pj.x - pi_[a].x, pj.y - pi_[a].y, pj.z - pi_[a].z,
-                                   sg * sg, sei[a] * cj.y, qi[a] * cj.z, fs, e);
+                                   sg * sg, eps, eps + eps, qi[a] * cj.z, fs, e);
                 e_acc += (double)e;
             }
         }

@@ -51,18 +51,19 @@ struct PropCfg {
 };
 
 // Lennard-Jones + Coulomb for one pair.  d = x_j - x_i.  With
-// sig2 = sigma_ij^2, eps = 24 sqrt(eps_i eps_j) and qq = k_e q_i q_j the force
-// on i is -fs * d and on j +fs * d; e is 4 eps_ij [(s/r)^12 - (s/r)^6] +
-// k_e q_i q_j / r.
+// sig2 = sigma_ij^2, eps = 24 sqrt(eps_i eps_j), e2 = 2 eps (exactly) and
+// qq = k_e q_i q_j the force on i is -fs * d and on j +fs * d, with
+// fs r^2 = eps (2 (s/r)^12 - (s/r)^6) + qq / r = (s/r)^6 (e2 (s/r)^6 - eps) + qq / r;
+// e is 4 eps_ij [(s/r)^12 - (s/r)^6] + k_e q_i q_j / r.
 template <bool ENERGY>
 __device__ __forceinline__ void pair_lj_coul(float dx, float dy, float dz, float sig2, float eps,
-                                             float qq, float& fs, float& e) {
+                                             float e2, float qq, float& fs, float& e) {
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     const float rinv = rsqrtf(r2);
     const float rinv2 = rinv * rinv;
     const float s2 = sig2 * rinv2;
     const float s6 = s2 * s2 * s2;
-    const float lj = eps * s6 * fmaf(2.0f, s6, -1.0f);
+    const float lj = s6 * fmaf(e2, s6, -eps);
     fs = fmaf(qq, rinv, lj) * rinv2;
     if (ENERGY) e = fmaf((eps * (1.0f / 6.0f)) * s6, s6 - 1.0f, qq * rinv);
 }
@@ -75,11 +76,12 @@ __device__ __forceinline__ void pair_lj_coul(float dx, float dy, float dz, float
 // that of a full B x B sweep (a inner for the partner, b increasing for the
 // lane's own atoms).
 //
-// With TABLE the pair parameters {sigma_ij^2, eps_ij, qq_ij} come from a
-// per-tile table in shared memory (entry (b, a) at tab[(b B + a) L]; the L
-// lanes of a group read consecutive float4s) instead of being mixed from the
-// per-atom parameters: the same values (the table holds exactly the FP32
-// products the mixing computes), four fewer FMA-pipe instructions per pair.
+// With TABLE the pair parameters {sigma_ij^2, eps_ij, qq_ij, 2 eps_ij} come
+// from a per-tile table in shared memory (entry (b, a) at tab[(b B + a) L];
+// the L lanes of a group read consecutive float4s) instead of being mixed
+// from the per-atom parameters: the same values (the table holds exactly the
+// FP32 products the mixing computes), five fewer FMA-pipe instructions per
+// pair.
 template <int B, bool MASKED, bool ENERGY, bool TABLE>
 __device__ __forceinline__ void pair_tile(const float (&xi)[B], const float (&yi)[B],
                                           const float (&zi)[B], const float (&hsi)[B],
@@ -99,20 +101,22 @@ __device__ __forceinline__ void pair_tile(const float (&xi)[B], const float (&yi
             const float dx = pj.x - xi[a];
             const float dy = pj.y - yi[a];
             const float dz = pj.z - zi[a];
-            float sig2, eps, qq;
+            float sig2, eps, e2, qq;
             if (TABLE) {
                 const float4 t = tab[(b * B + a) * L];
                 sig2 = t.x;
                 eps = t.y;
                 qq = t.z;
+                e2 = t.w;
             } else {
                 const float sg = hsi[a] + cj.x;
                 sig2 = sg * sg;
                 eps = sei[a] * cj.y;
                 qq = qi[a] * cj.z;
+                e2 = eps + eps;
             }
             float fs, e;
-            pair_lj_coul<ENERGY>(dx, dy, dz, sig2, eps, qq, fs, e);
+            pair_lj_coul<ENERGY>(dx, dy, dz, sig2, eps, e2, qq, fs, e);
             if (MASKED) {
                 const bool skip = (mask >> (a * B + b)) & 1ull;
                 fs = skip ? 0.0f : fs;
@@ -495,8 +499,9 @@ __device__ __forceinline__ void compute_forces(const unsigned char* sm, const To
             for (int b = a + 1; b < B; ++b) {
                 const float dx = xi[b] - xi[a], dy = yi[b] - yi[a], dz = zi[b] - zi[a];
                 const float sg = hsi[a] + hsi[b];
+                const float eps = sei[a] * sei[b];
                 float fs, e;
-                pair_lj_coul<ENERGY>(dx, dy, dz, sg * sg, sei[a] * sei[b], qi[a] * qi[b], fs, e);
+                pair_lj_coul<ENERGY>(dx, dy, dz, sg * sg, eps, eps + eps, qi[a] * qi[b], fs, e);
                 const bool skip = (m >> (a * B + b)) & 1ull;
                 fs = skip ? 0.0f : fs;
                 fx[a] = fmaf(-fs, dx, fx[a]);
@@ -571,9 +576,10 @@ __device__ __noinline__ double energy_pass(const unsigned char* sm, const TopoLa
             for (int b = a + 1; b < B; ++b) {
                 if ((m >> (a * B + b)) & 1ull) continue;
                 const float sg = hsi[a] + hsi[b];
+                const float eps = sei[a] * sei[b];
                 float fs, e;
-                pair_lj_coul<true>(xi[b] - xi[a], yi[b] - yi[a], zi[b] - zi[a], sg * sg,
-                                   sei[a] * sei[b], qi[a] * qi[b], fs, e);
+                pair_lj_coul<true>(xi[b] - xi[a], yi[b] - yi[a], zi[b] - zi[a], sg * sg, eps, eps + eps,
+                                   qi[a] * qi[b], fs, e);
                 e_acc += (double)e;
             }
         }
@@ -592,9 +598,10 @@ __device__ __noinline__ double energy_pass(const unsigned char* sm, const TopoLa
             for (int a = 0; a < B; ++a) {
                 if ((m >> (a * B + b)) & 1ull) continue;
                 const float sg = hsi[a] + cj.x;
+                const float eps = sei[a] * cj.y;
                 float fs, e;
-                pair_lj_coul<true>(pj.x - xi[a], pj.y - yi[a], pj.z - zi[a], sg * sg,
-                                   sei[a] * cj.y, qi[a] * cj.z, fs, e);
+                pair_lj_coul<true>(pj.x - xi[a], pj.y - yi[a], pj.z - zi[a], sg * sg, eps, eps + eps,
+                                   qi[a] * cj.z, fs, e);
                 e_acc += (double)e;
             }
         }

@@ -337,27 +337,41 @@ def test_anneal_graph_equals_stepwise_calls(lib):
 
 
 def test_c1_anneal_statistical_parity(lib, orc):
-    """22-atom chain, R=256, theta=100, 20 geometric steps 1000 -> 300 K."""
+    """22-atom chain, R=256, theta=100, 20 geometric steps 1000 -> 300 K.
+
+    Eight independent anneals (seeds) on each side.  One R = 256 anneal ends
+    with a handful of families, so its family-binned error understates the
+    spread of its means at low T and one realisation can sit 3 such errors
+    away by chance; the run-to-run spread of eight runs is an honest error.
+    The combined error of the two eight-run means takes, per side, the larger
+    of the run-to-run standard error and the pooled family-binned error.
+    """
     top = pi.make_chain(22, 1)
     temps = pi.geometric_schedule(1000.0, 300.0, 20)
-    R, theta, dt, gamma, seed = 256, 100, 0.001, 1.0, 12345
-    ctx = lib.pamd_init(top, R, temps[0], seed, _opts(lib, gamma_per_ps=gamma))
-    try:
-        og = lib.pamd_anneal(ctx, temps, theta, dt)
-    finally:
-        lib.pamd_destroy(ctx)
-    oo, *_ = orc.anneal(top, R, temps, theta, dt, gamma, seed)
-    for key, se in (("e_pot", "e_pot_se"), ("rg", "rg_se")):
-        g = np.array([o[key] for o in og])
-        o = np.array([o[key] for o in oo])
-        s = np.sqrt(np.array([x[se] for x in og]) ** 2 + np.array([x[se] for x in oo]) ** 2)
+    R, theta, dt, gamma = 256, 100, 0.001, 1.0
+    seeds = [12345 + 1000 * k for k in range(8)]
+    og, oo = [], []
+    for sd in seeds:
+        ctx = lib.pamd_init(top, R, temps[0], sd, _opts(lib, gamma_per_ps=gamma))
+        try:
+            og.append(lib.pamd_anneal(ctx, temps, theta, dt))
+        finally:
+            lib.pamd_destroy(ctx)
+        oo.append(orc.anneal(top, R, temps, theta, dt, gamma, sd)[0])
+
+    def mean_and_se(runs, key, se):
+        v = np.array([[o[key] for o in r] for r in runs])
+        f = np.array([[o[se] for o in r] for r in runs])
+        n = v.shape[0]
+        return v.mean(0), np.maximum(v.std(0, ddof=1) / np.sqrt(n), np.sqrt((f ** 2).sum(0)) / n)
+
+    # kinetic energy: theta = 100 is too short to equilibrate (the paper's
+    # point about theta), so it is compared GPU against oracle, not against T
+    for key, se in (("e_pot", "e_pot_se"), ("rg", "rg_se"), ("e_kin", "e_kin_se")):
+        g, sg = mean_and_se(og, key, se)
+        o, so = mean_and_se(oo, key, se)
+        s = np.hypot(sg, so)
         assert np.all(np.abs(g - o) <= 3 * s), (key, (g - o) / s)
-    # kinetic temperature: theta = 100 is too short to equilibrate (the
-    # paper's point about theta), so compare GPU with oracle, not with T
-    g = np.array([o["e_kin"] for o in og])
-    o = np.array([o["e_kin"] for o in oo])
-    s = np.sqrt(np.array([x["e_kin_se"] for x in og]) ** 2 + np.array([x["e_kin_se"] for x in oo]) ** 2)
-    assert np.all(np.abs(g - o) <= 3 * s), (g - o) / s
 
 
 def test_c1_anneal_control_statistical_parity(lib, orc):
