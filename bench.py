@@ -80,6 +80,8 @@ NCU_TRAFFIC = {
     # after the bonded terms moved to reciprocal square roots and the O-step
     # noise to the hardware sine/cosine: 15.09 MB read, 0 written
     "226d5425bfeba8c3": 15087360,
+    # after the Lennard-Jones force moved to s6 (2 eps s6 - eps): 15.09 MB read
+    "62276454e318c196": 15088128,
 }
 
 
