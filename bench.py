@@ -509,6 +509,19 @@ def run_control(args):
     a, b = out["pa_theta4375"], out["anneal_theta4375"]
     d = b["e_pot"][-1] - a["e_pot"][-1]
     out["anneal_minus_pa_e_pot_200K"] = {"kJmol": d, "combined_se": float(np.hypot(a["e_pot_se"][-1], b["e_pot_se"][-1]))}
+    if not args.no_cpu_baseline:
+        # the oracle on a bounded sample of the same runs: 128 replicas,
+        # theta = 100 at each of the eight temperatures, resampling off
+        import oracle
+        oracle.build()
+        cores = os.cpu_count() or 1
+        t0 = time.perf_counter()
+        oracle.anneal(top, 128, temps, 100, dt, 1.0, seed, resample=False, n_threads=cores)
+        t_or = time.perf_counter() - t0
+        units = N * 128 * 100 * len(temps)
+        out["cpu_baseline"] = {"value": units / t_or, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"128 replicas, theta=100 at the 8 temperatures, resampling off, "
+                                         f"{units:.3g} atom-steps, FP64, {cores} threads"}
     print(json.dumps(out), flush=True)
 
 
@@ -557,6 +570,17 @@ def run_wham(args):
         "lnZ_final": {"wham": float(g["lnZ"][-1]), "sum_lnQ": float(z[-1] - z[0])},
         "midpoint_e_mean_between_neighbours_fraction": float(between),
     }
+    if not args.no_cpu_baseline:
+        # the oracle on the same recorded energies, same bins, start values and stopping rule
+        from oracle import wham as owham
+        E_host = rec.cpu().numpy()
+        t0 = time.perf_counter()
+        o = owham.wham(E_host, temps, 2000, lnZ_init=z, max_iter=2000, tol=1e-10, T_eval=mids)
+        t_or = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": t_or, "unit": "s per WHAM call", "cores": 1, "kind": "oracle",
+                               "sample": f"the same {len(temps)} x {R} energies, 2000 bins, "
+                                         f"{o['iterations']} sweeps (numpy FP64)",
+                               "lnZ_max_abs_diff_vs_gpu": float(np.max(np.abs(o["lnZ"] - g["lnZ"])))}
     # synthetic large set: Gaussian energies whose mean and width follow the
     # 75-atom chain's (mean from the PA run, width sqrt(k_B T^2 C_v) ~ 10 kJ/mol)
     K4, R4 = 60, 1 << 20
@@ -639,6 +663,18 @@ def run_adaptive(args):
             pamd.pamd_overlap_temperature(E.data_ptr(), n, 1000.0, 250.0, 0.5, stream.cuda_stream)
             ts.append(time.perf_counter() - t0)
         out[f"overlap_step_ms_R{n}"] = 1e3 * statistics.median(ts)
+        if n == R and not args.no_cpu_baseline:
+            # the oracle's FP64 overlap root on the same energies
+            from oracle import adaptive as oadapt
+            E_host = E.cpu().numpy()
+            t0 = time.perf_counter()
+            T_or, _ = oadapt.next_temperature(E_host, 1000.0, 250.0, 0.5)
+            t_or = time.perf_counter() - t0
+            T_gpu, _ = pamd.pamd_overlap_temperature(E.data_ptr(), n, 1000.0, 250.0, 0.5, stream.cuda_stream)
+            out["cpu_baseline"] = {"value": 1e3 * t_or, "unit": "ms per overlap step", "cores": 1,
+                                   "kind": "oracle",
+                                   "sample": f"the same {n} energies, Brent root in FP64 (numpy)",
+                                   "T_next": {"oracle": T_or, "gpu": T_gpu}}
     print(json.dumps(out), flush=True)
 
 
