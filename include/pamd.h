@@ -49,7 +49,7 @@ extern "C" {
 #define PAMD_ETIMEOUT (-4)    /* a bounded device-side wait gave up */
 #define PAMD_ENONFINITE (-5)  /* a replica's energy became NaN or infinite */
 #define PAMD_ESTATE (-6)      /* the context is broken by an earlier failure */
-#define PAMD_EUNSUPPORTED (-7) /* valid request this build cannot serve */
+#define PAMD_EUNSUPPORTED (-7) /* valid request the library cannot serve */
 
 /* Largest molecule the shared-memory kernels hold (atoms). */
 #define PAMD_MAX_ATOMS 256

@@ -6,15 +6,15 @@
 //   tau_j = R exp(-dbeta E_j) / sum_k exp(-dbeta E_k),
 //   alpha(dbeta) = (1/R) sum_j min(1, tau_j),
 // and the next temperature is T_final if alpha(dbeta_final) >= alpha*, else
-// the T with alpha = alpha*.  The search is a multisection: round 0 tries
-// dbeta_final alone, each later round evaluates kG equally spaced candidates
+// the T with alpha = alpha*.  The search is a multisection: pass 0 tries
+// dbeta_final alone, each later pass evaluates kG equally spaced candidates
 // inside the current bracket (one block per candidate) and keeps the pair
-// that straddles alpha*, shrinking the bracket by kG + 1; after kRounds the
+// that straddles alpha*, shrinking the bracket by kG + 1; after kPasses the
 // bracket is below 1e-6 of dbeta_final, about the resolution of the FP32
 // candidate values.  The exponentials are FP32 on x_j = E_j - min E (FP64
 // difference, rounded once); partial sums of up to kChunk FP32 terms go into
 // FP64 accumulators and blocks reduce in a fixed order, so the result is
-// deterministic.  Launches per step: 2 (min and x), then 2 per round.
+// deterministic.  Launches per step: 2 (min and x), then 2 per pass.
 #include <cmath>
 #include <string>
 
@@ -25,14 +25,14 @@ namespace pamd {
 namespace {
 
 constexpr int kT = 256;
-constexpr int kG = 128;      // candidates per round
-constexpr int kRounds = 3;   // after round 0
+constexpr int kG = 128;      // candidates per pass
+constexpr int kPasses = 3;   // after pass 0
 constexpr int kChunk = 32;   // FP32 terms per FP64 partial sum
 constexpr int kMinBlocks = 1024;
 
 struct OvState {
     double lo, hi, alpha_lo, emin;
-    int done, at_final, round, n_cand, bad, pad_[3];
+    int done, at_final, pass, n_cand, bad, pad_[3];
     double cand[kG];
     double alpha[kG];
 };
@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kT) ov_min_kernel(const double* E, long long R
     if (threadIdx.x == 0) part[blockIdx.x] = bad ? NAN : m;
 }
 
-// x_j = E_j - min E in FP32; block 0 also sets up the search (round 0: the
+// x_j = E_j - min E in FP32; block 0 also sets up the search (pass 0: the
 // final temperature alone)
 __global__ void __launch_bounds__(kT) ov_x_kernel(const double* E, long long R, const double* part, int nparts,
                                                   double d_final, float* x, OvState* st) {
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(kT) ov_x_kernel(const double* E, long long R, 
         st->emin = m;
         st->done = bad;
         st->at_final = 0;
-        st->round = 0;
+        st->pass = 0;
         st->n_cand = 1;
         st->bad = bad;
         st->cand[0] = d_final;
@@ -137,11 +137,11 @@ __global__ void __launch_bounds__(kT) ov_eval_kernel(const float* x, long long R
     if (threadIdx.x == 0) st->alpha[blockIdx.x] = A / (double)R;
 }
 
-// keep the candidates that straddle alpha*, then lay out the next round
+// keep the candidates that straddle alpha*, then lay out the next pass
 __global__ void ov_pick_kernel(OvState* st, double target) {
     if (threadIdx.x != 0 || st->done) return;
     const int n = st->n_cand;
-    if (st->round == 0) {
+    if (st->pass == 0) {
         if (st->alpha[0] >= target) {
             st->lo = st->cand[0];
             st->alpha_lo = st->alpha[0];
@@ -158,7 +158,7 @@ __global__ void ov_pick_kernel(OvState* st, double target) {
         }
         if (g < n) st->hi = st->cand[g];
     }
-    st->round += 1;
+    st->pass += 1;
     const double lo = st->lo, w = (st->hi - st->lo) / (double)(kG + 1);
     for (int g = 0; g < kG; ++g) st->cand[g] = lo + (double)(g + 1) * w;
     st->n_cand = kG;
@@ -187,11 +187,11 @@ int overlap_step(cudaStream_t s, const double* E, long long R, double T_prev, do
     const int gx = (int)std::min<long long>((R + kT - 1) / kT, 8LL * num_sms);
     ov_min_kernel<<<nparts, kT, 0, s>>>(E, R, part);
     ov_x_kernel<<<gx, kT, 0, s>>>(E, R, part, nparts, d_final, x, st);
-    for (int r = 0; r <= kRounds; ++r) {
+    for (int r = 0; r <= kPasses; ++r) {
         ov_eval_kernel<<<r == 0 ? 1 : kG, kT, 0, s>>>(x, R, st);
         ov_pick_kernel<<<1, 32, 0, s>>>(st, alpha_target);
     }
-    if (launches) *launches += 2 + 2 * (kRounds + 1);
+    if (launches) *launches += 2 + 2 * (kPasses + 1);
     cudaError_t e = cudaGetLastError();
     OvState h;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, st, sizeof(OvState), cudaMemcpyDeviceToHost, s);
