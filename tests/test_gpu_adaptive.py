@@ -203,3 +203,26 @@ def test_systematic_resampling_keeps_the_harmonic_closed_forms(env):
     assert np.all(np.abs(e - e_exact) < 4 * se + 0.005 * e_exact), (e - e_exact) / se
     f = np.array([o["sum_lnQ"] for o in obs])
     assert np.all(np.abs(f - 1.5 * (n - 1) * np.log(temps / temps[0])) < 0.05)
+
+
+def test_adaptive_anneal_with_resampling_off(env):
+    """The control run on an overlap-chosen schedule: no family is pruned and
+    every step still meets the overlap condition on the recorded energies."""
+    torch, pamd, _, oa = env
+    top = pi.make_chain(22, 1)
+    R, alpha = 128, 0.6
+    rec = torch.empty((21, R), dtype=torch.float64, device="cuda")
+    ctx = pamd.pamd_init(top, R, 900.0, 5)
+    try:
+        pamd.pamd_record_energies(ctx, rec.data_ptr(), 21)
+        obs, temps = pamd.pamd_anneal_adaptive(ctx, 900.0, 400.0, alpha, 50, 0.001, 20, resample=False)
+        fam = pamd.pamd_get_state(ctx, False, False, False, True)[3]
+    finally:
+        pamd.pamd_destroy(ctx)
+    np.testing.assert_array_equal(fam, np.arange(R))
+    assert all(o["n_families"] == R for o in obs)
+    E = rec.cpu().numpy()
+    for i in range(1, len(temps)):
+        d = 1.0 / (KB * temps[i]) - 1.0 / (KB * temps[i - 1])
+        a = oa.overlap(E[i - 1], d)
+        assert (a >= alpha - 5e-5) if temps[i] == 400.0 else abs(a - alpha) < 5e-5

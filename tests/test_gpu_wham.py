@@ -66,7 +66,7 @@ def _compare(g, o, n_eval=0):
 
 
 @pytest.mark.parametrize("n_bins,R,n_temps", [(300, 5000, 9), (1, 17, 3), (257, 1, 4), (20000, 30000, 5),
-                                              (12288, 4099, 2)])
+                                              (12288, 4099, 2), (4096, 3001, 3), (4097, 3001, 3)])
 def test_wham_matches_oracle_at_fixed_sweeps(env, n_bins, R, n_temps):
     T = np.geomspace(500.0, 250.0, n_temps)
     E = _samples(n_bins + R, T, R, bad=R >= 8)
