@@ -658,6 +658,9 @@ int set_launch_shape(pamd_ctx* c, const TopoLayout& lay_in, int warps_req, int p
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int groups_per_warp = 32 / lay.lanes;  // idle lanes when L does not divide 32
     int warps = warps_req ? warps_req : 4;
+    // the single-replica kernel of some atoms-per-lane counts takes smaller blocks
+    if (!lay.paired && lay.per_lane >= 1 && lay.per_lane <= 8)
+        warps = std::min(warps, prop_max_threads(lay.per_lane) / 32);
     auto smem = [&](int w) {
         return (long long)lay.bytes + (long long)w * groups_per_warp * slot_f4(lay) * 16;
     };

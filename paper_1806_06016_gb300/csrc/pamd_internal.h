@@ -13,6 +13,10 @@
 namespace pamd {
 
 constexpr double kBoltzmann = 0.008314462618;  // kJ/mol/K
+
+// Largest block of the single-replica propagate kernel with B atoms per lane
+// (its launch bounds): 5 atoms per lane run 128-thread blocks, three per SM.
+__host__ __device__ constexpr int prop_max_threads(int B) { return B == 5 ? 128 : 256; }
 constexpr double kCoulomb = 138.935458;        // kJ mol^-1 nm e^-2
 constexpr int kNumBins = 64;                   // family bins for jackknife errors
 constexpr uint32_t kPurposeNoise = 0u, kPurposeInit = 1u, kPurposeResample = 2u;

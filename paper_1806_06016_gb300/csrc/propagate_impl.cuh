@@ -36,17 +36,22 @@
 
 namespace pamd {
 
-// Blocks of 256 threads per SM the compiler is asked to fit: 2 (128
-// registers per thread) for up to 3 atoms per lane, 1 (255) above, where the
-// cap would spill.  Chosen by measurement; a build may override it with
-// PAMD_PROP_MIN_BLOCKS.
+// Launch bounds, chosen by measurement: blocks of up to 256 threads, two per
+// SM (128 registers per thread) for up to 3 atoms per lane and one (255)
+// above, where the cap would spill; except 5 atoms per lane, whose blocks
+// are capped at 128 threads so that three fit per SM at 170 registers (12
+// warps instead of 8: 1.7 % faster than the best 256-thread shape on the
+// 75-atom chain).  A build may override the block count with
+// PAMD_PROP_MIN_BLOCKS.  prop_max_threads (pamd_internal.h) is the host's copy
+// of the block-size cap.
 template <int B>
 struct PropCfg {
     static constexpr int BS = (B % 2 == 1) ? B : B + 1;  // odd stride: conflict-free LDS.128
+    static constexpr int MAX_THREADS = prop_max_threads(B);
 #ifdef PAMD_PROP_MIN_BLOCKS
     static constexpr int MIN_BLOCKS = PAMD_PROP_MIN_BLOCKS;
 #else
-    static constexpr int MIN_BLOCKS = (B <= 3) ? 2 : 1;
+    static constexpr int MIN_BLOCKS = (B <= 3) ? 2 : (B == 5 ? 3 : 1);
 #endif
 };
 
@@ -765,7 +770,7 @@ __device__ __forceinline__ void advance_replica(const PropParams& p, const unsig
 }
 
 template <int B, bool CHAIN, bool TABLE>
-__global__ void __launch_bounds__(256, PropCfg<B>::MIN_BLOCKS) propagate_kernel(const PropParams p) {
+__global__ void __launch_bounds__(PropCfg<B>::MAX_THREADS, PropCfg<B>::MIN_BLOCKS) propagate_kernel(const PropParams p) {
     using C = PropCfg<B>;
     extern __shared__ float4 smem4[];
     unsigned char* sm = reinterpret_cast<unsigned char*>(smem4);
