@@ -49,7 +49,7 @@ int pamd_record_energies(pamd_ctx* ctx, double* E_dev, int32_t rows);
 typedef struct pamd_wham_args {
     const double* E;        /* device [n_temps][R] energies (kJ/mol), row i sampled at T[i] */
     int32_t n_temps;        /* >= 1 */
-    int64_t R;              /* samples per temperature, >= 1 */
+    int64_t R;              /* samples per temperature, 1 .. 2^32 - 1 (32-bit bin counters) */
     const double* T;        /* host [n_temps] K, > 0 */
     int32_t n_bins;         /* 1 .. 65536 */
     double e_min, e_max;    /* histogram range; e_max <= e_min: [min E, max E] over the

@@ -411,10 +411,10 @@ extern "C" int pamd_wham(const pamd_wham_args* a, pamd_wham_result* r) {
     }
     const int nT = a->n_temps, nb = a->n_bins, ne = a->n_eval;
     const long long R = a->R;
-    if (nT < 1 || nT > 65535 || R < 1 || nb < 1 || nb > kMaxBins || a->max_iter < 0 || ne < 0 ||
-        (ne > 0 && !a->T_eval) || !(a->tol >= 0)) {
-        set_last_error("pamd_wham: n_temps 1..65535, R >= 1, n_bins 1..65536, max_iter >= 0, "
-                       "n_eval >= 0 with T_eval, tol >= 0");
+    if (nT < 1 || nT > 65535 || R < 1 || R > 0xffffffffLL || nb < 1 || nb > kMaxBins || a->max_iter < 0 ||
+        ne < 0 || (ne > 0 && !a->T_eval) || !(a->tol >= 0)) {
+        set_last_error("pamd_wham: n_temps 1..65535, R 1..2^32-1 (32-bit counters), n_bins 1..65536, "
+                       "max_iter >= 0, n_eval >= 0 with T_eval, tol >= 0");
         return PAMD_EINVAL;
     }
     const bool given_range = a->e_max > a->e_min;
