@@ -1,5 +1,5 @@
 #!/usr/bin/env python3
-"""Benchmark of the PAMD hot path on one GB300 (or N independent GPUs).
+"""Benchmark of the PAMD hot path on one GB300.
 
 A step is one full anneal of the paper-shaped workload: a 75-atom synthetic
 peptide-like chain, R = 8192 replicas, theta = 1000 BAOAB steps of 1 fs per
@@ -58,13 +58,17 @@ METRIC = "atom-steps/sec over all replicas (full anneal)"
 UNIT = "atom-steps/s"
 
 # Algorithmic floating-point work per replica-step of the propagate kernel
-# (forces-only steps, Newton's third law): 36 flop per nonbonded pair (counted
-# from the kernel's pair arithmetic, fma = 2, rsqrt = 1), 30 per bond, 60 per
-# angle, 120 per dihedral, 20 per atom for the integrator and noise.
-FLOP_PAIR, FLOP_BOND, FLOP_ANGLE, FLOP_DIH, FLOP_ATOM = 36, 30, 60, 120, 20
+# (forces-only steps, Newton's third law): the nominal 40 flop per nonbonded
+# pair of the method's work model W(N), 30 per bond, 60 per angle, 120 per
+# dihedral, 20 per atom for the integrator and noise.  FLOP_PAIR_KERNEL is
+# the count of the kernel's own pair arithmetic (fma = 2, rsqrt = 1), reported
+# beside it.
+FLOP_PAIR, FLOP_BOND, FLOP_ANGLE, FLOP_DIH, FLOP_ATOM = 40, 30, 60, 120, 20
+FLOP_PAIR_KERNEL = 36
 
-# FP32 peak of one GB300: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# FP32 peak of one GB300 from unit counts: 152 SMs x 128 FP32 lanes x 2 flop
+# (FMA) x 2.07 GHz.  Reported beside the measured peak (pamd_fp32_peak).
+FP32_PEAK_DERIVED_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
 # dram bytes (read + write) of one propagate launch from the ncu capture in
 # profiles/, keyed by the hash of the kernel source it was taken on; the value
@@ -88,10 +92,20 @@ NCU_TRAFFIC = {
 }
 
 
-def flop_per_replica_step(n):
+def flop_per_replica_step(n, flop_pair=FLOP_PAIR):
     pairs = n * (n - 1) // 2 - max(2 * n - 3, 0)
-    return (FLOP_PAIR * pairs + FLOP_BOND * max(n - 1, 0) + FLOP_ANGLE * max(n - 2, 0)
+    return (flop_pair * pairs + FLOP_BOND * max(n - 1, 0) + FLOP_ANGLE * max(n - 2, 0)
             + FLOP_DIH * max(n - 3, 0) + FLOP_ATOM * n)
+
+
+def measured_fp32_peak(pamd, iters=20000, reps=100):
+    """FP32 FMA throughput measured on this GPU, scalar and packed FP32x2
+    forms (include/pamd_bench.h); the larger is the roofline's peak."""
+    scalar = pamd.pamd_fp32_peak(False, iters, reps)
+    packed = pamd.pamd_fp32_peak(True, iters, reps)
+    return {"ffma_tflops": scalar["tflops"], "ffma2_tflops": packed["tflops"],
+            "peak_tflops": max(scalar["tflops"], packed["tflops"]),
+            "timed_s": (scalar["ms"] + packed["ms"]) / 1e3}
 
 
 def kernel_source_hash():
@@ -221,30 +235,8 @@ def config_of(w, args):
             "theta": w["theta"], "temperature_steps": w["K"], "T_first_K": w["T0"],
             "T_last_K": w["TK"], "dt_fs": w["dt"] * 1e3, "gamma_per_ps": w["gamma"],
             "precision": "FP32 forces/integration, FP64 energies/weights/lnQ",
-            "parallelism": "replicas only" if args.gpus == 1 else f"independent anneals x{args.gpus}",
+            "parallelism": "one GPU",
             "l2": "flushed (512 MB write) between timed steps"}
-
-
-# ------------------------------------------------------- multi-rank logic
-
-def rank_seed(seed: int, rank: int) -> int:
-    """Run seed of rank `rank`: every GPU anneals an independent population."""
-    return seed + 7919 * rank
-
-
-def max_over_ranks(x: float, dist=None, device: str = "cpu") -> float:
-    """The largest of the ranks' values (the job is as slow as its slowest rank)."""
-    if dist is None:
-        return x
-    import torch
-    t = torch.tensor([x], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
-def job_throughput(units_per_rank: float, world: int, max_seconds: float) -> float:
-    """Whole-job units per second: all ranks' units over the slowest rank's time."""
-    return units_per_rank * world / max_seconds
 
 
 # ----------------------------------------------------------------- GPU leg
@@ -257,26 +249,14 @@ def run_gpu(args, w):
     from paper_1806_06016_gb300 import build as pbuild
     from paper_1806_06016_gb300 import pamd
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
+    torch.cuda.set_device(0)
     dev = torch.cuda.current_device()
-    if rank == 0 or world == 1:
-        pbuild.build()
-    if dist:
-        dist.barrier()
+    pbuild.build()
     pamd.load()
 
     temps = pi.geometric_schedule(w["T0"], w["TK"], w["K"])
     R, theta, dt = args.replicas or w["R"], w["theta"], w["dt"]
-    seed = rank_seed(w["seed"], rank)
+    seed = w["seed"]
     # the library launches on this stream; the timing events are recorded on it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
@@ -305,8 +285,6 @@ def run_gpu(args, w):
     torch.cuda.synchronize()
 
     sampler = ClockSampler(dev)
-    if dist:
-        dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
     launches0 = pamd.pamd_launch_count(pop.ctx)
@@ -322,26 +300,20 @@ def run_gpu(args, w):
         elapsed_ms += ev0.elapsed_time(ev1)
     torch.cuda.synchronize()
     launches = pamd.pamd_launch_count(pop.ctx) - launches0
-    if dist:
-        dist.barrier()
     clocks = sampler.stop()
-    max_ms = max_over_ranks(elapsed_ms, dist, "cuda")
-    total_units = atom_steps(w, R) * args.steps * world
+    total_units = atom_steps(w, R) * args.steps
     if w.get("batch"):
         # one batched launch advances all molecules; no single-kernel roofline
         pop.close()
-        line = {"metric": METRIC, "value": job_throughput(total_units / world, world, max_ms / 1e3), "unit": UNIT,
-                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        line = {"metric": METRIC, "value": total_units / (elapsed_ms / 1e3), "unit": UNIT,
+                "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": dict(config_of(w, args), launch_shape=tune, atoms=batch_sizes(w)),
                 "gpu_launches": int(launches), "clocks": clocks}
-        if rank == 0:
-            print(json.dumps(line), flush=True)
-        if dist:
-            dist.destroy_process_group()
+        print(json.dumps(line), flush=True)
         return
-    value = job_throughput(total_units / world, world, max_ms / 1e3)
+    value = total_units / (elapsed_ms / 1e3)
 
     # dominant kernel: the persistent propagate launch, timed alone in the
     # same shape (theta steps over all R replicas) with events on its stream
@@ -358,13 +330,23 @@ def run_gpu(args, w):
         prop_ms.append(ev0.elapsed_time(ev1))
     prop_avg = statistics.mean(prop_ms)
     flops = flop_per_replica_step(w["n_atoms"]) * R * theta
+    flops36 = flop_per_replica_step(w["n_atoms"], FLOP_PAIR_KERNEL) * R * theta
     achieved = flops / (prop_avg / 1e3) / 1e12
     traffic = NCU_TRAFFIC.get(kernel_source_hash())
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
-                "kernel": "propagate_kernel", "launch_ms": prop_avg,
-                "flop_per_launch": flops,
-                "peak_basis": "152 SM x 128 FP32 lanes x 2 flop x 2.07 GHz (derived, not measured)"}
+    peak = measured_fp32_peak(pamd)
+    shape = tune if isinstance(tune, dict) else {}
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak["peak_tflops"], "unit": "TFLOP/s",
+                "frac": achieved / peak["peak_tflops"], "traffic": traffic,
+                "kernel": "propagate_x2_kernel" if shape.get("pair_arith") == 2 else "propagate_kernel",
+                "launch_ms": prop_avg, "flop_per_launch": flops,
+                "flop_model": f"W(N) with {FLOP_PAIR} flop per nonbonded pair",
+                "frac_kernel_count": flops36 / (prop_avg / 1e3) / 1e12 / peak["peak_tflops"],
+                "flop_model_kernel_count": f"W(N) with {FLOP_PAIR_KERNEL} flop per pair (the kernel's own count)",
+                "peak_basis": "measured: pamd_fp32_peak, FMA chains filling every SM, larger of "
+                              "FFMA and packed FFMA2, event-timed in this run",
+                "peak_measured": peak,
+                "peak_derived_tflops": FP32_PEAK_DERIVED_TFLOPS,
+                "frac_of_derived": achieved / FP32_PEAK_DERIVED_TFLOPS}
 
     # end to end through the C-ABI with host buffers: upload the initial
     # population, run the anneal, read the per-temperature observables back
@@ -383,31 +365,24 @@ def run_gpu(args, w):
     np_ = (w["n_atoms"] + 3) // 4 * 4
     h2d = R * 6 * np_ * 4 + R * 4 + 8
     d2h = (w["K"] + 1) * ctypes.sizeof(pamd.PamdObs) + 48
-    e2e_max = max_over_ranks(e2e_s, dist, "cuda")
-    e2e = {"value": job_throughput(atom_steps(w, R) * e2e_steps, world, e2e_max), "unit": UNIT,
+    e2e = {"value": atom_steps(w, R) * e2e_steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
            "final_e_pot_kJmol": obs[-1]["e_pot"], "final_sum_lnQ": obs[-1]["sum_lnQ"]}
     pop.close()
 
-    if rank != 0:
-        if dist:
-            dist.destroy_process_group()
-        return
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
+    if not args.no_cpu_baseline:
         rate, dt_s, cores, sample = oracle_sample(w)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(config_of(w, args), launch_shape=tune), "roofline": roofline,
         "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": int(launches), "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
-    if dist:
-        dist.destroy_process_group()
 
 
 def run_kernel(args, w):
@@ -428,11 +403,13 @@ def run_kernel(args, w):
     torch.cuda.set_stream(stream)
     opts = pamd.torch_options(gamma_per_ps=w["gamma"], lanes_per_replica=args.lanes,
                               warps_per_block=args.warps, replicas_per_lane=args.rpl,
+                              pair_arith=args.pairs,
                               precision=1 if args.fp64 else 0)
     pop = pamd.Population(top, R, w["T0"], w["seed"], opts)
     if args.autotune:
         pop.autotune(50)
     info = pop.info()
+    shape = pamd.pamd_get_shape(pop.ctx) if not args.fp64 else None
     for _ in range(args.warmup):
         pamd.pamd_propagate(pop.ctx, theta, w["dt"], w["T0"])
     torch.cuda.synchronize()
@@ -449,9 +426,31 @@ def run_kernel(args, w):
     avg = statistics.mean(ms)
     flops = flop_per_replica_step(w["n_atoms"]) * R * theta
     achieved = flops / (avg / 1e3) / 1e12
+    peak = FP32_PEAK_DERIVED_TFLOPS
     print(json.dumps({"mode": "kernel", "n_atoms": w["n_atoms"], "replicas": R, "theta": theta,
-                      "launch": info, "rpl": args.rpl, "fp64": args.fp64, "ms": avg, "atom_steps_per_s": w["n_atoms"] * R * theta / (avg / 1e3),
-                      "achieved_tflops": achieved, "frac": achieved / FP32_PEAK_TFLOPS}), flush=True)
+                      "launch": info, "shape": shape,
+                      "rpl": args.rpl, "fp64": args.fp64, "ms": avg, "atom_steps_per_s": w["n_atoms"] * R * theta / (avg / 1e3),
+                      "achieved_tflops": achieved, "frac_of_derived_peak": achieved / peak}), flush=True)
+
+
+def run_fp32peak(args):
+    """The FP32 peak that the force kernel's roofline divides by: FMA chains
+    filling every SM, scalar and packed, timed for about a second each with
+    the clocks sampled meanwhile.  Prints one JSON line."""
+    import torch
+
+    from paper_1806_06016_gb300 import build as pbuild
+    from paper_1806_06016_gb300 import pamd
+    torch.cuda.set_device(0)
+    pbuild.build()
+    pamd.load()
+    pamd.pamd_fp32_peak(False, 2000, 5)  # warm-up
+    sampler = ClockSampler(0)
+    sampler.start()
+    peak = measured_fp32_peak(pamd, iters=20000, reps=max(1, args.steps) * 80)
+    clocks = sampler.stop()
+    print(json.dumps({"mode": "fp32peak", **peak, "derived_tflops": FP32_PEAK_DERIVED_TFLOPS,
+                      "clocks": clocks}), flush=True)
 
 
 def run_control(args):
@@ -1200,7 +1199,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", choices=["anneal", "kernel", "precision", "resample", "gemm", "surrogate",
-                                       "surrogate_kernel", "control", "wham", "adaptive"],
+                                       "surrogate_kernel", "control", "wham", "adaptive", "fp32peak"],
                     default="anneal")
     ap.add_argument("--theta", type=int, default=0,
                     help="kernel mode: steps per launch; control mode: equilibration steps at 700 K")
@@ -1210,6 +1209,8 @@ def main():
     ap.add_argument("--warps", type=int, default=0, help="kernel mode: warps per block")
     ap.add_argument("--autotune", action="store_true", help="kernel mode: tune the launch shape")
     ap.add_argument("--rpl", type=int, default=0, help="kernel mode: replicas per lane group (1, 2)")
+    ap.add_argument("--pairs", type=int, default=0,
+                    help="kernel mode: pair arithmetic (0 auto, 1 scalar, 2 packed FP32x2)")
     ap.add_argument("--fp64", action="store_true", help="kernel mode: all-FP64 propagate")
     ap.add_argument("--seeds", type=int, default=8, help="precision mode: independent anneals")
     ap.add_argument("--temps", type=int, default=0, help="surrogate mode: temperature steps")
@@ -1222,8 +1223,18 @@ def main():
     ap.add_argument("--refine-epochs", type=int, default=8, help="surrogate mode: epochs per round")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "ours" and (args.gpus != 1 or world > 1):
+        # every population runs on a single GPU: no sharding, no collectives
+        if int(os.environ.get("RANK", "0")) == 0:
+            print(json.dumps({"metric": METRIC, "unit": UNIT, "n_gpus": max(args.gpus, world),
+                              "unavailable": "one GPU only: a population is never split across GPUs"}),
+                  flush=True)
+        return
     if args.mode == "kernel":
         run_kernel(args, w)
+    elif args.mode == "fp32peak":
+        run_fp32peak(args)
     elif args.mode == "precision":
         run_precision(args)
     elif args.mode == "control":

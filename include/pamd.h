@@ -116,8 +116,11 @@ typedef struct pamd_topology {
 typedef struct pamd_options {
     double gamma_per_ps;        /* Langevin friction (MD-parameters paragraph: 1/ps) */
     int32_t precision;          /* PAMD_PREC_MIXED or PAMD_PREC_FP64 */
-    int32_t lanes_per_replica;  /* 0 = choose; else 4, 8, 16 or 32 */
-    int32_t warps_per_block;    /* 0 = choose (4); else 1..8 */
+    int32_t lanes_per_replica;  /* 0 = choose; else 1..32 lanes, with at most 8 atoms
+                                   per lane (ceil(n_atoms / lanes) <= 8) */
+    int32_t warps_per_block;    /* 0 = choose (4); else 1..8, lowered to the kernel's
+                                   block-size cap (4 warps for the packed-pair kernel
+                                   and for 5 atoms per lane) and to shared memory */
     int32_t mol_id;             /* molecule index mixed into the random counters */
     int32_t autotune;           /* 1: pamd_autotune(ctx, 20, NULL) at the end of pamd_init */
     int32_t replicas_per_lane;  /* 0 or 1: one replica per lane group; 2: two replicas per
@@ -128,7 +131,18 @@ typedef struct pamd_options {
     void* stream;               /* cudaStream_t; NULL = a non-blocking stream the context creates */
     int32_t resample_rule;      /* PAMD_RESAMPLE_MULTINOMIAL (the paper's choice) or
                                    PAMD_RESAMPLE_SYSTEMATIC */
+    int32_t pair_arith;         /* PAMD_PAIRS_AUTO (0), PAMD_PAIRS_SCALAR or PAMD_PAIRS_PACKED */
 } pamd_options;
+
+/* Arithmetic of the nonbonded pair loop (pamd_options.pair_arith).  PACKED
+ * holds each lane's own atoms in register pairs and evaluates two pairs per
+ * add/mul/fma.f32x2 instruction (same FP32 roundings as the scalar form);
+ * linear chains with 3..8 atoms per lane and one replica per lane group
+ * only.  AUTO starts with SCALAR; pamd_autotune times both where PACKED
+ * applies and keeps the faster. */
+#define PAMD_PAIRS_AUTO 0
+#define PAMD_PAIRS_SCALAR 1
+#define PAMD_PAIRS_PACKED 2
 
 /* Per-temperature population averages (PAMD scheme, step 4) with jackknife
  * errors over 64 family bins (paragraph on correlations after resampling). */
@@ -280,6 +294,8 @@ typedef struct pamd_tune {
     int32_t replicas_per_lane; /* 1, or 2 for the packed two-replica kernels */
     int32_t from_cache;        /* 1 if the shape came from the cache */
     double ms;                 /* probe time of the chosen shape (0 if cached) */
+    int32_t pair_arith;        /* PAMD_PAIRS_SCALAR or PAMD_PAIRS_PACKED */
+    int32_t pad_;
 } pamd_tune;
 
 /*
@@ -309,26 +325,33 @@ int pamd_autotune(pamd_ctx* ctx, int32_t theta_probe, pamd_tune* out);
  * Computes exactly what pamd_resample computes for copies_out and lnQ_out
  * (same integer weights, prefix sums, Philox targets and ancestors; copy
  * counts identical bit for bit) from R energies already on the device, but
- * does not gather a population.  E_dev: device [R] FP64 potential energies;
- * non-finite energies get weight 0.  resample_index and mol_id select the
- * Philox stream as in pamd_resample (its k-th call on a context uses index
- * k).  counts_dev: device [R] int32 output, n_j by ancestor.  lnQ_dev: device
- * double output or NULL.  stream: cudaStream_t (NULL = legacy default).
- * Asynchronous: returns after queuing the work.
+ * does not gather a population.  E_dev: device [R] FP64 potential energies.
+ * resample_index and mol_id select the Philox stream as in pamd_resample (its
+ * k-th call on a context uses index k).  counts_dev: device [R] int32 output,
+ * n_j by ancestor.  lnQ_dev: device double output or NULL.  status_dev:
+ * device int32 output or NULL; it receives 0, or PAMD_ENONFINITE when some
+ * energy was NaN or infinite.  Such replicas get weight 0 (pamd_resample
+ * reports the same case as PAMD_ENONFINITE); if every energy is non-finite
+ * the counts are meaningless and ln Q is NaN, so a caller that cannot rule
+ * this out must check status_dev.  stream: cudaStream_t (NULL = legacy
+ * default).  Asynchronous: returns after queuing the work.
  *
  * Its scratch is one static device array of 2.1 MiB inside the library,
  * which every GPU that loads the library holds until the process exits; R
  * is therefore limited to 262144 (PAMD_EINVAL above).  No cudaMalloc, cudaFree
- * or allocating library routine is called.  The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  All calls share the array: calls that overlap
- * on the GPU (different streams, or different host threads on one device)
- * race with each other and must be serialised by the caller.
+ * or allocating library routine is called.  Every call made outside stream
+ * capture looks up the array's device address on the current device
+ * (cudaGetSymbolAddress); a call on a stream that is being captured reuses the
+ * address of that device's last uncaptured call, so the first call on a
+ * device must come before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU (different streams, or different host threads
+ * on one device) race with each other and must be serialised by the caller.
  * Errors: PAMD_EINVAL (null pointer, R, temperatures, mol_id), PAMD_ECUDA.
  */
 int pamd_resample_counts_noalloc(const double* E_dev, int64_t R, double T_prev, double T_next,
                                  uint64_t seed, uint32_t resample_index, int32_t mol_id,
-                                 int32_t* counts_dev, double* lnQ_dev, void* stream);
+                                 int32_t* counts_dev, double* lnQ_dev, int32_t* status_dev,
+                                 void* stream);
 
 /*
  * Checkpoint files.  pamd_checkpoint writes the current population (state,
@@ -355,6 +378,11 @@ int pamd_set_counters(pamd_ctx* ctx, uint32_t step, uint32_t resample_index, dou
 /* Number of replicas and atoms; the launch shape in use for propagate. */
 int pamd_info(pamd_ctx* ctx, int64_t* R, int32_t* n_atoms, int32_t* lanes_per_replica,
               int32_t* atoms_per_lane, int32_t* replicas_per_block);
+
+/* Launch shape the propagate kernel of this context uses now (no
+ * counterpart in the paper).  out->from_cache and out->ms are 0.  Errors:
+ * PAMD_EINVAL (null argument, batch context). */
+int pamd_get_shape(pamd_ctx* ctx, pamd_tune* out);
 
 /* Number of kernel launches the library issued on this context so far. */
 int64_t pamd_launch_count(pamd_ctx* ctx);

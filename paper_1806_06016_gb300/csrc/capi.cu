@@ -412,6 +412,7 @@ cudaError_t propagate_dispatch_any(const TopoLayout& lay, const PropParams* p, i
                                    size_t smem, cudaStream_t s, int* occ) {
     const bool chain = lay.chain != 0;
     const bool table = lay.ptab != 0;
+    if (lay.packed) return propagate_x2_dispatch(lay.per_lane, p, warps, grid, smem, s, occ);
     if (lay.paired) {
         switch (lay.per_lane) {
             case 2: return propagate2_b2(p, chain, warps, grid, smem, s, occ);
@@ -433,12 +434,24 @@ cudaError_t propagate_dispatch_any(const TopoLayout& lay, const PropParams* p, i
     }
 }
 
-// float4s of shared memory per replica slot (single) or replica-pair slot (paired)
-int slot_f4(const TopoLayout& lay) { return lay.paired ? 3 * lay.nk + 1 : 2 * lay.nk + 1; }
+// float4s of shared memory per replica slot (single, packed) or replica-pair
+// slot (paired)
+int slot_f4(const TopoLayout& lay) {
+    if (lay.packed) return x2_slot_f4(lay);
+    return lay.paired ? 3 * lay.nk + 1 : 2 * lay.nk + 1;
+}
+
+// Shared memory of one propagate block with `units` replica (or replica-pair)
+// slots: the topology table (for the packed kernel without the pair table,
+// with its per-atom tables), then the slots.
+size_t prop_smem_units(const TopoLayout& lay, int units) {
+    const size_t table = lay.packed ? (size_t)x2_topo_bytes(lay) + (size_t)x2_table_f4(lay) * 16
+                                    : (size_t)lay.bytes;
+    return table + (size_t)units * slot_f4(lay) * 16;
+}
 
 size_t prop_smem(const pamd_ctx* c) {
-    const int units = c->lay.paired ? c->rpb / 2 : c->rpb;
-    return (size_t)c->lay.bytes + (size_t)units * slot_f4(c->lay) * 16;
+    return prop_smem_units(c->lay, c->lay.paired ? c->rpb / 2 : c->rpb);
 }
 
 float* cur_state(pamd_ctx* c) { return c->cur_is_alt ? c->b.state_alt : c->b.state; }
@@ -587,16 +600,19 @@ struct TuneKey {
     long long R;
     int chain;
     int lanes_req;
+    int pair_arith;
 };
 struct TuneShape {
-    int L, W, paired;
+    int L, W, variant;  // variant: kVarScalar, kVarPaired or kVarPacked
 };
 // Shapes a tuning run may choose: atoms per lane bmin..bmax, the given warp
-// counts, packed two-replica kernels or not.  The batched kernel needs
-// B = 3..7, kBatchThreads / 32 warps and single replicas.
+// counts, two-replica kernels or not, packed-pair kernels or not.  The batched
+// kernel needs B = 3..7, kBatchThreads / 32 warps, single replicas and
+// scalar pair arithmetic.
 struct TuneLimits {
     int bmin, bmax;
     bool paired_ok;
+    bool packed_ok;
     std::vector<int> warps;
     int key_tag;  // separates the cache entries of restricted searches
 };
@@ -607,7 +623,8 @@ std::vector<std::pair<TuneKey, TuneShape>> g_tune;
 bool tune_cache_lookup(const TuneKey& k, TuneShape* out) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto match = [&](const TuneKey& q) {
-        return q.N == k.N && q.R == k.R && q.chain == k.chain && q.lanes_req == k.lanes_req;
+        return q.N == k.N && q.R == k.R && q.chain == k.chain && q.lanes_req == k.lanes_req &&
+               q.pair_arith == k.pair_arith;
     };
     for (auto& e : g_tune)
         if (match(e.first)) {
@@ -621,10 +638,10 @@ bool tune_cache_lookup(const TuneKey& k, TuneShape* out) {
     TuneKey q;
     TuneShape t;
     bool found = false;
-    while (std::fscanf(f, "%d %lld %d %d %d %d %d", &q.N, &q.R, &q.chain, &q.lanes_req, &t.L, &t.W,
-                       &t.paired) == 7) {
+    while (std::fscanf(f, "%d %lld %d %d %d %d %d %d", &q.N, &q.R, &q.chain, &q.lanes_req,
+                       &q.pair_arith, &t.L, &t.W, &t.variant) == 8) {
         if (match(q) && t.L >= 1 && t.L <= 32 && (t.W == 2 || t.W == 4 || t.W == 8) &&
-            (t.paired == 0 || t.paired == 1)) {
+            (t.variant == kVarScalar || t.variant == kVarPaired || t.variant == kVarPacked)) {
             *out = t;
             found = true;
         }
@@ -640,30 +657,36 @@ void tune_cache_store(const TuneKey& k, const TuneShape& t) {
     const char* path = std::getenv("PAMD_TUNE_CACHE");
     if (!path || !*path) return;
     if (FILE* f = std::fopen(path, "a")) {
-        std::fprintf(f, "%d %lld %d %d %d %d %d\n", k.N, k.R, k.chain, k.lanes_req, t.L, t.W,
-                     t.paired);
+        std::fprintf(f, "%d %lld %d %d %d %d %d %d\n", k.N, k.R, k.chain, k.lanes_req, k.pair_arith,
+                     t.L, t.W, t.variant);
         std::fclose(f);
     }
 }
 
 // Warps per block (<= requested, shared memory permitting), replicas per
 // block and the persistent grid for layout `lay`.
-int set_launch_shape(pamd_ctx* c, const TopoLayout& lay_in, int warps_req, int paired) {
+// True when the packed-pair kernel can run layout `lay`.
+bool packed_ok(const TopoLayout& lay) { return lay.chain && lay.per_lane >= 3 && lay.per_lane <= 8; }
+
+int set_launch_shape(pamd_ctx* c, const TopoLayout& lay_in, int warps_req, int variant) {
     TopoLayout lay = lay_in;
-    lay.paired = paired ? 1 : 0;
+    lay.paired = variant == kVarPaired ? 1 : 0;
+    lay.packed = variant == kVarPacked ? 1 : 0;
     if (lay.paired && (lay.per_lane < 2 || lay.per_lane > 4))
         return fail(PAMD_EUNSUPPORTED, "two replicas per lane need 2..4 atoms per lane");
+    if (lay.packed && !packed_ok(lay))
+        return fail(PAMD_EUNSUPPORTED, "packed pair arithmetic needs a linear chain with 3..8 atoms per lane");
     int dev = 0, max_smem = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int groups_per_warp = 32 / lay.lanes;  // idle lanes when L does not divide 32
     int warps = warps_req ? warps_req : 4;
     // the single-replica kernel of some atoms-per-lane counts takes smaller blocks
-    if (!lay.paired && lay.per_lane >= 1 && lay.per_lane <= 8)
+    if (lay.packed)
+        warps = std::min(warps, kPackedMaxThreads / 32);
+    else if (!lay.paired && lay.per_lane >= 1 && lay.per_lane <= 8)
         warps = std::min(warps, prop_max_threads(lay.per_lane) / 32);
-    auto smem = [&](int w) {
-        return (long long)lay.bytes + (long long)w * groups_per_warp * slot_f4(lay) * 16;
-    };
+    auto smem = [&](int w) { return (long long)prop_smem_units(lay, w * groups_per_warp); };
     while (smem(warps) > max_smem && warps > 1) --warps;
     if (smem(warps) > max_smem) return fail(PAMD_EUNSUPPORTED, "molecule tables exceed shared memory");
     int occ = 0;
@@ -909,6 +932,10 @@ int pamd_init(pamd_ctx** out, const pamd_topology* top, int64_t R, double T0, ui
     if (o.mol_id < 0 || o.mol_id > 0xffffff) return fail(PAMD_EINVAL, "mol_id must be 0..2^24-1");
     if (o.replicas_per_lane < 0 || o.replicas_per_lane > 2)
         return fail(PAMD_EINVAL, "replicas_per_lane must be 0, 1 or 2");
+    if (o.pair_arith < PAMD_PAIRS_AUTO || o.pair_arith > PAMD_PAIRS_PACKED)
+        return fail(PAMD_EINVAL, "pair_arith must be PAMD_PAIRS_AUTO, _SCALAR or _PACKED");
+    if (o.pair_arith == PAMD_PAIRS_PACKED && o.replicas_per_lane == 2)
+        return fail(PAMD_EINVAL, "packed pair arithmetic runs one replica per lane group");
     if ((o.dev_alloc == nullptr) != (o.dev_free == nullptr))
         return fail(PAMD_EINVAL, "dev_alloc and dev_free must both be set or both be NULL");
     if (o.resample_rule != PAMD_RESAMPLE_MULTINOMIAL && o.resample_rule != PAMD_RESAMPLE_SYSTEMATIC)
@@ -934,6 +961,7 @@ int pamd_init(pamd_ctx** out, const pamd_topology* top, int64_t R, double T0, ui
     }
     c->host_top.assign(top);
     c->lanes_req = o.lanes_per_replica;
+    c->pair_arith = o.pair_arith;
     c->N = lay0.n_atoms;
     c->Np = lay0.n_pad;
     auto bail = [&](int code, const std::string& m) {
@@ -954,8 +982,12 @@ int pamd_init(pamd_ctx** out, const pamd_topology* top, int64_t R, double T0, ui
         c->own_stream = true;
     }
     // launch shape
-    if ((rc = set_launch_shape(c, lay0, o.warps_per_block,
-                               o.replicas_per_lane == 2 ? 1 : 0))) {
+    int variant = kVarScalar;
+    if (o.replicas_per_lane == 2)
+        variant = kVarPaired;
+    else if (o.pair_arith == PAMD_PAIRS_PACKED)
+        variant = kVarPacked;
+    if ((rc = set_launch_shape(c, lay0, o.warps_per_block, variant))) {
         const std::string m = g_err;
         return bail(rc, m);
     }
@@ -1084,6 +1116,7 @@ int pamd_init_batch(pamd_ctx** out, int32_t n_mol, const pamd_topology* tops, co
         so.warps_per_block = kBatchThreads / 32;
         so.autotune = 0;
         so.replicas_per_lane = 1;
+        so.pair_arith = PAMD_PAIRS_SCALAR;  // the batched kernel's arithmetic
         so.lanes_per_replica = tops[m].n_atoms >= 1 && tops[m].n_atoms <= PAMD_MAX_ATOMS
                                    ? batch_lanes(tops[m].n_atoms) : 0;
         pamd_ctx* sub = nullptr;
@@ -1095,7 +1128,7 @@ int pamd_init_batch(pamd_ctx** out, int32_t n_mol, const pamd_topology* tops, co
         c->subs.push_back(sub);
         if (o.autotune && sub->N >= 3) {
             // measured choice among the batched kernel's shapes
-            const int trc = autotune_with(sub, 20, TuneLimits{3, 7, false, {kBatchThreads / 32}, -2}, nullptr);
+            const int trc = autotune_with(sub, 20, TuneLimits{3, 7, false, false, {kBatchThreads / 32}, -2}, nullptr);
             if (trc && trc != PAMD_EUNSUPPORTED) {
                 const std::string msg = "molecule " + std::to_string(m) + ": " + g_err;
                 return bail(trc, msg);
@@ -1539,7 +1572,7 @@ int pamd_autotune(pamd_ctx* c, int32_t theta_probe, pamd_tune* out) {
     if (rc) return rc;
     if (is_batch(c)) return fail(PAMD_EINVAL, "batch context: call this on pamd_batch_sub(ctx, m)");
     if (theta_probe < 1 || theta_probe > 1000) return fail(PAMD_EINVAL, "theta_probe must be 1..1000");
-    return autotune_with(c, theta_probe, TuneLimits{1, 8, true, {2, 4, 8}, 0}, out);
+    return autotune_with(c, theta_probe, TuneLimits{1, 8, true, true, {2, 4, 8}, 0}, out);
 }
 
 }  // extern "C"
@@ -1561,7 +1594,8 @@ int autotune_with(pamd_ctx* c, int32_t theta_probe, const TuneLimits& lim, pamd_
     }
     const pamd_topology t = c->host_top.view();
     const int chain = (int)is_linear_chain(&t);
-    const TuneKey key{c->N, c->R, chain, lim.key_tag ? lim.key_tag : c->lanes_req};
+    const TuneKey key{c->N, c->R, chain, lim.key_tag ? lim.key_tag : c->lanes_req,
+                      lim.packed_ok ? c->pair_arith : PAMD_PAIRS_SCALAR};
     TuneShape best_shape{0, 0, 0};
     double best_ms = 0.0;
     bool cached = tune_cache_lookup(key, &best_shape);
@@ -1578,7 +1612,7 @@ int autotune_with(pamd_ctx* c, int32_t theta_probe, const TuneLimits& lim, pamd_
         }
         PAMD_CU(c, cudaMemcpyAsync(c->b.topo, blob.data(), blob.size(), cudaMemcpyHostToDevice, c->stream));
         PAMD_CU(c, cudaStreamSynchronize(c->stream));
-        return set_launch_shape(c, lay, sh.W, sh.paired);
+        return set_launch_shape(c, lay, sh.W, sh.variant);
     };
     if (!cached) {
         // scratch copy of the population; per-replica outputs go to scratch too
@@ -1598,12 +1632,15 @@ int autotune_with(pamd_ctx* c, int32_t theta_probe, const TuneLimits& lim, pamd_
             const int bb = (c->N + l - 1) / l;
             if (bb < lim.bmin || bb > lim.bmax) continue;
             l = (c->N + bb - 1) / bb;
-            for (int paired = 0; paired <= (lim.paired_ok ? 1 : 0); ++paired) {
-                if (paired && (bb < 2 || bb > 4)) continue;
+            for (int var = kVarScalar; var <= kVarPacked; ++var) {
+                if (var == kVarPaired && (!lim.paired_ok || bb < 2 || bb > 4)) continue;
+                if (var == kVarPacked && (!lim.packed_ok || !chain || bb < 3 || bb > 8)) continue;
+                if (var == kVarScalar && c->pair_arith == PAMD_PAIRS_PACKED) continue;
+                if (var == kVarPacked && c->pair_arith == PAMD_PAIRS_SCALAR) continue;
                 for (int w : lim.warps) {
                     bool dup = false;
-                    for (auto& s2 : shapes) dup = dup || (s2.L == l && s2.W == w && s2.paired == paired);
-                    if (!dup) shapes.push_back({l, w, paired});
+                    for (auto& s2 : shapes) dup = dup || (s2.L == l && s2.W == w && s2.variant == var);
+                    if (!dup) shapes.push_back({l, w, var});
                 }
             }
         }
@@ -1652,6 +1689,7 @@ int autotune_with(pamd_ctx* c, int32_t theta_probe, const TuneLimits& lim, pamd_
         out->atoms_per_lane = c->lay.per_lane;
         out->warps_per_block = c->warps_per_block;
         out->replicas_per_lane = c->lay.paired ? 2 : 1;
+        out->pair_arith = c->lay.packed ? PAMD_PAIRS_PACKED : PAMD_PAIRS_SCALAR;
         out->from_cache = cached ? 1 : 0;
         out->ms = best_ms;
     }
@@ -1702,6 +1740,18 @@ int pamd_info(pamd_ctx* c, int64_t* R, int32_t* n_atoms, int32_t* lanes, int32_t
     if (lanes) *lanes = c->lay.lanes;
     if (per_lane) *per_lane = c->lay.per_lane;
     if (rpb) *rpb = c->rpb;
+    return PAMD_OK;
+}
+
+int pamd_get_shape(pamd_ctx* c, pamd_tune* out) {
+    if (!c || !out) return fail(PAMD_EINVAL, "null argument");
+    if (is_batch(c)) return fail(PAMD_EINVAL, "batch context: call this on pamd_batch_sub(ctx, m)");
+    *out = pamd_tune{};
+    out->lanes_per_replica = c->lay.lanes;
+    out->atoms_per_lane = c->lay.per_lane;
+    out->warps_per_block = c->warps_per_block;
+    out->replicas_per_lane = c->lay.paired ? 2 : 1;
+    out->pair_arith = c->lay.packed ? PAMD_PAIRS_PACKED : PAMD_PAIRS_SCALAR;
     return PAMD_OK;
 }
 

@@ -479,10 +479,30 @@ bool encode_operand(CUtensorMap* map, const void* ptr, int rows, int cols, int l
 
 }  // namespace
 
+// True when p is device memory of device dev (not host, pinned host, managed
+// or another GPU's memory).
+bool on_device(const void* p, int dev) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
+constexpr int kMaxDevices = 64;
+
 cudaError_t launch_gemm_bf16(const GemmArgs& ga, cudaStream_t s) {
     if (ga.M <= 0 || ga.N <= 0 || ga.K <= 0 || (ga.K & 7) || (ga.lda & 7) || (ga.ldb & 7) ||
         (reinterpret_cast<uintptr_t>(ga.A) & 15) || (reinterpret_cast<uintptr_t>(ga.B) & 15))
         return cudaErrorInvalidValue;
+    int dev = 0;
+    cudaError_t de = cudaGetDevice(&dev);
+    if (de != cudaSuccess) return de;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    // The B tile is multicast by TMA into both CTAs of a cluster: the tensor
+    // maps must cover this GPU's own memory only.
+    if (!on_device(ga.A, dev) || !on_device(ga.B, dev)) return cudaErrorInvalidValue;
     CUtensorMap tmA, tmB;
     if (!encode_operand(&tmA, ga.A, ga.M, ga.K, ga.lda, kBM) ||
         !encode_operand(&tmB, ga.B, ga.N, ga.K, ga.ldb, kBN / 2))
@@ -493,24 +513,29 @@ cudaError_t launch_gemm_bf16(const GemmArgs& ga, cudaStream_t s) {
     const bool b_ok = (g.ldcb % 8 == 0) && al16(g.Cb);
     g.vec_ok = (f_ok ? 1 : 0) | (b_ok ? 2 : 0);
     const size_t smem = (size_t)kStages * kStageBytes + 1024;
-    static std::once_flag once;
-    static cudaError_t attr = cudaSuccess;
-    static int max_clusters = 0;
-    std::call_once(once, [&] {
-        attr = cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // kernel attribute and resident cluster count, once per device
+    static std::once_flag once[kMaxDevices];
+    static cudaError_t attr[kMaxDevices];
+    static int max_clusters[kMaxDevices];
+    std::call_once(once[dev], [&] {
+        cudaError_t e = cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
         // persistent grid: as many two-CTA clusters as can be resident at once
         // (an SM left without a partner in its GPC hosts none)
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(2, 1, 1);
         cfg.blockDim = dim3(kThreads, 1, 1);
         cfg.dynamicSmemBytes = smem;
-        if (attr == cudaSuccess) attr = cudaOccupancyMaxActiveClusters(&max_clusters, gemm_bf16_kernel, &cfg);
-        if (attr == cudaSuccess && max_clusters < 1) attr = cudaErrorInvalidConfiguration;
+        int mc = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&mc, gemm_bf16_kernel, &cfg);
+        if (e == cudaSuccess && mc < 1) e = cudaErrorInvalidConfiguration;
+        attr[dev] = e;
+        max_clusters[dev] = mc;
     });
-    if (attr != cudaSuccess) return attr;
+    if (attr[dev] != cudaSuccess) return attr[dev];
     // one cluster per pair of row blocks and column block, at most max_clusters
     const long long pairs = (long long)((g.M + 2 * kBM - 1) / (2 * kBM)) * ((g.N + kBN - 1) / kBN);
-    const int grid = 2 * (int)(pairs < max_clusters ? pairs : max_clusters);
+    const int grid = 2 * (int)(pairs < max_clusters[dev] ? pairs : max_clusters[dev]);
     gemm_bf16_kernel<<<grid, kThreads, smem, s>>>(tmA, tmB, g);
     return cudaGetLastError();
 }
@@ -530,11 +555,29 @@ int gemm_entry(const void* A, const void* B, float* C, int32_t M, int32_t N, int
                        "(K, lda, ldb multiples of 8; A, B 16-byte aligned; reps 1..1000)");
         return PAMD_EINVAL;
     }
-    static int* status = nullptr;
-    if (!status && cudaMalloc(&status, sizeof(int)) != cudaSuccess) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();
-        set_last_error("pamd_gemm_bf16: status word");
-        return PAMD_ENOMEM;
+        set_last_error("pamd_gemm_bf16: no usable current device");
+        return PAMD_ECUDA;
+    }
+    if (!on_device(A, dev) || !on_device(B, dev)) {
+        set_last_error("pamd_gemm_bf16: A and B must be device memory of the current device");
+        return PAMD_EINVAL;
+    }
+    // one status word per device, allocated on that device's first call
+    static std::mutex mu;
+    static int* status_of[kMaxDevices] = {};
+    int* status = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!status_of[dev] && cudaMalloc(&status_of[dev], sizeof(int)) != cudaSuccess) {
+            status_of[dev] = nullptr;
+            cudaGetLastError();
+            set_last_error("pamd_gemm_bf16: status word");
+            return PAMD_ENOMEM;
+        }
+        status = status_of[dev];
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     GemmArgs g{};

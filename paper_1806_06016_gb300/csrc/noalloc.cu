@@ -39,16 +39,25 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once
-// per device (the array's name in host code is only a stand-in).
-int scratch_address(unsigned char** out) {
+// Device address of the scratch array on the current device (the array's
+// name in host code is only a stand-in).  Looked up again on every call made
+// outside stream capture, so that a device reset, which may reload the module
+// at another address, leaves no stale pointer behind; a call whose stream is
+// being captured uses the address of the device's last uncaptured call.
+int scratch_address(cudaStream_t s, unsigned char** out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         set_last_error("no usable CUDA device");
         return PAMD_ECUDA;
     }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        set_last_error("cudaStreamIsCapturing failed");
+        return PAMD_ECUDA;
+    }
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_scratch_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
@@ -56,6 +65,9 @@ int scratch_address(unsigned char** out) {
             return PAMD_ECUDA;
         }
         g_scratch_ptr[dev] = p;
+    } else if (!g_scratch_ptr[dev]) {
+        set_last_error("the first call on a device must come before any stream capture");
+        return PAMD_ECUDA;
     }
     *out = static_cast<unsigned char*>(g_scratch_ptr[dev]);
     return PAMD_OK;
@@ -79,7 +91,7 @@ using namespace pamd;
 extern "C" int pamd_resample_counts_noalloc(const double* E_dev, int64_t R, double T_prev,
                                             double T_next, uint64_t seed, uint32_t resample_index,
                                             int32_t mol_id, int32_t* counts_dev, double* lnQ_dev,
-                                            void* stream) {
+                                            int32_t* status_dev, void* stream) {
     if (!E_dev || !counts_dev) {
         set_last_error("E_dev and counts_dev are required");
         return PAMD_EINVAL;
@@ -96,14 +108,14 @@ extern "C" int pamd_resample_counts_noalloc(const double* E_dev, int64_t R, doub
         set_last_error("mol_id must be 0..2^24-1");
         return PAMD_EINVAL;
     }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned char* base = nullptr;
-    int rc = scratch_address(&base);
+    int rc = scratch_address(s, &base);
     if (rc) return rc;
     unsigned long long* C = reinterpret_cast<unsigned long long*>(base + kOffC);
     unsigned long long* blk_w = reinterpret_cast<unsigned long long*>(base + kOffBlkW);
     double* blk_e = reinterpret_cast<double*>(base + kOffBlkE);
     DevScalars* scal = reinterpret_cast<DevScalars*>(base + kOffScal);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
 
     const int nblk = (int)((R + 1023) / 1024);
     const double dbeta = 1.0 / (kBoltzmann * T_next) - 1.0 / (kBoltzmann * T_prev);
@@ -133,6 +145,13 @@ extern "C" int pamd_resample_counts_noalloc(const double* E_dev, int64_t R, doub
         e = cudaMemcpyAsync(lnQ_dev, &scal->lnQ, sizeof(double), cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) {
             set_last_error(std::string("ln Q copy: ") + cudaGetErrorString(e));
+            return PAMD_ECUDA;
+        }
+    }
+    if (status_dev) {  // 0, or PAMD_ENONFINITE when an energy was NaN or infinite
+        e = cudaMemcpyAsync(status_dev, &scal->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) {
+            set_last_error(std::string("status copy: ") + cudaGetErrorString(e));
             return PAMD_ECUDA;
         }
     }

@@ -50,10 +50,23 @@ struct TopoLayout {
     int off_cdih;              // chain: float4 [N-3] {k, n, cos phase, sin phase} of (d..d+3)
     float s14_lj, s14_c;       // chain: 1-4 scale factors
     int paired;                // launch: 1 = two replicas per lane group (packed FP32x2)
+    int packed;                // launch: 1 = own-atom pairs in packed FP32x2 (chain, B = 3..8)
     int ptab, off_ptab;        // chain: 1 if float4 [L/2][B][B][L] {sigma_ij^2, eps_ij, qq_ij, 0}
                                //   of the half-ring tiles follows (entry ((t-1) B^2 + b B + a) L + g)
     int bytes;                 // total, multiple of 16
 };
+
+// Shared memory of the packed-pair propagate kernel: the topology table
+// without the pair-parameter table; the duplicated mixing parameters
+// {sigma/2, sigma/2, sqrt(24 eps), sqrt(24 eps)} (float4) and the integrator
+// constants {dt/(2m), noise scale} (float2) of the nk atom slots; then per
+// replica slot posA[nk] {x,x,y,y}, posB[nk] {z,z,q,q} and vel[nk] {vx,vy,vz,0}
+// (+1 float4 to spread the replicas over the banks).
+__host__ __device__ inline int x2_topo_bytes(const TopoLayout& lay) {
+    return lay.ptab ? lay.off_ptab : lay.bytes;
+}
+__host__ __device__ inline int x2_table_f4(const TopoLayout& lay) { return lay.nk + (lay.nk + 1) / 2; }
+__host__ __device__ inline int x2_slot_f4(const TopoLayout& lay) { return 3 * lay.nk + 1; }
 
 struct PropParams {
     const float* state_in;     // [R][6][Np]
@@ -276,6 +289,7 @@ struct pamd_ctx {
     int rec_rows = 0;
     void* ov_work = nullptr;      // scratch of the adaptive temperature step (allocated on first use)
     int resample_rule = PAMD_RESAMPLE_MULTINOMIAL;
+    int pair_arith = PAMD_PAIRS_AUTO;  // pamd_options.pair_arith
 };
 
 namespace pamd {
@@ -295,6 +309,13 @@ PAMD_DECLARE_PROPAGATE(6)
 PAMD_DECLARE_PROPAGATE(7)
 PAMD_DECLARE_PROPAGATE(8)
 #undef PAMD_DECLARE_PROPAGATE
+// kernels with the pair arithmetic in packed FP32x2 (own atoms in register
+// pairs; linear chains, 3..8 atoms per lane)
+cudaError_t propagate_x2_dispatch(int B, const PropParams* p, int warps, int grid, size_t smem,
+                                  cudaStream_t s, int* blocks_per_sm);
+// launch variants of the single-molecule propagate kernel
+constexpr int kVarScalar = 0, kVarPaired = 1, kVarPacked = 2;
+constexpr int kPackedMaxThreads = 128;  // block-size cap of the packed-pair kernel
 // paired kernels (two replicas per lane group), 2..4 atoms per lane
 cudaError_t propagate2_b2(const PropParams* p, bool chain, int warps, int grid, size_t smem,
                           cudaStream_t s, int* blocks_per_sm);

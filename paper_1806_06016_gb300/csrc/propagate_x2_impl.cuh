@@ -1,0 +1,563 @@
+// propagate_x2_impl.cuh -- persistent BAOAB Langevin kernel (PAMD scheme,
+// step 3) with the nonbonded pair arithmetic in packed FP32x2 instructions.
+//
+// Same replica mapping as propagate_impl.cuh: a replica is owned by L lanes
+// of a warp (G = floor(32/L) replicas per warp), lane g owns the B atoms
+// [gB, gB+B), nonbonded pairs follow the half ring of lane blocks (step t:
+// block g against block (g+t) mod L).  What differs:
+//
+// * Packed arithmetic.  The lane's own atoms are held as P = floor(B/2)
+//   register pairs (atoms 2p, 2p+1) plus one scalar atom when B is odd.  One
+//   partner atom against one own pair is evaluated by add/mul/fma.rn.f32x2
+//   instructions (two FP32 results per instruction: the same FP32 roundings
+//   as two scalar instructions, half the issue slots).  The reciprocal square
+//   root stays scalar (no packed form).
+// * Partner atoms are read from shared memory already duplicated, {x,x,y,y}
+//   and {z,z,q,q} per atom, so no instruction is spent forming the broadcast
+//   operand of a packed instruction; the per-atom mixing parameters
+//   {sigma/2, sigma/2, sqrt(24 eps), sqrt(24 eps)} sit in a per-block table.
+// * Forces on partner atoms are summed in registers over the tile and handed
+//   to the owner lane with warp shuffles (lane g receives from lane g - t the
+//   forces on its own block), so shared memory holds positions only and the
+//   pair loop has no shared-memory stores.
+// * Chain bonded terms are those of propagate_impl.cuh; forces on the next
+//   block's first three atoms are also handed over by shuffles.
+//
+// Linear-chain layouts only (B >= 3); other topologies use propagate_impl.cuh.
+#pragma once
+
+#include "propagate_impl.cuh"
+
+namespace pamd {
+
+template <int B>
+struct X2Cfg {
+    static constexpr int P = B / 2;             // packed own-atom pairs
+    static constexpr bool TAIL = (B % 2) == 1;  // one scalar own atom
+    static constexpr int BS = (B % 2 == 1) ? B : B + 1;
+    static constexpr int MAX_THREADS = kPackedMaxThreads;
+#ifdef PAMD_X2_MIN_BLOCKS
+    static constexpr int MIN_BLOCKS = PAMD_X2_MIN_BLOCKS;
+#else
+    static constexpr int MIN_BLOCKS = (B <= 4) ? 4 : 3;
+#endif
+};
+
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+
+// Own atoms of a lane: packed pairs plus the scalar tail.
+template <int B>
+struct Own {
+    static constexpr int P = X2Cfg<B>::P;
+    float2 x[P > 0 ? P : 1], y[P > 0 ? P : 1], z[P > 0 ? P : 1];
+    float xt, yt, zt;
+    __device__ __forceinline__ float gx(int a) const {
+        return (a < 2 * P) ? ((a & 1) ? x[a >> 1].y : x[a >> 1].x) : xt;
+    }
+    __device__ __forceinline__ float gy(int a) const {
+        return (a < 2 * P) ? ((a & 1) ? y[a >> 1].y : y[a >> 1].x) : yt;
+    }
+    __device__ __forceinline__ float gz(int a) const {
+        return (a < 2 * P) ? ((a & 1) ? z[a >> 1].y : z[a >> 1].x) : zt;
+    }
+    __device__ __forceinline__ void add(int a, float vx, float vy, float vz) {
+        if (a < 2 * P) {
+            if (a & 1) {
+                x[a >> 1].y += vx;
+                y[a >> 1].y += vy;
+                z[a >> 1].y += vz;
+            } else {
+                x[a >> 1].x += vx;
+                y[a >> 1].x += vy;
+                z[a >> 1].x += vz;
+            }
+        } else {
+            xt += vx;
+            yt += vy;
+            zt += vz;
+        }
+    }
+    __device__ __forceinline__ void set(int a, float vx, float vy, float vz) {
+        if (a < 2 * P) {
+            if (a & 1) {
+                x[a >> 1].y = vx;
+                y[a >> 1].y = vy;
+                z[a >> 1].y = vz;
+            } else {
+                x[a >> 1].x = vx;
+                y[a >> 1].x = vy;
+                z[a >> 1].x = vz;
+            }
+        } else {
+            xt = vx;
+            yt = vy;
+            zt = vz;
+        }
+    }
+    __device__ __forceinline__ void zero() {
+#pragma unroll
+        for (int p = 0; p < (P > 0 ? P : 1); ++p) x[p] = y[p] = z[p] = make_float2(0.f, 0.f);
+        xt = yt = zt = 0.f;
+    }
+};
+
+// One partner atom (duplicated operands) against the lane's own atoms.
+// d = x_own - x_partner; the force on an own atom is +fs d, on the partner
+// -fs d; the partner's share is summed into (gx, gy, gz) as +fs d (the caller
+// subtracts it).  Masked own/partner pairs (bit a*B + b) contribute zero.
+template <int B, bool MASKED>
+__device__ __forceinline__ void partner_x2(const Own<B>& r, const Own<B>& hs, const Own<B>& se,
+                                           const Own<B>& qq, Own<B>& f, float4 pa, float4 pb,
+                                           float4 pp, int b, unsigned long long mask, float& gx,
+                                           float& gy, float& gz) {
+    using C = X2Cfg<B>;
+    const float2 xj = f2(pa.x, pa.y), yj = f2(pa.z, pa.w), zj = f2(pb.x, pb.y);
+    const float2 qj = f2(pb.z, pb.w), hj = f2(pp.x, pp.y), ej = f2(pp.z, pp.w);
+    float2 Gx = f2(0.f), Gy = f2(0.f), Gz = f2(0.f);
+#pragma unroll
+    for (int p = 0; p < C::P; ++p) {
+        const float2 dx = sub2(r.x[p], xj);
+        const float2 dy = sub2(r.y[p], yj);
+        const float2 dz = sub2(r.z[p], zj);
+        const float2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+        const float2 rinv = f2(rsqrtf(r2.x), rsqrtf(r2.y));
+        const float2 rinv2 = mul2(rinv, rinv);
+        const float2 sg = add2(hs.x[p], hj);
+        const float2 s2 = mul2(mul2(sg, sg), rinv2);
+        const float2 s6 = mul2(mul2(s2, s2), s2);
+        const float2 eps = mul2(se.x[p], ej);
+        const float2 e2 = add2(eps, eps);
+        const float2 lj = mul2(s6, fma2(e2, s6, f2(-eps.x, -eps.y)));
+        const float2 q2 = mul2(qq.x[p], qj);
+        float2 fs = mul2(fma2(q2, rinv, lj), rinv2);
+        if (MASKED) {
+            if ((mask >> ((2 * p) * B + b)) & 1ull) fs.x = 0.f;
+            if ((mask >> ((2 * p + 1) * B + b)) & 1ull) fs.y = 0.f;
+        }
+        f.x[p] = fma2(fs, dx, f.x[p]);
+        f.y[p] = fma2(fs, dy, f.y[p]);
+        f.z[p] = fma2(fs, dz, f.z[p]);
+        Gx = fma2(fs, dx, Gx);
+        Gy = fma2(fs, dy, Gy);
+        Gz = fma2(fs, dz, Gz);
+    }
+    gx = Gx.x + Gx.y;
+    gy = Gy.x + Gy.y;
+    gz = Gz.x + Gz.y;
+    if (C::TAIL) {
+        const float dx = r.xt - pa.x, dy = r.yt - pa.z, dz = r.zt - pb.x;
+        const float sg = hs.xt + pp.x;
+        const float eps = se.xt * pp.z;
+        float fs, e;
+        pair_lj_coul<false>(dx, dy, dz, sg * sg, eps, eps + eps, qq.xt * pb.z, fs, e);
+        if (MASKED && ((mask >> ((B - 1) * B + b)) & 1ull)) fs = 0.f;
+        // pair_lj_coul's fs multiplies d = x_j - x_i; here d = x_i - x_j
+        f.xt = fmaf(fs, dx, f.xt);
+        f.yt = fmaf(fs, dy, f.yt);
+        f.zt = fmaf(fs, dz, f.zt);
+        gx = fmaf(fs, dx, gx);
+        gy = fmaf(fs, dy, gy);
+        gz = fmaf(fs, dz, gz);
+    }
+}
+
+// Chain bonded pass (terms starting in the lane's block): forces on the own
+// atoms go to f, those on the next block's first three atoms to sf.
+template <int B>
+__device__ __forceinline__ void bonded_chain_x2(const unsigned char* sm, const TopoLayout& lay,
+                                                const float4* prm, const float4* posA,
+                                                const float4* posB, int L, int g, const Own<B>& r,
+                                                Own<B>& f, float3 (&sf)[3]) {
+    using C = X2Cfg<B>;
+    const int i0 = g * B;
+    const int N = lay.n_atoms;
+    const bool has_next = (g + 1 < L);
+    const int nbase = (g + 1) * C::BS;
+    float3 sp[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        sf[m] = make_float3(0.f, 0.f, 0.f);
+        if (has_next) {
+            const float4 a = posA[nbase + m];
+            const float4 c = posB[nbase + m];
+            sp[m] = make_float3(a.x, a.z, c.x);
+        } else {
+            sp[m] = make_float3(0.f, 0.f, 0.f);
+        }
+    }
+    if (i0 + 1 >= N) return;  // no term starts here
+    auto P = [&](int o) -> float3 {
+        return (o < B) ? make_float3(r.gx(o < B ? o : 0), r.gy(o < B ? o : 0), r.gz(o < B ? o : 0))
+                       : sp[o >= B ? o - B : 0];
+    };
+    auto F = [&](int o, float3 v) {
+        if (o < B) {
+            f.add(o < B ? o : 0, v.x, v.y, v.z);
+        } else {
+            float3& s = sf[o >= B ? o - B : 0];
+            s.x += v.x;
+            s.y += v.y;
+            s.z += v.z;
+        }
+    };
+    const float2* cb = reinterpret_cast<const float2*>(sm + lay.off_cbond);
+    const float2* ca = reinterpret_cast<const float2*>(sm + lay.off_cangle);
+    const float4* cd = reinterpret_cast<const float4*>(sm + lay.off_cdih);
+    double e_unused = 0.0;
+#pragma unroll
+    for (int a = 0; a < B; ++a) {
+        const int d = i0 + a;
+        if (d + 1 < N) {  // bond (d, d+1)
+            const float2 q = cb[d];
+            const float3 fb = bond_force<false>(P(a), P(a + 1), q.x, q.y, e_unused);
+            F(a, fb);
+            F(a + 1, make_float3(-fb.x, -fb.y, -fb.z));
+        }
+        if (d + 2 < N) {  // angle (d, d+1, d+2)
+            const float2 q = ca[d];
+            float3 fi, fj, fk;
+            angle_force<false>(P(a), P(a + 1), P(a + 2), q.x, q.y, fi, fj, fk, e_unused);
+            F(a, fi);
+            F(a + 1, fj);
+            F(a + 2, fk);
+        }
+        if (d + 3 < N) {  // dihedral (d..d+3) and 1-4 pair (d, d+3)
+            float3 fi, fj, fk, fl;
+            dihedral_force<false>(P(a), P(a + 1), P(a + 2), P(a + 3), cd[d], fi, fj, fk, fl,
+                                  e_unused);
+            F(a, fi);
+            F(a + 1, fj);
+            F(a + 2, fk);
+            F(a + 3, fl);
+            const int s0 = g * C::BS + a;
+            const int s3 = (a + 3 < B) ? (s0 + 3) : (nbase + a + 3 - B);
+            const float3 fp = pair14_force<false>(P(a), P(a + 3), prm[s0], prm[s3], lay.s14_lj,
+                                                  lay.s14_c, e_unused);
+            F(a, fp);
+            F(a + 3, make_float3(-fp.x, -fp.y, -fp.z));
+        }
+    }
+}
+
+// Partner-side sums (g) of one partner atom go to the lane that owns it; this
+// lane receives from `src` the sums for its own atom b (force = -sum).
+template <int B>
+__device__ __forceinline__ void hand_over(Own<B>& f, int b, float gx, float gy, float gz,
+                                          unsigned gmask, int src) {
+    const float rx = __shfl_sync(gmask, gx, src);
+    const float ry = __shfl_sync(gmask, gy, src);
+    const float rz = __shfl_sync(gmask, gz, src);
+    f.add(b, -rx, -ry, -rz);
+}
+
+// Forces on the lane's own atoms (f).  Positions must be in shared memory
+// (posA/posB of the replica), published by a __syncwarp.  Every lane of the
+// group must call this (the hand-over of partner forces is a warp shuffle).
+template <int B>
+__device__ __forceinline__ void forces_x2(const unsigned char* sm, const TopoLayout& lay,
+                                          const float4* prm, const float4* dprm,
+                                          const unsigned long long* masks, const float4* posA,
+                                          const float4* posB, int L, int g, int base,
+                                          unsigned gmask, const Own<B>& r, const Own<B>& hs,
+                                          const Own<B>& se, const Own<B>& qq, Own<B>& f) {
+    using C = X2Cfg<B>;
+    f.zero();
+    // pairs inside the lane's own block (masked: the 1-2/1-3/1-4 pairs live here)
+    {
+        const unsigned long long m = masks[g];
+#pragma unroll
+        for (int a = 0; a < B; ++a) {
+#pragma unroll
+            for (int b = a + 1; b < B; ++b) {
+                const float dx = r.gx(b) - r.gx(a), dy = r.gy(b) - r.gy(a), dz = r.gz(b) - r.gz(a);
+                const float sg = hs.gx(a) + hs.gx(b);
+                const float eps = se.gx(a) * se.gx(b);
+                float fs, e;
+                pair_lj_coul<false>(dx, dy, dz, sg * sg, eps, eps + eps, qq.gx(a) * qq.gx(b), fs, e);
+                if ((m >> (a * B + b)) & 1ull) fs = 0.f;
+                f.add(a, -fs * dx, -fs * dy, -fs * dz);
+                f.add(b, fs * dx, fs * dy, fs * dz);
+            }
+        }
+    }
+    // half ring over partner blocks
+    const int TH = L / 2;
+#pragma unroll 1
+    for (int t = 1; t <= TH; ++t) {
+        const bool active = !(2 * t == L && g >= t);
+        int J = g + t;
+        J = (J >= L) ? J - L : J;
+        const int sJ = J * C::BS;
+        // lane g receives from lane g - t the forces on its own atom b
+        int src = g - t;
+        src = (src < 0) ? src + L : src;
+        const unsigned long long m = active ? masks[t * L + g] : 0ull;
+        // one branch for the whole group (the hand-over shuffles must not diverge)
+        if (!__any_sync(gmask, m != 0ull)) {
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                float gx = 0.f, gy = 0.f, gz = 0.f;
+                if (active)
+                    partner_x2<B, false>(r, hs, se, qq, f, posA[sJ + b], posB[sJ + b],
+                                         dprm[sJ + b], b, m, gx, gy, gz);
+                hand_over<B>(f, b, gx, gy, gz, gmask, base + src);
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                float gx = 0.f, gy = 0.f, gz = 0.f;
+                if (active)
+                    partner_x2<B, true>(r, hs, se, qq, f, posA[sJ + b], posB[sJ + b],
+                                        dprm[sJ + b], b, m, gx, gy, gz);
+                hand_over<B>(f, b, gx, gy, gz, gmask, base + src);
+            }
+        }
+    }
+    // bonded terms; forces on the next block's first atoms go to lane g + 1
+    float3 sf[3];
+    bonded_chain_x2<B>(sm, lay, prm, posA, posB, L, g, r, f, sf);
+    {
+        int src = g - 1;
+        src = (src < 0) ? src + L : src;  // lane L-1 has no next block and sends zeros
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            const float rx = __shfl_sync(gmask, sf[m].x, base + src);
+            const float ry = __shfl_sync(gmask, sf[m].y, base + src);
+            const float rz = __shfl_sync(gmask, sf[m].z, base + src);
+            if (g > 0) f.add(m, rx, ry, rz);
+        }
+    }
+}
+
+template <int B>
+__device__ __forceinline__ void store_pos_x2(float4* posA, float4* posB, int s, float x, float y,
+                                             float z) {
+    posA[s] = make_float4(x, x, y, y);
+    *reinterpret_cast<float2*>(&posB[s]) = make_float2(z, z);
+}
+
+// theta BAOAB steps of replica k by the L lanes of one group.  Velocities
+// live in shared memory (vel, {vx, vy, vz, 0} per atom slot) and are touched
+// only by the integrator; aux holds {dt/(2m), sqrt((1 - c1^2) k_B T / m)}.
+template <int B>
+__device__ __forceinline__ void advance_replica_x2(const PropParams& p, const unsigned char* sm,
+                                                   const float4* prm, const float4* dprm,
+                                                   const float2* aux,
+                                                   const unsigned long long* masks, float4* posA,
+                                                   float4* posB, float4* vel, long long k, int L,
+                                                   int g, int base, unsigned gmask) {
+    using C = X2Cfg<B>;
+    const TopoLayout& lay = p.lay;
+    const int N = lay.n_atoms, Np = lay.n_pad;
+    const int s0 = g * C::BS;  // the lane's first atom slot
+    const uint32_t step_base = (p.dev_counters ? p.dev_counters[0] : 0u) + p.step0;
+    const float* st = p.state_in + (size_t)k * 6 * Np;
+    Own<B> r, f, hs, se, qq;
+#pragma unroll
+    for (int a = 0; a < B; ++a) {
+        const int i = g * B + a;
+        const int sl = s0 + a;
+        float4 vv = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < N) {
+            r.set(a, st[i], st[Np + i], st[2 * Np + i]);
+            vv = make_float4(st[3 * Np + i], st[4 * Np + i], st[5 * Np + i], 0.f);
+        } else {
+            r.set(a, 1000.0f + 4.0f * (float)i, 0.0f, 0.0f);
+        }
+        vel[sl] = vv;
+        const float4 c = prm[sl];
+        hs.set(a, c.x, 0.f, 0.f);
+        se.set(a, c.y, 0.f, 0.f);
+        qq.set(a, c.z, 0.f, 0.f);
+        posA[sl] = make_float4(r.gx(a), r.gx(a), r.gy(a), r.gy(a));
+        posB[sl] = make_float4(r.gz(a), r.gz(a), c.z, c.z);
+    }
+    __syncwarp(gmask);
+    const float hdt = p.hdt, c1 = p.c1;
+    // s = -1 evaluates the forces of the incoming state; s >= 0 are BAOAB
+    // steps.  The closing kick of step s - 1 is applied at the start of step
+    // s (same operations in the same order as kicking at the end of s - 1).
+    for (int s = -1; s < p.theta; ++s) {
+        if (s >= 0) {
+            const uint32_t step = step_base + (uint32_t)s;
+#pragma unroll
+            for (int a = 0; a < B; ++a) {
+                const int i = g * B + a;
+                const int sl = s0 + a;
+                const float2 cf = aux[sl];
+                float4 vv = vel[sl];
+                float x = r.gx(a), y = r.gy(a), z = r.gz(a);
+                const float fx = f.gx(a), fy = f.gy(a), fz = f.gz(a);
+                if (s > 0) {  // closing B of the previous step
+                    vv.x = fmaf(cf.x, fx, vv.x);
+                    vv.y = fmaf(cf.x, fy, vv.y);
+                    vv.z = fmaf(cf.x, fz, vv.z);
+                }
+                vv.x = fmaf(cf.x, fx, vv.x);  // B
+                vv.y = fmaf(cf.x, fy, vv.y);
+                vv.z = fmaf(cf.x, fz, vv.z);
+                x = fmaf(hdt, vv.x, x);  // A
+                y = fmaf(hdt, vv.y, y);
+                z = fmaf(hdt, vv.z, z);
+                if (i < N) {  // O
+                    const float3 w = normal3_fast(p.seed, (uint32_t)i, (uint32_t)k, step, p.purpose_mol);
+                    vv.x = fmaf(c1, vv.x, cf.y * w.x);
+                    vv.y = fmaf(c1, vv.y, cf.y * w.y);
+                    vv.z = fmaf(c1, vv.z, cf.y * w.z);
+                }
+                x = fmaf(hdt, vv.x, x);  // A
+                y = fmaf(hdt, vv.y, y);
+                z = fmaf(hdt, vv.z, z);
+                r.set(a, x, y, z);
+                vel[sl] = vv;
+            }
+            __syncwarp(gmask);  // every lane has finished reading the previous positions
+#pragma unroll
+            for (int a = 0; a < B; ++a) store_pos_x2<B>(posA, posB, s0 + a, r.gx(a), r.gy(a), r.gz(a));
+            __syncwarp(gmask);
+        }
+        forces_x2<B>(sm, lay, prm, dprm, masks, posA, posB, L, g, base, gmask, r, hs, se, qq, f);
+    }
+    // closing B of the last step
+    Own<B> v;
+#pragma unroll
+    for (int a = 0; a < B; ++a) {
+        const int sl = s0 + a;
+        float4 vv = vel[sl];
+        if (p.theta > 0) {
+            const float h = aux[sl].x;
+            vv.x = fmaf(h, f.gx(a), vv.x);
+            vv.y = fmaf(h, f.gy(a), vv.y);
+            vv.z = fmaf(h, f.gz(a), vv.z);
+        }
+        v.set(a, vv.x, vv.y, vv.z);
+    }
+    // potential energy of the final positions: the scalar energy pass of
+    // propagate_impl.cuh on {x, y, z, 0} records in posA
+    __syncwarp(gmask);
+#pragma unroll
+    for (int a = 0; a < B; ++a) posA[g * C::BS + a] = make_float4(r.gx(a), r.gy(a), r.gz(a), 0.f);
+    __syncwarp(gmask);
+    const double e_acc = energy_pass<B, true>(sm, lay, prm, posA, masks, L, g);
+
+    // write back and per-replica observables
+    float* so = p.state_out + (size_t)k * 6 * Np;
+    double ek = 0.0, cx = 0.0, cy = 0.0, cz = 0.0;
+#pragma unroll
+    for (int a = 0; a < B; ++a) {
+        const int i = g * B + a;
+        if (i < N) {
+            const float xa = r.gx(a), ya = r.gy(a), za = r.gz(a);
+            const float vxa = v.gx(a), vya = v.gy(a), vza = v.gz(a);
+            if (p.theta > 0) {
+                so[i] = xa;
+                so[Np + i] = ya;
+                so[2 * Np + i] = za;
+                so[3 * Np + i] = vxa;
+                so[4 * Np + i] = vya;
+                so[5 * Np + i] = vza;
+            }
+            if (p.fout) {
+                float* fo = p.fout + (size_t)k * 3 * Np;
+                fo[i] = f.gx(a);
+                fo[Np + i] = f.gy(a);
+                fo[2 * Np + i] = f.gz(a);
+            }
+            const double m = (double)p.masses[i];
+            ek += 0.5 * m * ((double)vxa * vxa + (double)vya * vya + (double)vza * vza);
+            cx += xa;
+            cy += ya;
+            cz += za;
+        }
+    }
+    const double E = group_sum(e_acc, gmask, base, L);
+    ek = group_sum(ek, gmask, base, L);
+    cx = group_sum(cx, gmask, base, L) / N;
+    cy = group_sum(cy, gmask, base, L) / N;
+    cz = group_sum(cz, gmask, base, L) / N;
+    double r2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < B; ++a) {
+        const int i = g * B + a;
+        if (i < N) {
+            const double dx = r.gx(a) - cx, dy = r.gy(a) - cy, dz = r.gz(a) - cz;
+            r2 += dx * dx + dy * dy + dz * dz;
+        }
+    }
+    r2 = group_sum(r2, gmask, base, L);
+    if (g == 0) {
+        p.E[k] = E;
+        p.ke[k] = ek;
+        p.rg[k] = sqrt(r2 / N);
+        if (!isfinite(E) && atomicCAS(&p.status[0], 0, PAMD_ENONFINITE) == 0)
+            p.status[1] = (int)k;
+    }
+    __syncwarp(gmask);
+}
+
+template <int B>
+__global__ void __launch_bounds__(X2Cfg<B>::MAX_THREADS, X2Cfg<B>::MIN_BLOCKS)
+    propagate_x2_kernel(const PropParams p) {
+    using C = X2Cfg<B>;
+    extern __shared__ float4 smem4[];
+    unsigned char* sm = reinterpret_cast<unsigned char*>(smem4);
+    const TopoLayout& lay = p.lay;
+    const int tb = x2_topo_bytes(lay);
+    {
+        const float4* src = reinterpret_cast<const float4*>(p.topo);
+        for (int i = threadIdx.x; i < tb / 16; i += blockDim.x) smem4[i] = src[i];
+    }
+    __syncthreads();
+    const float4* prm = reinterpret_cast<const float4*>(sm + lay.off_params);
+    float4* dprm = smem4 + tb / 16;
+    float2* aux = reinterpret_cast<float2*>(dprm + lay.nk);
+    for (int i = threadIdx.x; i < lay.nk; i += blockDim.x) {
+        const float4 c = prm[i];
+        dprm[i] = make_float4(c.x, c.x, c.y, c.y);
+        aux[i] = make_float2(p.hdt * c.w, p.c2kT * sqrtf(c.w));
+    }
+    __syncthreads();
+    const unsigned long long* masks = reinterpret_cast<const unsigned long long*>(sm + lay.off_masks);
+    float4* slots = dprm + lay.nk + (lay.nk + 1) / 2;
+
+    const int L = lay.lanes;
+    const int G = 32 / L;
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / L;
+    if (grp >= G) return;  // idle lanes when L does not divide 32
+    const int g = lane - grp * L;
+    const int base = grp * L;
+    const unsigned gmask = (L == 32) ? 0xffffffffu : (((1u << L) - 1u) << base);
+    const int slot_local = (threadIdx.x >> 5) * G + grp;
+    const int rpb = (blockDim.x >> 5) * G;
+    float4* posA = slots + slot_local * x2_slot_f4(lay);
+    float4* posB = posA + lay.nk;
+    float4* vel = posB + lay.nk;
+
+    for (long long k = (long long)blockIdx.x * rpb + slot_local; k < p.R;
+         k += (long long)gridDim.x * rpb)
+        advance_replica_x2<B>(p, sm, prm, dprm, aux, masks, posA, posB, vel, k, L, g, base, gmask);
+}
+
+template <int B>
+cudaError_t propagate_x2_launch(const PropParams* p, int warps, int grid, size_t smem,
+                                cudaStream_t s, int* blocks_per_sm) {
+    auto kern = propagate_x2_kernel<B>;
+    static size_t configured = 0;
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    if (!p) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, warps * 32, smem);
+    kern<<<grid, warps * 32, smem, s>>>(*p);
+    return cudaGetLastError();
+}
+
+}  // namespace pamd

@@ -21,6 +21,7 @@ PAMD_EINVAL, PAMD_ENOMEM, PAMD_ECUDA, PAMD_ETIMEOUT = -1, -2, -3, -4
 PAMD_ENONFINITE, PAMD_ESTATE, PAMD_EUNSUPPORTED = -5, -6, -7
 PAMD_PREC_MIXED, PAMD_PREC_FP64 = 0, 1
 PAMD_RESAMPLE_MULTINOMIAL, PAMD_RESAMPLE_SYSTEMATIC = 0, 1
+PAMD_PAIRS_AUTO, PAMD_PAIRS_SCALAR, PAMD_PAIRS_PACKED = 0, 1, 2
 PAMD_MAX_ATOMS = 256
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -62,16 +63,18 @@ class PamdOptions(C.Structure):
         ("alloc_user", C.c_void_p),
         ("stream", C.c_void_p),
         ("resample_rule", C.c_int32),
+        ("pair_arith", C.c_int32),
     ]
 
 
 class PamdTune(C.Structure):
     _fields_ = [("lanes_per_replica", C.c_int32), ("atoms_per_lane", C.c_int32),
                 ("warps_per_block", C.c_int32), ("replicas_per_lane", C.c_int32),
-                ("from_cache", C.c_int32), ("ms", C.c_double)]
+                ("from_cache", C.c_int32), ("ms", C.c_double), ("pair_arith", C.c_int32),
+                ("pad_", C.c_int32)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
 
 
 class PamdObs(C.Structure):
@@ -91,7 +94,7 @@ EXPORTS = [
     "pamd_options_default", "pamd_init", "pamd_init_batch", "pamd_batch_size", "pamd_batch_sub",
     "pamd_reset", "pamd_propagate", "pamd_resample", "pamd_observables",
     "pamd_anneal", "pamd_get_state", "pamd_set_state", "pamd_forces", "pamd_get_counters",
-    "pamd_set_counters", "pamd_autotune", "pamd_resample_counts_noalloc", "pamd_info", "pamd_launch_count", "pamd_sync", "pamd_destroy",
+    "pamd_set_counters", "pamd_autotune", "pamd_get_shape", "pamd_fp32_peak", "pamd_fp32_peak_threads", "pamd_resample_counts_noalloc", "pamd_info", "pamd_launch_count", "pamd_sync", "pamd_destroy",
     "pamd_last_error",
     # learned surrogate (include/pamd_mlp.h), wrapped in surrogate.py
     "pamd_gemm_bf16", "pamd_gemm_bf16_time", "pamd_mlp_create", "pamd_mlp_info", "pamd_mlp_set_params",
@@ -153,7 +156,10 @@ def load(path: str | None = None):
             "pamd_get_counters": (C.c_int, [P, C.POINTER(U32), C.POINTER(U32), C.POINTER(D)]),
             "pamd_set_counters": (C.c_int, [P, U32, U32, D]),
             "pamd_autotune": (C.c_int, [P, I32, C.POINTER(PamdTune)]),
-            "pamd_resample_counts_noalloc": (C.c_int, [P, I64, D, D, U64, U32, I32, P, P, P]),
+            "pamd_get_shape": (C.c_int, [P, C.POINTER(PamdTune)]),
+            "pamd_fp32_peak": (C.c_int, [I32, I32, I32, P, P, C.POINTER(D), C.POINTER(D)]),
+            "pamd_fp32_peak_threads": (I32, []),
+            "pamd_resample_counts_noalloc": (C.c_int, [P, I64, D, D, U64, U32, I32, P, P, P, P]),
             "pamd_info": (C.c_int, [P, C.POINTER(I64), C.POINTER(I32), C.POINTER(I32),
                                     C.POINTER(I32), C.POINTER(I32)]),
             "pamd_launch_count": (I64, [P]),
@@ -400,6 +406,26 @@ def pamd_set_counters(ctx, step: int, resample_index: int, sum_lnQ: float) -> No
     _check(load().pamd_set_counters(ctx, int(step), int(resample_index), float(sum_lnQ)))
 
 
+def pamd_fp32_peak(packed: bool, iters: int = 20000, reps: int = 100, stream: int = 0) -> dict:
+    """FP32 FMA throughput of the current device (include/pamd_bench.h):
+    {"tflops", "ms"} of `reps` timed launches, scalar or packed FP32x2."""
+    import torch
+    n = load().pamd_fp32_peak_threads()
+    if n <= 0:
+        raise PamdError(PAMD_ECUDA, "no CUDA device")
+    out = torch.empty(n, dtype=torch.float32, device="cuda")
+    tf, ms = C.c_double(), C.c_double()
+    _check(load().pamd_fp32_peak(1 if packed else 0, int(iters), int(reps), C.c_void_p(stream or None),
+                                 C.c_void_p(out.data_ptr()), C.byref(tf), C.byref(ms)))
+    return {"tflops": tf.value, "ms": ms.value}
+
+
+def pamd_get_shape(ctx) -> dict:
+    t = PamdTune()
+    _check(load().pamd_get_shape(ctx, C.byref(t)))
+    return t.as_dict()
+
+
 def pamd_autotune(ctx, theta_probe: int = 20) -> dict:
     t = PamdTune()
     _check(load().pamd_autotune(ctx, int(theta_probe), C.byref(t)))
@@ -408,12 +434,14 @@ def pamd_autotune(ctx, theta_probe: int = 20) -> dict:
 
 def pamd_resample_counts_noalloc(E_dev: int, R: int, T_prev: float, T_next: float, seed: int,
                                  resample_index: int, counts_dev: int, lnQ_dev: int = 0,
-                                 mol_id: int = 0, stream: int = 0) -> None:
+                                 mol_id: int = 0, stream: int = 0, status_dev: int = 0) -> None:
     """Copy counts and ln Q from device energies into device outputs without
-    allocating (pointers are device addresses, e.g. ``tensor.data_ptr()``)."""
+    allocating (pointers are device addresses, e.g. ``tensor.data_ptr()``);
+    status_dev (int32) receives 0 or PAMD_ENONFINITE."""
     _check(load().pamd_resample_counts_noalloc(
         C.c_void_p(E_dev), int(R), float(T_prev), float(T_next), int(seed), int(resample_index),
-        int(mol_id), C.c_void_p(counts_dev), C.c_void_p(lnQ_dev or None), C.c_void_p(stream or None)))
+        int(mol_id), C.c_void_p(counts_dev), C.c_void_p(lnQ_dev or None),
+        C.c_void_p(status_dev or None), C.c_void_p(stream or None)))
 
 
 def pamd_record_energies(ctx, E_dev: int, rows: int) -> None:

@@ -89,6 +89,39 @@ def test_argument_validation_before_device_use(lib):
     assert _init_rc(pi.make_chain(75, 1), lanes_per_replica=8)[0] == pamd.PAMD_EINVAL
 
 
+def _header_range(field):
+    """The 'a..b' range the header states for a pamd_options field."""
+    txt = open(os.path.join(ROOT, "include", "pamd.h")).read()
+    m = re.search(r"\b" + field + r";\s*/\*[^*]*?(\d+)\.\.(\d+)", txt)
+    assert m, field
+    return int(m.group(1)), int(m.group(2))
+
+
+def test_header_ranges_match_validation(lib):
+    """The ranges include/pamd.h states for the launch-shape options are the
+    ones pamd_init accepts: both ends pass argument validation (without a GPU
+    the call then fails at the device, never with PAMD_EINVAL) and one past
+    either end is rejected."""
+    from paper_1806_06016_gb300 import pamd
+    top = pi.make_chain(10, 1)
+    lo, hi = _header_range("lanes_per_replica")
+    assert (lo, hi) == (1, 32)
+    small = pi.make_chain(6, 1)  # one lane holds at most 8 atoms
+    for lanes, t in ((lo, small), (2, top), (hi, top), (hi, pi.make_chain(256, 1))):
+        assert _init_rc(t, lanes_per_replica=lanes)[0] != pamd.PAMD_EINVAL, lanes
+    assert _init_rc(top, lanes_per_replica=hi + 1)[0] == pamd.PAMD_EINVAL
+    assert _init_rc(top, lanes_per_replica=-1)[0] == pamd.PAMD_EINVAL
+    lo, hi = _header_range("warps_per_block")
+    assert (lo, hi) == (1, 8)
+    for w in (0, lo, hi):
+        assert _init_rc(top, warps_per_block=w)[0] != pamd.PAMD_EINVAL, w
+    assert _init_rc(top, warps_per_block=hi + 1)[0] == pamd.PAMD_EINVAL
+    for pa in (pamd.PAMD_PAIRS_AUTO, pamd.PAMD_PAIRS_SCALAR, pamd.PAMD_PAIRS_PACKED):
+        assert _init_rc(top, pair_arith=pa)[0] != pamd.PAMD_EINVAL
+    assert _init_rc(top, pair_arith=3)[0] == pamd.PAMD_EINVAL
+    assert _init_rc(top, pair_arith=pamd.PAMD_PAIRS_PACKED, replicas_per_lane=2)[0] == pamd.PAMD_EINVAL
+
+
 def test_null_context_calls_fail_cleanly(lib):
     from paper_1806_06016_gb300 import pamd
     assert lib.pamd_propagate(None, 1, 0.001, 300.0) == pamd.PAMD_EINVAL

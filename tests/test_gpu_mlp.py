@@ -77,6 +77,59 @@ def test_gemm_within_fp32_accumulation_bound(env, M, N, K):
     assert np.all(np.abs(C - A @ B.T) <= bound)
 
 
+# Shapes of the surrogate's production calls: far more 128 x 256 tile pairs
+# than the 76 resident two-CTA clusters, so every cluster walks several tiles,
+# both tensor-memory accumulators are used and the TMA ring wraps across tiles.
+FULL_SIZE_SHAPES = [(40000, 512, 2776), (65536, 512, 512)]
+
+
+@pytest.mark.parametrize("M,N,K", FULL_SIZE_SHAPES)
+def test_gemm_full_size_multi_tile(env, M, N, K):
+    torch, _, S = env
+    rng = np.random.default_rng(M + N + K)
+    # small integers: every partial sum is an integer below 2^24, so the
+    # product is exact and a float32 product on the host is exact as well
+    A = rng.integers(-4, 5, (M, K)).astype(np.float32)
+    B = rng.integers(-4, 5, (N, K)).astype(np.float32)
+    C = S.gemm_bf16(_bf16_tensor(torch, A), _bf16_tensor(torch, B)).cpu().numpy()
+    np.testing.assert_array_equal(C, A @ B.T)
+    # Gaussian operands within the FP32 accumulation bound, on sampled rows of
+    # every cluster's tiles (rows from all 128-row blocks)
+    A = bf16_round(rng.normal(0, 1, (M, K))).astype(np.float32)
+    B = bf16_round(rng.normal(0, 1, (N, K))).astype(np.float32)
+    C = S.gemm_bf16(_bf16_tensor(torch, A), _bf16_tensor(torch, B)).cpu().numpy()
+    rows = np.unique(np.concatenate([np.arange(0, M, 97), [M - 1]]))
+    A64, B64 = A[rows].astype(np.float64), B.astype(np.float64)
+    bound = K * 2.0 ** -22 * (np.abs(A64) @ np.abs(B64).T)
+    assert np.all(np.abs(C[rows] - A64 @ B64.T) <= bound)
+
+
+def test_gemm_rejects_memory_of_another_device(env):
+    """The B tile is multicast by TMA into both CTAs of a cluster, so the
+    operands must be device memory of the current GPU: host memory and
+    page-locked host memory (torch's pin_memory, a cudaHostAlloc allocation
+    with the default flags, i.e. what cudaMallocHost returns) are refused."""
+    torch, pamd, _ = env
+    lib = pamd.load()
+    M = N = K = 64
+    dev = torch.ones((M, K), dtype=torch.bfloat16, device="cuda")
+    out = torch.zeros((M, N), dtype=torch.float32, device="cuda")
+    raw = np.zeros(M * K + 64, np.uint16)
+    off = (-raw.ctypes.data % 64) // 2
+    host = raw[off:off + M * K]
+    pinned = torch.ones((M, K), dtype=torch.bfloat16).pin_memory()
+    for bad in (host.ctypes.data, pinned.data_ptr()):
+        assert lib.pamd_gemm_bf16(bad, dev.data_ptr(), out.data_ptr(), M, N, K, K, K, N, None) \
+            == pamd.PAMD_EINVAL
+        assert lib.pamd_gemm_bf16(dev.data_ptr(), bad, out.data_ptr(), M, N, K, K, K, N, None) \
+            == pamd.PAMD_EINVAL
+    # device operands still work afterwards
+    assert lib.pamd_gemm_bf16(dev.data_ptr(), dev.data_ptr(), out.data_ptr(), M, N, K, K, K, N,
+                              None) == 0
+    torch.cuda.synchronize()
+    assert torch.all(out == K)
+
+
 def _model_and_params(env, n, hidden, seed, x):
     """A GPU model with non-trivial normalisation and biases, and the oracle's
     FP64 copy of it with the BF16-rounded weights the tensor cores use."""
@@ -112,6 +165,26 @@ def test_energy_forces_match_oracle(env, n, hidden, M):
         # energy without the backward pass is the same number
         E2, _ = model.energy_forces(torch.from_numpy(x.astype(np.float32)).cuda(), forces=False)
         np.testing.assert_array_equal(E2.cpu().numpy(), E)
+    finally:
+        model.close()
+
+
+def test_energy_forces_full_size_sampled(env):
+    """75 atoms, 20 000 configurations: the GEMMs run the persistent
+    multi-tile path of production calls; 64 sampled rows against the oracle."""
+    torch, _, _ = env
+    n, hidden, M = 75, 512, 20000
+    top = pi.make_chain(n, 1)
+    x = pi.perturbed_positions(top, M, 0.03, 11)
+    model, q = _model_and_params(env, n, hidden, 77, x[:2000])
+    try:
+        E, F = model.energy_forces(torch.from_numpy(x.astype(np.float32)).cuda())
+        E, F = E.cpu().numpy(), F.cpu().numpy()
+        rows = np.unique(np.linspace(0, M - 1, 64).astype(int))
+        assert len(rows) >= 64
+        Eo, Fo = omlp.energy_forces(q, x[rows].astype(np.float32).astype(np.float64))
+        assert np.abs(E[rows] - Eo).max() <= 2e-2 * q["sigma_E"]
+        assert np.sqrt(np.mean((F[rows] - Fo) ** 2)) <= 2e-2 * np.sqrt(np.mean(Fo ** 2))
     finally:
         model.close()
 

@@ -61,14 +61,27 @@ FORCE_CASES = [(1, 0), (2, 0), (3, 0), (4, 0), (5, 0), (13, 0), (22, 0), (22, 8)
                (31, 0), (33, 0), (64, 0), (75, 0), (75, 32), (129, 0), (200, 0), (256, 0)]
 
 
+def _init_arith(lib, top, R, T, seed, arith, **kw):
+    """Context with the scalar or the packed pair arithmetic; shapes the
+    packed kernel does not serve (fewer than 3 atoms per lane) are skipped."""
+    pa = lib.PAMD_PAIRS_SCALAR if arith == "scalar" else lib.PAMD_PAIRS_PACKED
+    try:
+        return lib.pamd_init(top, R, T, seed, _opts(lib, pair_arith=pa, **kw))
+    except lib.PamdError as e:
+        if arith == "packed" and e.code == lib.PAMD_EUNSUPPORTED:
+            pytest.skip("packed pair arithmetic does not apply to this shape")
+        raise
+
+
+@pytest.mark.parametrize("arith", ["scalar", "packed"])
 @pytest.mark.parametrize("n,lanes", FORCE_CASES)
-def test_forces_and_energies(lib, orc, n, lanes):
+def test_forces_and_energies(lib, orc, n, lanes, arith):
     top = pi.make_chain(n, 100 + n)
     top.dih_phase = np.linspace(0.2, 1.7, len(top.dih_phase))  # exercise the torsion sign
     R = 7
     x = f32(pi.perturbed_positions(top, R, 0.01, n))
     v = np.zeros_like(x)
-    ctx = lib.pamd_init(top, R, 300.0, 1, _opts(lib, lanes_per_replica=lanes))
+    ctx = _init_arith(lib, top, R, 300.0, 1, arith, lanes_per_replica=lanes)
     try:
         lib.pamd_set_state(ctx, x, v)
         fg, eg = lib.pamd_forces(ctx)
@@ -80,6 +93,66 @@ def test_forces_and_energies(lib, orc, n, lanes):
         if rms > 0:
             assert math.sqrt(np.mean((fg[k] - fo[k]) ** 2)) <= 1e-5 * rms, (k, n)
         assert abs(eg[k] - eo[k]) <= 1e-5 * max(scale[k], 1e-3), (k, eg[k], eo[k])
+
+
+# Packed FP32x2 pair arithmetic: every atoms-per-lane count 3..8, odd and
+# even lane counts (the even ones halve the antipodal tile), lane counts that
+# leave idle lanes, padding atoms, and R not a multiple of the replicas per
+# block (a ragged last block).
+PACKED_CASES = [(75, 25), (75, 19), (75, 15), (75, 13), (75, 11), (75, 10), (22, 8), (22, 6),
+                (22, 4), (22, 3), (40, 8), (9, 3), (200, 29), (256, 32)]
+
+
+@pytest.mark.parametrize("n,lanes", PACKED_CASES)
+def test_packed_kernel_forces(lib, orc, n, lanes):
+    top = pi.make_chain(n, 300 + n)
+    top.dih_phase = np.linspace(0.3, 2.1, len(top.dih_phase))
+    R = 11
+    x = f32(pi.perturbed_positions(top, R, 0.01, n + 3))
+    ctx = lib.pamd_init(top, R, 300.0, 1, _opts(lib, lanes_per_replica=lanes,
+                                               pair_arith=lib.PAMD_PAIRS_PACKED))
+    try:
+        shape = lib.pamd_get_shape(ctx)
+        assert shape["pair_arith"] == lib.PAMD_PAIRS_PACKED and shape["lanes_per_replica"] == lanes
+        lib.pamd_set_state(ctx, x, np.zeros_like(x))
+        fg, eg = lib.pamd_forces(ctx)
+    finally:
+        lib.pamd_destroy(ctx)
+    fo, eo, scale = _oracle_forces(orc, top, x)
+    for k in range(R):
+        rms = math.sqrt(np.mean(fo[k] ** 2))
+        assert math.sqrt(np.mean((fg[k] - fo[k]) ** 2)) <= 1e-5 * rms, (k, n)
+        assert abs(eg[k] - eo[k]) <= 1e-5 * scale[k], (k, eg[k], eo[k])
+
+
+@pytest.mark.parametrize("n,lanes,R", [(75, 15, 5), (75, 10, 3), (22, 6, 7), (40, 8, 9)])
+def test_packed_kernel_trajectory(lib, orc, n, lanes, R):
+    top = pi.make_chain(n, 7)
+    T, dt, gamma, seed = 400.0, 0.001, 1.0, 4242
+    x = f32(pi.perturbed_positions(top, R, 0.005, 1))
+    x = f32(x - x.mean(axis=1, keepdims=True))
+    v = f32(pi.gaussian_velocities(R, n, math.sqrt(KB * T / 12.0), 2))
+    ctx = lib.pamd_init(top, R, T, seed, _opts(lib, gamma_per_ps=gamma, lanes_per_replica=lanes,
+                                                pair_arith=lib.PAMD_PAIRS_PACKED))
+    try:
+        assert lib.pamd_get_shape(ctx)["pair_arith"] == lib.PAMD_PAIRS_PACKED
+        lib.pamd_set_state(ctx, x, v)
+        xo, vo = x.copy(), v.copy()
+        for s in range(10):
+            lib.pamd_propagate(ctx, 1, dt, T)
+            xg, vg, eg, _ = lib.pamd_get_state(ctx)
+            xo, vo, eo = orc.propagate(top, xo, vo, 1, dt, T, gamma, seed, s)
+            assert np.abs(xg - xo).max() < 1e-4, (s, np.abs(xg - xo).max())
+        assert np.abs(vg - vo).max() < 1e-2 * np.abs(vo).max()
+        assert np.abs(eg - eo).max() < 1e-4 * max(np.abs(eo).max(), 1.0)
+        # ten steps in one launch: the same trajectory as ten launches of one step
+        lib.pamd_set_state(ctx, x, v)
+        lib.pamd_set_counters(ctx, 0, 0, 0.0)
+        lib.pamd_propagate(ctx, 10, dt, T)
+        x10, v10, _, _ = lib.pamd_get_state(ctx)
+        assert np.abs(x10 - xo).max() < 1e-4
+    finally:
+        lib.pamd_destroy(ctx)
 
 
 PAIRED_CASES = [(13, 7, 6), (13, 7, 5), (22, 8, 7), (75, 25, 4), (75, 25, 3), (75, 19, 2),
@@ -194,15 +267,16 @@ def test_forces_excluded_overlapping_pairs(lib, orc):
     np.testing.assert_allclose(eg, eo, rtol=1e-5, atol=1e-6)
 
 
+@pytest.mark.parametrize("arith", ["scalar", "packed"])
 @pytest.mark.parametrize("n,R", [(22, 5), (75, 3), (200, 2), (7, 40)])
-def test_ten_step_trajectory(lib, orc, n, R):
+def test_ten_step_trajectory(lib, orc, n, R, arith):
     top = pi.make_chain(n, 7)
     T, dt, gamma, seed = 400.0, 0.001, 1.0, 4242
     x = f32(pi.perturbed_positions(top, R, 0.005, 1))
     x -= x.mean(axis=1, keepdims=True)
     x = f32(x)
     v = f32(pi.gaussian_velocities(R, n, math.sqrt(KB * T / 12.0), 2))
-    ctx = lib.pamd_init(top, R, T, seed, _opts(lib, gamma_per_ps=gamma))
+    ctx = _init_arith(lib, top, R, T, seed, arith, gamma_per_ps=gamma)
     try:
         lib.pamd_set_state(ctx, x, v)
         xo, vo = x.copy(), v.copy()

@@ -53,6 +53,66 @@ def test_noalloc_counts_match_resample(env, R):
         pamd.pamd_destroy(ctx)
 
 
+def test_noalloc_molecule_stream_and_optional_outputs(env):
+    """mol_id > 0 selects that molecule's Philox stream: counts equal those of
+    molecule 1 of a batch context; lnQ_dev and status_dev may be NULL."""
+    torch, pamd = env
+    tops = [pi.make_chain(12, 3), pi.make_chain(15, 4)]
+    Rs, T0, T1, seed = [700, 900], 800.0, 760.0, 31
+    ctx = pamd.pamd_init_batch(tops, Rs, [T0, T0], seed)
+    try:
+        pamd.pamd_propagate(ctx, 3, 0.001, T0)
+        _, _, E1, _ = pamd.pamd_get_state(pamd.pamd_batch_sub(ctx, 1), positions=False,
+                                          velocities=False, families=False)
+        ref_counts, ref_lnq = pamd.pamd_resample(ctx, T0, T1)
+        ref1 = ref_counts[Rs[0]:]
+        E_dev = torch.tensor(E1, dtype=torch.float64, device="cuda")
+        counts = torch.full((Rs[1],), -7, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        pamd.pamd_resample_counts_noalloc(E_dev.data_ptr(), Rs[1], T0, T1, seed, 1, counts.data_ptr(),
+                                          0, mol_id=1)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(counts.cpu().numpy(), ref1)
+        lnq = torch.zeros(1, dtype=torch.float64, device="cuda")
+        status = torch.full((1,), 99, dtype=torch.int32, device="cuda")
+        pamd.pamd_resample_counts_noalloc(E_dev.data_ptr(), Rs[1], T0, T1, seed, 1, counts.data_ptr(),
+                                          lnq.data_ptr(), mol_id=1, status_dev=status.data_ptr())
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(counts.cpu().numpy(), ref1)
+        assert abs(lnq.item() - ref_lnq[1]) <= 1e-12 * max(1.0, abs(ref_lnq[1]))
+        assert status.item() == 0
+    finally:
+        pamd.pamd_destroy(ctx)
+
+
+def test_noalloc_nonfinite_energy_gets_weight_zero(env, orc):
+    """An infinite energy: status PAMD_ENONFINITE, that replica weight 0, and
+    the counts equal the oracle's bit for bit (on cooling the oracle's weight
+    of E = +inf is exactly 0 as well)."""
+    torch, pamd = env
+    R, Tp, Tn, seed, ridx = 5000, 700.0, 650.0, 1234, 3
+    E = pi.random_energies(R, -80.0, 25.0, 4)
+    E[17] = np.inf
+    _, W = orc.resample_weights(E, Tp, Tn)
+    assert W[17] == 0
+    ref = orc.multinomial_counts(W, seed, ridx)
+    E_dev = torch.tensor(E, dtype=torch.float64, device="cuda")
+    counts = torch.zeros(R, dtype=torch.int32, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for _ in range(2):  # the second call starts from the first call's scratch
+        pamd.pamd_resample_counts_noalloc(E_dev.data_ptr(), R, Tp, Tn, seed, ridx, counts.data_ptr(),
+                                          status_dev=status.data_ptr())
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(counts.cpu().numpy(), ref)
+        assert status.item() == pamd.PAMD_ENONFINITE
+    # a finite population afterwards reports 0 again
+    E_dev[17] = -80.0
+    pamd.pamd_resample_counts_noalloc(E_dev.data_ptr(), R, Tp, Tn, seed, ridx, counts.data_ptr(),
+                                      status_dev=status.data_ptr())
+    torch.cuda.synchronize()
+    assert status.item() == 0
+
+
 def test_noalloc_rejects_oversized_population(env):
     torch, pamd = env
     E = torch.zeros(1, dtype=torch.float64, device="cuda")
