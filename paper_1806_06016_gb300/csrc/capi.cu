@@ -334,9 +334,13 @@ int build_topology(const pamd_topology* t, int lanes_req, TopoLayout* lay_out,
     lay.off_dihs = off; off += round_up(lay.n_dihs * 32, 16);
     lay.off_p14 = off; off += round_up(lay.n_p14 * 16, 16);
     lay.off_colors = off; off += round_up(4 * (kMaxColors + 1) * 4, 16);
-    lay.off_cbond = off; off += round_up(std::max(N - 1, 0) * 8, 16);
-    lay.off_cangle = off; off += round_up(std::max(N - 2, 0) * 8, 16);
-    lay.off_cdih = off; off += round_up(std::max(N - 3, 0) * 16, 16);
+    // chain term parameters, indexed by the term's first atom; one entry per
+    // atom slot of the lanes (L B), zero beyond the chain's last term, so that
+    // the packed kernel can evaluate every lane's terms without branches
+    const int n_slots = std::max(L * B, N);
+    lay.off_cbond = off; off += round_up(n_slots * 8, 16);
+    lay.off_cangle = off; off += round_up(n_slots * 8, 16);
+    lay.off_cdih = off; off += round_up(n_slots * 16, 16);
     // pair-parameter table of the half-ring tiles (chain layouts, when small)
     const size_t tab_bytes = (size_t)TH * B * B * L * 16;
     if (chain && TH > 0 && tab_bytes <= kPairTableMaxBytes) {

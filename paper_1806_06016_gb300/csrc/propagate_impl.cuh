@@ -232,13 +232,17 @@ __device__ __forceinline__ void dihedral_force(float3 pi_, float3 pj_, float3 pk
     // sin phi = ((B x A) . G) / (|A| |B| |G|), and (B x A) . G = -(F . B) |G|^2
     // because B . G = 0, so sin phi = -(F . B) |G| / (|A| |B|)
     const float sphi = -dot3(F, Bv) * lg * rab;
-    float cn = cphi, sn = sphi;
+    // cos(n phi), sin(n phi) for n = 1..6 without a loop (straight-line code,
+    // so the terms of a lane interleave): multiple-angle formulas up to 3 phi,
+    // then n phi = 3 phi + (n - 3) phi for n > 3
     const int n = (int)nn;
-    for (int q = 1; q < n; ++q) {
-        const float c2 = cn * cphi - sn * sphi;
-        sn = fmaf(sn, cphi, cn * sphi);
-        cn = c2;
-    }
+    const float c2 = fmaf(cphi + cphi, cphi, -1.0f), s2 = (sphi + sphi) * cphi;
+    const float c3 = fmaf(c2, cphi, -s2 * sphi), s3 = fmaf(s2, cphi, c2 * sphi);
+    const int m = (n > 3) ? n - 3 : n;
+    const float ca = (m == 1) ? cphi : ((m == 2) ? c2 : c3);
+    const float sa = (m == 1) ? sphi : ((m == 2) ? s2 : s3);
+    const float cn = (n > 3) ? fmaf(c3, ca, -s3 * sa) : ca;
+    const float sn = (n > 3) ? fmaf(s3, ca, c3 * sa) : sa;
     const float dEdphi = -kd * nn * (sn * cph - cn * sph);
     const float ia = lg * rA2, ib = lg * rB2;
     const float pa = dot3(F, G) * rA2 * rlg, pb = dot3(H, G) * rB2 * rlg;
@@ -687,7 +691,7 @@ __device__ __forceinline__ void advance_replica(const PropParams& p, const unsig
                 xi[a] = fmaf(p.hdt, vx[a], xi[a]);          // A
                 yi[a] = fmaf(p.hdt, vy[a], yi[a]);
                 zi[a] = fmaf(p.hdt, vz[a], zi[a]);
-                if (i < N) {                                // O
+                {  // O (padding atoms: zero noise scale, velocity stays 0)
                     const float3 z = normal3_fast(p.seed, (uint32_t)i, (uint32_t)k, step, p.purpose_mol);
                     vx[a] = fmaf(p.c1, vx[a], sd[a] * z.x);
                     vy[a] = fmaf(p.c1, vy[a], sd[a] * z.y);

@@ -12,10 +12,13 @@
 //   instructions (two FP32 results per instruction: the same FP32 roundings
 //   as two scalar instructions, half the issue slots).  The reciprocal square
 //   root stays scalar (no packed form).
-// * Partner atoms are read from shared memory already duplicated, {x,x,y,y}
-//   and {z,z,q,q} per atom, so no instruction is spent forming the broadcast
-//   operand of a packed instruction; the per-atom mixing parameters
-//   {sigma/2, sigma/2, sqrt(24 eps), sqrt(24 eps)} sit in a per-block table.
+// * Partner atoms are read from shared memory already duplicated and with
+//   their coordinates negated, {-x,-x,-y,-y} and {-z,-z,q,q} per atom, so that
+//   d = x_own + (-x_partner) is one add and no instruction is spent forming
+//   the broadcast operand of a packed instruction; the per-atom mixing
+//   parameters {sigma/2, sigma/2, sqrt(24 eps), sqrt(24 eps)} sit in a
+//   per-block table.  Own sqrt(24 eps) are kept negated, so -eps_ij is a
+//   product as well: the packed path needs no sign changes.
 // * Forces on partner atoms are summed in registers over the tile and handed
 //   to the owner lane with warp shuffles (lane g receives from lane g - t the
 //   forces on its own block), so shared memory holds positions only and the
@@ -49,6 +52,13 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+
+// A point about 1000 nm or more from the molecule, distinct for every index
+// and never collinear with the points of the two neighbouring indices: where
+// padding atoms (and the missing next block of the last lane) sit.
+__device__ __forceinline__ float3 far_point(int i) {
+    return make_float3(1000.0f + 4.0f * (float)i, 2.0f * (float)(i & 1), 2.0f * (float)((i >> 1) & 1));
+}
 
 // Own atoms of a lane: packed pairs plus the scalar tail.
 template <int B>
@@ -106,33 +116,36 @@ struct Own {
     }
 };
 
-// One partner atom (duplicated operands) against the lane's own atoms.
-// d = x_own - x_partner; the force on an own atom is +fs d, on the partner
-// -fs d; the partner's share is summed into (gx, gy, gz) as +fs d (the caller
-// subtracts it).  Masked own/partner pairs (bit a*B + b) contribute zero.
+// One partner atom (duplicated operands, negated coordinates) against the
+// lane's own atoms.  d = x_own - x_partner; the force on an own atom is +fs d,
+// on the partner -fs d; the partner's share is summed into (gx, gy, gz) as
+// +fs d (the caller subtracts it).  nse holds -sqrt(24 eps) of the own atoms:
+// neps = -eps_ij and e2 = -2 neps = 2 eps_ij.  Masked own/partner pairs (bit
+// a*B + b) contribute zero.
 template <int B, bool MASKED>
-__device__ __forceinline__ void partner_x2(const Own<B>& r, const Own<B>& hs, const Own<B>& se,
+__device__ __forceinline__ void partner_x2(const Own<B>& r, const Own<B>& hs, const Own<B>& nse,
                                            const Own<B>& qq, Own<B>& f, float4 pa, float4 pb,
                                            float4 pp, int b, unsigned long long mask, float& gx,
                                            float& gy, float& gz) {
     using C = X2Cfg<B>;
-    const float2 xj = f2(pa.x, pa.y), yj = f2(pa.z, pa.w), zj = f2(pb.x, pb.y);
+    const float2 nxj = f2(pa.x, pa.y), nyj = f2(pa.z, pa.w), nzj = f2(pb.x, pb.y);
     const float2 qj = f2(pb.z, pb.w), hj = f2(pp.x, pp.y), ej = f2(pp.z, pp.w);
-    float2 Gx = f2(0.f), Gy = f2(0.f), Gz = f2(0.f);
+    const float2 m2 = f2(-2.0f);
+    float2 Gx, Gy, Gz;
 #pragma unroll
     for (int p = 0; p < C::P; ++p) {
-        const float2 dx = sub2(r.x[p], xj);
-        const float2 dy = sub2(r.y[p], yj);
-        const float2 dz = sub2(r.z[p], zj);
+        const float2 dx = add2(r.x[p], nxj);
+        const float2 dy = add2(r.y[p], nyj);
+        const float2 dz = add2(r.z[p], nzj);
         const float2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
         const float2 rinv = f2(rsqrtf(r2.x), rsqrtf(r2.y));
         const float2 rinv2 = mul2(rinv, rinv);
         const float2 sg = add2(hs.x[p], hj);
         const float2 s2 = mul2(mul2(sg, sg), rinv2);
         const float2 s6 = mul2(mul2(s2, s2), s2);
-        const float2 eps = mul2(se.x[p], ej);
-        const float2 e2 = add2(eps, eps);
-        const float2 lj = mul2(s6, fma2(e2, s6, f2(-eps.x, -eps.y)));
+        const float2 neps = mul2(nse.x[p], ej);
+        const float2 e2 = mul2(neps, m2);
+        const float2 lj = mul2(s6, fma2(e2, s6, neps));
         const float2 q2 = mul2(qq.x[p], qj);
         float2 fs = mul2(fma2(q2, rinv, lj), rinv2);
         if (MASKED) {
@@ -142,19 +155,25 @@ __device__ __forceinline__ void partner_x2(const Own<B>& r, const Own<B>& hs, co
         f.x[p] = fma2(fs, dx, f.x[p]);
         f.y[p] = fma2(fs, dy, f.y[p]);
         f.z[p] = fma2(fs, dz, f.z[p]);
-        Gx = fma2(fs, dx, Gx);
-        Gy = fma2(fs, dy, Gy);
-        Gz = fma2(fs, dz, Gz);
+        if (p == 0) {
+            Gx = mul2(fs, dx);
+            Gy = mul2(fs, dy);
+            Gz = mul2(fs, dz);
+        } else {
+            Gx = fma2(fs, dx, Gx);
+            Gy = fma2(fs, dy, Gy);
+            Gz = fma2(fs, dz, Gz);
+        }
     }
     gx = Gx.x + Gx.y;
     gy = Gy.x + Gy.y;
     gz = Gz.x + Gz.y;
     if (C::TAIL) {
-        const float dx = r.xt - pa.x, dy = r.yt - pa.z, dz = r.zt - pb.x;
+        const float dx = r.xt + pa.x, dy = r.yt + pa.z, dz = r.zt + pb.x;
         const float sg = hs.xt + pp.x;
-        const float eps = se.xt * pp.z;
+        const float neps = nse.xt * pp.z;
         float fs, e;
-        pair_lj_coul<false>(dx, dy, dz, sg * sg, eps, eps + eps, qq.xt * pb.z, fs, e);
+        pair_lj_coul<false>(dx, dy, dz, sg * sg, -neps, -2.0f * neps, qq.xt * pb.z, fs, e);
         if (MASKED && ((mask >> ((B - 1) * B + b)) & 1ull)) fs = 0.f;
         // pair_lj_coul's fs multiplies d = x_j - x_i; here d = x_i - x_j
         f.xt = fmaf(fs, dx, f.xt);
@@ -167,7 +186,13 @@ __device__ __forceinline__ void partner_x2(const Own<B>& r, const Own<B>& hs, co
 }
 
 // Chain bonded pass (terms starting in the lane's block): forces on the own
-// atoms go to f, those on the next block's first three atoms to sf.
+// atoms go to f, those on the next block's first three atoms to sf.  Every
+// lane evaluates B terms of each kind without branches: the term parameters
+// past the chain's end are zero (the topology table has one entry per atom
+// slot), padding atoms and the missing next block of the last lane sit at
+// distinct, non-collinear points far away (so a term with zero parameters
+// gives exactly zero, never 0 * inf), and the scaled 1-4 pair, whose
+// parameters are per atom, is multiplied by its existence.
 template <int B>
 __device__ __forceinline__ void bonded_chain_x2(const unsigned char* sm, const TopoLayout& lay,
                                                 const float4* prm, const float4* posA,
@@ -182,15 +207,14 @@ __device__ __forceinline__ void bonded_chain_x2(const unsigned char* sm, const T
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
         sf[m] = make_float3(0.f, 0.f, 0.f);
-        if (has_next) {
+        if (has_next) {  // stored negated
             const float4 a = posA[nbase + m];
             const float4 c = posB[nbase + m];
-            sp[m] = make_float3(a.x, a.z, c.x);
+            sp[m] = make_float3(-a.x, -a.z, -c.x);
         } else {
-            sp[m] = make_float3(0.f, 0.f, 0.f);
+            sp[m] = far_point(2000 + m);
         }
     }
-    if (i0 + 1 >= N) return;  // no term starts here
     auto P = [&](int o) -> float3 {
         return (o < B) ? make_float3(r.gx(o < B ? o : 0), r.gy(o < B ? o : 0), r.gz(o < B ? o : 0))
                        : sp[o >= B ? o - B : 0];
@@ -212,13 +236,13 @@ __device__ __forceinline__ void bonded_chain_x2(const unsigned char* sm, const T
 #pragma unroll
     for (int a = 0; a < B; ++a) {
         const int d = i0 + a;
-        if (d + 1 < N) {  // bond (d, d+1)
+        {  // bond (d, d+1)
             const float2 q = cb[d];
             const float3 fb = bond_force<false>(P(a), P(a + 1), q.x, q.y, e_unused);
             F(a, fb);
             F(a + 1, make_float3(-fb.x, -fb.y, -fb.z));
         }
-        if (d + 2 < N) {  // angle (d, d+1, d+2)
+        {  // angle (d, d+1, d+2)
             const float2 q = ca[d];
             float3 fi, fj, fk;
             angle_force<false>(P(a), P(a + 1), P(a + 2), q.x, q.y, fi, fj, fk, e_unused);
@@ -226,7 +250,7 @@ __device__ __forceinline__ void bonded_chain_x2(const unsigned char* sm, const T
             F(a + 1, fj);
             F(a + 2, fk);
         }
-        if (d + 3 < N) {  // dihedral (d..d+3) and 1-4 pair (d, d+3)
+        {  // dihedral (d..d+3) and 1-4 pair (d, d+3)
             float3 fi, fj, fk, fl;
             dihedral_force<false>(P(a), P(a + 1), P(a + 2), P(a + 3), cd[d], fi, fj, fk, fl,
                                   e_unused);
@@ -235,9 +259,12 @@ __device__ __forceinline__ void bonded_chain_x2(const unsigned char* sm, const T
             F(a + 2, fk);
             F(a + 3, fl);
             const int s0 = g * C::BS + a;
-            const int s3 = (a + 3 < B) ? (s0 + 3) : (nbase + a + 3 - B);
-            const float3 fp = pair14_force<false>(P(a), P(a + 3), prm[s0], prm[s3], lay.s14_lj,
-                                                  lay.s14_c, e_unused);
+            int s3 = (a + 3 < B) ? (s0 + 3) : (nbase + a + 3 - B);
+            s3 = (s3 < lay.nk) ? s3 : s0;  // the last lane: any slot, the term is then zeroed
+            const float exists = (d + 3 < N) ? 1.0f : 0.0f;
+            float3 fp = pair14_force<false>(P(a), P(a + 3), prm[s0], prm[s3], lay.s14_lj,
+                                            lay.s14_c, e_unused);
+            fp = f3scale(exists, fp);
             F(a, fp);
             F(a + 3, make_float3(-fp.x, -fp.y, -fp.z));
         }
@@ -264,7 +291,7 @@ __device__ __forceinline__ void forces_x2(const unsigned char* sm, const TopoLay
                                           const unsigned long long* masks, const float4* posA,
                                           const float4* posB, int L, int g, int base,
                                           unsigned gmask, const Own<B>& r, const Own<B>& hs,
-                                          const Own<B>& se, const Own<B>& qq, Own<B>& f) {
+                                          const Own<B>& nse, const Own<B>& qq, Own<B>& f) {
     using C = X2Cfg<B>;
     f.zero();
     // pairs inside the lane's own block (masked: the 1-2/1-3/1-4 pairs live here)
@@ -276,7 +303,7 @@ __device__ __forceinline__ void forces_x2(const unsigned char* sm, const TopoLay
             for (int b = a + 1; b < B; ++b) {
                 const float dx = r.gx(b) - r.gx(a), dy = r.gy(b) - r.gy(a), dz = r.gz(b) - r.gz(a);
                 const float sg = hs.gx(a) + hs.gx(b);
-                const float eps = se.gx(a) * se.gx(b);
+                const float eps = nse.gx(a) * nse.gx(b);
                 float fs, e;
                 pair_lj_coul<false>(dx, dy, dz, sg * sg, eps, eps + eps, qq.gx(a) * qq.gx(b), fs, e);
                 if ((m >> (a * B + b)) & 1ull) fs = 0.f;
@@ -285,38 +312,53 @@ __device__ __forceinline__ void forces_x2(const unsigned char* sm, const TopoLay
             }
         }
     }
-    // half ring over partner blocks
-    const int TH = L / 2;
+    // half ring over partner blocks: steps 1..(L-1)/2 give every lane a
+    // partner block; for even L the antipodal step L/2 follows, where only
+    // lanes g < L/2 work.  Lane g receives from lane g - t the forces on its
+    // own atom b.
+    const int TF = (L - 1) / 2;
 #pragma unroll 1
-    for (int t = 1; t <= TH; ++t) {
-        const bool active = !(2 * t == L && g >= t);
+    for (int t = 1; t <= TF; ++t) {
         int J = g + t;
         J = (J >= L) ? J - L : J;
         const int sJ = J * C::BS;
-        // lane g receives from lane g - t the forces on its own atom b
         int src = g - t;
         src = (src < 0) ? src + L : src;
-        const unsigned long long m = active ? masks[t * L + g] : 0ull;
-        // one branch for the whole group (the hand-over shuffles must not diverge)
-        if (!__any_sync(gmask, m != 0ull)) {
+        const unsigned long long m = masks[t * L + g];
+        // the partner sums of the whole tile are handed over after it, so
+        // that the partners' arithmetic can interleave
+        float gx[B], gy[B], gz[B];
+        if (m == 0ull) {
 #pragma unroll
-            for (int b = 0; b < B; ++b) {
-                float gx = 0.f, gy = 0.f, gz = 0.f;
-                if (active)
-                    partner_x2<B, false>(r, hs, se, qq, f, posA[sJ + b], posB[sJ + b],
-                                         dprm[sJ + b], b, m, gx, gy, gz);
-                hand_over<B>(f, b, gx, gy, gz, gmask, base + src);
-            }
+            for (int b = 0; b < B; ++b)
+                partner_x2<B, false>(r, hs, nse, qq, f, posA[sJ + b], posB[sJ + b], dprm[sJ + b], b,
+                                     m, gx[b], gy[b], gz[b]);
         } else {
 #pragma unroll
-            for (int b = 0; b < B; ++b) {
-                float gx = 0.f, gy = 0.f, gz = 0.f;
-                if (active)
-                    partner_x2<B, true>(r, hs, se, qq, f, posA[sJ + b], posB[sJ + b],
-                                        dprm[sJ + b], b, m, gx, gy, gz);
-                hand_over<B>(f, b, gx, gy, gz, gmask, base + src);
-            }
+            for (int b = 0; b < B; ++b)
+                partner_x2<B, true>(r, hs, nse, qq, f, posA[sJ + b], posB[sJ + b], dprm[sJ + b], b,
+                                    m, gx[b], gy[b], gz[b]);
         }
+#pragma unroll
+        for (int b = 0; b < B; ++b) hand_over<B>(f, b, gx[b], gy[b], gz[b], gmask, base + src);
+    }
+    if ((L & 1) == 0) {
+        const int t = L / 2;
+        const int J = (g + t) % L;
+        const int sJ = J * C::BS;
+        float gx[B], gy[B], gz[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) gx[b] = gy[b] = gz[b] = 0.f;
+        if (g < t) {
+            const unsigned long long m = masks[t * L + g];
+#pragma unroll
+            for (int b = 0; b < B; ++b)
+                partner_x2<B, true>(r, hs, nse, qq, f, posA[sJ + b], posB[sJ + b], dprm[sJ + b], b,
+                                    m, gx[b], gy[b], gz[b]);
+        }
+        const int src = (g - t + L) % L;
+#pragma unroll
+        for (int b = 0; b < B; ++b) hand_over<B>(f, b, gx[b], gy[b], gz[b], gmask, base + src);
     }
     // bonded terms; forces on the next block's first atoms go to lane g + 1
     float3 sf[3];
@@ -334,11 +376,12 @@ __device__ __forceinline__ void forces_x2(const unsigned char* sm, const TopoLay
     }
 }
 
+// Positions of one atom as partners read them: duplicated and negated.
 template <int B>
 __device__ __forceinline__ void store_pos_x2(float4* posA, float4* posB, int s, float x, float y,
                                              float z) {
-    posA[s] = make_float4(x, x, y, y);
-    *reinterpret_cast<float2*>(&posB[s]) = make_float2(z, z);
+    posA[s] = make_float4(-x, -x, -y, -y);
+    *reinterpret_cast<float2*>(&posB[s]) = make_float2(-z, -z);
 }
 
 // theta BAOAB steps of replica k by the L lanes of one group.  Velocities
@@ -357,7 +400,7 @@ __device__ __forceinline__ void advance_replica_x2(const PropParams& p, const un
     const int s0 = g * C::BS;  // the lane's first atom slot
     const uint32_t step_base = (p.dev_counters ? p.dev_counters[0] : 0u) + p.step0;
     const float* st = p.state_in + (size_t)k * 6 * Np;
-    Own<B> r, f, hs, se, qq;
+    Own<B> r, f, hs, nse, qq;
 #pragma unroll
     for (int a = 0; a < B; ++a) {
         const int i = g * B + a;
@@ -367,15 +410,16 @@ __device__ __forceinline__ void advance_replica_x2(const PropParams& p, const un
             r.set(a, st[i], st[Np + i], st[2 * Np + i]);
             vv = make_float4(st[3 * Np + i], st[4 * Np + i], st[5 * Np + i], 0.f);
         } else {
-            r.set(a, 1000.0f + 4.0f * (float)i, 0.0f, 0.0f);
+            const float3 q = far_point(i);
+            r.set(a, q.x, q.y, q.z);
         }
         vel[sl] = vv;
         const float4 c = prm[sl];
         hs.set(a, c.x, 0.f, 0.f);
-        se.set(a, c.y, 0.f, 0.f);
+        nse.set(a, -c.y, 0.f, 0.f);
         qq.set(a, c.z, 0.f, 0.f);
-        posA[sl] = make_float4(r.gx(a), r.gx(a), r.gy(a), r.gy(a));
-        posB[sl] = make_float4(r.gz(a), r.gz(a), c.z, c.z);
+        posA[sl] = make_float4(-r.gx(a), -r.gx(a), -r.gy(a), -r.gy(a));
+        posB[sl] = make_float4(-r.gz(a), -r.gz(a), c.z, c.z);
     }
     __syncwarp(gmask);
     const float hdt = p.hdt, c1 = p.c1;
@@ -404,7 +448,7 @@ __device__ __forceinline__ void advance_replica_x2(const PropParams& p, const un
                 x = fmaf(hdt, vv.x, x);  // A
                 y = fmaf(hdt, vv.y, y);
                 z = fmaf(hdt, vv.z, z);
-                if (i < N) {  // O
+                {  // O (padding atoms: zero noise scale, velocity stays 0)
                     const float3 w = normal3_fast(p.seed, (uint32_t)i, (uint32_t)k, step, p.purpose_mol);
                     vv.x = fmaf(c1, vv.x, cf.y * w.x);
                     vv.y = fmaf(c1, vv.y, cf.y * w.y);
@@ -421,7 +465,7 @@ __device__ __forceinline__ void advance_replica_x2(const PropParams& p, const un
             for (int a = 0; a < B; ++a) store_pos_x2<B>(posA, posB, s0 + a, r.gx(a), r.gy(a), r.gz(a));
             __syncwarp(gmask);
         }
-        forces_x2<B>(sm, lay, prm, dprm, masks, posA, posB, L, g, base, gmask, r, hs, se, qq, f);
+        forces_x2<B>(sm, lay, prm, dprm, masks, posA, posB, L, g, base, gmask, r, hs, nse, qq, f);
     }
     // closing B of the last step
     Own<B> v;
