@@ -89,6 +89,9 @@ NCU_TRAFFIC = {
     # 5 atoms per lane in 128-thread blocks (the shape the tuner now picks,
     # 15 x 5, two replicas per warp): 15.27 MB read, 0 written, 4.85 ms cold
     "534aba4b3a6abf48": 15266304,
+    # packed FP32x2 kernel (propagate_x2_kernel<5>, 15 x 5 shape): 15.12 MB
+    # read, 768 B written per theta = 100 launch
+    "938d23f1e613472b": 15118336,
 }
 
 
@@ -108,9 +111,14 @@ def measured_fp32_peak(pamd, iters=20000, reps=100):
             "timed_s": (scalar["ms"] + packed["ms"]) / 1e3}
 
 
-def kernel_source_hash():
-    p = os.path.join(ROOT, "paper_1806_06016_gb300", "csrc", "propagate_impl.cuh")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+def kernel_source_hash(packed=False):
+    """Hash of the source of the timed propagate kernel (the packed kernel
+    includes the scalar kernel's header)."""
+    names = ["propagate_impl.cuh"] + (["propagate_x2_impl.cuh"] if packed else [])
+    h = hashlib.sha256()
+    for n in names:
+        h.update(open(os.path.join(ROOT, "paper_1806_06016_gb300", "csrc", n), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def batch_sizes(w):
@@ -332,9 +340,9 @@ def run_gpu(args, w):
     flops = flop_per_replica_step(w["n_atoms"]) * R * theta
     flops36 = flop_per_replica_step(w["n_atoms"], FLOP_PAIR_KERNEL) * R * theta
     achieved = flops / (prop_avg / 1e3) / 1e12
-    traffic = NCU_TRAFFIC.get(kernel_source_hash())
-    peak = measured_fp32_peak(pamd)
     shape = tune if isinstance(tune, dict) else {}
+    traffic = NCU_TRAFFIC.get(kernel_source_hash(shape.get("pair_arith") == 2))
+    peak = measured_fp32_peak(pamd)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak["peak_tflops"], "unit": "TFLOP/s",
                 "frac": achieved / peak["peak_tflops"], "traffic": traffic,
                 "kernel": "propagate_x2_kernel" if shape.get("pair_arith") == 2 else "propagate_kernel",
@@ -609,10 +617,11 @@ def run_wham(args):
 
 
 def run_adaptive(args):
-    """Temperature schedules from the overlap condition and systematic
-    resampling on the 75-atom R = 8192 workload (theta = 1000, 1000 -> 250 K):
-    the geometric 100-step schedule with multinomial and with systematic
-    resampling, and adaptive schedules for two overlap targets; plus the cost
+    """Temperature schedules from the overlap condition and the resampling
+    rules on the 75-atom R = 8192 workload (theta = 1000, 1000 -> 250 K): the
+    geometric 100-step schedule with multinomial, systematic, nearest-integer
+    and Poisson resampling (the last two with a fluctuating population), and
+    adaptive schedules for two overlap targets; plus the cost
     of one overlap step at R = 8192 and R = 2^20.  Prints one JSON line."""
     import numpy as np
     import torch
@@ -640,7 +649,9 @@ def run_adaptive(args):
                 "T_first_steps": [float(t) for t in temps_used[:6]]}
 
     for rule, name in ((pamd.PAMD_RESAMPLE_MULTINOMIAL, "geometric_multinomial"),
-                       (pamd.PAMD_RESAMPLE_SYSTEMATIC, "geometric_systematic")):
+                       (pamd.PAMD_RESAMPLE_SYSTEMATIC, "geometric_systematic"),
+                       (pamd.PAMD_RESAMPLE_NEAREST, "geometric_nearest_integer"),
+                       (pamd.PAMD_RESAMPLE_POISSON, "geometric_poisson")):
         with pamd.Population(top, R, temps[0], w["seed"], pamd.torch_options(resample_rule=rule)) as pop:
             pop.anneal(temps, w["theta"], w["dt"])  # graph capture and warm-up
             pop.reset(temps[0], w["seed"])
@@ -648,6 +659,9 @@ def run_adaptive(args):
             t0 = time.perf_counter()
             obs = pop.anneal(temps, w["theta"], w["dt"])
             out[name] = summary(obs, time.perf_counter() - t0, temps)
+            sizes = [o["R_live"] for o in obs]
+            out[name]["population_size"] = {"min": min(sizes), "max": max(sizes),
+                                            "mean": float(np.mean(sizes)), "final": sizes[-1]}
     for alpha in (0.5, 0.8):
         with pamd.Population(top, R, temps[0], w["seed"], pamd.torch_options()) as pop:
             torch.cuda.synchronize()

@@ -50,6 +50,7 @@ extern "C" {
 #define PAMD_ENONFINITE (-5)  /* a replica's energy became NaN or infinite */
 #define PAMD_ESTATE (-6)      /* the context is broken by an earlier failure */
 #define PAMD_EUNSUPPORTED (-7) /* valid request the library cannot serve */
+#define PAMD_EPOPSIZE (-8)    /* a variable-size resampling left the population empty or above its capacity */
 
 /* Largest molecule the shared-memory kernels hold (atoms). */
 #define PAMD_MAX_ATOMS 256
@@ -71,6 +72,27 @@ extern "C" {
  */
 #define PAMD_RESAMPLE_MULTINOMIAL 0
 #define PAMD_RESAMPLE_SYSTEMATIC 1
+/*
+ * Two more rules let the population size fluctuate around the target R
+ * given to pamd_init (Wang, Machta & Katzgraber 2015): copy numbers with
+ * E[n_j] = tau_j = R W_j / C, the same integer weights, C their sum over the
+ * live population:
+ *   NEAREST  n_j = floor(tau_j), plus one with probability frac(tau_j) (the
+ *            64-bit Philox uniform u_j of ancestor j: one more copy when
+ *            floor(u_j C / 2^64) < R W_j - C floor(tau_j), exact integers);
+ *   POISSON  n_j ~ Poisson(tau_j): lambda = (double(R) double(W_j)) / double(C)
+ *            split into m = ceil(lambda / 500) chunks, each drawn by FP64
+ *            inversion of the Poisson CDF with the uniform of Philox counter
+ *            (j, resampling index, chunk, 2 | mol << 8).
+ * ln Q stays ln((1/R~) sum_j w_j) over the live size R~.  The context then
+ * holds a capacity of R + 8 ceil(sqrt(R)) + 64 slots (pamd_info reports the
+ * capacity as R; pamd_population_size the live size); the live replicas are
+ * the first slots.  Mixed precision, exact forces, one replica per lane
+ * group, single-molecule contexts only; pamd_record_energies, the adaptive
+ * schedule and checkpoint files are not available with them.
+ */
+#define PAMD_RESAMPLE_NEAREST 2
+#define PAMD_RESAMPLE_POISSON 3
 
 typedef struct pamd_ctx pamd_ctx; /* opaque, owned by the library */
 
@@ -158,6 +180,7 @@ typedef struct pamd_obs {
     int64_t n_families; /* distinct family ids (ancestors at T0) alive */
     int32_t max_copies; /* largest copy count of the resampling that led here */
     int32_t pad_;
+    int64_t R_live;     /* population size at this measurement */
 } pamd_obs;
 
 /* Fill *opt with the defaults: gamma 1/ps, mixed precision, automatic
@@ -182,10 +205,12 @@ int pamd_init(pamd_ctx** out, const pamd_topology* top, int64_t R, double T0, ui
 /*
  * Batched independent anneals: n_mol molecules (1..64) of uneven size, each
  * with its own population R[m], start temperature T0[m] and Philox stream
- * (molecule index m mixed into the counters), advanced by ONE persistent
- * launch per pamd_propagate (a device work queue of (molecule, replica
- * batch) items, largest molecules first; each molecule keeps its own launch
- * shape with 3..7 atoms per lane).  On a batch context pamd_reset,
+ * (molecule index m mixed into the counters).  pamd_propagate advances them
+ * all with one persistent launch per group of molecules sharing an
+ * atoms-per-lane count (3..7, a kernel compiled for each, so that each group
+ * gets its own register allocation); the group launches run concurrently on
+ * streams forked from the context's stream, each taking (molecule, replica
+ * batch) items from its own device work queue, largest molecules first.  On a batch context pamd_reset,
  * pamd_propagate, pamd_resample (copies_out: [sum R] in molecule order, lnQ_out:
  * [n_mol]), pamd_observables (out: [n_mol]) and pamd_anneal (per_step_out:
  * [(K+1) * n_mol], temperature-major; one CUDA graph for the whole batch) act
@@ -378,6 +403,11 @@ int pamd_set_counters(pamd_ctx* ctx, uint32_t step, uint32_t resample_index, dou
 /* Number of replicas and atoms; the launch shape in use for propagate. */
 int pamd_info(pamd_ctx* ctx, int64_t* R, int32_t* n_atoms, int32_t* lanes_per_replica,
               int32_t* atoms_per_lane, int32_t* replicas_per_block);
+
+/* Live population size and capacity (slots of the population buffers); they
+ * differ only under the NEAREST and POISSON resampling rules.  Synchronises
+ * the context's stream.  Errors: PAMD_EINVAL (null context, batch context). */
+int pamd_population_size(pamd_ctx* ctx, int64_t* live, int64_t* capacity);
 
 /* Launch shape the propagate kernel of this context uses now (no
  * counterpart in the paper).  out->from_cache and out->ms are 0.  Errors:

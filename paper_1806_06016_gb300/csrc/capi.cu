@@ -508,6 +508,7 @@ void fill_prop_params(pamd_ctx* c, PropParams& p, float* state, double* E, doubl
     p.topo = c->b.topo;
     p.status = &c->b.scal->status;
     p.dev_counters = dev_ctr;
+    p.live = c->variable ? c->b.counters + 2 : nullptr;
     p.lay = c->lay;
     p.R = c->R;
     p.theta = theta;
@@ -707,7 +708,10 @@ int set_launch_shape(pamd_ctx* c, const TopoLayout& lay_in, int warps_req, int v
 
 bool is_batch(const pamd_ctx* c) { return !c->subs.empty(); }
 
-// One launch of the batched kernel over every molecule of a batch context.
+// One launch of the batched kernel per atoms-per-lane group, the groups on
+// streams of their own forked from and joined back to the context's stream
+// (parallel branches when the anneal is captured as a graph), so that one
+// group's last work items overlap the next group's instead of idling SMs.
 // graph: counters come from each molecule's device counters plus step_off.
 int launch_prop_batch(pamd_ctx* c, int theta, double dt, double T, bool graph, uint32_t step_off) {
     BatchParams bp{};
@@ -717,14 +721,22 @@ int launch_prop_batch(pamd_ctx* c, int theta, double dt, double T, bool graph, u
                          graph ? s->b.counters : nullptr, graph ? step_off : s->step, nullptr);
     }
     PAMD_CU(c, cudaMemsetAsync(c->queue, 0, sizeof(int) * c->groups.size(), c->stream));
+    const bool fork = c->groups.size() > 1 && c->group_streams.size() == c->groups.size();
+    if (fork) PAMD_CU(c, cudaEventRecord(c->fork_event, c->stream));
     for (size_t q = 0; q < c->groups.size(); ++q) {
         const pamd_ctx::BatchGroup& gr = c->groups[q];
         bp.n_items = gr.n_items;
         bp.items = c->items + gr.first_item;
         bp.queue = c->queue + q;
-        const cudaError_t e = launch_propagate_batch(bp, gr.B, gr.grid, gr.smem, c->stream);
+        cudaStream_t s = fork ? c->group_streams[q] : c->stream;
+        if (fork) PAMD_CU(c, cudaStreamWaitEvent(s, c->fork_event, 0));
+        const cudaError_t e = launch_propagate_batch(bp, gr.B, gr.grid, gr.smem, s);
         c->launches += 1;
         if (e != cudaSuccess) return cuda_fail(c, e, "batched propagate launch");
+        if (fork) {
+            PAMD_CU(c, cudaEventRecord(c->group_events[q], s));
+            PAMD_CU(c, cudaStreamWaitEvent(c->stream, c->group_events[q], 0));
+        }
     }
     return PAMD_OK;
 }
@@ -755,6 +767,9 @@ int read_status(pamd_ctx* c) {
     PAMD_CU(c, cudaStreamSynchronize(c->stream));
     if (s.status == PAMD_ENONFINITE)
         return fail(PAMD_ENONFINITE, "non-finite energy in replica " + std::to_string(s.bad_replica));
+    if (s.status == PAMD_EPOPSIZE)
+        return fail(PAMD_EPOPSIZE, "resampling produced " + std::to_string(s.R_new) +
+                                       " replicas (capacity " + std::to_string(c->R) + ")");
     return fail(s.status, "device status " + std::to_string(s.status));
 }
 
@@ -942,12 +957,24 @@ int pamd_init(pamd_ctx** out, const pamd_topology* top, int64_t R, double T0, ui
         return fail(PAMD_EINVAL, "packed pair arithmetic runs one replica per lane group");
     if ((o.dev_alloc == nullptr) != (o.dev_free == nullptr))
         return fail(PAMD_EINVAL, "dev_alloc and dev_free must both be set or both be NULL");
-    if (o.resample_rule != PAMD_RESAMPLE_MULTINOMIAL && o.resample_rule != PAMD_RESAMPLE_SYSTEMATIC)
-        return fail(PAMD_EINVAL, "resample_rule must be PAMD_RESAMPLE_MULTINOMIAL or PAMD_RESAMPLE_SYSTEMATIC");
+    if (o.resample_rule < PAMD_RESAMPLE_MULTINOMIAL || o.resample_rule > PAMD_RESAMPLE_POISSON)
+        return fail(PAMD_EINVAL, "resample_rule must be one of the PAMD_RESAMPLE_* rules");
+    // rules whose copy numbers change the population size: a fixed capacity
+    // of slots, the live size on the device
+    const bool variable = o.resample_rule == PAMD_RESAMPLE_NEAREST || o.resample_rule == PAMD_RESAMPLE_POISSON;
+    long long capacity = R;
+    if (variable) {
+        if (o.precision != PAMD_PREC_MIXED || o.replicas_per_lane == 2)
+            return fail(PAMD_EUNSUPPORTED, "variable population sizes need mixed precision and one replica per lane group");
+        capacity = R + 8 * (long long)std::ceil(std::sqrt((double)R)) + 64;
+        if (capacity > 0x7fffffffLL) return fail(PAMD_EINVAL, "R too large for a variable population");
+    }
 
     pamd_ctx* c = new (std::nothrow) pamd_ctx();
     if (!c) return fail(PAMD_ENOMEM, "host allocation");
-    c->R = R;
+    c->R = capacity;
+    c->R_target = R;
+    c->variable = variable;
     c->resample_rule = o.resample_rule;
     c->precision = o.precision;
     c->gamma = o.gamma_per_ps;
@@ -1010,28 +1037,28 @@ int pamd_init(pamd_ctx** out, const pamd_topology* top, int64_t R, double T0, ui
     }
     // buffers
     const size_t st_bytes = state_bytes(c);
-    c->n_blk = (int)((R + 1023) / 1024);
+    c->n_blk = (int)((c->R + 1023) / 1024);  // R here: the slots (capacity)
     Buffers& b = c->b;
     b.state = (float*)dalloc(c, st_bytes);
     b.state_alt = (float*)dalloc(c, st_bytes);
-    b.E = (double*)dalloc(c, sizeof(double) * R);
-    b.E_alt = (double*)dalloc(c, sizeof(double) * R);
-    b.fam = (int32_t*)dalloc(c, sizeof(int32_t) * R);
-    b.fam_alt = (int32_t*)dalloc(c, sizeof(int32_t) * R);
-    b.ke = (double*)dalloc(c, sizeof(double) * R);
-    b.rg = (double*)dalloc(c, sizeof(double) * R);
+    b.E = (double*)dalloc(c, sizeof(double) * c->R);
+    b.E_alt = (double*)dalloc(c, sizeof(double) * c->R);
+    b.fam = (int32_t*)dalloc(c, sizeof(int32_t) * c->R);
+    b.fam_alt = (int32_t*)dalloc(c, sizeof(int32_t) * c->R);
+    b.ke = (double*)dalloc(c, sizeof(double) * c->R);
+    b.rg = (double*)dalloc(c, sizeof(double) * c->R);
     b.masses = (float*)dalloc(c, sizeof(float) * c->Np);
     b.topo = (unsigned char*)dalloc(c, blob.size());
     c->topo_cap = blob.size();
     b.x0 = (float*)dalloc(c, sizeof(float) * 3 * c->Np);
-    b.W = (unsigned long long*)dalloc(c, 8 * (size_t)R);
-    b.C = (unsigned long long*)dalloc(c, 8 * (size_t)R);
-    b.cnt = (int32_t*)dalloc(c, 4 * (size_t)R);
-    b.cnt_incl = (int32_t*)dalloc(c, 4 * (size_t)R);
+    b.W = (unsigned long long*)dalloc(c, 8 * (size_t)c->R);
+    b.C = (unsigned long long*)dalloc(c, 8 * (size_t)c->R);
+    b.cnt = (int32_t*)dalloc(c, 4 * (size_t)c->R);
+    b.cnt_incl = (int32_t*)dalloc(c, 4 * (size_t)c->R);
     b.blk_u64 = (unsigned long long*)dalloc(c, 8 * (size_t)c->n_blk);
     b.blk_f64 = (double*)dalloc(c, 8 * (size_t)c->n_blk);
     b.blk_i32 = (int32_t*)dalloc(c, 8 * (size_t)c->n_blk);
-    b.flags = (unsigned char*)dalloc(c, (size_t)R);
+    b.flags = (unsigned char*)dalloc(c, (size_t)c->R);
     b.obs_part = (double*)dalloc(c, sizeof(double) * (64 * 5 + 1) * (size_t)c->n_blk);
     b.scal = (DevScalars*)dalloc(c, sizeof(DevScalars));
     b.counters = (uint32_t*)dalloc(c, 16);
@@ -1051,8 +1078,8 @@ int pamd_init(pamd_ctx** out, const pamd_topology* top, int64_t R, double T0, ui
               cudaMemcpyAsync(b.topo, blob.data(), blob.size(), cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
               cudaMemcpyAsync(b.x0, x0.data(), sizeof(float) * 3 * c->Np, cudaMemcpyHostToDevice, c->stream) == cudaSuccess &&
               cudaMemsetAsync(b.state_alt, 0, st_bytes, c->stream) == cudaSuccess &&
-              cudaMemsetAsync(b.ke, 0, sizeof(double) * R, c->stream) == cudaSuccess &&
-              cudaMemsetAsync(b.rg, 0, sizeof(double) * R, c->stream) == cudaSuccess &&
+              cudaMemsetAsync(b.ke, 0, sizeof(double) * c->R, c->stream) == cudaSuccess &&
+              cudaMemsetAsync(b.rg, 0, sizeof(double) * c->R, c->stream) == cudaSuccess &&
               (t64.empty() || cudaMemcpyAsync(c->top64_blob, t64.data(), t64.size(),
                                               cudaMemcpyHostToDevice, c->stream) == cudaSuccess) &&
               launch_init(c, T0) == cudaSuccess &&
@@ -1082,6 +1109,8 @@ int pamd_init_batch(pamd_ctx** out, int32_t n_mol, const pamd_topology* tops, co
     if (o.precision != PAMD_PREC_MIXED)
         return fail(PAMD_EUNSUPPORTED, "the batched kernel runs the mixed-precision path only");
     if (o.replicas_per_lane > 1) return fail(PAMD_EUNSUPPORTED, "the batched kernel runs one replica per lane group");
+    if (o.resample_rule == PAMD_RESAMPLE_NEAREST || o.resample_rule == PAMD_RESAMPLE_POISSON)
+        return fail(PAMD_EUNSUPPORTED, "batched anneals keep a fixed population size");
     if ((o.dev_alloc == nullptr) != (o.dev_free == nullptr))
         return fail(PAMD_EINVAL, "dev_alloc and dev_free must both be set or both be NULL");
     for (int m = 0; m < n_mol; ++m)
@@ -1095,6 +1124,9 @@ int pamd_init_batch(pamd_ctx** out, int32_t n_mol, const pamd_topology* tops, co
     auto bail = [&](int code, const std::string& m) {
         for (pamd_ctx* s : c->subs) pamd_destroy(s);
         c->subs.clear();
+        for (cudaStream_t gs : c->group_streams) cudaStreamDestroy(gs);
+        for (cudaEvent_t ge : c->group_events) cudaEventDestroy(ge);
+        if (c->fork_event) cudaEventDestroy(c->fork_event);
         free_all(c);
         if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
         delete c;
@@ -1172,6 +1204,21 @@ int pamd_init_batch(pamd_ctx** out, int32_t n_mol, const pamd_topology* tops, co
     }
     std::stable_sort(groups.begin(), groups.end(), [](auto a, auto b) { return a.first > b.first; });
     for (auto& wg : groups) c->groups.push_back(wg.second);
+    // one stream and completion event per group, forked from the context's stream
+    if (c->groups.size() > 1) {
+        if (cudaEventCreateWithFlags(&c->fork_event, cudaEventDisableTiming) != cudaSuccess)
+            return bail(PAMD_ECUDA, "group streams");
+        for (size_t q = 0; q < c->groups.size(); ++q) {
+            cudaStream_t gs = nullptr;
+            cudaEvent_t ge = nullptr;
+            if (cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking) != cudaSuccess)
+                return bail(PAMD_ECUDA, "group streams");
+            c->group_streams.push_back(gs);
+            if (cudaEventCreateWithFlags(&ge, cudaEventDisableTiming) != cudaSuccess)
+                return bail(PAMD_ECUDA, "group streams");
+            c->group_events.push_back(ge);
+        }
+    }
     c->n_items = (int)items.size();
     c->items = (int4*)dalloc(c, sizeof(int4) * items.size());
     c->queue = (int*)dalloc(c, sizeof(int) * c->groups.size());
@@ -1291,6 +1338,7 @@ cudaError_t record_energies(pamd_ctx* c, int i) {
 int pamd_record_energies(pamd_ctx* c, double* E_dev, int32_t rows) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if (c->variable) return fail(PAMD_EUNSUPPORTED, "not available with a variable population size");
     if (is_batch(c)) return fail(PAMD_EINVAL, "energy recording: single-molecule contexts only");
     if (rows < 0 || (rows > 0 && !E_dev)) return fail(PAMD_EINVAL, "energy recording: rows >= 0, E_dev for rows > 0");
     c->rec_E = rows > 0 ? E_dev : nullptr;
@@ -1302,6 +1350,7 @@ int pamd_next_temperature(pamd_ctx* c, double T_prev, double T_final, double alp
                           double* T_next_out, double* alpha_out) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if (c->variable) return fail(PAMD_EUNSUPPORTED, "not available with a variable population size");
     if (is_batch(c)) return fail(PAMD_EINVAL, "overlap step: single-molecule contexts only");
     if (!T_next_out) return fail(PAMD_EINVAL, "overlap step: T_next_out is required");
     if ((rc = overlap_check_args(c->R, T_prev, T_final, alpha_target))) return rc;
@@ -1320,6 +1369,7 @@ int pamd_anneal_adaptive(pamd_ctx* c, double T0, double T_final, double alpha_ta
                          double* T_out, int32_t* n_temps_out) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if (c->variable) return fail(PAMD_EUNSUPPORTED, "not available with a variable population size");
     if (is_batch(c)) return fail(PAMD_EINVAL, "adaptive anneal: single-molecule contexts only");
     if (!(T0 > 0) || !std::isfinite(T0) || !(T_final > 0) || !(T_final < T0))
         return fail(PAMD_EINVAL, "adaptive anneal: 0 < T_final < T0 required");
@@ -1747,6 +1797,22 @@ int pamd_info(pamd_ctx* c, int64_t* R, int32_t* n_atoms, int32_t* lanes, int32_t
     return PAMD_OK;
 }
 
+int pamd_population_size(pamd_ctx* c, int64_t* live, int64_t* capacity) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    if (is_batch(c)) return fail(PAMD_EINVAL, "batch context: call this on pamd_batch_sub(ctx, m)");
+    int64_t n = c->R;
+    if (c->variable) {
+        uint32_t v = 0;
+        PAMD_CU(c, cudaMemcpyAsync(&v, c->b.counters + 2, sizeof(v), cudaMemcpyDeviceToHost, c->stream));
+        PAMD_CU(c, cudaStreamSynchronize(c->stream));
+        n = v;
+    }
+    if (live) *live = n;
+    if (capacity) *capacity = c->R;
+    return PAMD_OK;
+}
+
 int pamd_get_shape(pamd_ctx* c, pamd_tune* out) {
     if (!c || !out) return fail(PAMD_EINVAL, "null argument");
     if (is_batch(c)) return fail(PAMD_EINVAL, "batch context: call this on pamd_batch_sub(ctx, m)");
@@ -1827,6 +1893,7 @@ extern "C" {
 int pamd_checkpoint(pamd_ctx* c, const char* path) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if (c->variable) return fail(PAMD_EUNSUPPORTED, "not available with a variable population size");
     if (is_batch(c)) return fail(PAMD_EUNSUPPORTED, "checkpoint a batch molecule by molecule (pamd_batch_sub)");
     if (!path) return fail(PAMD_EINVAL, "null path");
     CkptHeader h{};
@@ -1871,6 +1938,7 @@ int pamd_checkpoint(pamd_ctx* c, const char* path) {
 int pamd_restore(pamd_ctx* c, const char* path) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if (c->variable) return fail(PAMD_EUNSUPPORTED, "not available with a variable population size");
     if (is_batch(c)) return fail(PAMD_EUNSUPPORTED, "restore a batch molecule by molecule (pamd_batch_sub)");
     if (!path) return fail(PAMD_EINVAL, "null path");
     FILE* f = std::fopen(path, "rb");
@@ -1921,6 +1989,7 @@ int pamd_restore(pamd_ctx* c, const char* path) {
 int pamd_set_force_model(pamd_ctx* c, pamd_mlp* m) {
     int rc = check_ctx(c);
     if (rc) return rc;
+    if (c->variable) return fail(PAMD_EUNSUPPORTED, "not available with a variable population size");
     if (is_batch(c) || is_f64(c))
         return fail(PAMD_EUNSUPPORTED, "force models need a single-molecule mixed-precision context");
     if (m) {
@@ -1940,6 +2009,9 @@ void pamd_destroy(pamd_ctx* c) {
     for (pamd_ctx* sub : c->subs) pamd_destroy(sub);
     c->subs.clear();
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    for (cudaStream_t s : c->group_streams) cudaStreamDestroy(s);
+    for (cudaEvent_t e : c->group_events) cudaEventDestroy(e);
+    if (c->fork_event) cudaEventDestroy(c->fork_event);
     free_all(c);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;

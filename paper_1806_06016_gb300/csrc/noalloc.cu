@@ -20,7 +20,7 @@ namespace pamd {
 
 __global__ void weights_kernel(const double* E, long long R, double dbeta, double two_s,
                                DevScalars* s, ExpCoef cf, unsigned long long* W,
-                               unsigned long long* blk_w, double* blk_e);
+                               unsigned long long* blk_w, double* blk_e, const uint32_t* live);
 
 namespace {
 
@@ -133,14 +133,15 @@ extern "C" int pamd_resample_counts_noalloc(const double* E_dev, int64_t R, doub
         set_last_error(std::string("clearing counts: ") + cudaGetErrorString(e));
         return PAMD_ECUDA;
     }
-    amax_kernel<<<nblk, 256, 0, s>>>(E_dev, R, dbeta, blk_e);
+    amax_kernel<<<nblk, 256, 0, s>>>(E_dev, R, dbeta, blk_e, nullptr);
     max_top_kernel<<<1, 1024, 0, s>>>(blk_e, nblk, scal);
     // W is written into C and scanned in place, block by block
-    weights_kernel<<<nblk, 256, 0, s>>>(E_dev, R, dbeta, two_s, scal, cf, C, blk_w, blk_e);
-    weights_top_kernel<<<1, 256, 0, s>>>(blk_w, blk_e, nblk, R, scal);
-    scan_local_u64_kernel<<<nblk, 256, 0, s>>>(C, R, blk_w, C);
+    weights_kernel<<<nblk, 256, 0, s>>>(E_dev, R, dbeta, two_s, scal, cf, C, blk_w, blk_e, nullptr);
+    weights_top_kernel<<<1, 256, 0, s>>>(blk_w, blk_e, nblk, R, scal, nullptr);
+    scan_local_u64_kernel<<<nblk, 256, 0, s>>>(C, R, blk_w, C, nullptr);
     counts_kernel<<<grid, 256, 0, s>>>(C, R, scal, seed, nullptr, resample_index,
-                                       kPurposeResample | ((uint32_t)mol_id << 8), 1, counts_dev);
+                                       kPurposeResample | ((uint32_t)mol_id << 8), 1, counts_dev,
+                                       nullptr);
     if (lnQ_dev) {
         e = cudaMemcpyAsync(lnQ_dev, &scal->lnQ, sizeof(double), cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) {

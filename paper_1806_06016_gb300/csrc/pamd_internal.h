@@ -79,6 +79,7 @@ struct PropParams {
     const unsigned char* topo; // TopoLayout.bytes
     int* status;               // [2]: code, replica
     const uint32_t* dev_counters;  // null, or {step, resample index} base
+    const uint32_t* live;      // null, or the live size of a variable population (R = capacity)
     TopoLayout lay;
     long long R;
     int theta;
@@ -148,6 +149,7 @@ struct DevScalars {
     int status;                // PAMD status code set by kernels (0 = ok)
     int bad_replica;
     int pad_;
+    long long R_new;           // size of the population a resampling produces
 };
 
 struct Buffers {
@@ -283,6 +285,9 @@ struct pamd_ctx {
         size_t smem;
     };
     std::vector<BatchGroup> groups;
+    std::vector<cudaStream_t> group_streams;  // one per group (launches overlap)
+    std::vector<cudaEvent_t> group_events;    // completion of each group's launch
+    cudaEvent_t fork_event = nullptr;         // the groups start after this
     unsigned char* top64_blob = nullptr;
     pamd_mlp* mlp = nullptr;      // force model replacing the exact forces (pamd_set_force_model)
     double* rec_E = nullptr;      // caller's [rec_rows][R] energy record of pamd_anneal, or null
@@ -290,6 +295,11 @@ struct pamd_ctx {
     void* ov_work = nullptr;      // scratch of the adaptive temperature step (allocated on first use)
     int resample_rule = PAMD_RESAMPLE_MULTINOMIAL;
     int pair_arith = PAMD_PAIRS_AUTO;  // pamd_options.pair_arith
+    // variable population (nearest-integer or Poisson resampling): R is the
+    // capacity of the buffers, R_target the size the copy numbers aim at, and
+    // the live size is device counter word 2
+    bool variable = false;
+    long long R_target = 0;
 };
 
 namespace pamd {
@@ -362,17 +372,22 @@ int overlap_step(cudaStream_t s, const double* E, long long R, double T_prev, do
                  double alpha_target, void* work, int num_sms, double* T_next, double* alpha_out,
                  long long* launches);
 
-// resampling kernels defined in resample.cu, also launched by noalloc.cu
+// resampling kernels defined in resample.cu, also launched by noalloc.cu;
+// `live`, when not null, holds the live size of a variable population (R is
+// then the capacity of the buffers)
 __global__ void reset_scalars_kernel(DevScalars* s);
-__global__ void amax_kernel(const double* E, long long R, double dbeta, double* blk_max);
+__global__ void amax_kernel(const double* E, long long R, double dbeta, double* blk_max,
+                            const uint32_t* live);
 __global__ void max_top_kernel(const double* blk_max, int nblk, DevScalars* s);
 __global__ void weights_top_kernel(unsigned long long* blk_w, const double* blk_e, int nblk,
-                                   long long R, DevScalars* s);
+                                   long long R, DevScalars* s, const uint32_t* live);
 __global__ void scan_local_u64_kernel(unsigned long long* W, long long R,
-                                      const unsigned long long* blk_off, unsigned long long* C);
+                                      const unsigned long long* blk_off, unsigned long long* C,
+                                      const uint32_t* live);
 __global__ void counts_kernel(const unsigned long long* C, long long R, const DevScalars* s,
                               unsigned long long seed, const uint32_t* dev_counters,
-                              uint32_t ridx_off, uint32_t purpose, int do_resample, int32_t* cnt);
+                              uint32_t ridx_off, uint32_t purpose, int do_resample, int32_t* cnt,
+                              const uint32_t* live);
 
 // resampling / observables / init kernels (resample.cu)
 cudaError_t launch_init(pamd_ctx* c, double T0);

@@ -802,7 +802,8 @@ __global__ void __launch_bounds__(PropCfg<B>::MAX_THREADS, PropCfg<B>::MIN_BLOCK
     float4* pos = slots + slot_local * slot_f4;
     float4* frc = pos + lay.nk;
 
-    for (long long k = (long long)blockIdx.x * rpb + slot_local; k < p.R;
+    const long long R = p.live ? (long long)*p.live : p.R;
+    for (long long k = (long long)blockIdx.x * rpb + slot_local; k < R;
          k += (long long)gridDim.x * rpb)
         advance_replica<B, CHAIN, TABLE>(p, sm, prm, masks, pos, frc, k, L, g, base, gmask);
 }

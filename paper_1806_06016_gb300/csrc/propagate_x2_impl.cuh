@@ -583,7 +583,8 @@ __global__ void __launch_bounds__(X2Cfg<B>::MAX_THREADS, X2Cfg<B>::MIN_BLOCKS)
     float4* posB = posA + lay.nk;
     float4* vel = posB + lay.nk;
 
-    for (long long k = (long long)blockIdx.x * rpb + slot_local; k < p.R;
+    const long long R = p.live ? (long long)*p.live : p.R;
+    for (long long k = (long long)blockIdx.x * rpb + slot_local; k < R;
          k += (long long)gridDim.x * rpb)
         advance_replica_x2<B>(p, sm, prm, dprm, aux, masks, posA, posB, vel, k, L, g, base, gmask);
 }

@@ -126,11 +126,22 @@ __global__ void set_counters_kernel(uint32_t* ctr, uint32_t step, uint32_t ridx)
     ctr[1] = ridx;
 }
 
+// Population size of a context with a variable population (device counter
+// word 2, read by every kernel that loops over the population).
+__global__ void set_live_kernel(uint32_t* ctr, uint32_t live) { ctr[2] = live; }
+
+// Live population size: *live when the population size varies, else R.
+__device__ __forceinline__ long long live_size(const uint32_t* live, long long R) {
+    return live ? (long long)*live : R;
+}
+
 // ------------------------------------------------------------------ weights
 
 // a_j = -(beta_next - beta_prev) E_j ; block maxima.
-__global__ void amax_kernel(const double* E, long long R, double dbeta, double* blk_max) {
+__global__ void amax_kernel(const double* E, long long R, double dbeta, double* blk_max,
+                            const uint32_t* live) {
     __shared__ double sh[32];
+    R = live_size(live, R);
     const long long base = (long long)blockIdx.x * kScanBlock;
     double m = -INFINITY;
 #pragma unroll
@@ -154,9 +165,14 @@ __global__ void max_top_kernel(const double* blk_max, int nblk, DevScalars* s) {
 // exponentials (for Q).
 __global__ void weights_kernel(const double* E, long long R, double dbeta, double two_s,
                                DevScalars* s, ExpCoef cf, unsigned long long* W,
-                               unsigned long long* blk_w, double* blk_e) {
+                               unsigned long long* blk_w, double* blk_e, const uint32_t* live) {
     __shared__ double sh[32];
     __shared__ unsigned long long shw[8];
+    if (live) {  // 2^s with s = 63 - ceil(log2 R) of the live population
+        R = (long long)*live;
+        const int bits = (R > 1) ? 64 - __clzll((unsigned long long)(R - 1)) : 0;
+        two_s = ldexp(1.0, 63 - bits);
+    }
     const long long base = (long long)blockIdx.x * kScanBlock;
     const double m = s->m;
     unsigned long long w[4];
@@ -189,7 +205,8 @@ __global__ void weights_kernel(const double* E, long long R, double dbeta, doubl
 
 // Exclusive scan of the block sums of W (in place), C_total, ln Q.
 __global__ void weights_top_kernel(unsigned long long* blk_w, const double* blk_e, int nblk,
-                                   long long R, DevScalars* s) {
+                                   long long R, DevScalars* s, const uint32_t* live) {
+    R = live_size(live, R);
     __shared__ unsigned long long shw[8];
     __shared__ unsigned long long carry;
     if (threadIdx.x == 0) carry = 0ull;
@@ -238,8 +255,10 @@ __global__ void weights_top_kernel(unsigned long long* blk_w, const double* blk_
 
 // C_j = block offset + inclusive scan of W inside the block.
 __global__ void scan_local_u64_kernel(unsigned long long* W, long long R,
-                                      const unsigned long long* blk_off, unsigned long long* C) {
+                                      const unsigned long long* blk_off, unsigned long long* C,
+                                      const uint32_t* live) {
     __shared__ unsigned long long shw[8];
+    R = live_size(live, R);
     const long long base = (long long)blockIdx.x * kScanBlock;
     unsigned long long v[4];
 #pragma unroll
@@ -263,7 +282,8 @@ __global__ void scan_local_u64_kernel(unsigned long long* W, long long R,
 __global__ void counts_kernel(const unsigned long long* C, long long R, const DevScalars* s,
                               unsigned long long seed, const uint32_t* dev_counters,
                               uint32_t ridx_off, uint32_t purpose, int do_resample,
-                              int32_t* cnt) {
+                              int32_t* cnt, const uint32_t* live) {
+    R = live_size(live, R);
     const uint32_t ridx = (dev_counters ? dev_counters[1] : 0u) + ridx_off;
     const unsigned long long total = s->C_total;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < R;
@@ -309,8 +329,102 @@ __global__ void counts_kernel(const unsigned long long* C, long long R, const De
     }
 }
 
+// ------------------------------------------------------------------ copy numbers
+// of the rules that let the population size vary around a target R_t
+
+// q = floor(a b / c), r = a b - q c exactly, for a < 2^32, b <= c, c >= 1:
+// an FP64 estimate corrected in 128-bit integer arithmetic.
+__device__ __forceinline__ void muldiv_exact(unsigned long long a, unsigned long long b,
+                                             unsigned long long c, unsigned long long& q,
+                                             unsigned long long& r) {
+    const unsigned long long plo = a * b, phi = __umul64hi(a, b);
+    unsigned long long qq = (unsigned long long)__ddiv_rn(
+        __dmul_rn(__ull2double_rn(a), __ull2double_rn(b)), __ull2double_rn(c));
+    for (int it = 0; it < 8; ++it) {
+        const unsigned long long tlo = qq * c, thi = __umul64hi(qq, c);
+        if (thi > phi || (thi == phi && tlo > plo)) {  // qq c > a b
+            --qq;
+            continue;
+        }
+        const unsigned long long rlo = plo - tlo;
+        const unsigned long long rhi = phi - thi - (plo < tlo ? 1ull : 0ull);
+        if (rhi == 0ull && rlo < c) {
+            q = qq;
+            r = rlo;
+            return;
+        }
+        ++qq;
+    }
+    q = qq;  // not reached: the estimate is within one of the quotient
+    r = 0ull;
+}
+
+// Smallest n with F(n) >= u for the Poisson CDF F of mean lam, summed as
+// p_0 = e^-lam, p_n = (p_{n-1} lam) / n (every operation rounded to FP64 as
+// written); at most floor(lam + 20 sqrt(lam)) + 50.
+__device__ __forceinline__ long long poisson_inverse(double lam, double u, const ExpCoef& cf) {
+    const long long n_max = (long long)floor(__dadd_rn(lam, __dmul_rn(20.0, __dsqrt_rn(lam)))) + 50;
+    double p = exp_det(-lam, cf);
+    double F = p;
+    long long n = 0;
+    while (u > F && n < n_max) {
+        ++n;
+        p = __ddiv_rn(__dmul_rn(p, lam), (double)n);
+        F = __dadd_rn(F, p);
+    }
+    return n;
+}
+
+// Copy numbers of ancestor j with E[n_j] = tau_j = R_t W_j / C (C = sum of
+// the integer weights W of the live population): rule 3 nearest integer
+// (floor(tau_j) plus a Bernoulli draw of the fractional part), rule 4
+// Poisson (CDF inversion, in chunks of at most 500 of the mean).
+__global__ void varsize_counts_kernel(const unsigned long long* W, long long R, const DevScalars* s,
+                                      long long R_target, unsigned long long seed,
+                                      const uint32_t* dev_counters, uint32_t ridx_off,
+                                      uint32_t purpose, int rule, ExpCoef cf, int32_t* cnt,
+                                      const uint32_t* live) {
+    R = live_size(live, R);
+    const uint32_t ridx = (dev_counters ? dev_counters[1] : 0u) + ridx_off;
+    const unsigned long long C = s->C_total;
+    for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < R;
+         j += (long long)gridDim.x * blockDim.x) {
+        long long n = 0;
+        if (C > 0ull && rule == 3) {
+            unsigned long long q, r;
+            muldiv_exact((unsigned long long)R_target, W[j], C, q, r);
+            const uint4 o = philox4x32_10(make_uint4((uint32_t)j, ridx, 0u, purpose), seed_key(seed));
+            const unsigned long long u = (unsigned long long)o.x | ((unsigned long long)o.y << 32);
+            n = (long long)q + ((__umul64hi(u, C) < r) ? 1 : 0);
+        } else if (C > 0ull) {
+            const double lam = __ddiv_rn(__dmul_rn((double)R_target, __ull2double_rn(W[j])),
+                                         __ull2double_rn(C));
+            int m = (int)ceil(__ddiv_rn(lam, 500.0));
+            m = m < 1 ? 1 : m;
+            const double chunk = __ddiv_rn(lam, (double)m);
+            for (int c = 0; c < m; ++c) {
+                const uint4 o = philox4x32_10(make_uint4((uint32_t)j, ridx, (uint32_t)c, purpose),
+                                              seed_key(seed));
+                const unsigned long long u64 = (unsigned long long)o.x | ((unsigned long long)o.y << 32);
+                const double u = __dmul_rn(__dadd_rn(__ull2double_rn(u64 >> 11), 0.5), 0x1p-53);
+                n += poisson_inverse(chunk, u, cf);
+            }
+        }
+        cnt[j] = (int32_t)n;
+    }
+}
+
+// After the gather: the new population size becomes the live size (at most
+// the capacity R); an empty or overflowing population is reported.
+__global__ void commit_size_kernel(DevScalars* s, uint32_t* ctr, long long R) {
+    const long long n = s->R_new;
+    if ((n == 0 || n > R) && atomicCAS(&s->status, 0, PAMD_EPOPSIZE) == 0) s->bad_replica = -1;
+    ctr[2] = (uint32_t)(n < R ? n : R);
+}
+
 __global__ void cnt_block_kernel(const int32_t* cnt, long long R, int32_t* blk_sum,
-                                 int32_t* blk_max) {
+                                 int32_t* blk_max, const uint32_t* live) {
+    R = live_size(live, R);
     __shared__ int32_t shs[8];
     __shared__ int32_t shm[8];
     const long long base = (long long)blockIdx.x * kScanBlock;
@@ -368,12 +482,14 @@ __global__ void cnt_top_kernel(int32_t* blk_sum, const int32_t* blk_max, int nbl
         int32_t m = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = max(m, wmax[w]);
         s->max_copies = m;
+        s->R_new = carry;  // size of the new population (sum of the copy counts)
     }
 }
 
 __global__ void cnt_local_kernel(const int32_t* cnt, long long R, const int32_t* blk_off,
-                                 int32_t* incl) {
+                                 int32_t* incl, const uint32_t* live) {
     __shared__ int32_t shs[8];
+    R = live_size(live, R);
     const long long base = (long long)blockIdx.x * kScanBlock;
     int32_t v[4];
 #pragma unroll
@@ -394,8 +510,16 @@ __global__ void cnt_local_kernel(const int32_t* cnt, long long R, const int32_t*
 
 // Ancestor of every new slot: anc[k] = first j with incl_j > k (copies of j
 // fill slots incl_{j-1} .. incl_j - 1).  One thread per slot.
-__global__ void ancestor_kernel(const int32_t* __restrict__ incl, long long R, int32_t* anc) {
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < R;
+// With a variable population (live != null) the ancestors are the live
+// population and the new slots number min(R_new, R), R the capacity.
+__global__ void ancestor_kernel(const int32_t* __restrict__ incl, long long R, int32_t* anc,
+                                const uint32_t* live, const DevScalars* s) {
+    long long n_new = R;
+    if (live) {
+        n_new = s->R_new < R ? s->R_new : R;
+        R = (long long)*live;
+    }
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n_new;
          k += (long long)gridDim.x * blockDim.x) {
         long long lo = 0, hi = R;
         while (lo < hi) {
@@ -418,8 +542,9 @@ __global__ void __launch_bounds__(256) gather_kernel(
     const float* __restrict__ st_in, float* __restrict__ st_out, const double* E_in,
     double* E_out, const int32_t* fam_in, int32_t* fam_out, double* ke_out, double* rg_out,
     const int32_t* __restrict__ anc, const float* __restrict__ masses, long long R, int N, int Np,
-    float vscale, float inv_mtot) {
+    float vscale, float inv_mtot, const uint32_t* live, const DevScalars* sc) {
     const int lane = threadIdx.x & 31;
+    if (live) R = sc->R_new < R ? sc->R_new : R;  // new slots of a variable population
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const int q4 = Np / 4;          // float4s per component
@@ -504,8 +629,12 @@ __global__ void __launch_bounds__(256) gather_kernel(
 
 // ------------------------------------------------------------------ observables
 
-__global__ void mark_kernel(const int32_t* fam, long long R, unsigned char* flags) {
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < R;
+// Family ids lie in 0 .. R-1 (R the slots of the population buffers); the
+// live replicas are the first live_size(live, R).
+__global__ void mark_kernel(const int32_t* fam, long long R, unsigned char* flags,
+                            const uint32_t* live) {
+    const long long n = live_size(live, R);
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
          k += (long long)gridDim.x * blockDim.x) {
         const int32_t f = fam[k];
         if (f >= 0 && f < R) flags[f] = 1;
@@ -518,7 +647,8 @@ constexpr int kObsStride = kNumBins * kObsVals + 1;
 // Partial sums per family bin over 1024 replicas, in replica order per bin.
 __global__ void obs_partial_kernel(const int32_t* fam, const double* E, const double* ke,
                                    const double* rg, const unsigned char* flags, long long R,
-                                   double* part) {
+                                   double* part, const uint32_t* live) {
+    const long long n = live_size(live, R);  // replicas; family flags span R
     __shared__ int32_t sf[kScanBlock];
     __shared__ double se[kScanBlock], sk[kScanBlock], sr[kScanBlock];
     __shared__ int32_t famcount[kScanThreads / 32];
@@ -526,15 +656,15 @@ __global__ void obs_partial_kernel(const int32_t* fam, const double* E, const do
     int fc = 0;
     for (int t = threadIdx.x; t < kScanBlock; t += blockDim.x) {
         const long long k = base + t;
-        if (k < R) {
+        if (k < n) {
             sf[t] = fam[k] & (kNumBins - 1);
             se[t] = E[k];
             sk[t] = ke[k];
             sr[t] = rg[k];
-            fc += flags[k];
         } else {
             sf[t] = -1;
         }
+        if (k < R) fc += flags[k];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) fc += __shfl_xor_sync(0xffffffffu, fc, o);
@@ -583,7 +713,8 @@ __device__ double jackknife_se(const double* cnt, const double* sum, double tot,
 }
 
 __global__ void obs_final_kernel(const double* part, int nblk, long long R, int N, double T,
-                                 const DevScalars* s, pamd_obs* dst) {
+                                 const DevScalars* s, pamd_obs* dst, const uint32_t* live) {
+    R = live_size(live, R);
     __shared__ double bins[kObsVals][kNumBins];
     __shared__ double nfam;
     if (threadIdx.x < kNumBins) {
@@ -623,6 +754,7 @@ __global__ void obs_final_kernel(const double* part, int nblk, long long R, int 
         o.n_families = (int64_t)nfam;
         o.max_copies = s->max_copies;
         o.pad_ = s->status;
+        o.R_live = R;
         *dst = o;
     }
 }
@@ -650,6 +782,10 @@ cudaError_t launch_init(pamd_ctx* c, double T0) {
         (float)(kBoltzmann * T0), c->seed, kPurposeInit | ((uint32_t)c->mol << 8));
     reset_scalars_kernel<<<1, 1, 0, c->stream>>>(c->b.scal);
     c->launches += 2;
+    if (c->variable) {  // the population starts at its target size
+        set_live_kernel<<<1, 1, 0, c->stream>>>(c->b.counters, (uint32_t)c->R_target);
+        c->launches += 1;
+    }
     return cudaGetLastError();
 }
 
@@ -671,7 +807,10 @@ static ExpCoef exp_coefficients() {
 
 cudaError_t launch_resample(pamd_ctx* c, double T_prev, double T_next, int do_resample,
                             const uint32_t* dev_counters, uint32_t resample_offset) {
+    // R: slots of the population buffers (the capacity of a variable
+    // population, whose live size the kernels read from counter word 2)
     const long long R = c->R;
+    const uint32_t* live = c->variable ? c->b.counters + 2 : nullptr;
     const int nblk = c->n_blk;
     cudaStream_t s = c->stream;
     const double dbeta = 1.0 / (kBoltzmann * T_next) - 1.0 / (kBoltzmann * T_prev);
@@ -682,21 +821,28 @@ cudaError_t launch_resample(pamd_ctx* c, double T_prev, double T_next, int do_re
 
     // energies of the current population (the ping-pong buffers alternate)
     const double* Ecur = c->cur_is_alt ? c->b.E_alt : c->b.E;
-    amax_kernel<<<nblk, kScanThreads, 0, s>>>(Ecur, R, dbeta, c->b.blk_f64);
+    amax_kernel<<<nblk, kScanThreads, 0, s>>>(Ecur, R, dbeta, c->b.blk_f64, live);
     max_top_kernel<<<1, 1024, 0, s>>>(c->b.blk_f64, nblk, c->b.scal);
     weights_kernel<<<nblk, kScanThreads, 0, s>>>(Ecur, R, dbeta, two_s, c->b.scal, cf, c->b.W,
-                                                 c->b.blk_u64, c->b.blk_f64);
-    weights_top_kernel<<<1, kScanThreads, 0, s>>>(c->b.blk_u64, c->b.blk_f64, nblk, R, c->b.scal);
-    scan_local_u64_kernel<<<nblk, kScanThreads, 0, s>>>(c->b.W, R, c->b.blk_u64, c->b.C);
+                                                 c->b.blk_u64, c->b.blk_f64, live);
+    weights_top_kernel<<<1, kScanThreads, 0, s>>>(c->b.blk_u64, c->b.blk_f64, nblk, R, c->b.scal, live);
+    scan_local_u64_kernel<<<nblk, kScanThreads, 0, s>>>(c->b.W, R, c->b.blk_u64, c->b.C, live);
     cudaError_t e = cudaMemsetAsync(c->b.cnt, 0, sizeof(int32_t) * (size_t)R, s);
     if (e != cudaSuccess) return e;
-    const int rule = !do_resample ? 0 : (c->resample_rule == PAMD_RESAMPLE_SYSTEMATIC ? 2 : 1);
-    counts_kernel<<<grid_for(R, 256, c->num_sms * 16), 256, 0, s>>>(
-        c->b.C, R, c->b.scal, c->seed, dev_counters, resample_offset,
-        kPurposeResample | ((uint32_t)c->mol << 8), rule, c->b.cnt);
-    cnt_block_kernel<<<nblk, kScanThreads, 0, s>>>(c->b.cnt, R, c->b.blk_i32, c->b.blk_i32 + nblk);
+    if (c->variable && do_resample) {
+        varsize_counts_kernel<<<grid_for(R, 256, c->num_sms * 16), 256, 0, s>>>(
+            c->b.W, R, c->b.scal, c->R_target, c->seed, dev_counters, resample_offset,
+            kPurposeResample | ((uint32_t)c->mol << 8),
+            c->resample_rule == PAMD_RESAMPLE_NEAREST ? 3 : 4, cf, c->b.cnt, live);
+    } else {
+        const int rule = !do_resample ? 0 : (c->resample_rule == PAMD_RESAMPLE_SYSTEMATIC ? 2 : 1);
+        counts_kernel<<<grid_for(R, 256, c->num_sms * 16), 256, 0, s>>>(
+            c->b.C, R, c->b.scal, c->seed, dev_counters, resample_offset,
+            kPurposeResample | ((uint32_t)c->mol << 8), rule, c->b.cnt, live);
+    }
+    cnt_block_kernel<<<nblk, kScanThreads, 0, s>>>(c->b.cnt, R, c->b.blk_i32, c->b.blk_i32 + nblk, live);
     cnt_top_kernel<<<1, kScanThreads, 0, s>>>(c->b.blk_i32, c->b.blk_i32 + nblk, nblk, c->b.scal);
-    cnt_local_kernel<<<nblk, kScanThreads, 0, s>>>(c->b.cnt, R, c->b.blk_i32, c->b.cnt_incl);
+    cnt_local_kernel<<<nblk, kScanThreads, 0, s>>>(c->b.cnt, R, c->b.blk_i32, c->b.cnt_incl, live);
     double mt = 0.0;
     for (double m : c->host_mass) mt += m;
     const float* src = c->cur_is_alt ? c->b.state_alt : c->b.state;
@@ -714,14 +860,16 @@ cudaError_t launch_resample(pamd_ctx* c, double T_prev, double T_next, int do_re
     }
     // ancestors of the new slots (into the weight buffer, no longer needed)
     int32_t* anc = reinterpret_cast<int32_t*>(c->b.W);
-    ancestor_kernel<<<grid_for(R, 256, c->num_sms * 16), 256, 0, s>>>(c->b.cnt_incl, R, anc);
+    ancestor_kernel<<<grid_for(R, 256, c->num_sms * 16), 256, 0, s>>>(c->b.cnt_incl, R, anc, live,
+                                                                       c->b.scal);
     const int gridg = grid_for(R * 32, 256, c->num_sms * 64);
     const float vs = (float)sqrt(T_next / T_prev), imt = (float)(1.0 / mt);
     switch ((6 * (c->Np / 4) + 31) / 32) {
 #define PAMD_GATHER_CASE(P)                                                                     \
     case P:                                                                                     \
         gather_kernel<P><<<gridg, 256, 0, s>>>(src, dst, Ein, Eout, fin, fout, c->b.ke, c->b.rg, \
-                                               anc, c->b.masses, R, c->N, c->Np, vs, imt);      \
+                                               anc, c->b.masses, R, c->N, c->Np, vs, imt, live, \
+                                               c->b.scal);                                      \
         break;
         PAMD_GATHER_CASE(1) PAMD_GATHER_CASE(2) PAMD_GATHER_CASE(3) PAMD_GATHER_CASE(4)
         PAMD_GATHER_CASE(5) PAMD_GATHER_CASE(6) PAMD_GATHER_CASE(7) PAMD_GATHER_CASE(8)
@@ -730,6 +878,10 @@ cudaError_t launch_resample(pamd_ctx* c, double T_prev, double T_next, int do_re
         default: return cudaErrorInvalidValue;
     }
     c->launches += 11;
+    if (c->variable) {
+        commit_size_kernel<<<1, 1, 0, s>>>(c->b.scal, c->b.counters, R);
+        c->launches += 1;
+    }
     return cudaGetLastError();
 }
 
@@ -740,10 +892,11 @@ cudaError_t launch_observe(pamd_ctx* c, double T, pamd_obs* dst) {
     const double* E = c->cur_is_alt ? c->b.E_alt : c->b.E;
     cudaError_t e = cudaMemsetAsync(c->b.flags, 0, (size_t)R, s);
     if (e != cudaSuccess) return e;
-    mark_kernel<<<grid_for(R, 256, c->num_sms * 16), 256, 0, s>>>(fam, R, c->b.flags);
+    const uint32_t* live = c->variable ? c->b.counters + 2 : nullptr;
+    mark_kernel<<<grid_for(R, 256, c->num_sms * 16), 256, 0, s>>>(fam, R, c->b.flags, live);
     obs_partial_kernel<<<c->n_blk, kScanThreads, 0, s>>>(fam, E, c->b.ke, c->b.rg, c->b.flags, R,
-                                                        c->b.obs_part);
-    obs_final_kernel<<<1, 128, 0, s>>>(c->b.obs_part, c->n_blk, R, c->N, T, c->b.scal, dst);
+                                                        c->b.obs_part, live);
+    obs_final_kernel<<<1, 128, 0, s>>>(c->b.obs_part, c->n_blk, R, c->N, T, c->b.scal, dst, live);
     c->launches += 3;
     return cudaGetLastError();
 }

@@ -21,6 +21,8 @@ PAMD_EINVAL, PAMD_ENOMEM, PAMD_ECUDA, PAMD_ETIMEOUT = -1, -2, -3, -4
 PAMD_ENONFINITE, PAMD_ESTATE, PAMD_EUNSUPPORTED = -5, -6, -7
 PAMD_PREC_MIXED, PAMD_PREC_FP64 = 0, 1
 PAMD_RESAMPLE_MULTINOMIAL, PAMD_RESAMPLE_SYSTEMATIC = 0, 1
+PAMD_RESAMPLE_NEAREST, PAMD_RESAMPLE_POISSON = 2, 3
+PAMD_EPOPSIZE = -8
 PAMD_PAIRS_AUTO, PAMD_PAIRS_SCALAR, PAMD_PAIRS_PACKED = 0, 1, 2
 PAMD_MAX_ATOMS = 256
 
@@ -84,6 +86,7 @@ class PamdObs(C.Structure):
         ("e_kin_se", C.c_double), ("t_meas", C.c_double),
         ("rg", C.c_double), ("rg_se", C.c_double), ("rg2", C.c_double), ("rg2_se", C.c_double),
         ("n_families", C.c_int64), ("max_copies", C.c_int32), ("pad_", C.c_int32),
+        ("R_live", C.c_int64),
     ]
 
     def as_dict(self):
@@ -94,7 +97,7 @@ EXPORTS = [
     "pamd_options_default", "pamd_init", "pamd_init_batch", "pamd_batch_size", "pamd_batch_sub",
     "pamd_reset", "pamd_propagate", "pamd_resample", "pamd_observables",
     "pamd_anneal", "pamd_get_state", "pamd_set_state", "pamd_forces", "pamd_get_counters",
-    "pamd_set_counters", "pamd_autotune", "pamd_get_shape", "pamd_fp32_peak", "pamd_fp32_peak_threads", "pamd_resample_counts_noalloc", "pamd_info", "pamd_launch_count", "pamd_sync", "pamd_destroy",
+    "pamd_set_counters", "pamd_autotune", "pamd_get_shape", "pamd_population_size", "pamd_fp32_peak", "pamd_fp32_peak_threads", "pamd_resample_counts_noalloc", "pamd_info", "pamd_launch_count", "pamd_sync", "pamd_destroy",
     "pamd_last_error",
     # learned surrogate (include/pamd_mlp.h), wrapped in surrogate.py
     "pamd_gemm_bf16", "pamd_gemm_bf16_time", "pamd_mlp_create", "pamd_mlp_info", "pamd_mlp_set_params",
@@ -157,6 +160,7 @@ def load(path: str | None = None):
             "pamd_set_counters": (C.c_int, [P, U32, U32, D]),
             "pamd_autotune": (C.c_int, [P, I32, C.POINTER(PamdTune)]),
             "pamd_get_shape": (C.c_int, [P, C.POINTER(PamdTune)]),
+            "pamd_population_size": (C.c_int, [P, C.POINTER(I64), C.POINTER(I64)]),
             "pamd_fp32_peak": (C.c_int, [I32, I32, I32, P, P, C.POINTER(D), C.POINTER(D)]),
             "pamd_fp32_peak_threads": (I32, []),
             "pamd_resample_counts_noalloc": (C.c_int, [P, I64, D, D, U64, U32, I32, P, P, P, P]),
@@ -418,6 +422,13 @@ def pamd_fp32_peak(packed: bool, iters: int = 20000, reps: int = 100, stream: in
     _check(load().pamd_fp32_peak(1 if packed else 0, int(iters), int(reps), C.c_void_p(stream or None),
                                  C.c_void_p(out.data_ptr()), C.byref(tf), C.byref(ms)))
     return {"tflops": tf.value, "ms": ms.value}
+
+
+def pamd_population_size(ctx) -> tuple:
+    """(live population size, capacity)."""
+    live, cap = C.c_int64(), C.c_int64()
+    _check(load().pamd_population_size(ctx, C.byref(live), C.byref(cap)))
+    return live.value, cap.value
 
 
 def pamd_get_shape(ctx) -> dict:

@@ -211,4 +211,11 @@ def test_adaptive_and_rule_arguments_rejected_before_touching_the_gpu(lib):
         pamd.pamd_next_temperature(None, 300.0, 200.0, 0.5)
     with pytest.raises(pamd.PamdError):
         pamd.pamd_anneal_adaptive(None, 300.0, 200.0, 0.5, 10, 0.001, 5)
-    assert _init_rc(pi.make_chain(5, 1), resample_rule=2)[0] == pamd.PAMD_EINVAL
+    assert _init_rc(pi.make_chain(5, 1), resample_rule=4)[0] == pamd.PAMD_EINVAL
+    assert _init_rc(pi.make_chain(5, 1), resample_rule=-1)[0] == pamd.PAMD_EINVAL
+    # the variable-size rules: mixed precision and one replica per lane group only
+    for rule in (pamd.PAMD_RESAMPLE_NEAREST, pamd.PAMD_RESAMPLE_POISSON):
+        assert _init_rc(pi.make_chain(5, 1), resample_rule=rule, precision=1)[0] == pamd.PAMD_EUNSUPPORTED
+        assert _init_rc(pi.make_chain(5, 1), resample_rule=rule, replicas_per_lane=2)[0] == \
+            pamd.PAMD_EUNSUPPORTED
+        assert _init_rc(pi.make_chain(5, 1), R=0x7fff0000, resample_rule=rule)[0] == pamd.PAMD_EINVAL
