@@ -250,24 +250,29 @@ int build_topology(const pamd_topology* t, int lanes_req, TopoLayout* lay_out,
     }
     // tile masks
     const int TH = L / 2;
-    std::vector<unsigned long long> masks((size_t)(TH + 1) * L, 0ull);
-    auto mask_pair = [&](int i, int j) {
+    // masks: every pair left out of the plain nonbonded sum (excluded or
+    // scaled 1-4); m14: the scaled 1-4 pairs among them
+    std::vector<unsigned long long> masks((size_t)(TH + 1) * L, 0ull), m14((size_t)(TH + 1) * L, 0ull);
+    auto mask_pair = [&](int i, int j, std::vector<unsigned long long>& mk) {
         const int gi = i / B, gj = j / B, ai = i % B, aj = j % B;
         if (gi == gj) {
             const int a = std::min(ai, aj), b = std::max(ai, aj);
-            masks[gi] |= 1ull << (a * B + b);
+            mk[gi] |= 1ull << (a * B + b);
             return;
         }
         const int tt = ((gj - gi) % L + L) % L;
         if (2 * tt < L || (2 * tt == L && gi < tt)) {
-            masks[(size_t)tt * L + gi] |= 1ull << (ai * B + aj);
+            mk[(size_t)tt * L + gi] |= 1ull << (ai * B + aj);
         } else {
             const int t2 = L - tt;
-            masks[(size_t)t2 * L + gj] |= 1ull << (aj * B + ai);
+            mk[(size_t)t2 * L + gj] |= 1ull << (aj * B + ai);
         }
     };
-    for (int p = 0; p < t->n_excl; ++p) mask_pair(t->excl[2 * p], t->excl[2 * p + 1]);
-    for (auto& q : p14) mask_pair(q.first, q.second);
+    for (int p = 0; p < t->n_excl; ++p) mask_pair(t->excl[2 * p], t->excl[2 * p + 1], masks);
+    for (auto& q : p14) {
+        mask_pair(q.first, q.second, masks);
+        mask_pair(q.first, q.second, m14);
+    }
 
     // bonded records, coloured
     std::vector<BondRec> bonds;
@@ -329,6 +334,7 @@ int build_topology(const pamd_topology* t, int lanes_req, TopoLayout* lay_out,
     int off = 0;
     lay.off_params = off; off += round_up(lay.nk * 16, 16);
     lay.off_masks = off; off += round_up((int)masks.size() * 8, 16);
+    lay.off_m14 = off; off += round_up((int)m14.size() * 8, 16);
     lay.off_bonds = off; off += round_up(lay.n_bonds * 16, 16);
     lay.off_angles = off; off += round_up(lay.n_angles * 32, 16);
     lay.off_dihs = off; off += round_up(lay.n_dihs * 32, 16);
@@ -360,6 +366,7 @@ int build_topology(const pamd_topology* t, int lanes_req, TopoLayout* lay_out,
         q[3] = (float)(1.0 / t->mass[i]);
     }
     std::memcpy(blob.data() + lay.off_masks, masks.data(), masks.size() * 8);
+    std::memcpy(blob.data() + lay.off_m14, m14.data(), m14.size() * 8);
     if (lay.ptab) {
         // the FP32 products the kernel's mixing would form, so both paths agree bitwise
         float* tb = reinterpret_cast<float*>(blob.data() + lay.off_ptab);

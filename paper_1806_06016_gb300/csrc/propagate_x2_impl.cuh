@@ -23,8 +23,12 @@
 //   to the owner lane with warp shuffles (lane g receives from lane g - t the
 //   forces on its own block), so shared memory holds positions only and the
 //   pair loop has no shared-memory stores.
-// * Chain bonded terms are those of propagate_impl.cuh; forces on the next
-//   block's first three atoms are also handed over by shuffles.
+// * Chain bonded terms share their geometry (bond vectors, normals, dot
+//   products) between consecutive terms; forces on the next block's first
+//   three atoms are also handed over by shuffles.  The scaled 1-4 pairs,
+//   which in a chain always fall in the own block or the t = 1 tile, are
+//   evaluated there with their scale factors instead of being masked out and
+//   recomputed with the bonded terms.
 //
 // Linear-chain layouts only (B >= 3); other topologies use propagate_impl.cuh.
 #pragma once
@@ -58,6 +62,30 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a
 // padding atoms (and the missing next block of the last lane) sit.
 __device__ __forceinline__ float3 far_point(int i) {
     return make_float3(1000.0f + 4.0f * (float)i, 2.0f * (float)(i & 1), 2.0f * (float)((i >> 1) & 1));
+}
+
+// atan2(y, x) for y >= 0 (a bond angle from |u x w| and u . w), without
+// branches: t = min(|x|, y) / max(|x|, y) in [0, 1], atan(t) = t P(t^2) with
+// P a degree-7 polynomial fitted to atan(t)/t on [0, 1] (least squares with
+// Lawson reweighting toward the minimax fit; largest error 1.3e-7 rad when
+// evaluated in FP32), then pi/2 - atan(t) when y > |x| and pi - (...) when
+// x < 0.
+__device__ __forceinline__ float atan2_nonneg(float y, float x) {
+    const float ax = fabsf(x);
+    const float mn = fminf(ax, y), mx = fmaxf(ax, y);
+    const float t = mn / mx;
+    const float t2 = t * t;
+    float p = -0.00405456218868494f;
+    p = fmaf(p, t2, 0.021862944588065147f);
+    p = fmaf(p, t2, -0.0559123195707798f);
+    p = fmaf(p, t2, 0.096421979367733f);
+    p = fmaf(p, t2, -0.1390863060951233f);
+    p = fmaf(p, t2, 0.19946566224098206f);
+    p = fmaf(p, t2, -0.33329859375953674f);
+    p = fmaf(p, t2, 0.9999993443489075f);
+    float a = p * t;
+    a = (y > ax) ? 1.57079632679489662f - a : a;
+    return (x < 0.0f) ? 3.14159265358979324f - a : a;
 }
 
 // Own atoms of a lane: packed pairs plus the scalar tail.
@@ -116,17 +144,28 @@ struct Own {
     }
 };
 
+// Factors of a pair left out of the plain nonbonded sum: (0, 0) when it is
+// excluded, (LJ scale, Coulomb scale) when it is a scaled 1-4 pair, else
+// (1, 1).  Applied to eps, 2 eps and qq, which the pair force is linear in.
+__device__ __forceinline__ float2 pair_factors(unsigned long long mask, unsigned long long m14,
+                                               int bit, float s_lj, float s_c) {
+    const bool out = (mask >> bit) & 1ull;
+    const bool is14 = (m14 >> bit) & 1ull;
+    return make_float2(out ? (is14 ? s_lj : 0.0f) : 1.0f, out ? (is14 ? s_c : 0.0f) : 1.0f);
+}
+
 // One partner atom (duplicated operands, negated coordinates) against the
 // lane's own atoms.  d = x_own - x_partner; the force on an own atom is +fs d,
 // on the partner -fs d; the partner's share is summed into (gx, gy, gz) as
 // +fs d (the caller subtracts it).  nse holds -sqrt(24 eps) of the own atoms:
-// neps = -eps_ij and e2 = -2 neps = 2 eps_ij.  Masked own/partner pairs (bit
-// a*B + b) contribute zero.
+// neps = -eps_ij and e2 = -2 neps = 2 eps_ij.  In a masked tile the own/partner
+// pair of bit a*B + b takes the factors of pair_factors.
 template <int B, bool MASKED>
 __device__ __forceinline__ void partner_x2(const Own<B>& r, const Own<B>& hs, const Own<B>& nse,
                                            const Own<B>& qq, Own<B>& f, float4 pa, float4 pb,
-                                           float4 pp, int b, unsigned long long mask, float& gx,
-                                           float& gy, float& gz) {
+                                           float4 pp, int b, unsigned long long mask,
+                                           unsigned long long m14, float s_lj, float s_c,
+                                           float& gx, float& gy, float& gz) {
     using C = X2Cfg<B>;
     const float2 nxj = f2(pa.x, pa.y), nyj = f2(pa.z, pa.w), nzj = f2(pb.x, pb.y);
     const float2 qj = f2(pb.z, pb.w), hj = f2(pp.x, pp.y), ej = f2(pp.z, pp.w);
@@ -143,15 +182,17 @@ __device__ __forceinline__ void partner_x2(const Own<B>& r, const Own<B>& hs, co
         const float2 sg = add2(hs.x[p], hj);
         const float2 s2 = mul2(mul2(sg, sg), rinv2);
         const float2 s6 = mul2(mul2(s2, s2), s2);
-        const float2 neps = mul2(nse.x[p], ej);
+        float2 neps = mul2(nse.x[p], ej);
+        float2 q2 = mul2(qq.x[p], qj);
+        if (MASKED) {
+            const float2 k0 = pair_factors(mask, m14, (2 * p) * B + b, s_lj, s_c);
+            const float2 k1 = pair_factors(mask, m14, (2 * p + 1) * B + b, s_lj, s_c);
+            neps = mul2(neps, f2(k0.x, k1.x));
+            q2 = mul2(q2, f2(k0.y, k1.y));
+        }
         const float2 e2 = mul2(neps, m2);
         const float2 lj = mul2(s6, fma2(e2, s6, neps));
-        const float2 q2 = mul2(qq.x[p], qj);
-        float2 fs = mul2(fma2(q2, rinv, lj), rinv2);
-        if (MASKED) {
-            if ((mask >> ((2 * p) * B + b)) & 1ull) fs.x = 0.f;
-            if ((mask >> ((2 * p + 1) * B + b)) & 1ull) fs.y = 0.f;
-        }
+        const float2 fs = mul2(fma2(q2, rinv, lj), rinv2);
         f.x[p] = fma2(fs, dx, f.x[p]);
         f.y[p] = fma2(fs, dy, f.y[p]);
         f.z[p] = fma2(fs, dz, f.z[p]);
@@ -171,10 +212,15 @@ __device__ __forceinline__ void partner_x2(const Own<B>& r, const Own<B>& hs, co
     if (C::TAIL) {
         const float dx = r.xt + pa.x, dy = r.yt + pa.z, dz = r.zt + pb.x;
         const float sg = hs.xt + pp.x;
-        const float neps = nse.xt * pp.z;
+        float neps = nse.xt * pp.z;
+        float qt = qq.xt * pb.z;
+        if (MASKED) {
+            const float2 k = pair_factors(mask, m14, (B - 1) * B + b, s_lj, s_c);
+            neps *= k.x;
+            qt *= k.y;
+        }
         float fs, e;
-        pair_lj_coul<false>(dx, dy, dz, sg * sg, -neps, -2.0f * neps, qq.xt * pb.z, fs, e);
-        if (MASKED && ((mask >> ((B - 1) * B + b)) & 1ull)) fs = 0.f;
+        pair_lj_coul<false>(dx, dy, dz, sg * sg, -neps, -2.0f * neps, qt, fs, e);
         // pair_lj_coul's fs multiplies d = x_j - x_i; here d = x_i - x_j
         f.xt = fmaf(fs, dx, f.xt);
         f.yt = fmaf(fs, dy, f.yt);
@@ -185,14 +231,13 @@ __device__ __forceinline__ void partner_x2(const Own<B>& r, const Own<B>& hs, co
     }
 }
 
-// Chain bonded pass (terms starting in the lane's block): forces on the own
-// atoms go to f, those on the next block's first three atoms to sf.  Every
-// lane evaluates B terms of each kind without branches: the term parameters
-// past the chain's end are zero (the topology table has one entry per atom
-// slot), padding atoms and the missing next block of the last lane sit at
-// distinct, non-collinear points far away (so a term with zero parameters
-// gives exactly zero, never 0 * inf), and the scaled 1-4 pair, whose
-// parameters are per atom, is multiplied by its existence.
+// Chain bonded pass (bonds, angles and dihedrals starting in the lane's
+// block): forces on the own atoms go to f, those on the next block's first
+// three atoms to sf.  Every lane evaluates B terms of each kind without
+// branches: the term parameters past the chain's end are zero (the topology
+// table has one entry per atom slot), and padding atoms and the missing next
+// block of the last lane sit at distinct, non-collinear points far away (so a
+// term with zero parameters gives exactly zero, never 0 * inf).
 template <int B>
 __device__ __forceinline__ void bonded_chain_x2(const unsigned char* sm, const TopoLayout& lay,
                                                 const float4* prm, const float4* posA,
@@ -200,7 +245,6 @@ __device__ __forceinline__ void bonded_chain_x2(const unsigned char* sm, const T
                                                 Own<B>& f, float3 (&sf)[3]) {
     using C = X2Cfg<B>;
     const int i0 = g * B;
-    const int N = lay.n_atoms;
     const bool has_next = (g + 1 < L);
     const int nbase = (g + 1) * C::BS;
     float3 sp[3];
@@ -232,41 +276,78 @@ __device__ __forceinline__ void bonded_chain_x2(const unsigned char* sm, const T
     const float2* cb = reinterpret_cast<const float2*>(sm + lay.off_cbond);
     const float2* ca = reinterpret_cast<const float2*>(sm + lay.off_cangle);
     const float4* cd = reinterpret_cast<const float4*>(sm + lay.off_cdih);
-    double e_unused = 0.0;
+    // Geometry shared by consecutive terms: bond vectors b_k = P(k+1) - P(k)
+    // with |b_k|^2 and 1/|b_k|, normals c_k = b_k x b_{k+1} with |c_k|^2 and
+    // 1/|c_k|, and d_k = b_k . b_{k+1}.  Bond a uses b_a; the angle at a+1
+    // uses b_a, b_{a+1}, c_a, d_a; the dihedral (a..a+3) uses A = c_a,
+    // B = c_{a+1}, G = -b_{a+1} and d_a, d_{a+1} (the torsion's F.G and H.G).
+    float3 bv[B + 2];
+    float bb[B + 2], rb[B + 2];
+#pragma unroll
+    for (int k = 0; k < B + 2; ++k) {
+        bv[k] = f3sub(P(k + 1), P(k));
+        bb[k] = dot3(bv[k], bv[k]);
+        rb[k] = rsqrtf(bb[k]);
+    }
+    float3 cv[B + 1];
+    float cc[B + 1], rc[B + 1], dd[B + 1];
+#pragma unroll
+    for (int k = 0; k < B + 1; ++k) {
+        cv[k] = cross3(bv[k], bv[k + 1]);
+        cc[k] = dot3(cv[k], cv[k]);
+        rc[k] = rsqrtf(cc[k]);
+        dd[k] = dot3(bv[k], bv[k + 1]);
+    }
 #pragma unroll
     for (int a = 0; a < B; ++a) {
         const int d = i0 + a;
-        {  // bond (d, d+1)
+        {  // bond (d, d+1): 1/2 k (r - r0)^2, force on d is +g b_a
             const float2 q = cb[d];
-            const float3 fb = bond_force<false>(P(a), P(a + 1), q.x, q.y, e_unused);
+            const float r = bb[a] * rb[a];
+            const float gk = (q.x == 0.0f) ? q.y : q.y * (r - q.x) * rb[a];
+            const float3 fb = f3scale(gk, bv[a]);
             F(a, fb);
             F(a + 1, make_float3(-fb.x, -fb.y, -fb.z));
         }
-        {  // angle (d, d+1, d+2)
+        {  // angle (d, d+1, d+2) at d+1: u = -b_a, w = b_{a+1}, |u x w| = |c_a|, u.w = -d_a
             const float2 q = ca[d];
-            float3 fi, fj, fk;
-            angle_force<false>(P(a), P(a + 1), P(a + 2), q.x, q.y, fi, fj, fk, e_unused);
+            const float cw = -dd[a];
+            const float dth = atan2_nonneg(cc[a] * rc[a], cw) - q.x;
+            const float is = q.y * dth * rc[a];
+            const float cu = cw * (rb[a] * rb[a]), cvv = cw * (rb[a + 1] * rb[a + 1]);
+            // F_i = is (w - cu u), F_k = is (u - cv w), F_j = -F_i - F_k
+            const float3 fi = f3scale(is, f3axpby(1.0f, bv[a + 1], cu, bv[a]));
+            const float3 fk = f3scale(-is, f3axpby(1.0f, bv[a], cvv, bv[a + 1]));
             F(a, fi);
-            F(a + 1, fj);
+            F(a + 1, make_float3(-fi.x - fk.x, -fi.y - fk.y, -fi.z - fk.z));
             F(a + 2, fk);
         }
-        {  // dihedral (d..d+3) and 1-4 pair (d, d+3)
-            float3 fi, fj, fk, fl;
-            dihedral_force<false>(P(a), P(a + 1), P(a + 2), P(a + 3), cd[d], fi, fj, fk, fl,
-                                  e_unused);
-            F(a, fi);
-            F(a + 1, fj);
-            F(a + 2, fk);
-            F(a + 3, fl);
-            const int s0 = g * C::BS + a;
-            int s3 = (a + 3 < B) ? (s0 + 3) : (nbase + a + 3 - B);
-            s3 = (s3 < lay.nk) ? s3 : s0;  // the last lane: any slot, the term is then zeroed
-            const float exists = (d + 3 < N) ? 1.0f : 0.0f;
-            float3 fp = pair14_force<false>(P(a), P(a + 3), prm[s0], prm[s3], lay.s14_lj,
-                                            lay.s14_c, e_unused);
-            fp = f3scale(exists, fp);
-            F(a, fp);
-            F(a + 3, make_float3(-fp.x, -fp.y, -fp.z));
+        {  // dihedral (d..d+3), gradient of phi after Blondel & Karplus (1996)
+            const float4 prm_d = cd[d];
+            const float kd = prm_d.x, nn = prm_d.y, cph = prm_d.z, sph = prm_d.w;
+            const float3 A = cv[a], Bn = cv[a + 1];
+            const float rlg = rb[a + 1], lg = bb[a + 1] * rlg;
+            const float rA2 = rc[a] * rc[a], rB2 = rc[a + 1] * rc[a + 1];
+            const float rab = rc[a] * rc[a + 1];
+            const float cphi = dot3(A, Bn) * rab;
+            // sin phi = -(F . B) |G| / (|A||B|) with F = -b_a
+            const float sphi = dot3(bv[a], Bn) * lg * rab;
+            const int n = (int)nn;
+            const float c2 = fmaf(cphi + cphi, cphi, -1.0f), s2 = (sphi + sphi) * cphi;
+            const float c3 = fmaf(c2, cphi, -s2 * sphi), s3 = fmaf(s2, cphi, c2 * sphi);
+            const int m = (n > 3) ? n - 3 : n;
+            const float cA = (m == 1) ? cphi : ((m == 2) ? c2 : c3);
+            const float sA = (m == 1) ? sphi : ((m == 2) ? s2 : s3);
+            const float cn = (n > 3) ? fmaf(c3, cA, -s3 * sA) : cA;
+            const float sn = (n > 3) ? fmaf(s3, cA, c3 * sA) : sA;
+            const float dEdphi = -kd * nn * (sn * cph - cn * sph);
+            const float ia = lg * rA2, ib = lg * rB2;
+            // F.G = d_a, H.G = -d_{a+1} (F = -b_a, G = -b_{a+1}, H = b_{a+2})
+            const float pa = dd[a] * rA2 * rlg, pb = -dd[a + 1] * rB2 * rlg;
+            F(a, f3scale(dEdphi * ia, A));
+            F(a + 1, f3axpby(-dEdphi * (ia + pa), A, dEdphi * pb, Bn));
+            F(a + 2, f3axpby(dEdphi * pa, A, -dEdphi * (pb - ib), Bn));
+            F(a + 3, f3scale(-dEdphi * ib, Bn));
         }
     }
 }
@@ -293,20 +374,25 @@ __device__ __forceinline__ void forces_x2(const unsigned char* sm, const TopoLay
                                           unsigned gmask, const Own<B>& r, const Own<B>& hs,
                                           const Own<B>& nse, const Own<B>& qq, Own<B>& f) {
     using C = X2Cfg<B>;
+    // 1-4 pairs of a chain lie in the own block or the t = 1 tile: they are
+    // evaluated there with their scale factors, not in the bonded pass
+    const unsigned long long* m14s = reinterpret_cast<const unsigned long long*>(sm + lay.off_m14);
+    const float s_lj = lay.s14_lj, s_c = lay.s14_c;
     f.zero();
-    // pairs inside the lane's own block (masked: the 1-2/1-3/1-4 pairs live here)
+    // pairs inside the lane's own block (the 1-2/1-3/1-4 pairs live here)
     {
-        const unsigned long long m = masks[g];
+        const unsigned long long m = masks[g], m4 = m14s[g];
 #pragma unroll
         for (int a = 0; a < B; ++a) {
 #pragma unroll
             for (int b = a + 1; b < B; ++b) {
                 const float dx = r.gx(b) - r.gx(a), dy = r.gy(b) - r.gy(a), dz = r.gz(b) - r.gz(a);
                 const float sg = hs.gx(a) + hs.gx(b);
-                const float eps = nse.gx(a) * nse.gx(b);
+                const float2 k = pair_factors(m, m4, a * B + b, s_lj, s_c);
+                const float eps = nse.gx(a) * nse.gx(b) * k.x;
                 float fs, e;
-                pair_lj_coul<false>(dx, dy, dz, sg * sg, eps, eps + eps, qq.gx(a) * qq.gx(b), fs, e);
-                if ((m >> (a * B + b)) & 1ull) fs = 0.f;
+                pair_lj_coul<false>(dx, dy, dz, sg * sg, eps, eps + eps, qq.gx(a) * qq.gx(b) * k.y, fs,
+                                    e);
                 f.add(a, -fs * dx, -fs * dy, -fs * dz);
                 f.add(b, fs * dx, fs * dy, fs * dz);
             }
@@ -324,20 +410,22 @@ __device__ __forceinline__ void forces_x2(const unsigned char* sm, const TopoLay
         const int sJ = J * C::BS;
         int src = g - t;
         src = (src < 0) ? src + L : src;
-        const unsigned long long m = masks[t * L + g];
+        const unsigned long long m = masks[t * L + g], m4 = m14s[t * L + g];
         // the partner sums of the whole tile are handed over after it, so
-        // that the partners' arithmetic can interleave
+        // that the partners' arithmetic can interleave; one branch for the
+        // whole group (a lane whose tile has no masked pair runs the masked
+        // code with an empty mask)
         float gx[B], gy[B], gz[B];
-        if (m == 0ull) {
+        if (!__any_sync(gmask, m != 0ull)) {
 #pragma unroll
             for (int b = 0; b < B; ++b)
                 partner_x2<B, false>(r, hs, nse, qq, f, posA[sJ + b], posB[sJ + b], dprm[sJ + b], b,
-                                     m, gx[b], gy[b], gz[b]);
+                                     m, m4, s_lj, s_c, gx[b], gy[b], gz[b]);
         } else {
 #pragma unroll
             for (int b = 0; b < B; ++b)
                 partner_x2<B, true>(r, hs, nse, qq, f, posA[sJ + b], posB[sJ + b], dprm[sJ + b], b,
-                                    m, gx[b], gy[b], gz[b]);
+                                    m, m4, s_lj, s_c, gx[b], gy[b], gz[b]);
         }
 #pragma unroll
         for (int b = 0; b < B; ++b) hand_over<B>(f, b, gx[b], gy[b], gz[b], gmask, base + src);
@@ -350,11 +438,11 @@ __device__ __forceinline__ void forces_x2(const unsigned char* sm, const TopoLay
 #pragma unroll
         for (int b = 0; b < B; ++b) gx[b] = gy[b] = gz[b] = 0.f;
         if (g < t) {
-            const unsigned long long m = masks[t * L + g];
+            const unsigned long long m = masks[t * L + g], m4 = m14s[t * L + g];
 #pragma unroll
             for (int b = 0; b < B; ++b)
                 partner_x2<B, true>(r, hs, nse, qq, f, posA[sJ + b], posB[sJ + b], dprm[sJ + b], b,
-                                    m, gx[b], gy[b], gz[b]);
+                                    m, m4, s_lj, s_c, gx[b], gy[b], gz[b]);
         }
         const int src = (g - t + L) % L;
 #pragma unroll
