@@ -1439,34 +1439,17 @@ int pamd_anneal(pamd_ctx* c, int32_t K, const double* T, int32_t theta, double d
         c->cur_is_alt = false;
     }
     if (c->mlp) {
-        // A force model issues five launches per MD step: queue the anneal
-        // directly instead of capturing a graph of that size.
-        PAMD_CU(c, launch_set_counters(c, c->step, c->resample_index));
-        int err = launch_prop(c, theta, dt_ps, T[0], c->b.counters, 0u, nullptr);
-        if (!err && launch_observe(c, T[0], c->b.obs) != cudaSuccess) err = PAMD_ECUDA;
-        if (!err && record_energies(c, 0) != cudaSuccess) err = PAMD_ECUDA;
-        for (int i = 1; i <= K && !err; ++i) {
-            if (launch_resample(c, T[i - 1], T[i], resample ? 1 : 0, c->b.counters, (uint32_t)i) != cudaSuccess) {
-                err = PAMD_ECUDA;
-                break;
-            }
-            c->cur_is_alt = !c->cur_is_alt;
-            err = launch_prop(c, theta, dt_ps, T[i], c->b.counters, (uint32_t)i * (uint32_t)theta, nullptr);
-            if (!err && launch_observe(c, T[i], c->b.obs + i) != cudaSuccess) err = PAMD_ECUDA;
-            if (!err && record_energies(c, i) != cudaSuccess) err = PAMD_ECUDA;
-        }
-        if (err) {
-            c->broken = true;
-            return err == PAMD_ECUDA ? fail(PAMD_ECUDA, "anneal with force model: " + g_err) : err;
-        }
-        if (c->cur_is_alt) {
-            const size_t st_bytes = state_bytes(c);
-            PAMD_CU(c, cudaMemcpyAsync(c->b.state, c->b.state_alt, st_bytes, cudaMemcpyDeviceToDevice, c->stream));
-            PAMD_CU(c, cudaMemcpyAsync(c->b.E, c->b.E_alt, 8 * (size_t)c->R, cudaMemcpyDeviceToDevice, c->stream));
-            PAMD_CU(c, cudaMemcpyAsync(c->b.fam, c->b.fam_alt, 4 * (size_t)c->R, cudaMemcpyDeviceToDevice, c->stream));
-            c->cur_is_alt = false;
-        }
-    } else if (!c->graph_exec || !(c->graph_key == key)) {
+        // With a force model each temperature's theta MD steps are one WHILE
+        // node of the graph (step kernel and four GEMMs per iteration).  The
+        // graph holds the model's workspace pointers and energy scale.
+        if (c->mlp->broken) return fail(PAMD_ESTATE, "force model unusable after an earlier CUDA error");
+        if ((rc = mlp_prepare_capture(c->mlp))) return rc;
+        key.model = c->mlp;
+        key.model_gen = c->mlp->work_gen;
+        key.mu_E = c->mlp->mu_E;
+        key.sigma_E = c->mlp->sigma_E;
+    }
+    if (!c->graph_exec || !(c->graph_key == key)) {
         if (c->graph_exec) {
             cudaGraphExecDestroy(c->graph_exec);
             c->graph_exec = nullptr;
@@ -1508,7 +1491,7 @@ int pamd_anneal(pamd_ctx* c, int32_t K, const double* T, int32_t theta, double d
         if (ei != cudaSuccess) return cuda_fail(c, ei, "graph instantiate");
         c->graph_key = key;
     }
-    if (!c->mlp) {
+    {
         cudaError_t e = launch_set_counters(c, c->step, c->resample_index);
         if (e != cudaSuccess) return cuda_fail(c, e, "set counters");
         PAMD_CU(c, cudaGraphLaunch(c->graph_exec, c->stream));

@@ -449,6 +449,7 @@ int mlp_ensure_work(pamd_mlp* m, long long M, bool train) {
         cudaStreamSynchronize(m->stream);
         cudaFree(w.base);
     }
+    m->work_gen += 1;  // graphs captured over the old workspace are stale
     MlpWork nw;
     nw.cap = cap;
     nw.train = tr;
@@ -485,6 +486,22 @@ int mlp_ensure_work(pamd_mlp* m, long long M, bool train) {
             return mcuda(m, cudaGetLastError(), "workspace clear");
     }
     w = nw;
+    return PAMD_OK;
+}
+
+int mlp_prepare_capture(pamd_mlp* m) {
+    if (!m->loop_ctr && cudaMalloc(&m->loop_ctr, sizeof(int)) != cudaSuccess) {
+        m->loop_ctr = nullptr;
+        cudaGetLastError();
+        return mfail(PAMD_ENOMEM, "surrogate loop counter");
+    }
+    if (!m->body_stream && cudaStreamCreateWithFlags(&m->body_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        m->body_stream = nullptr;
+        cudaGetLastError();
+        return mfail(PAMD_ECUDA, "surrogate capture stream");
+    }
+    const cudaError_t e = gemm_prepare_device();
+    if (e != cudaSuccess) return mcuda(m, e, "tensor-core GEMM set-up");
     return PAMD_OK;
 }
 
@@ -997,6 +1014,8 @@ int64_t pamd_mlp_launch_count(pamd_mlp* m) { return m ? m->launches : 0; }
 void pamd_mlp_destroy(pamd_mlp* m) {
     if (!m) return;
     if (m->stream) cudaStreamSynchronize(m->stream);
+    if (m->loop_ctr) cudaFree(m->loop_ctr);
+    if (m->body_stream) cudaStreamDestroy(m->body_stream);
     if (m->w.base) cudaFree(m->w.base);
     if (m->base) cudaFree(m->base);
     if (m->own_stream && m->stream) cudaStreamDestroy(m->stream);

@@ -51,7 +51,7 @@ __device__ __forceinline__ void block_features(const float* xs, const ushort2* _
             const float dx = xs[ij.x] - xs[ij.y];
             const float dy = xs[kXs + ij.x] - xs[kXs + ij.y];
             const float dz = xs[2 * kXs + ij.x] - xs[2 * kXs + ij.y];
-            const float g = rsqrtf(dx * dx + dy * dy + dz * dz);
+            const float g = rsqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
             v = (g - mu[p]) * inv_sd[p];
         }
         const __nv_bfloat16 b = __float2bfloat16(v);
@@ -69,7 +69,7 @@ __device__ __forceinline__ float3 atom_force(int k, const float* xs, const float
         if (j == k) continue;
         const int p = k < j ? pair_id(k, j, N) : pair_id(j, k, N);
         const float dx = xk - xs[j], dy = yk - xs[kXs + j], dz = zk - xs[2 * kXs + j];
-        const float ir = rsqrtf(dx * dx + dy * dy + dz * dz);
+        const float ir = rsqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
         const float c = gam[p] * ir * ir * ir;
         fx = fmaf(c, dx, fx);
         fy = fmaf(c, dy, fy);
@@ -113,7 +113,7 @@ __device__ __forceinline__ void load_gamma(const float* xs, const __nv_bfloat16*
             const float dx = xs[ij.x] - xs[ij.y];
             const float dy = xs[kXs + ij.x] - xs[kXs + ij.y];
             const float dz = xs[2 * kXs + ij.x] - xs[2 * kXs + ij.y];
-            const float ir = rsqrtf(dx * dx + dy * dy + dz * dz);
+            const float ir = rsqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
             const float c = __bfloat162float(ga_row[p]) * inv_sd[p] * ir * ir * ir;
             gam[ij.x * S + ij.y] = c;
             gam[ij.y * S + ij.x] = c;
@@ -137,6 +137,93 @@ __device__ __forceinline__ float3 atom_force_any(int k, const float* xs, const f
         fz = fmaf(c, zk - xs[2 * kXs + j], fz);
     }
     return make_float3(fx, fy, fz);
+}
+
+// ------------------------------------------------ pair passes of the MD step kernel
+// Consecutive threads take consecutive row-order pairs, so that the lanes of
+// a warp read consecutive atoms (no shared-memory bank conflicts) and
+// consecutive table entries.  The pair table (i, j) and the per-pair tables
+// may sit in shared or global memory.  Positions sit in shared memory as
+// float4 (x, y, z, 0).  The arithmetic of every pair is that of
+// block_features / load_gamma / atom_force_any, bit for bit.
+
+__host__ __device__ __forceinline__ size_t step_pos_bytes(int N) { return 16 * (size_t)(N + 1); }
+
+__device__ __forceinline__ float inv_dist4(const float4 a, const float4 b) {
+    const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+    return rsqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+}
+
+// positions of one replica from the population layout [6][Np] (whole block)
+__device__ __forceinline__ void load_pos4(const float* st, int N, int Np, float4* xs4) {
+    for (int i = threadIdx.x; i < N; i += blockDim.x)
+        xs4[i] = make_float4(st[i], st[Np + i], st[2 * Np + i], 0.0f);
+}
+
+// features of the configuration in xs4 (whole block)
+__device__ __forceinline__ void pass_features(const float4* xs4, const ushort2* pij, int P, int Pp,
+                                              const float* mu, const float* inv_sd, __nv_bfloat16* a_row) {
+#pragma unroll 4
+    for (int p = threadIdx.x; p < Pp; p += blockDim.x) {
+        float v = 0.0f;
+        if (p < P) {
+            const ushort2 ij = pij[p];
+            v = (inv_dist4(xs4[ij.x], xs4[ij.y]) - mu[p]) * inv_sd[p];
+        }
+        a_row[p] = __float2bfloat16(v);
+    }
+}
+
+// the table of load_gamma from de/da of the configuration in xs4 (whole block)
+__device__ __forceinline__ void pass_gamma(const float4* xs4, const ushort2* pij, int P, int N,
+                                           const __nv_bfloat16* ga_row, const float* inv_sd, float* gam) {
+    if (!gamma_matrix(N)) {
+        for (int p = threadIdx.x; p < P; p += blockDim.x) gam[p] = __bfloat162float(ga_row[p]) * inv_sd[p];
+        return;
+    }
+    const int S = gamma_stride(N);
+#pragma unroll 4
+    for (int p = threadIdx.x; p < P; p += blockDim.x) {
+        const ushort2 ij = pij[p];
+        const float ir = inv_dist4(xs4[ij.x], xs4[ij.y]);
+        const float c = __bfloat162float(ga_row[p]) * inv_sd[p] * ir * ir * ir;
+        gam[ij.x * S + ij.y] = c;
+        gam[ij.y * S + ij.x] = c;
+    }
+}
+
+// sum over j != k of gam_kj (x_k - x_j) / r_kj^3 (atom_force_any on xs4)
+__device__ __forceinline__ float3 atom_force4(int k, const float4* xs4, const float* gam, int N) {
+    const float4 xk = xs4[k];
+    float fx = 0.0f, fy = 0.0f, fz = 0.0f;
+    if (!gamma_matrix(N)) {
+        for (int j = 0; j < N; ++j) {
+            if (j == k) continue;
+            const int p = k < j ? pair_id(k, j, N) : pair_id(j, k, N);
+            const float4 xj = xs4[j];
+            const float dx = xk.x - xj.x, dy = xk.y - xj.y, dz = xk.z - xj.z;
+            const float ir = rsqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+            const float c = gam[p] * ir * ir * ir;
+            fx = fmaf(c, dx, fx);
+            fy = fmaf(c, dy, fy);
+            fz = fmaf(c, dz, fz);
+        }
+        return make_float3(fx, fy, fz);
+    }
+    const float* row = gam + k * gamma_stride(N);
+    // x and y as one packed pair: d = x_k - x_j (a multiply by -1 is exact,
+    // so the fused form rounds like the subtraction), f += c d
+    float2 fxy = make_float2(0.0f, 0.0f);
+    const float2 xky = make_float2(xk.x, xk.y), m1 = make_float2(-1.0f, -1.0f);
+#pragma unroll 5
+    for (int j = 0; j < N; ++j) {
+        const float c = row[j];
+        const float4 xj = xs4[j];
+        const float2 d = __ffma2_rn(m1, make_float2(xj.x, xj.y), xky);
+        fxy = __ffma2_rn(make_float2(c, c), d, fxy);
+        fz = fmaf(c, xk.z - xj.z, fz);
+    }
+    return make_float3(fxy.x, fxy.y, fz);
 }
 
 // normalised energy e = b3 + sum of the layer-2 partial sums

@@ -492,6 +492,39 @@ bool on_device(const void* p, int dev) {
 
 constexpr int kMaxDevices = 64;
 
+// Kernel attribute and resident cluster count, once per device.
+cudaError_t gemm_setup(int dev, int* max_clusters_out) {
+    const size_t smem = (size_t)kStages * kStageBytes + 1024;
+    static std::once_flag once[kMaxDevices];
+    static cudaError_t attr[kMaxDevices];
+    static int max_clusters[kMaxDevices];
+    std::call_once(once[dev], [&] {
+        cudaError_t e = cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        // persistent grid: as many two-CTA clusters as can be resident at once
+        // (an SM left without a partner in its GPC hosts none)
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(2, 1, 1);
+        cfg.blockDim = dim3(kThreads, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        int mc = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&mc, gemm_bf16_kernel, &cfg);
+        if (e == cudaSuccess && mc < 1) e = cudaErrorInvalidConfiguration;
+        attr[dev] = e;
+        max_clusters[dev] = mc;
+    });
+    if (max_clusters_out) *max_clusters_out = max_clusters[dev];
+    return attr[dev];
+}
+
+cudaError_t gemm_prepare_device() {
+    int dev = 0;
+    const cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    return gemm_setup(dev, nullptr);
+}
+
 cudaError_t launch_gemm_bf16(const GemmArgs& ga, cudaStream_t s) {
     if (ga.M <= 0 || ga.N <= 0 || ga.K <= 0 || (ga.K & 7) || (ga.lda & 7) || (ga.ldb & 7) ||
         (reinterpret_cast<uintptr_t>(ga.A) & 15) || (reinterpret_cast<uintptr_t>(ga.B) & 15))
@@ -513,29 +546,12 @@ cudaError_t launch_gemm_bf16(const GemmArgs& ga, cudaStream_t s) {
     const bool b_ok = (g.ldcb % 8 == 0) && al16(g.Cb);
     g.vec_ok = (f_ok ? 1 : 0) | (b_ok ? 2 : 0);
     const size_t smem = (size_t)kStages * kStageBytes + 1024;
-    // kernel attribute and resident cluster count, once per device
-    static std::once_flag once[kMaxDevices];
-    static cudaError_t attr[kMaxDevices];
-    static int max_clusters[kMaxDevices];
-    std::call_once(once[dev], [&] {
-        cudaError_t e = cudaFuncSetAttribute(gemm_bf16_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        // persistent grid: as many two-CTA clusters as can be resident at once
-        // (an SM left without a partner in its GPC hosts none)
-        cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3(2, 1, 1);
-        cfg.blockDim = dim3(kThreads, 1, 1);
-        cfg.dynamicSmemBytes = smem;
-        int mc = 0;
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&mc, gemm_bf16_kernel, &cfg);
-        if (e == cudaSuccess && mc < 1) e = cudaErrorInvalidConfiguration;
-        attr[dev] = e;
-        max_clusters[dev] = mc;
-    });
-    if (attr[dev] != cudaSuccess) return attr[dev];
+    int max_clusters = 0;
+    const cudaError_t se = gemm_setup(dev, &max_clusters);
+    if (se != cudaSuccess) return se;
     // one cluster per pair of row blocks and column block, at most max_clusters
     const long long pairs = (long long)((g.M + 2 * kBM - 1) / (2 * kBM)) * ((g.N + kBN - 1) / kBN);
-    const int grid = 2 * (int)(pairs < max_clusters[dev] ? pairs : max_clusters[dev]);
+    const int grid = 2 * (int)(pairs < max_clusters ? pairs : max_clusters);
     gemm_bf16_kernel<<<grid, kThreads, smem, s>>>(tmA, tmB, g);
     return cudaGetLastError();
 }

@@ -112,6 +112,7 @@ struct MlpStepParams {
     long long R;
     int N, Np, P, Pp, nparts;
     int mode, step_index, theta;
+    const int* step_index_dev;  // mode 1 inside a captured loop: the step index in device memory
     const __nv_bfloat16* ga;
     const float* part;
     const float* mu;
@@ -126,7 +127,7 @@ struct MlpStepParams {
     uint32_t purpose_mol;
 };
 cudaError_t launch_mlp_step(const MlpStepParams& p, cudaStream_t s);
-size_t mlp_step_smem(int N, int Pp);
+size_t mlp_step_smem(int N, int Np, int Pp);
 
 }  // namespace pamd
 
@@ -157,6 +158,9 @@ struct pamd_mlp {
     double* scratch = nullptr;      // [4] loss and statistics
     void* base = nullptr;           // allocation holding the members above
     pamd::MlpWork w;
+    long long work_gen = 0;         // incremented whenever the workspace is reallocated
+    int* loop_ctr = nullptr;        // step index of a captured MD loop (device int)
+    cudaStream_t body_stream = nullptr;  // captures the body of that loop
 };
 
 namespace pamd {
@@ -168,6 +172,12 @@ int mlp_propagate(pamd_mlp* m, float* state, double* E, double* ke, double* rg, 
                   int Np, int theta, double dt, double T, double gamma, unsigned long long seed,
                   uint32_t step0, uint32_t purpose_mol, cudaStream_t s, long long* launches);
 int mlp_ensure_work(pamd_mlp* m, long long M, bool train);
+// The theta steps of mlp_propagate as one WHILE node of the graph being
+// captured on stream s (needs mlp_prepare_capture).
+int mlp_loop_captured(pamd_mlp* m, MlpStepParams p, int theta, int M, cudaStream_t s, int* status);
+// Everything a capture of mlp_propagate needs allocated or configured before
+// the capture starts (loop counter, body stream, tensor-core GEMM set-up).
+int mlp_prepare_capture(pamd_mlp* m);
 // GEMMs of one evaluation of the M configurations whose features are in
 // m->w.a: layers 1 and 2 (energy partial sums), and with forces the two
 // backward products (de/da in m->w.ga).  Tensor-core timeouts are recorded

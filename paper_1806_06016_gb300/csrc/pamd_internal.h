@@ -187,9 +187,14 @@ struct GraphKey {
     std::vector<double> T;
     const double* rec = nullptr;  // energy recording target (pamd_record_energies)
     int rec_rows = 0;
+    // force model: which one, the generation of its workspace, its energy scale
+    const void* model = nullptr;
+    long long model_gen = 0;
+    double mu_E = 0, sigma_E = 0;
     bool operator==(const GraphKey& o) const {
         return K == o.K && theta == o.theta && resample == o.resample && dt == o.dt && T == o.T &&
-               rec == o.rec && rec_rows == o.rec_rows;
+               rec == o.rec && rec_rows == o.rec_rows && model == o.model && model_gen == o.model_gen &&
+               mu_E == o.mu_E && sigma_E == o.sigma_E;
     }
 };
 
@@ -362,6 +367,9 @@ struct GemmArgs {
     int vec_ok;                // set by the launcher: 1 FP32 rows, 2 BF16 rows 16-byte aligned
 };
 cudaError_t launch_gemm_bf16(const GemmArgs& g, cudaStream_t s);
+// the GEMM's once-per-device set-up (kernel attribute, resident clusters) for
+// the current device, so that a later launch can be captured in a graph
+cudaError_t gemm_prepare_device();
 
 // message returned by pamd_last_error() on this thread (capi.cu)
 void set_last_error(const std::string& msg);

@@ -282,6 +282,80 @@ def test_surrogate_dynamics_match_oracle(env):
         model.close()
 
 
+def test_surrogate_anneal_graph_equals_stepwise_calls(env):
+    """pamd_anneal with a force model runs as one CUDA graph in which each
+    temperature's theta steps are a WHILE node (step kernel, four GEMMs and
+    a loop counter per iteration).  It must reproduce, bit for bit, the same
+    anneal issued as separate propagate / observables / resample calls (each
+    queued step by step); a second launch continues with fresh counters, a
+    new energy scale or detaching the model re-captures."""
+    torch, pamd, S = env
+    n, R, theta, dt, seed = 22, 300, 7, 0.001, 41
+    top = pi.make_chain(n, 2)
+    temps = pi.geometric_schedule(700.0, 500.0, 3)
+    x = pi.perturbed_positions(top, 64, 0.03, 8)
+    model, q = _model_and_params(env, n, 128, 9, x)
+    a = pamd.pamd_init(top, R, temps[0], seed)
+    b = pamd.pamd_init(top, R, temps[0], seed)
+    try:
+        S.attach(a, model)
+        S.attach(b, model)
+        l0 = pamd.pamd_launch_count(a)
+        obs_a = pamd.pamd_anneal(a, temps, theta, dt)
+        # every MD step ran: at least the step kernel and four GEMMs per step
+        assert pamd.pamd_launch_count(a) - l0 >= len(temps) * theta * 5
+        obs_b = []
+        pamd.pamd_propagate(b, theta, dt, temps[0])
+        obs_b.append(pamd.pamd_observables(b, temps[0]))
+        for i in range(1, len(temps)):
+            pamd.pamd_resample(b, temps[i - 1], temps[i], want_copies=False)
+            pamd.pamd_propagate(b, theta, dt, temps[i])
+            obs_b.append(pamd.pamd_observables(b, temps[i]))
+        for u, w in zip(pamd.pamd_get_state(a), pamd.pamd_get_state(b)):
+            np.testing.assert_array_equal(u, w)
+        for oa, ob in zip(obs_a, obs_b):
+            for k in oa:
+                assert oa[k] == ob[k], k
+        assert pamd.pamd_get_counters(a) == pamd.pamd_get_counters(b)
+        # second launch of the same graph: fresh counters, still equal to the stepwise calls
+        obs_a2 = pamd.pamd_anneal(a, temps, theta, dt)
+        pamd.pamd_propagate(b, theta, dt, temps[0])
+        ob0 = pamd.pamd_observables(b, temps[0])
+        assert obs_a2[0]["e_pot"] == ob0["e_pot"] and obs_a2[0]["rg"] == ob0["rg"]
+        assert obs_a2[-1]["e_pot"] != obs_a[-1]["e_pot"]
+        # a new energy scale is seen by the next anneal (the graph is re-captured)
+        p = model.get_params()
+        p["mu_E"] = p["mu_E"] + 100.0
+        model.set_params(p)
+        c = pamd.pamd_init(top, R, temps[0], seed)
+        try:
+            S.attach(c, model)
+            pamd.pamd_set_state(c, *pamd.pamd_get_state(a))
+            pamd.pamd_set_counters(c, *pamd.pamd_get_counters(a))
+            o1 = pamd.pamd_anneal(a, temps, theta, dt)
+            o2 = pamd.pamd_anneal(c, temps, theta, dt)
+            for k in o1[-1]:
+                assert o1[-1][k] == o2[-1][k], k
+        finally:
+            pamd.pamd_destroy(c)
+        # detaching restores the exact force field in the graph as well
+        S.attach(a, None)
+        e = pamd.pamd_init(top, R, temps[0], seed)
+        try:
+            pamd.pamd_set_state(e, *pamd.pamd_get_state(a))
+            pamd.pamd_set_counters(e, *pamd.pamd_get_counters(a))
+            oa = pamd.pamd_anneal(a, temps, theta, dt)
+            oe = pamd.pamd_anneal(e, temps, theta, dt)
+            for k in oa[-1]:
+                assert oa[-1][k] == oe[-1][k], k
+        finally:
+            pamd.pamd_destroy(e)
+    finally:
+        pamd.pamd_destroy(a)
+        pamd.pamd_destroy(b)
+        model.close()
+
+
 def test_training_gain_over_untrained_network(env):
     """What training buys: on exact data harvested by the GPU path, Adam lowers
     the held-out force error, and a PAMD anneal driven by the trained network
