@@ -552,7 +552,7 @@ int pamd_mlp_create(pamd_mlp** out, int32_t n_atoms, int32_t hidden, uint64_t se
     m->P = n_atoms * (n_atoms - 1) / 2;
     m->Pp = (m->P + 7) / 8 * 8;
     m->H = hidden;
-    m->nparts = (hidden + kGemmTileN - 1) / kGemmTileN;
+    m->nparts = kGemmHeadParts * ((hidden + kGemmTileN - 1) / kGemmTileN);
     const size_t H = (size_t)hidden, Pp = (size_t)m->Pp;
     m->oW1 = 0;
     m->ob1 = H * Pp;

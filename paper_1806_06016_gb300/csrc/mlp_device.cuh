@@ -226,6 +226,25 @@ __device__ __forceinline__ float3 atom_force4(int k, const float4* xs4, const fl
     return make_float3(fxy.x, fxy.y, fz);
 }
 
+// the terms j0 <= j < j1 of atom_force4's matrix-form sum (same arithmetic)
+__device__ __forceinline__ float3 atom_force4_range(int k, const float4* xs4, const float* gam, int N, int j0,
+                                                    int j1) {
+    const float4 xk = xs4[k];
+    const float* row = gam + k * gamma_stride(N);
+    float2 fxy = make_float2(0.0f, 0.0f);
+    float fz = 0.0f;
+    const float2 xky = make_float2(xk.x, xk.y), m1 = make_float2(-1.0f, -1.0f);
+#pragma unroll 5
+    for (int j = j0; j < j1; ++j) {
+        const float c = row[j];
+        const float4 xj = xs4[j];
+        const float2 d = __ffma2_rn(m1, make_float2(xj.x, xj.y), xky);
+        fxy = __ffma2_rn(make_float2(c, c), d, fxy);
+        fz = fmaf(c, xk.z - xj.z, fz);
+    }
+    return make_float3(fxy.x, fxy.y, fz);
+}
+
 // normalised energy e = b3 + sum of the layer-2 partial sums
 __device__ __forceinline__ double head_energy(const float* part, int nparts, int m, const float* b3) {
     double e = (double)*b3;

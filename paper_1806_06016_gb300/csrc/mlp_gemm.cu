@@ -42,7 +42,9 @@ namespace pamd {
 namespace {
 
 constexpr int kBM = 128, kBN = kGemmTileN, kBK = 64, kStages = 4;
-constexpr int kThreads = 192, kEpiThreads = 128;
+// warp 0: TMA producer, warp 1: MMA issuer, warps 2..9: epilogue (two warps
+// per tensor-memory lane quarter, each taking one half of the tile's columns)
+constexpr int kEpiWarps = 8, kThreads = 64 + 32 * kEpiWarps, kEpiThreads = 32 * kEpiWarps;
 constexpr int kTileA = kBM * kBK * 2;  // 16 KiB
 constexpr int kTileB = kBN * kBK * 2;  // 32 KiB
 constexpr int kStageBytes = kTileA + kTileB;
@@ -185,7 +187,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 }
 
 
-__device__ __forceinline__ float sigmoid(float z) { return 1.0f / (1.0f + __expf(-z)); }
+__device__ __forceinline__ float sigmoid(float z) { return __fdividef(1.0f, 1.0f + __expf(-z)); }
 
 // 32 consecutive FP32 values of one row: vector stores when the whole chunk
 // is inside the matrix and 16-byte aligned, else element by element
@@ -226,17 +228,18 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
-// Epilogue of one 128 x 256 tile: accumulator columns acc_col.. of this
-// warp's 32 tensor-memory lanes (rows m0 + 32q + lane).
+// Epilogue of one half (128 columns) of a 128 x 256 tile: accumulator
+// columns of this warp's 32 tensor-memory lanes (rows m0 + 32q + lane);
+// taddr and n0 point at the half's first column.
 __device__ __forceinline__ void epilogue_tile(const GemmArgs& g, uint32_t taddr, int row, int n0,
-                                              int ntile, int ntiles) {
+                                              int ntile, int ntiles, int half) {
     const bool row_ok = row < g.M;
     float head = 0.0f;
     __nv_bfloat16* Cb = static_cast<__nv_bfloat16*>(g.Cb);
     __nv_bfloat16* CbT = static_cast<__nv_bfloat16*>(g.CbT);
     const bool vf = (g.vec_ok & 1) != 0, vb = (g.vec_ok & 2) != 0;
 #pragma unroll 1
-    for (int cc = 0; cc < kBN / 32; ++cc) {
+    for (int cc = 0; cc < kBN / 64; ++cc) {
         float v[32];
         tmem_ld32(taddr + (uint32_t)(cc * 32), v);
         const int col0 = n0 + cc * 32;
@@ -288,7 +291,8 @@ __device__ __forceinline__ void epilogue_tile(const GemmArgs& g, uint32_t taddr,
                 if (j < n) CbT[(size_t)(col0 + j) * g.ldt + row] = __float2bfloat16(v[j]);
         }
     }
-    if (g.epi == kEpiHead && row_ok) g.part[(size_t)row * ntiles + ntile] = head;
+    if (g.epi == kEpiHead && row_ok)
+        g.part[(size_t)row * (kGemmHeadParts * ntiles) + kGemmHeadParts * ntile + half] = head;
 }
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
@@ -411,8 +415,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             // tracks every product issued before it, also on the abort path
             mma_commit(smem_u32(&done_bar));
         }
-    } else {  // epilogue warps 2..5
+    } else {  // epilogue warps 2..9
         const int q = warp & 3;  // tensor-memory lane quarter this warp may access
+        const int half = (warp - 2) >> 2;
         int i = 0;
         for (int t = cid; t < tiles; t += ncl, ++i) {
             const int acc = i & 1;
@@ -421,8 +426,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
             if (*abort_flag) break;
             tc_fence_after();
             const int m0 = (2 * (t / NT) + crank) * kBM, nt = t % NT;
-            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kBN);
-            epilogue_tile(g, taddr, m0 + q * 32 + lane, nt * kBN, nt, NT);
+            const uint32_t taddr =
+                tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * kBN + half * (kBN / 2));
+            epilogue_tile(g, taddr, m0 + q * 32 + lane, nt * kBN + half * (kBN / 2), nt, NT, half);
             tc_fence_before();
             mbar_arrive(smem_u32(&acce_bar[acc]));
         }

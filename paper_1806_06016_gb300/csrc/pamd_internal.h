@@ -346,11 +346,12 @@ cudaError_t propagate2_b4(const PropParams* p, bool chain, int warps, int grid, 
 //   kEpiStore  C = z, Cb = bf16(z)                       (each output optional)
 //   kEpiSilu   C = z, Cs = silu'(z), Cb = bf16(silu(z)), CbT = Cb transposed
 //   kEpiHead   C = z, Cs = silu'(z), Cb = bf16(vec[n] silu'(z)), CbT, and
-//              part[m * ntiles + tile] = sum over the tile's n of vec[n] silu(z),
-//              ntiles = ceil(N / kGemmTileN)
+//              part[m * 2 ntiles + 2 tile + h] = sum over the n of half h of
+//              the tile of vec[n] silu(z), ntiles = ceil(N / kGemmTileN)
 //   kEpiMul    C = z, Cb = bf16(z * mul[m, n]) (mul FP32, leading dim ldc), CbT
 enum GemmEpi { kEpiStore = 0, kEpiSilu = 1, kEpiHead = 2, kEpiMul = 3 };
-constexpr int kGemmTileN = 256;  // output columns per tile (part[] has ceil(N / kGemmTileN) columns)
+constexpr int kGemmTileN = 256;   // output columns per tile
+constexpr int kGemmHeadParts = 2;  // kEpiHead partial sums per tile (part[] has 2 ceil(N / kGemmTileN) columns)
 struct GemmArgs {
     const void* A;             // __nv_bfloat16 [M][lda]
     const void* B;             // __nv_bfloat16 [N][ldb]
@@ -361,7 +362,7 @@ struct GemmArgs {
     const float* bias;         // [N] or null
     const float* vec;          // [N] (kEpiHead)
     const float* mul;          // [M][ldc] (kEpiMul)
-    float* part;               // [M][ceil(N / kGemmTileN)] (kEpiHead)
+    float* part;               // [M][kGemmHeadParts ceil(N / kGemmTileN)] (kEpiHead)
     int* status;               // PAMD status word (timeouts)
     int M, N, K, lda, ldb, ldc, ldcb, ldt, epi;
     int vec_ok;                // set by the launcher: 1 FP32 rows, 2 BF16 rows 16-byte aligned

@@ -21,18 +21,27 @@ namespace pamd {
 namespace {
 
 constexpr int kStepThreads = 256;
-constexpr int kAtomsPerThread = (PAMD_MAX_ATOMS + kStepThreads - 1) / kStepThreads;
+static_assert(PAMD_MAX_ATOMS <= kStepThreads, "one atom per thread in the update");
+// Molecules with gamma_matrix(N) split each atom's force sum over up to this
+// many threads (consecutive thirds of the row, added in order afterwards).
+constexpr int kForceSplit = 3;
+
+__host__ __device__ __forceinline__ int force_split(int N) {
+    if (!gamma_matrix(N)) return 1;
+    return N * kForceSplit <= kStepThreads ? kForceSplit : (2 * N <= kStepThreads ? 2 : 1);
+}
 // The per-pair tables and the double buffers live in shared memory when the
 // whole layout fits in this many bytes (two blocks per SM at least).
 constexpr size_t kFastSmemMax = 113 * 1024;
 
 // Byte offsets of the step kernel's dynamic shared memory.  Always: the
-// positions (float4 per atom) and the force table of load_gamma.  With
+// positions (float4 per atom), the force table of load_gamma and the partial
+// force sums (float4 per atom and part).  With
 // `fast`: the pair table, the feature means and inverse SDs, and two buffers
 // of one replica's state [6][Np] and de/da row [Pp], filled ahead by
 // cp.async.
 struct StepSmem {
-    size_t pos, gam, pij, mu, isd, gbuf, sbuf, total;
+    size_t pos, gam, fpart, pij, mu, isd, gbuf, sbuf, total;
     bool fast;
 };
 
@@ -42,7 +51,8 @@ __host__ __device__ __forceinline__ StepSmem step_smem_layout(int N, int Np, int
     StepSmem L{};
     L.pos = 0;
     L.gam = L.pos + up16(step_pos_bytes(N));
-    L.pij = L.gam + up16(4 * (size_t)gamma_floats(N, Pp));
+    L.fpart = L.gam + up16(4 * (size_t)gamma_floats(N, Pp));
+    L.pij = L.fpart + up16(16 * (size_t)kForceSplit * N);
     L.mu = L.pij + up16(4 * (size_t)Pp);
     L.isd = L.mu + up16(4 * (size_t)Pp);
     L.gbuf = L.isd + up16(4 * (size_t)Pp);
@@ -89,6 +99,8 @@ __global__ void __launch_bounds__(kStepThreads) mlp_step_kernel(const MlpStepPar
     const StepSmem L = step_smem_layout(N, Np, p.Pp);
     float4* xs4 = reinterpret_cast<float4*>(sm + L.pos);
     float* gam = reinterpret_cast<float*>(sm + L.gam);
+    float4* fpart = reinterpret_cast<float4*>(sm + L.fpart);
+    const int nsplit = force_split(N);
     const ushort2* pij = p.pairs;
     const float* mu_t = p.mu;
     const float* isd_t = p.inv_sd;
@@ -132,38 +144,45 @@ __global__ void __launch_bounds__(kStepThreads) mlp_step_kernel(const MlpStepPar
         }
         pass_gamma(xs4, pij, p.P, N, gs, isd_t, gam);
         __syncthreads();
-        // forces of the current positions, F = -dE/dx
-        float fx[kAtomsPerThread], fy[kAtomsPerThread], fz[kAtomsPerThread];
-#pragma unroll
-        for (int q = 0; q < kAtomsPerThread; ++q) {
-            const int i = threadIdx.x + q * kStepThreads;
-            fx[q] = fy[q] = fz[q] = 0.0f;
+        // forces of the current positions, F = -dE/dx (thread i: atom i)
+        const int i = threadIdx.x;
+        float3 f = make_float3(0.0f, 0.0f, 0.0f);
+        if (nsplit == 1) {
+            if (i < N) f = atom_force4(i, xs4, gam, N);
+        } else {
+            const int h = threadIdx.x / N, kk = threadIdx.x - h * N, len = (N + nsplit - 1) / nsplit;
+            if (h < nsplit) {
+                const int j0 = h * len, j1 = min(N, j0 + len);
+                const float3 fp = atom_force4_range(kk, xs4, gam, N, j0, j1);
+                fpart[h * N + kk] = make_float4(fp.x, fp.y, fp.z, 0.0f);
+            }
+            __syncthreads();
             if (i < N) {
-                const float3 f = atom_force4(i, xs4, gam, N);
-                fx[q] = sE * f.x;
-                fy[q] = sE * f.y;
-                fz[q] = sE * f.z;
+                for (int hh = 0; hh < nsplit; ++hh) {
+                    const float4 fp = fpart[hh * N + i];
+                    f.x += fp.x;
+                    f.y += fp.y;
+                    f.z += fp.z;
+                }
             }
         }
+        f = make_float3(sE * f.x, sE * f.y, sE * f.z);
         __syncthreads();  // every force sum has read xs4
         double ek = 0.0;
-#pragma unroll
-        for (int q = 0; q < kAtomsPerThread; ++q) {
-            const int i = threadIdx.x + q * kStepThreads;
-            if (i >= N) continue;
+        if (i < N) {
             const float im = 1.0f / p.masses[i];
             const float4 x4 = xs4[i];
             float x = x4.x, y = x4.y, z = x4.z;
             float vx = ss[3 * Np + i], vy = ss[4 * Np + i], vz = ss[5 * Np + i];
             if (p.mode == 1) {
                 if (step_index > 0) {  // closing B of the previous step
-                    vx = fmaf(p.hdt * im, fx[q], vx);
-                    vy = fmaf(p.hdt * im, fy[q], vy);
-                    vz = fmaf(p.hdt * im, fz[q], vz);
+                    vx = fmaf(p.hdt * im, f.x, vx);
+                    vy = fmaf(p.hdt * im, f.y, vy);
+                    vz = fmaf(p.hdt * im, f.z, vz);
                 }
-                vx = fmaf(p.hdt * im, fx[q], vx);  // B
-                vy = fmaf(p.hdt * im, fy[q], vy);
-                vz = fmaf(p.hdt * im, fz[q], vz);
+                vx = fmaf(p.hdt * im, f.x, vx);  // B
+                vy = fmaf(p.hdt * im, f.y, vy);
+                vz = fmaf(p.hdt * im, f.z, vz);
                 x = fmaf(p.hdt, vx, x);  // A
                 y = fmaf(p.hdt, vy, y);
                 z = fmaf(p.hdt, vz, z);
@@ -181,15 +200,15 @@ __global__ void __launch_bounds__(kStepThreads) mlp_step_kernel(const MlpStepPar
                 st[2 * Np + i] = z;
             } else {
                 if (p.theta > 0) {  // closing B of the last step
-                    vx = fmaf(p.hdt * im, fx[q], vx);
-                    vy = fmaf(p.hdt * im, fy[q], vy);
-                    vz = fmaf(p.hdt * im, fz[q], vz);
+                    vx = fmaf(p.hdt * im, f.x, vx);
+                    vy = fmaf(p.hdt * im, f.y, vy);
+                    vz = fmaf(p.hdt * im, f.z, vz);
                 }
                 if (p.fout) {
                     float* fo = p.fout + (size_t)k * 3 * Np;
-                    fo[i] = fx[q];
-                    fo[Np + i] = fy[q];
-                    fo[2 * Np + i] = fz[q];
+                    fo[i] = f.x;
+                    fo[Np + i] = f.y;
+                    fo[2 * Np + i] = f.z;
                 }
                 const double ms = (double)p.masses[i];
                 ek += 0.5 * ms * ((double)vx * vx + (double)vy * vy + (double)vz * vz);
