@@ -375,23 +375,11 @@ int pack(pamd_mlp* m) {
 size_t forces_smem(const pamd_mlp* m) { return sizeof(float) * (3 * kXs + (size_t)gamma_floats(m->N, m->Pp)); }
 size_t loss_smem(const pamd_mlp* m) { return sizeof(float) * (6 * kXs + (size_t)gamma_floats(m->N, m->Pp)); }
 
-// The dynamic shared-memory limit of a kernel is process-wide: raise it to the
-// largest model created so far, never lower it.
+// The dynamic shared-memory limits of the force and loss kernels on the
+// current device, raised to what this model needs.
 int set_smem_attrs(const pamd_mlp* m) {
-    static std::mutex mu;
-    static size_t forces_max = 0, loss_max = 0;
-    std::lock_guard<std::mutex> lock(mu);
-    cudaError_t e = cudaSuccess;
-    if (forces_smem(m) > forces_max) {
-        e = cudaFuncSetAttribute(mlp_forces_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)forces_smem(m));
-        if (e == cudaSuccess) forces_max = forces_smem(m);
-    }
-    if (e == cudaSuccess && loss_smem(m) > loss_max) {
-        e = cudaFuncSetAttribute(mlp_loss_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)loss_smem(m));
-        if (e == cudaSuccess) loss_max = loss_smem(m);
-    }
+    cudaError_t e = ensure_dyn_smem((const void*)mlp_forces_kernel, forces_smem(m));
+    if (e == cudaSuccess) e = ensure_dyn_smem((const void*)mlp_loss_kernel, loss_smem(m));
     return e == cudaSuccess ? PAMD_OK : mfail(PAMD_ECUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
 }
 

@@ -368,6 +368,11 @@ struct GemmArgs {
     int vec_ok;                // set by the launcher: 1 FP32 rows, 2 BF16 rows 16-byte aligned
 };
 cudaError_t launch_gemm_bf16(const GemmArgs& g, cudaStream_t s);
+
+// Raise the dynamic shared-memory limit of kernel `fn` on the current device
+// to at least `bytes` (the attribute belongs to the device's context; the
+// largest value asked for so far is kept per kernel and device; thread-safe).
+cudaError_t ensure_dyn_smem(const void* fn, size_t bytes);
 // the GEMM's once-per-device set-up (kernel attribute, resident clusters) for
 // the current device, so that a later launch can be captured in a graph
 cudaError_t gemm_prepare_device();

@@ -649,13 +649,8 @@ template <int B, bool CHAIN>
 cudaError_t propagate2_launch_one(const PropParams* p, int warps, int grid, size_t smem,
                                   cudaStream_t s, int* blocks_per_sm) {
     auto kern = propagate2_kernel<B, CHAIN>;
-    static size_t configured = 0;
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
+    const cudaError_t e = ensure_dyn_smem((const void*)kern, smem);
+    if (e != cudaSuccess) return e;
     if (!p) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, warps * 32, smem);
     kern<<<grid, warps * 32, smem, s>>>(*p);
     return cudaGetLastError();

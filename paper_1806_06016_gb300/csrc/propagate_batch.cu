@@ -78,13 +78,8 @@ __global__ void __launch_bounds__(kBatchThreads, BatchCfg<B>::MIN_BLOCKS)
 
 template <int B>
 cudaError_t launch_b(const BatchParams& bp, int grid, size_t smem, cudaStream_t s, int* blocks_per_sm) {
-    static size_t configured = 0;
-    if (smem > configured) {
-        const cudaError_t e = cudaFuncSetAttribute(propagate_batch_kernel<B>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
+    const cudaError_t e = ensure_dyn_smem((const void*)propagate_batch_kernel<B>, smem);
+    if (e != cudaSuccess) return e;
     if (blocks_per_sm)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, propagate_batch_kernel<B>,
                                                              kBatchThreads, smem);

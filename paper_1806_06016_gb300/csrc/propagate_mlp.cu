@@ -11,7 +11,9 @@
 // one-thread counter kernel.  The update arithmetic and the Philox noise
 // stream are those of the exact propagate kernel (same key, counter and
 // purpose), so that the two force fields can be compared on identical noise.
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "mlp_device.cuh"
 #include "pamd_device.cuh"
@@ -266,34 +268,31 @@ __global__ void mlp_loop_next_kernel(cudaGraphConditionalHandle h, int* ctr, int
 size_t mlp_step_smem(int N, int Np, int Pp) { return step_smem_layout(N, Np, Pp).total; }
 
 cudaError_t launch_mlp_step(const MlpStepParams& p, cudaStream_t s) {
-    // per device and kernel variant: the dynamic shared memory opted in so
-    // far and the resident grid for it (one block per resident slot; each
-    // block walks the replicas with stride gridDim.x)
-    constexpr int kMaxDevices = 64;
+    // the resident grid for this shared-memory size on the current device
+    // (one block per resident slot; each block walks the replicas with
+    // stride gridDim.x), looked up once per device, variant and size
     static std::mutex mu;
-    static size_t configured[kMaxDevices][2];
-    static int resident[kMaxDevices][2];
+    static std::map<std::tuple<int, bool, size_t>, int> resident;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     const StepSmem L = step_smem_layout(p.N, p.Np, p.Pp);
     const void* fn = L.fast ? (const void*)mlp_step_kernel<true> : (const void*)mlp_step_kernel<false>;
+    e = ensure_dyn_smem(fn, L.total);
+    if (e != cudaSuccess) return e;
     int grid_max = 0;
     {
         std::lock_guard<std::mutex> lk(mu);
-        if (L.total > configured[dev][L.fast]) {
-            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
-            if (e != cudaSuccess) return e;
+        int& r = resident[std::make_tuple(dev, L.fast, L.total)];
+        if (r == 0) {
             int per_sm = 0, sms = 0;
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kStepThreads, L.total);
             if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             if (e != cudaSuccess) return e;
             if (per_sm < 1) return cudaErrorInvalidConfiguration;
-            configured[dev][L.fast] = L.total;
-            resident[dev][L.fast] = per_sm * sms;
+            r = per_sm * sms;
         }
-        grid_max = resident[dev][L.fast];
+        grid_max = r;
     }
     const long long g = p.R < grid_max ? p.R : grid_max;
     if (L.fast)

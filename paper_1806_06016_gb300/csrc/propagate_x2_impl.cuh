@@ -681,13 +681,8 @@ template <int B>
 cudaError_t propagate_x2_launch(const PropParams* p, int warps, int grid, size_t smem,
                                 cudaStream_t s, int* blocks_per_sm) {
     auto kern = propagate_x2_kernel<B>;
-    static size_t configured = 0;
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
+    const cudaError_t e = ensure_dyn_smem((const void*)kern, smem);
+    if (e != cudaSuccess) return e;
     if (!p) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, warps * 32, smem);
     kern<<<grid, warps * 32, smem, s>>>(*p);
     return cudaGetLastError();
