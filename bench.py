@@ -92,6 +92,9 @@ NCU_TRAFFIC = {
     # packed FP32x2 kernel (propagate_x2_kernel<5>, 15 x 5 shape): 15.12 MB
     # read, 768 B written per theta = 100 launch
     "938d23f1e613472b": 15118336,
+    # after the fast hardware logarithm in the O-step noise (hash now covers
+    # the device helpers): 15.38 MB read, 16 KB written
+    "95216bfda12f5b00": 15393792,
 }
 
 
@@ -113,8 +116,8 @@ def measured_fp32_peak(pamd, iters=20000, reps=100):
 
 def kernel_source_hash(packed=False):
     """Hash of the source of the timed propagate kernel (the packed kernel
-    includes the scalar kernel's header)."""
-    names = ["propagate_impl.cuh"] + (["propagate_x2_impl.cuh"] if packed else [])
+    includes the scalar kernel's header; both include the device helpers)."""
+    names = ["pamd_device.cuh", "propagate_impl.cuh"] + (["propagate_x2_impl.cuh"] if packed else [])
     h = hashlib.sha256()
     for n in names:
         h.update(open(os.path.join(ROOT, "paper_1806_06016_gb300", "csrc", n), "rb").read())

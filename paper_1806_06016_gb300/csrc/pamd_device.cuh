@@ -43,17 +43,18 @@ __device__ __forceinline__ float3 normal3(unsigned long long seed, uint32_t atom
     return make_float3(r0 * c0, r0 * s0, r1 * c1);
 }
 
-// The same three normals with the hardware sine and cosine (absolute error
-// below 2^-21 on [-pi, pi)) in place of sincospi / cospi: the O-step noise of
-// the FP32 dynamics kernels, where that error is far below the FP32 rounding
-// of the velocities.  cos(2 pi u) = -cos(2 pi (u - 1/2)) keeps the argument in
-// [-pi, pi); the logarithm stays the accurate one (near u = 1 the fast one
-// could change sign).
+// The same three normals with the hardware sine, cosine and logarithm in
+// place of sincospi / cospi / logf: the O-step noise of the FP32 dynamics
+// kernels, where their errors (a few 1e-7 absolute) are far below the FP32
+// rounding of the velocities.  cos(2 pi u) = -cos(2 pi (u - 1/2)) keeps the
+// argument in [-pi, pi).  For the top one or two values of u the hardware
+// logarithm of u (exactly ~ -6e-8) may come out positive: -2 ln u is clamped
+// at 0, an error below 1e-3 in a normal on a set of probability ~2e-7.
 __device__ __forceinline__ float3 normal3_fast(unsigned long long seed, uint32_t atom, uint32_t slot,
                                                uint32_t step, uint32_t purpose) {
     const uint4 o = philox4x32_10(make_uint4(atom, slot, step, purpose), seed_key(seed));
-    const float r0 = sqrtf(-2.0f * logf(uniform23(o.x)));
-    const float r1 = sqrtf(-2.0f * logf(uniform23(o.z)));
+    const float r0 = sqrtf(fmaxf(-2.0f * __logf(uniform23(o.x)), 0.0f));
+    const float r1 = sqrtf(fmaxf(-2.0f * __logf(uniform23(o.z)), 0.0f));
     const float two_pi = 6.2831853071795864769f;
     float s0, c0;
     __sincosf(two_pi * (uniform23(o.y) - 0.5f), &s0, &c0);
