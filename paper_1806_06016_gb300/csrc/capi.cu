@@ -336,6 +336,9 @@ int build_topology(const pamd_topology* t, int lanes_req, TopoLayout* lay_out,
     lay.off_params = off; off += round_up(lay.nk * 16, 16);
     lay.off_masks = off; off += round_up((int)masks.size() * 8, 16);
     lay.off_m14 = off; off += round_up((int)m14.size() * 8, 16);
+    lay.far_masks = 0;
+    for (size_t q = 2 * (size_t)L; q < masks.size(); ++q)
+        if (masks[q]) lay.far_masks = 1;
     lay.off_bonds = off; off += round_up(lay.n_bonds * 16, 16);
     lay.off_angles = off; off += round_up(lay.n_angles * 32, 16);
     lay.off_dihs = off; off += round_up(lay.n_dihs * 32, 16);

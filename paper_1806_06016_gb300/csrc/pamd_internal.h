@@ -39,6 +39,7 @@ struct TopoLayout {
     int off_params;            // float4 [nk]: {sigma/2, sqrt(24 eps), q sqrt(k_e), 1/m}
     int off_masks;             // uint64 [(L/2+1) * L]: excluded and scaled 1-4 pairs per tile
     int off_m14;               // uint64 [(L/2+1) * L]: the scaled 1-4 pairs among them
+    int far_masks;             // 1 if a tile at ring step t >= 2 has a masked pair
     int off_bonds, n_bonds;
     int off_angles, n_angles;
     int off_dihs, n_dihs;

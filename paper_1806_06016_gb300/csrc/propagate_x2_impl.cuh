@@ -33,6 +33,8 @@
 // Linear-chain layouts only (B >= 3); other topologies use propagate_impl.cuh.
 #pragma once
 
+#include <type_traits>
+
 #include "propagate_impl.cuh"
 
 namespace pamd {
@@ -401,34 +403,40 @@ __device__ __forceinline__ void forces_x2(const unsigned char* sm, const TopoLay
     // half ring over partner blocks: steps 1..(L-1)/2 give every lane a
     // partner block; for even L the antipodal step L/2 follows, where only
     // lanes g < L/2 work.  Lane g receives from lane g - t the forces on its
-    // own atom b.
-    const int TF = (L - 1) / 2;
-#pragma unroll 1
-    for (int t = 1; t <= TF; ++t) {
+    // own atom b.  The partner sums of a whole tile are handed over after
+    // it, so that the partners' arithmetic can interleave.
+    auto tile = [&](int t, auto masked) {
+        constexpr bool MASKED = decltype(masked)::value;
         int J = g + t;
         J = (J >= L) ? J - L : J;
         const int sJ = J * C::BS;
         int src = g - t;
         src = (src < 0) ? src + L : src;
-        const unsigned long long m = masks[t * L + g], m4 = m14s[t * L + g];
-        // the partner sums of the whole tile are handed over after it, so
-        // that the partners' arithmetic can interleave; one branch for the
-        // whole group (a lane whose tile has no masked pair runs the masked
-        // code with an empty mask)
-        float gx[B], gy[B], gz[B];
-        if (!__any_sync(gmask, m != 0ull)) {
-#pragma unroll
-            for (int b = 0; b < B; ++b)
-                partner_x2<B, false>(r, hs, nse, qq, f, posA[sJ + b], posB[sJ + b], dprm[sJ + b], b,
-                                     m, m4, s_lj, s_c, gx[b], gy[b], gz[b]);
-        } else {
-#pragma unroll
-            for (int b = 0; b < B; ++b)
-                partner_x2<B, true>(r, hs, nse, qq, f, posA[sJ + b], posB[sJ + b], dprm[sJ + b], b,
-                                    m, m4, s_lj, s_c, gx[b], gy[b], gz[b]);
+        unsigned long long m = 0ull, m4 = 0ull;
+        if (MASKED) {
+            m = masks[t * L + g];
+            m4 = m14s[t * L + g];
         }
+        float gx[B], gy[B], gz[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b)
+            partner_x2<B, MASKED>(r, hs, nse, qq, f, posA[sJ + b], posB[sJ + b], dprm[sJ + b], b, m, m4,
+                                  s_lj, s_c, gx[b], gy[b], gz[b]);
 #pragma unroll
         for (int b = 0; b < B; ++b) hand_over<B>(f, b, gx[b], gy[b], gz[b], gmask, base + src);
+    };
+    const int TF = (L - 1) / 2;
+    // The excluded and scaled 1-4 pairs of a chain lie in the own block and
+    // the t = 1 tile: that tile runs the masked code, the others the plain
+    // code.  A topology with masked pairs further out (lay.far_masks) runs
+    // the masked code on every tile.
+    if (TF >= 1) tile(1, std::true_type{});
+    if (!lay.far_masks) {
+#pragma unroll 1
+        for (int t = 2; t <= TF; ++t) tile(t, std::false_type{});
+    } else {
+#pragma unroll 1
+        for (int t = 2; t <= TF; ++t) tile(t, std::true_type{});
     }
     if ((L & 1) == 0) {
         const int t = L / 2;

@@ -234,6 +234,31 @@ def test_paired_and_single_kernels_agree_statistically(lib):
         assert np.all(np.abs(a - b) <= 3 * np.hypot(sa, sb)), (key, (a - b) / np.hypot(sa, sb))
 
 
+@pytest.mark.parametrize("arith", ["scalar", "packed"])
+@pytest.mark.parametrize("n,lanes", [(75, 15), (40, 8), (23, 5)])
+def test_forces_chain_with_far_exclusions(lib, orc, n, lanes, arith):
+    """A chain in index order (chain layout) with extra exclusions between
+    distant atoms: masked pairs in ring tiles beyond the first, which the
+    kernels must evaluate with the masked code."""
+    top = pi.make_chain(n, 6)
+    far = [(0, n - 1), (2, n // 2), (n // 3, n - 4), (1, 9)]
+    top.excl = np.concatenate([np.asarray(top.excl, np.int32).reshape(-1, 2),
+                               np.asarray(far, np.int32)]).astype(np.int32)
+    R = 4
+    x = f32(pi.perturbed_positions(top, R, 0.01, 3))
+    ctx = _init_arith(lib, top, R, 300.0, 1, arith, lanes_per_replica=lanes)
+    try:
+        lib.pamd_set_state(ctx, x, np.zeros_like(x))
+        fg, eg = lib.pamd_forces(ctx)
+    finally:
+        lib.pamd_destroy(ctx)
+    fo, eo, scale = _oracle_forces(orc, top, x)
+    for k in range(R):
+        rms = math.sqrt(np.mean(fo[k] ** 2))
+        assert math.sqrt(np.mean((fg[k] - fo[k]) ** 2)) <= 1e-5 * rms
+        assert abs(eg[k] - eo[k]) <= 1e-5 * scale[k]
+
+
 @pytest.mark.parametrize("n", [13, 40, 75])
 def test_forces_relabelled_chain(lib, orc, n):
     """Atoms of a chain relabelled at random: the bonded terms are no longer a
