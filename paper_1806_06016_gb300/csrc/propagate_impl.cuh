@@ -31,6 +31,8 @@
 // positions 1000 nm away from everything, so they contribute exactly zero.
 #pragma once
 
+#include <type_traits>
+
 #include "pamd_device.cuh"
 #include "pamd_internal.h"
 
@@ -523,10 +525,13 @@ __device__ __forceinline__ void compute_forces(const unsigned char* sm, const To
             }
         }
     }
-    // half ring over partner blocks
+    // half ring over partner blocks.  Without masked pairs beyond the first
+    // ring step (lay.far_masks == 0: a chain with at least 3 atoms per lane)
+    // the tiles t >= 2 run the plain code with no test of the mask; otherwise
+    // each lane picks the plain or the masked code by its tile's mask.
     const int TH = L / 2;
-#pragma unroll 1
-    for (int t = 1; t <= TH; ++t) {
+    auto tile = [&](int t, auto mode) {
+        constexpr int MODE = decltype(mode)::value;  // 0 plain, 1 masked, 2 by mask
         const bool active = !(2 * t == L && g >= t);
         if (active) {
             int J = g + t;
@@ -535,8 +540,8 @@ __device__ __forceinline__ void compute_forces(const unsigned char* sm, const To
             const float4* tab = nullptr;
             if (TABLE)
                 tab = reinterpret_cast<const float4*>(sm + lay.off_ptab) + (size_t)(t - 1) * B * B * L + g;
-            const unsigned long long m = masks[t * L + g];
-            if (m == 0ull)
+            const unsigned long long m = MODE == 0 ? 0ull : masks[t * L + g];
+            if (MODE == 0 || (MODE == 2 && m == 0ull))
                 pair_tile<B, false, ENERGY, TABLE>(xi, yi, zi, hsi, sei, qi, fx, fy, fz, pos + sJ,
                                                    prm + sJ, frc + sJ, tab, L, m, e_acc);
             else
@@ -544,6 +549,14 @@ __device__ __forceinline__ void compute_forces(const unsigned char* sm, const To
                                                   prm + sJ, frc + sJ, tab, L, m, e_acc);
         }
         __syncwarp(gmask);
+    };
+    if (!lay.far_masks) {
+        if (TH >= 1) tile(1, std::integral_constant<int, 2>{});
+#pragma unroll 1
+        for (int t = 2; t <= TH; ++t) tile(t, std::integral_constant<int, 0>{});
+    } else {
+#pragma unroll 1
+        for (int t = 1; t <= TH; ++t) tile(t, std::integral_constant<int, 2>{});
     }
     if constexpr (CHAIN)
         bonded_chain<B, ENERGY>(sm, lay, prm, pos, frc, L, g, xi, yi, zi, fx, fy, fz, e_acc);
