@@ -207,10 +207,13 @@ int pamd_init(pamd_ctx** out, const pamd_topology* top, int64_t R, double T0, ui
  * with its own population R[m], start temperature T0[m] and Philox stream
  * (molecule index m mixed into the counters).  pamd_propagate advances them
  * all with one persistent launch per group of molecules sharing an
- * atoms-per-lane count (3..7, a kernel compiled for each, so that each group
- * gets its own register allocation); the group launches run concurrently on
- * streams forked from the context's stream, each taking (molecule, replica
- * batch) items from its own device work queue, largest molecules first.  On a batch context pamd_reset,
+ * atoms-per-lane count (3..7) and pair arithmetic (a kernel compiled for
+ * each, so that each group gets its own register allocation); the group
+ * launches run concurrently on streams forked from the context's stream,
+ * each taking (molecule, replica batch) items from its own device work queue,
+ * largest molecules first.  A molecule whose topology is a linear chain
+ * takes the packed FP32x2 pair arithmetic unless opt->pair_arith is
+ * PAMD_PAIRS_SCALAR; other molecules take the scalar one.  On a batch context pamd_reset,
  * pamd_propagate, pamd_resample (copies_out: [sum R] in molecule order, lnQ_out:
  * [n_mol]), pamd_observables (out: [n_mol]) and pamd_anneal (per_step_out:
  * [(K+1) * n_mol], temperature-major; one CUDA graph for the whole batch) act

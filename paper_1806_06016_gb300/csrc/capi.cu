@@ -719,10 +719,11 @@ int set_launch_shape(pamd_ctx* c, const TopoLayout& lay_in, int warps_req, int v
 
 bool is_batch(const pamd_ctx* c) { return !c->subs.empty(); }
 
-// One launch of the batched kernel per atoms-per-lane group, the groups on
-// streams of their own forked from and joined back to the context's stream
-// (parallel branches when the anneal is captured as a graph), so that one
-// group's last work items overlap the next group's instead of idling SMs.
+// One launch of the batched kernel per group (atoms per lane, pair
+// arithmetic), the groups on streams of their own forked from and joined back
+// to the context's stream (parallel branches when the anneal is captured as
+// a graph), so that one group's last work items overlap the next group's
+// instead of idling SMs.
 // graph: counters come from each molecule's device counters plus step_off.
 int launch_prop_batch(pamd_ctx* c, int theta, double dt, double T, bool graph, uint32_t step_off) {
     BatchParams bp{};
@@ -741,7 +742,8 @@ int launch_prop_batch(pamd_ctx* c, int theta, double dt, double T, bool graph, u
         bp.queue = c->queue + q;
         cudaStream_t s = fork ? c->group_streams[q] : c->stream;
         if (fork) PAMD_CU(c, cudaStreamWaitEvent(s, c->fork_event, 0));
-        const cudaError_t e = launch_propagate_batch(bp, gr.B, gr.grid, gr.smem, s);
+        const cudaError_t e = gr.packed ? launch_propagate_batch_x2(bp, gr.B, gr.grid, gr.smem, s)
+                                        : launch_propagate_batch(bp, gr.B, gr.grid, gr.smem, s);
         c->launches += 1;
         if (e != cudaSuccess) return cuda_fail(c, e, "batched propagate launch");
         if (fork) {
@@ -1177,11 +1179,18 @@ int pamd_init_batch(pamd_ctx** out, int32_t n_mol, const pamd_topology* tops, co
         so.warps_per_block = kBatchThreads / 32;
         so.autotune = 0;
         so.replicas_per_lane = 1;
-        so.pair_arith = PAMD_PAIRS_SCALAR;  // the batched kernel's arithmetic
         so.lanes_per_replica = tops[m].n_atoms >= 1 && tops[m].n_atoms <= PAMD_MAX_ATOMS
                                    ? batch_lanes(tops[m].n_atoms) : 0;
+        // the packed pair arithmetic wherever its chain layout applies,
+        // unless the caller asked for the scalar one
+        const bool try_packed = o.pair_arith != PAMD_PAIRS_SCALAR && is_linear_chain(&tops[m]);
+        so.pair_arith = try_packed ? PAMD_PAIRS_PACKED : PAMD_PAIRS_SCALAR;
         pamd_ctx* sub = nullptr;
-        const int rc = pamd_init(&sub, &tops[m], R[m], T0[m], seed, &so);
+        int rc = pamd_init(&sub, &tops[m], R[m], T0[m], seed, &so);
+        if (rc == PAMD_EUNSUPPORTED && try_packed) {
+            so.pair_arith = PAMD_PAIRS_SCALAR;
+            rc = pamd_init(&sub, &tops[m], R[m], T0[m], seed, &so);
+        }
         if (rc) {
             const std::string msg = "molecule " + std::to_string(m) + ": " + g_err;
             return bail(rc, msg);
@@ -1189,7 +1198,8 @@ int pamd_init_batch(pamd_ctx** out, int32_t n_mol, const pamd_topology* tops, co
         c->subs.push_back(sub);
         if (o.autotune && sub->N >= 3) {
             // measured choice among the batched kernel's shapes
-            const int trc = autotune_with(sub, 20, TuneLimits{3, 7, false, false, {kBatchThreads / 32}, -2}, nullptr);
+            const int trc = autotune_with(sub, 20, TuneLimits{3, 7, false, sub->pair_arith == PAMD_PAIRS_PACKED,
+                                                                  {kBatchThreads / 32}, -2}, nullptr);
             if (trc && trc != PAMD_EUNSUPPORTED) {
                 const std::string msg = "molecule " + std::to_string(m) + ": " + g_err;
                 return bail(trc, msg);
@@ -1201,18 +1211,20 @@ int pamd_init_batch(pamd_ctx** out, int32_t n_mol, const pamd_topology* tops, co
         c->N = std::max(c->N, sub->N);
         order.push_back({sub->N, m});
     }
-    // work lists: molecules grouped by atoms per lane (one launch per group,
-    // largest total work first), by decreasing size within a group, each cut
-    // into one CTA's worth of replicas
+    // work lists: molecules grouped by atoms per lane and pair arithmetic
+    // (one launch per group, largest total work first), by decreasing size
+    // within a group, each cut into one CTA's worth of replicas
     std::stable_sort(order.begin(), order.end(), [](auto a, auto b) { return a.first > b.first; });
     std::vector<int4> items;
     std::vector<std::pair<double, pamd_ctx::BatchGroup>> groups;
-    for (int Bg = 3; Bg <= 7; ++Bg) {
-        pamd_ctx::BatchGroup gr{Bg, (int)items.size(), 0, 0, 0};
+    for (int gk = 0; gk < 10; ++gk) {
+        const int Bg = 3 + gk / 2;
+        const bool packed = (gk & 1) != 0;
+        pamd_ctx::BatchGroup gr{Bg, (int)items.size(), 0, 0, 0, packed};
         double work = 0.0;
         for (auto& om : order) {
             pamd_ctx* sub = c->subs[om.second];
-            if (sub->lay.per_lane != Bg) continue;
+            if (sub->lay.per_lane != Bg || (sub->lay.packed != 0) != packed) continue;
             for (long long k0 = 0; k0 < sub->R; k0 += sub->rpb)
                 items.push_back(make_int4(om.second, (int)k0, (int)std::min<long long>(k0 + sub->rpb, sub->R), 0));
             gr.smem = std::max(gr.smem, prop_smem(sub));
@@ -1221,7 +1233,8 @@ int pamd_init_batch(pamd_ctx** out, int32_t n_mol, const pamd_topology* tops, co
         gr.n_items = (int)items.size() - gr.first_item;
         if (gr.n_items == 0) continue;
         int occ = 0;
-        const cudaError_t e = propagate_batch_occupancy(Bg, gr.smem, &occ);
+        const cudaError_t e = packed ? propagate_batch_x2_occupancy(Bg, gr.smem, &occ)
+                                     : propagate_batch_occupancy(Bg, gr.smem, &occ);
         if (e != cudaSuccess || occ < 1)
             return bail(PAMD_ECUDA, std::string("batched kernel occupancy: ") + cudaGetErrorString(e));
         gr.grid = std::min(gr.n_items, c->num_sms * occ);

@@ -287,9 +287,10 @@ struct pamd_ctx {
     int4* items = nullptr;        // device work lists of the batched propagate, group by group
     int n_items = 0;
     int* queue = nullptr;         // device work counters, one per group
-    struct BatchGroup {           // molecules sharing one atoms-per-lane count B
+    struct BatchGroup {           // molecules sharing one atoms-per-lane count B and pair arithmetic
         int B, first_item, n_items, grid;
         size_t smem;
+        bool packed;
     };
     std::vector<BatchGroup> groups;
     std::vector<cudaStream_t> group_streams;  // one per group (launches overlap)
@@ -415,6 +416,9 @@ cudaError_t launch_set_counters(pamd_ctx* c, uint32_t step, uint32_t ridx);
 // one launch of the batched kernel for atoms-per-lane B (3..7)
 cudaError_t launch_propagate_batch(const BatchParams& bp, int B, int grid, size_t smem, cudaStream_t s);
 cudaError_t propagate_batch_occupancy(int B, size_t smem, int* blocks_per_sm);
+// the same for molecules in the packed FP32x2 layout (propagate_batch_x2.cu)
+cudaError_t launch_propagate_batch_x2(const BatchParams& bp, int B, int grid, size_t smem, cudaStream_t s);
+cudaError_t propagate_batch_x2_occupancy(int B, size_t smem, int* blocks_per_sm);
 
 // all-FP64 mode (propagate_f64.cu)
 cudaError_t launch_propagate_f64(pamd_ctx* c, double* state, double* E, double* ke, double* rg,

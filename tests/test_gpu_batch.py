@@ -1,8 +1,9 @@
 """Batched uneven anneals: many molecules in one persistent launch.
 
 * Every molecule of a batch advances exactly as a standalone context with the
-  same launch shape and molecule index would (same kernel body, same Philox
-  stream), and matches the FP64 oracle over 10 steps.
+  same launch shape, pair arithmetic and molecule index would (same kernel
+  body, same Philox stream), and matches the FP64 oracle over 10 steps;
+  chains take the packed pair arithmetic unless the scalar one is asked for.
 * Resampling, observables and the graph-captured anneal act per molecule.
 * The 16-molecule workload (N ~ U{20..200}, 4096 replicas each) runs and
   sampled replicas match the oracle.
@@ -34,6 +35,7 @@ def _sub_opts(lib, sub):
     o = lib.pamd_options_default()
     o.lanes_per_replica = info["lanes_per_replica"]
     o.warps_per_block = 4
+    o.pair_arith = lib.pamd_get_shape(sub)["pair_arith"]
     return o
 
 
@@ -45,6 +47,8 @@ def test_batch_matches_standalone_and_oracle(lib, orc):
     try:
         assert lib.pamd_batch_size(batch) == 3
         subs = [lib.pamd_batch_sub(batch, m) for m in range(3)]
+        # chains take the packed pair arithmetic in a batch
+        assert all(lib.pamd_get_shape(s_)["pair_arith"] == lib.PAMD_PAIRS_PACKED for s_ in subs)
         starts = [lib.pamd_get_state(s) for s in subs]
         lib.pamd_propagate(batch, 10, dt, T)
         for m, (top, R, sub) in enumerate(zip(tops, Rs, subs)):
@@ -125,6 +129,30 @@ def test_batch_anneal_matches_stepwise(lib):
     finally:
         lib.pamd_destroy(A)
         lib.pamd_destroy(B)
+
+
+def test_batch_scalar_arithmetic_on_request(lib, orc):
+    """pair_arith = PAMD_PAIRS_SCALAR keeps every molecule of a batch on the
+    scalar pair arithmetic, and that batch matches the oracle as well."""
+    sizes, R = [22, 75], 128
+    tops = [pi.make_chain(n, 40 + n) for n in sizes]
+    T, dt, seed = 650.0, 0.001, 19
+    o = lib.pamd_options_default()
+    o.pair_arith = lib.PAMD_PAIRS_SCALAR
+    batch = lib.pamd_init_batch(tops, [R] * 2, [T] * 2, seed, o)
+    try:
+        subs = [lib.pamd_batch_sub(batch, m) for m in range(2)]
+        assert all(lib.pamd_get_shape(s_)["pair_arith"] == lib.PAMD_PAIRS_SCALAR for s_ in subs)
+        starts = [lib.pamd_get_state(s_) for s_ in subs]
+        lib.pamd_propagate(batch, 8, dt, T)
+        for m in range(2):
+            x, _, _, _ = lib.pamd_get_state(subs[m])
+            sample = np.array([0, R - 1])
+            xo, _, _ = orc.propagate(tops[m], starts[m][0][sample], starts[m][1][sample], 8, dt, T,
+                                     1.0, seed, 0, mol=m, slots=sample)
+            assert np.abs(x[sample] - xo).max() < 1e-4
+    finally:
+        lib.pamd_destroy(batch)
 
 
 def test_sixteen_uneven_molecules(lib, orc):
