@@ -160,8 +160,9 @@ typedef struct pamd_options {
  * holds each lane's own atoms in register pairs and evaluates two pairs per
  * add/mul/fma.f32x2 instruction (same FP32 roundings as the scalar form);
  * linear chains with 3..8 atoms per lane and one replica per lane group
- * only.  AUTO starts with SCALAR; pamd_autotune times both where PACKED
- * applies and keeps the faster. */
+ * only.  AUTO starts with PACKED where it applies (mixed precision, one
+ * replica per lane group), else SCALAR; pamd_autotune times both where
+ * PACKED applies and keeps the faster. */
 #define PAMD_PAIRS_AUTO 0
 #define PAMD_PAIRS_SCALAR 1
 #define PAMD_PAIRS_PACKED 2

@@ -1045,6 +1045,8 @@ int pamd_init(pamd_ctx** out, const pamd_topology* top, int64_t R, double T0, ui
         variant = kVarPaired;
     else if (o.pair_arith == PAMD_PAIRS_PACKED)
         variant = kVarPacked;
+    else if (o.pair_arith == PAMD_PAIRS_AUTO && o.precision == PAMD_PREC_MIXED && packed_ok(lay0))
+        variant = kVarPacked;  // the faster arithmetic wherever its layout applies
     if ((rc = set_launch_shape(c, lay0, o.warps_per_block, variant))) {
         const std::string m = g_err;
         return bail(rc, m);

@@ -259,6 +259,29 @@ def test_forces_chain_with_far_exclusions(lib, orc, n, lanes, arith):
         assert abs(eg[k] - eo[k]) <= 1e-5 * scale[k]
 
 
+def test_default_pair_arithmetic(lib):
+    """PAMD_PAIRS_AUTO starts with the packed arithmetic where its layout
+    applies (a chain with 3..8 atoms per lane, mixed precision, one replica
+    per lane group) and with the scalar one elsewhere."""
+    def arith(top, **kw):
+        ctx = lib.pamd_init(top, 64, 300.0, 1, _opts(lib, **kw))
+        try:
+            return lib.pamd_get_shape(ctx)["pair_arith"]
+        finally:
+            lib.pamd_destroy(ctx)
+    chain = pi.make_chain(75, 2)
+    assert arith(chain) == lib.PAMD_PAIRS_PACKED
+    assert arith(chain, lanes_per_replica=15) == lib.PAMD_PAIRS_PACKED
+    assert arith(pi.make_chain(40, 2), lanes_per_replica=20) == lib.PAMD_PAIRS_SCALAR  # 2 atoms per lane
+    assert arith(chain, replicas_per_lane=2, lanes_per_replica=25) == lib.PAMD_PAIRS_SCALAR
+    assert arith(pi.make_chain(8, 2), lanes_per_replica=8) == lib.PAMD_PAIRS_SCALAR  # 1 atom per lane
+    relabelled = pi.make_chain(40, 5)
+    perm = np.random.default_rng(3).permutation(40)
+    for name in ("bond", "angle", "dihedral", "excl", "pair14"):
+        setattr(relabelled, name, perm[getattr(relabelled, name)].astype(np.int32))
+    assert arith(relabelled) == lib.PAMD_PAIRS_SCALAR
+
+
 @pytest.mark.parametrize("n", [13, 40, 75])
 def test_forces_relabelled_chain(lib, orc, n):
     """Atoms of a chain relabelled at random: the bonded terms are no longer a
