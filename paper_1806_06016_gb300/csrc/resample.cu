@@ -645,13 +645,26 @@ constexpr int kObsVals = 5;  // count, E, E_kin, R_g, R_g^2
 constexpr int kObsStride = kNumBins * kObsVals + 1;
 
 // Partial sums per family bin over 1024 replicas, in replica order per bin.
+// Per-bin partial sums of one 1024-replica chunk.  Each bin's sums are
+// accumulated by one thread over the chunk's replicas of that bin in
+// increasing index order.  The replicas are first ordered by bin with a
+// stable counting sort (ranks within 32-replica pieces from
+// __match_any_sync, prefix counts over the pieces), so that the 64 bin
+// threads run side by side over their own segments instead of each scanning
+// the whole chunk.
 __global__ void obs_partial_kernel(const int32_t* fam, const double* E, const double* ke,
                                    const double* rg, const unsigned char* flags, long long R,
                                    double* part, const uint32_t* live) {
+    constexpr int kPieces = kScanBlock / 32;
+    constexpr int kPerWarp = kPieces / (kScanThreads / 32);
+    static_assert(kPieces % (kScanThreads / 32) == 0, "pieces per warp");
     const long long n = live_size(live, R);  // replicas; family flags span R
     __shared__ int32_t sf[kScanBlock];
     __shared__ double se[kScanBlock], sk[kScanBlock], sr[kScanBlock];
     __shared__ int32_t famcount[kScanThreads / 32];
+    __shared__ int32_t pcount[kPieces][kNumBins];  // per piece and bin: count, then prefix
+    __shared__ int32_t bstart[kNumBins + 1];
+    __shared__ int16_t order[kScanBlock];          // chunk entries sorted by bin (stable)
     const long long base = (long long)blockIdx.x * kScanBlock;
     int fc = 0;
     for (int t = threadIdx.x; t < kScanBlock; t += blockDim.x) {
@@ -666,22 +679,61 @@ __global__ void obs_partial_kernel(const int32_t* fam, const double* E, const do
         }
         if (k < R) fc += flags[k];
     }
+    for (int i = threadIdx.x; i < kPieces * kNumBins; i += blockDim.x) (&pcount[0][0])[i] = 0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) fc += __shfl_xor_sync(0xffffffffu, fc, o);
     if ((threadIdx.x & 31) == 0) famcount[threadIdx.x >> 5] = fc;
+    __syncthreads();
+    // ranks within each piece, and the pieces' counts per bin
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int rank[kPerWarp];
+#pragma unroll
+    for (int q = 0; q < kPerWarp; ++q) {
+        const int c = w + q * (kScanThreads / 32);
+        const int bin = sf[32 * c + lane];
+        const unsigned peers = __match_any_sync(0xffffffffu, bin);
+        rank[q] = __popc(peers & ((1u << lane) - 1u));
+        if (bin >= 0 && rank[q] == 0) pcount[c][bin] = __popc(peers);
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumBins) {  // prefix over the pieces, per bin
+        int s = 0;
+        for (int c = 0; c < kPieces; ++c) {
+            const int x = pcount[c][threadIdx.x];
+            pcount[c][threadIdx.x] = s;
+            s += x;
+        }
+        bstart[threadIdx.x + 1] = s;  // the bin's size, turned into starts below
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int s = 0;
+        bstart[0] = 0;
+        for (int b = 0; b < kNumBins; ++b) {
+            s += bstart[b + 1];
+            bstart[b + 1] = s;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kPerWarp; ++q) {
+        const int c = w + q * (kScanThreads / 32);
+        const int t = 32 * c + lane;
+        const int bin = sf[t];
+        if (bin >= 0) order[bstart[bin] + pcount[c][bin] + rank[q]] = (int16_t)t;
+    }
     __syncthreads();
     double* out = part + (size_t)blockIdx.x * kObsStride;
     if (threadIdx.x < kNumBins) {
         const int b = threadIdx.x;
         double c = 0, e = 0, k2 = 0, r = 0, r2 = 0;
-        for (int t = 0; t < kScanBlock; ++t) {
-            if (sf[t] == b) {
-                c += 1.0;
-                e += se[t];
-                k2 += sk[t];
-                r += sr[t];
-                r2 += sr[t] * sr[t];
-            }
+        for (int i = bstart[b]; i < bstart[b + 1]; ++i) {
+            const int t = order[i];
+            c += 1.0;
+            e += se[t];
+            k2 += sk[t];
+            r += sr[t];
+            r2 += sr[t] * sr[t];
         }
         out[b * kObsVals + 0] = c;
         out[b * kObsVals + 1] = e;
@@ -696,19 +748,24 @@ __global__ void obs_partial_kernel(const int32_t* fam, const double* E, const do
     }
 }
 
-__device__ double jackknife_se(const double* cnt, const double* sum, double tot, double R) {
-    double jk[kNumBins];
+// Jackknife standard error over the family bins from the leave-one-bin-out
+// means jk[b] (computed in parallel by the caller), bins that are empty or
+// hold the whole population left out; the sums run over the bins in order.
+__device__ double jackknife_se(const double* cnt, const double* jk, double R) {
     int nb = 0;
+    double jm = 0.0;
     for (int b = 0; b < kNumBins; ++b) {
         if (cnt[b] == 0.0 || cnt[b] == R) continue;
-        jk[nb++] = (tot - sum[b]) / (R - cnt[b]);
+        jm += jk[b];
+        ++nb;
     }
     if (nb < 2) return 0.0;
-    double jm = 0.0;
-    for (int b = 0; b < nb; ++b) jm += jk[b];
     jm /= nb;
     double ss = 0.0;
-    for (int b = 0; b < nb; ++b) ss += (jk[b] - jm) * (jk[b] - jm);
+    for (int b = 0; b < kNumBins; ++b) {
+        if (cnt[b] == 0.0 || cnt[b] == R) continue;
+        ss += (jk[b] - jm) * (jk[b] - jm);
+    }
     return sqrt((double)(nb - 1) / nb * ss);
 }
 
@@ -716,6 +773,8 @@ __global__ void obs_final_kernel(const double* part, int nblk, long long R, int 
                                  const DevScalars* s, pamd_obs* dst, const uint32_t* live) {
     R = live_size(live, R);
     __shared__ double bins[kObsVals][kNumBins];
+    __shared__ double jk[kObsVals][kNumBins];
+    __shared__ double tot[kObsVals];
     __shared__ double nfam;
     if (threadIdx.x < kNumBins) {
         const int b = threadIdx.x;
@@ -730,27 +789,33 @@ __global__ void obs_final_kernel(const double* part, int nblk, long long R, int 
         nfam = f;
     }
     __syncthreads();
+    if (threadIdx.x >= 1 && threadIdx.x < kObsVals) {  // totals over the bins, in bin order
+        const int v = threadIdx.x;
+        double t = 0;
+        for (int b = 0; b < kNumBins; ++b) t += bins[v][b];
+        tot[v] = t;
+    }
+    __syncthreads();
+    const double Rd = (double)R;
+    if (threadIdx.x < kNumBins) {  // leave-one-bin-out means
+        const int b = threadIdx.x;
+        for (int v = 1; v < kObsVals; ++v) jk[v][b] = (tot[v] - bins[v][b]) / (Rd - bins[0][b]);
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        const double Rd = (double)R;
-        double tot[kObsVals];
-        for (int v = 1; v < kObsVals; ++v) {
-            double t = 0;
-            for (int b = 0; b < kNumBins; ++b) t += bins[v][b];
-            tot[v] = t;
-        }
         pamd_obs o;
         o.T = T;
         o.lnQ = s->lnQ;
         o.sum_lnQ = s->sum_lnQ;
         o.e_pot = tot[1] / Rd;
-        o.e_pot_se = jackknife_se(bins[0], bins[1], tot[1], Rd);
+        o.e_pot_se = jackknife_se(bins[0], jk[1], Rd);
         o.e_kin = tot[2] / Rd;
-        o.e_kin_se = jackknife_se(bins[0], bins[2], tot[2], Rd);
+        o.e_kin_se = jackknife_se(bins[0], jk[2], Rd);
         o.t_meas = 2.0 * o.e_kin / (3.0 * N * kBoltzmann);
         o.rg = tot[3] / Rd;
-        o.rg_se = jackknife_se(bins[0], bins[3], tot[3], Rd);
+        o.rg_se = jackknife_se(bins[0], jk[3], Rd);
         o.rg2 = tot[4] / Rd;
-        o.rg2_se = jackknife_se(bins[0], bins[4], tot[4], Rd);
+        o.rg2_se = jackknife_se(bins[0], jk[4], Rd);
         o.n_families = (int64_t)nfam;
         o.max_copies = s->max_copies;
         o.pad_ = s->status;
