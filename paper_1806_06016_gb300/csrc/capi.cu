@@ -339,6 +339,21 @@ int build_topology(const pamd_topology* t, int lanes_req, TopoLayout* lay_out,
     lay.far_masks = 0;
     for (size_t q = 2 * (size_t)L; q < masks.size(); ++q)
         if (masks[q]) lay.far_masks = 1;
+    // the usual chain exclusions only: the kernels may then leave the own
+    // block's 1-2 and 1-3 pairs out by position instead of by mask
+    lay.std_chain = 0;
+    if (chain) {
+        bool std_excl = true;
+        for (int i = 0; i < N && std_excl; ++i)
+            for (int j = i + 1; j < N; ++j) {
+                const bool ex = excl[(size_t)i * N + j] != 0;
+                if (ex != (j - i <= 2)) {
+                    std_excl = false;
+                    break;
+                }
+            }
+        lay.std_chain = std_excl ? 1 : 0;
+    }
     lay.off_bonds = off; off += round_up(lay.n_bonds * 16, 16);
     lay.off_angles = off; off += round_up(lay.n_angles * 32, 16);
     lay.off_dihs = off; off += round_up(lay.n_dihs * 32, 16);

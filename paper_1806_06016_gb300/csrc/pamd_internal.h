@@ -40,6 +40,7 @@ struct TopoLayout {
     int off_masks;             // uint64 [(L/2+1) * L]: excluded and scaled 1-4 pairs per tile
     int off_m14;               // uint64 [(L/2+1) * L]: the scaled 1-4 pairs among them
     int far_masks;             // 1 if a tile at ring step t >= 2 has a masked pair
+    int std_chain;             // chain whose excluded pairs are exactly (i, i+1) and (i, i+2)
     int off_bonds, n_bonds;
     int off_angles, n_angles;
     int off_dihs, n_dihs;

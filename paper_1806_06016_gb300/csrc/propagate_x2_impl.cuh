@@ -381,22 +381,40 @@ __device__ __forceinline__ void forces_x2(const unsigned char* sm, const TopoLay
     const unsigned long long* m14s = reinterpret_cast<const unsigned long long*>(sm + lay.off_m14);
     const float s_lj = lay.s14_lj, s_c = lay.s14_c;
     f.zero();
-    // pairs inside the lane's own block (the 1-2/1-3/1-4 pairs live here)
-    {
+    // pairs inside the lane's own block (the 1-2/1-3/1-4 pairs live here).
+    // With the usual chain exclusions the pair pattern of a block is the same
+    // for every lane: atoms d = b - a apart are excluded for d <= 2 and
+    // scaled for d = 3, which the unrolled loop resolves at compile time
+    // (padding slots carry zero parameters, so leaving their pairs out by
+    // position changes nothing); otherwise the block's masks decide.
+    auto own_pair = [&](int a, int b, float kx, float ky) {
+        const float dx = r.gx(b) - r.gx(a), dy = r.gy(b) - r.gy(a), dz = r.gz(b) - r.gz(a);
+        const float sg = hs.gx(a) + hs.gx(b);
+        const float eps = nse.gx(a) * nse.gx(b) * kx;
+        float fs, e;
+        pair_lj_coul<false>(dx, dy, dz, sg * sg, eps, eps + eps, qq.gx(a) * qq.gx(b) * ky, fs, e);
+        f.add(a, -fs * dx, -fs * dy, -fs * dz);
+        f.add(b, fs * dx, fs * dy, fs * dz);
+    };
+    if (lay.std_chain) {
+#pragma unroll
+        for (int a = 0; a < B; ++a) {
+#pragma unroll
+            for (int b = a + 3; b < B; ++b) {
+                if (b - a == 3)
+                    own_pair(a, b, s_lj, s_c);
+                else
+                    own_pair(a, b, 1.0f, 1.0f);
+            }
+        }
+    } else {
         const unsigned long long m = masks[g], m4 = m14s[g];
 #pragma unroll
         for (int a = 0; a < B; ++a) {
 #pragma unroll
             for (int b = a + 1; b < B; ++b) {
-                const float dx = r.gx(b) - r.gx(a), dy = r.gy(b) - r.gy(a), dz = r.gz(b) - r.gz(a);
-                const float sg = hs.gx(a) + hs.gx(b);
                 const float2 k = pair_factors(m, m4, a * B + b, s_lj, s_c);
-                const float eps = nse.gx(a) * nse.gx(b) * k.x;
-                float fs, e;
-                pair_lj_coul<false>(dx, dy, dz, sg * sg, eps, eps + eps, qq.gx(a) * qq.gx(b) * k.y, fs,
-                                    e);
-                f.add(a, -fs * dx, -fs * dy, -fs * dz);
-                f.add(b, fs * dx, fs * dy, fs * dz);
+                own_pair(a, b, k.x, k.y);
             }
         }
     }
