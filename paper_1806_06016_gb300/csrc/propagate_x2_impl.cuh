@@ -146,6 +146,21 @@ struct Own {
     }
 };
 
+// Masks of the t = 1 tile of a chain with the usual exclusions (bit a*B + b:
+// own atom a of block g against atom b of block g + 1, B + b - a apart):
+// excluded pairs (at most 2 apart) and scaled 1-4 pairs (3 apart), or with
+// only14 the 1-4 pairs alone.
+template <int B>
+__host__ __device__ constexpr unsigned long long std_t1_mask(bool only14) {
+    unsigned long long m = 0ull;
+    for (int a = 0; a < B; ++a)
+        for (int b = 0; b < B; ++b) {
+            const int d = B + b - a;
+            if (d == 3 || (!only14 && d <= 2)) m |= 1ull << (a * B + b);
+        }
+    return m;
+}
+
 // Factors of a pair left out of the plain nonbonded sum: (0, 0) when it is
 // excluded, (LJ scale, Coulomb scale) when it is a scaled 1-4 pair, else
 // (1, 1).  Applied to eps, 2 eps and qq, which the pair force is linear in.
@@ -423,17 +438,26 @@ __device__ __forceinline__ void forces_x2(const unsigned char* sm, const TopoLay
     // lanes g < L/2 work.  Lane g receives from lane g - t the forces on its
     // own atom b.  The partner sums of a whole tile are handed over after
     // it, so that the partners' arithmetic can interleave.
-    auto tile = [&](int t, auto masked) {
-        constexpr bool MASKED = decltype(masked)::value;
+    // mode 0: plain code; 1: the tile's masks from the table; 2: the t = 1
+    // tile of a chain with the usual exclusions, whose masks are fixed by
+    // position (own atom a against partner b, B + b - a apart) except on the
+    // last lane, whose t = 1 partner is block 0 and has none
+    auto tile = [&](int t, auto mode) {
+        constexpr int MODE = decltype(mode)::value;
+        constexpr bool MASKED = MODE != 0;
         int J = g + t;
         J = (J >= L) ? J - L : J;
         const int sJ = J * C::BS;
         int src = g - t;
         src = (src < 0) ? src + L : src;
         unsigned long long m = 0ull, m4 = 0ull;
-        if (MASKED) {
+        if (MODE == 1) {
             m = masks[t * L + g];
             m4 = m14s[t * L + g];
+        } else if (MODE == 2) {
+            const bool last = g == L - 1;
+            m = last ? 0ull : std_t1_mask<B>(false);
+            m4 = last ? 0ull : std_t1_mask<B>(true);
         }
         float gx[B], gy[B], gz[B];
 #pragma unroll
@@ -448,13 +472,18 @@ __device__ __forceinline__ void forces_x2(const unsigned char* sm, const TopoLay
     // the t = 1 tile: that tile runs the masked code, the others the plain
     // code.  A topology with masked pairs further out (lay.far_masks) runs
     // the masked code on every tile.
-    if (TF >= 1) tile(1, std::true_type{});
+    if (TF >= 1) {
+        if (lay.std_chain && L >= 3)
+            tile(1, std::integral_constant<int, 2>{});
+        else
+            tile(1, std::integral_constant<int, 1>{});
+    }
     if (!lay.far_masks) {
 #pragma unroll 1
-        for (int t = 2; t <= TF; ++t) tile(t, std::false_type{});
+        for (int t = 2; t <= TF; ++t) tile(t, std::integral_constant<int, 0>{});
     } else {
 #pragma unroll 1
-        for (int t = 2; t <= TF; ++t) tile(t, std::true_type{});
+        for (int t = 2; t <= TF; ++t) tile(t, std::integral_constant<int, 1>{});
     }
     if ((L & 1) == 0) {
         const int t = L / 2;
