@@ -155,6 +155,33 @@ def test_batch_scalar_arithmetic_on_request(lib, orc):
         lib.pamd_destroy(batch)
 
 
+def test_batch_chain_with_far_exclusions(lib, orc):
+    """A batch holding a standard chain and a chain with extra exclusions
+    between distant atoms (masked pairs beyond the first ring step): both run
+    the packed batched kernel and match the oracle."""
+    sizes, R = [40, 75], 96
+    tops = [pi.make_chain(n, 50 + n) for n in sizes]
+    far = [(2, 37), (10, 70), (0, 74), (5, 50)]
+    tops[1].excl = np.concatenate([np.asarray(tops[1].excl, np.int32).reshape(-1, 2),
+                                   np.asarray(far, np.int32)]).astype(np.int32)
+    T, dt, seed = 550.0, 0.001, 23
+    batch = lib.pamd_init_batch(tops, [R] * 2, [T] * 2, seed)
+    try:
+        subs = [lib.pamd_batch_sub(batch, m) for m in range(2)]
+        assert all(lib.pamd_get_shape(s_)["pair_arith"] == lib.PAMD_PAIRS_PACKED for s_ in subs)
+        starts = [lib.pamd_get_state(s_) for s_ in subs]
+        lib.pamd_propagate(batch, 8, dt, T)
+        for m in range(2):
+            x, _, E, _ = lib.pamd_get_state(subs[m])
+            sample = np.array([0, R // 3, R - 1])
+            xo, _, eo = orc.propagate(tops[m], starts[m][0][sample], starts[m][1][sample], 8, dt, T,
+                                      1.0, seed, 0, mol=m, slots=sample)
+            assert np.abs(x[sample] - xo).max() < 1e-4
+            assert np.abs(E[sample] - eo).max() < 1e-4 * np.abs(eo).max()
+    finally:
+        lib.pamd_destroy(batch)
+
+
 def test_sixteen_uneven_molecules(lib, orc):
     """The batched workload shape: 16 chains, N ~ U{20..200}, 4096 replicas each."""
     sizes = pi.batched_chain_sizes()
