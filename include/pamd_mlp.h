@@ -31,7 +31,12 @@
  *
  * A model attached to a population (pamd_set_force_model) replaces the exact
  * forces and energies in pamd_propagate and pamd_anneal; the BAOAB update,
- * the noise stream and the resampling are unchanged.
+ * the noise stream and the resampling are unchanged.  Each MD step is one
+ * step kernel and four GEMM launches; pamd_anneal captures the whole anneal
+ * as one CUDA graph in which every temperature's theta steps are a
+ * conditional WHILE node (the step index is kept in device memory), and
+ * re-captures it when the model, its workspace or its energy scale changes.
+ * The model must not be used from another stream while such an anneal runs.
  *
  * Memory layouts (all row-major, C order):
  *   positions, forces  [M][N][3] FP32 (nm, kJ/mol/nm) in device memory;
